@@ -1,0 +1,341 @@
+"""FP64 CPU oracle for the sketched Equivariant Imaging hot path.
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by ``__graft_entry__.smoke()``
+and by the benchmark's CPU-baseline / reference leg, never by the product
+package.  It shares no code with the CUDA library; the primitive operators
+live in ``skei_oracle.c`` (plain loops), and this module composes them into
+the paper's quantities with numpy in float64.
+
+Paper map:
+  * Sec. 2.1       y ~ A x, reconstruction F_theta(A^dagger y), A^dagger = FBP
+  * Sec. 2.2, Eq. (e:eiloss)      EI loss = MC + lambda * EI regulariser
+  * Sec. 3.1, Eq. (e:skeiloss)    sketched loss: A -> A_S = S A, y -> S y,
+                                  A^dagger -> A_S^dagger
+  * Sec. 3.2, Eq. (e:skeilossttt) the test-time (single measurement) form
+  * Algorithm 2   per iteration: draw S_k and T_i, MC + lambda SkEI, Adam step
+  * Sec. 4.2.1    CT sketch = one of N interleaved angle subsets
+  * Sec. 4.1.3    transforms = rotations; Adam with lr 5e-4
+
+Readings where the paper is silent (all recorded in the design notes):
+  A_S^dagger is the FBP over the sketch's angles, (pi/m) B_S H; the sketch is
+  an unscaled row selection, with the sketched MC term multiplied by
+  ``mc_scale``; norms are sums of squares; loss = (1/B) sum_b
+  [mc_b + lambda/G sum_g ei_bg].
+
+Parity status: every function here is pinned by tests/test_oracle_*.py
+(closed forms, exact symmetries, explicit small matrices, analytic Radon and
+FBP convergence, finite differences, torch's Adam); none is "parity unpinned"
+except the noise model of the inputs module, which is not part of the oracle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "skei_oracle.c")
+_LIB_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIB_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (FP contraction off, so x86 and Arm
+    round identically)."""
+    os.makedirs(_LIB_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
+               "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            D = ctypes.POINTER(ctypes.c_double)
+            I = ctypes.c_int
+            lib.oracle_ndet.argtypes = [I]
+            lib.oracle_ndet.restype = I
+            lib.oracle_trig.argtypes = [ctypes.c_double, D, D]
+            lib.oracle_row_mode.argtypes = [ctypes.c_double]
+            lib.oracle_row_mode.restype = I
+            lib.oracle_ramlak_tap.argtypes = [I]
+            lib.oracle_ramlak_tap.restype = ctypes.c_double
+            for name in ("oracle_joseph_fwd", "oracle_joseph_adj",
+                         "oracle_backproject", "oracle_backproject_adj"):
+                getattr(lib, name).argtypes = [I, I, I, D, D, D]
+            lib.oracle_ramlak.argtypes = [I, I, D, D]
+            lib.oracle_rotate.argtypes = [I, ctypes.c_double, D, D]
+            lib.oracle_rotate_adj.argtypes = [I, ctypes.c_double, D, D]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+# --------------------------------------------------------------------------
+# geometry
+# --------------------------------------------------------------------------
+
+def ndet(N: int) -> int:
+    """Detector bins: smallest odd integer >= N sqrt(2)."""
+    return _load().oracle_ndet(int(N))
+
+
+def trig(deg: float):
+    c, s = ctypes.c_double(), ctypes.c_double()
+    _load().oracle_trig(float(deg), ctypes.byref(c), ctypes.byref(s))
+    return c.value, s.value
+
+
+def row_mode(deg: float) -> bool:
+    return bool(_load().oracle_row_mode(float(deg)))
+
+
+def ramlak_tap(n: int) -> float:
+    return _load().oracle_ramlak_tap(int(n))
+
+
+# --------------------------------------------------------------------------
+# primitive operators (batched over leading dims)
+# --------------------------------------------------------------------------
+
+def proj_fwd(x, angles_deg, n_det: int) -> np.ndarray:
+    """A x: [..., N, N] -> [..., n_angles, n_det] (Joseph, Sec. 4.1.1)."""
+    x = _f64(x)
+    ang = _f64(angles_deg).ravel()
+    N = x.shape[-1]
+    lead = x.shape[:-2]
+    xs = x.reshape(-1, N, N)
+    out = np.empty((xs.shape[0], ang.size, n_det))
+    for b in range(xs.shape[0]):
+        xb = np.ascontiguousarray(xs[b])
+        ob = np.empty((ang.size, n_det))
+        _load().oracle_joseph_fwd(N, n_det, ang.size, _ptr(ang), _ptr(xb), _ptr(ob))
+        out[b] = ob
+    return out.reshape(lead + (ang.size, n_det))
+
+
+def proj_adj(p, angles_deg, N: int) -> np.ndarray:
+    """A^T p: [..., n_angles, n_det] -> [..., N, N] (scatter)."""
+    p = _f64(p)
+    ang = _f64(angles_deg).ravel()
+    n_det = p.shape[-1]
+    lead = p.shape[:-2]
+    ps = p.reshape(-1, ang.size, n_det)
+    out = np.empty((ps.shape[0], N, N))
+    for b in range(ps.shape[0]):
+        pb = np.ascontiguousarray(ps[b])
+        ob = np.empty((N, N))
+        _load().oracle_joseph_adj(N, n_det, ang.size, _ptr(ang), _ptr(pb), _ptr(ob))
+        out[b] = ob
+    return out.reshape(lead + (N, N))
+
+
+def ramlak(p) -> np.ndarray:
+    """H p, row by row: [..., n_det] -> [..., n_det]."""
+    p = _f64(p)
+    n_det = p.shape[-1]
+    rows = int(np.prod(p.shape[:-1])) if p.ndim > 1 else 1
+    q = np.empty_like(p)
+    _load().oracle_ramlak(n_det, rows, _ptr(p), _ptr(q))
+    return q
+
+
+def backproject(q, angles_deg, N: int) -> np.ndarray:
+    """B q (unscaled): [..., n_angles, n_det] -> [..., N, N]."""
+    q = _f64(q)
+    ang = _f64(angles_deg).ravel()
+    n_det = q.shape[-1]
+    lead = q.shape[:-2]
+    qs = q.reshape(-1, ang.size, n_det)
+    out = np.empty((qs.shape[0], N, N))
+    for b in range(qs.shape[0]):
+        qb = np.ascontiguousarray(qs[b])
+        ob = np.empty((N, N))
+        _load().oracle_backproject(N, n_det, ang.size, _ptr(ang), _ptr(qb), _ptr(ob))
+        out[b] = ob
+    return out.reshape(lead + (N, N))
+
+
+def backproject_adj(x, angles_deg, n_det: int) -> np.ndarray:
+    """B^T x (scatter): [..., N, N] -> [..., n_angles, n_det]."""
+    x = _f64(x)
+    ang = _f64(angles_deg).ravel()
+    N = x.shape[-1]
+    lead = x.shape[:-2]
+    xs = x.reshape(-1, N, N)
+    out = np.empty((xs.shape[0], ang.size, n_det))
+    for b in range(xs.shape[0]):
+        xb = np.ascontiguousarray(xs[b])
+        ob = np.empty((ang.size, n_det))
+        _load().oracle_backproject_adj(N, n_det, ang.size, _ptr(ang), _ptr(xb), _ptr(ob))
+        out[b] = ob
+    return out.reshape(lead + (ang.size, n_det))
+
+
+def fbp(p, angles_deg, N: int) -> np.ndarray:
+    """A^dagger p = (pi/m') B H p, m' = number of angles (Sec. 2.1: FBP as the
+    stable approximation of the pseudo-inverse)."""
+    ang = _f64(angles_deg).ravel()
+    return (np.pi / ang.size) * backproject(ramlak(p), ang, N)
+
+
+def fbp_adj(x, angles_deg, n_det: int) -> np.ndarray:
+    """(A^dagger)^T x = (pi/m') H B^T x (H is symmetric)."""
+    ang = _f64(angles_deg).ravel()
+    return (np.pi / ang.size) * ramlak(backproject_adj(x, ang, n_det))
+
+
+def rotate(x, g_deg: float) -> np.ndarray:
+    """T_g x for one image [N, N]."""
+    x = _f64(x)
+    N = x.shape[-1]
+    out = np.empty((N, N))
+    _load().oracle_rotate(N, float(g_deg), _ptr(x), _ptr(out))
+    return out
+
+
+def rotate_adj(gout, g_deg: float) -> np.ndarray:
+    gout = _f64(gout)
+    N = gout.shape[-1]
+    out = np.empty((N, N))
+    _load().oracle_rotate_adj(N, float(g_deg), _ptr(gout), _ptr(out))
+    return out
+
+
+def rotate_batch(x, g_deg) -> np.ndarray:
+    """x [B, N, N], g_deg [B, G] -> [B, G, N, N]."""
+    x = _f64(x)
+    g = np.asarray(g_deg, dtype=np.float64)
+    B, G = g.shape
+    return np.stack([np.stack([rotate(x[b], g[b, k]) for k in range(G)]) for b in range(B)])
+
+
+def rotate_adj_batch(gout, g_deg) -> np.ndarray:
+    """sum_g T_g^T gout[b, g]: [B, G, N, N] -> [B, N, N]."""
+    gout = _f64(gout)
+    g = np.asarray(g_deg, dtype=np.float64)
+    B, G = g.shape
+    return np.stack([sum(rotate_adj(gout[b, k], g[b, k]) for k in range(G)) for b in range(B)])
+
+
+# --------------------------------------------------------------------------
+# sketch (Sec. 3.1 and 4.2.1)
+# --------------------------------------------------------------------------
+
+def select(angles_deg, idx):
+    """Angles of the sketch S: the rows of A kept by the selection."""
+    ang = _f64(angles_deg).ravel()
+    if idx is None:
+        return ang
+    return ang[np.asarray(idx, dtype=np.int64)]
+
+
+# --------------------------------------------------------------------------
+# EI / SkEI loss, split around the network F (Eq. e:skeiloss, Algorithm 2)
+# --------------------------------------------------------------------------
+
+def ei_stage1(x1, y, angles_deg, mc_idx, sk_idx, g_deg):
+    """Everything the loss needs before the second network call.
+
+    x1 = F(A^dagger y) [B, N, N]; y [B, n_angles, n_det].
+    Returns r = S y - A_S x1 (MC residual, [B, m_mc, n_det]),
+    x2 = T_g x1 ([B, G, N, N]) and z = A_S^dagger A_S x2 ([B, G, N, N])."""
+    x1 = _f64(x1)
+    y = _f64(y)
+    N = x1.shape[-1]
+    n_det = y.shape[-1]
+    ang_mc = select(angles_deg, mc_idx)
+    ang_sk = select(angles_deg, sk_idx)
+    y_mc = y if mc_idx is None else y[:, np.asarray(mc_idx, dtype=np.int64), :]
+    r = y_mc - proj_fwd(x1, ang_mc, n_det)
+    x2 = rotate_batch(x1, g_deg)
+    z = fbp(proj_fwd(x2, ang_sk, n_det), ang_sk, N)
+    return r, x2, z
+
+
+def ei_finish(x2, x3, r, lam: float, mc_scale: float):
+    """mc_b = mc_scale ||r_b||^2, ei_bg = ||x2 - x3||^2,
+    L = (1/B) sum_b [mc_b + (lambda/G) sum_g ei_bg]; also the seeds
+    dL/dx2 = 2 lambda/(B G) (x2 - x3) = -dL/dx3."""
+    x2, x3, r = _f64(x2), _f64(x3), _f64(r)
+    B, G = x2.shape[:2]
+    mc = mc_scale * np.sum(r.reshape(B, -1) ** 2, axis=1)
+    d = x2 - x3
+    ei = np.sum(d.reshape(B, G, -1) ** 2, axis=2)
+    loss = float(np.mean(mc + (lam / G) * np.sum(ei, axis=1)))
+    g_x2 = (2.0 * lam / (B * G)) * d
+    return loss, mc, ei, g_x2, -g_x2
+
+
+def ei_backward(r, g_x2, g_z, angles_deg, mc_idx, sk_idx, g_deg, mc_scale: float):
+    """dL/dx1 = -(2 mc_scale / B) A_S^T r
+               + sum_g T_g^T [g_x2 + (pi/m) A_S^T H B_S^T g_z]."""
+    r, g_x2, g_z = _f64(r), _f64(g_x2), _f64(g_z)
+    B, G, N = g_x2.shape[0], g_x2.shape[1], g_x2.shape[-1]
+    n_det = r.shape[-1]
+    ang_mc = select(angles_deg, mc_idx)
+    ang_sk = select(angles_deg, sk_idx)
+    g_tot = g_x2 + proj_adj(fbp_adj(g_z, ang_sk, n_det), ang_sk, N)
+    return -(2.0 * mc_scale / B) * proj_adj(r, ang_mc, N) + rotate_adj_batch(g_tot, g_deg)
+
+
+# --------------------------------------------------------------------------
+# stand-in network F_theta(u) = u + theta and the full test-time objective
+# --------------------------------------------------------------------------
+
+def ttt_loss(theta, x0, y, angles_deg, mc_idx, sk_idx, g_deg, lam, mc_scale):
+    """Loss of Eq. (e:skeilossttt) (batched over B measurements) with the
+    residual stand-in F(u) = u + theta (theta [N, N], shared by all b)."""
+    x1 = _f64(x0) + _f64(theta)[None]
+    r, x2, z = ei_stage1(x1, y, angles_deg, mc_idx, sk_idx, g_deg)
+    x3 = z + _f64(theta)[None, None]
+    loss, mc, ei, g_x2, g_x3 = ei_finish(x2, x3, r, lam, mc_scale)
+    return loss, dict(r=r, x2=x2, z=z, x3=x3, mc=mc, ei=ei, g_x2=g_x2, g_x3=g_x3)
+
+
+def ttt_grad(theta, x0, y, angles_deg, mc_idx, sk_idx, g_deg, lam, mc_scale):
+    """(loss, dL/dtheta) for F(u) = u + theta: the chain rule through both
+    network calls gives dL/dtheta = sum_b dL/dx1_b + sum_{b,g} dL/dx3_bg."""
+    loss, t = ttt_loss(theta, x0, y, angles_deg, mc_idx, sk_idx, g_deg, lam, mc_scale)
+    g_x1 = ei_backward(t["r"], t["g_x2"], t["g_x3"], angles_deg, mc_idx, sk_idx,
+                       g_deg, mc_scale)
+    return loss, g_x1.sum(axis=0) + t["g_x3"].sum(axis=(0, 1)), t
+
+
+def adam_step(theta, grad, m, v, step: int, lr=5e-4, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma and Ba 2015), the optimiser of Algorithm 2 with
+    the paper's lr 5e-4 (Sec. 4.1.3).  step counts from 1.  Returns new
+    (theta, m, v)."""
+    theta, grad, m, v = _f64(theta), _f64(grad), _f64(m), _f64(v)
+    m = beta1 * m + (1.0 - beta1) * grad
+    v = beta2 * v + (1.0 - beta2) * grad * grad
+    m_hat = m / (1.0 - beta1 ** step)
+    v_hat = v / (1.0 - beta2 ** step)
+    return theta - lr * m_hat / (np.sqrt(v_hat) + eps), m, v
+
+
+def psnr(x, ref) -> float:
+    """10 log10(range^2 / MSE), range = max(ref) - min(ref)."""
+    x, ref = _f64(x), _f64(ref)
+    mse = float(np.mean((x - ref) ** 2))
+    rng = float(ref.max() - ref.min())
+    return 10.0 * np.log10(rng * rng / mse)

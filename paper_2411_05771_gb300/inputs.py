@@ -1,0 +1,154 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle and the benchmark.
+
+This module holds no arithmetic of the method itself (no discrete projector,
+filter, back-projector, rotation or loss).  It only draws and rasterises the
+test objects that stand in for the CT100 images of the paper (Sec. 4.1.1:
+512x512 CT images, 100-view parallel-beam sinograms), and the random choices
+the method makes per iteration (Algorithm 2: one sketch S_k and one transform
+T_i per iteration), so that both sides of a parity test receive identical
+inputs.
+
+Conventions (pixel units, shared by every consumer):
+  * image pixel (i, j), i = row from the top, centre
+    x_j = j - (N-1)/2, y_i = (N-1)/2 - i  (y points up);
+  * the physical field of view is [-1, 1]^2, so physical = pixel * 2/N;
+  * detector bin k sits at u_k = k - (n_det-1)/2 (unit spacing);
+  * projection angle theta (degrees) has ray normal (cos theta, sin theta),
+    and a ray is the line x cos theta + y sin theta = u.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+__all__ = [
+    "Ellipses",
+    "random_ellipses",
+    "rasterize",
+    "analytic_sinogram",
+    "disk_sinogram",
+    "noisy_sinogram",
+    "uniform_angles",
+    "sketch_indices",
+    "random_sketch_offset",
+    "rotation_angles",
+    "step_rng",
+]
+
+
+@dataclass(frozen=True)
+class Ellipses:
+    """A sum of constant-intensity ellipses in physical coordinates [-1,1]^2."""
+
+    cx: np.ndarray
+    cy: np.ndarray
+    a: np.ndarray      # semi-axis along the direction phi
+    b: np.ndarray      # semi-axis across it
+    phi_deg: np.ndarray
+    rho: np.ndarray    # intensity (added where ellipses overlap)
+
+
+def random_ellipses(seed: int, count: int = 10) -> Ellipses:
+    """Ten random ellipses: centres U[-0.8,0.8]^2, semi-axes U(0.05,0.4),
+    intensities U(0,1), orientation U[0,180) degrees."""
+    rng = np.random.default_rng(seed)
+    cx = rng.uniform(-0.8, 0.8, count)
+    cy = rng.uniform(-0.8, 0.8, count)
+    a = rng.uniform(0.05, 0.4, count)
+    b = rng.uniform(0.05, 0.4, count)
+    phi = rng.uniform(0.0, 180.0, count)
+    rho = rng.uniform(0.0, 1.0, count)
+    return Ellipses(cx, cy, a, b, phi, rho)
+
+
+def rasterize(e: Ellipses, N: int, supersample: int = 1) -> np.ndarray:
+    """Point-sample the phantom at pixel centres (optionally s x s sub-samples
+    averaged).  Returns float64 [N, N], row 0 at the top."""
+    s = int(supersample)
+    offs = (np.arange(s) + 0.5) / s - 0.5
+    idx = np.arange(N, dtype=np.float64)
+    img = np.zeros((N, N), dtype=np.float64)
+    for oy in offs:
+        for ox in offs:
+            X = (idx[None, :] - (N - 1) / 2.0 + ox) * (2.0 / N)
+            Y = ((N - 1) / 2.0 - idx[:, None] - oy) * (2.0 / N)
+            for cx, cy, a, b, phi, rho in zip(e.cx, e.cy, e.a, e.b, e.phi_deg, e.rho):
+                cp, sp = math.cos(math.radians(phi)), math.sin(math.radians(phi))
+                dx, dy = X - cx, Y - cy
+                xr = dx * cp + dy * sp
+                yr = -dx * sp + dy * cp
+                img += rho * ((xr / a) ** 2 + (yr / b) ** 2 <= 1.0)
+    return img / (s * s)
+
+
+def analytic_sinogram(e: Ellipses, N: int, angles_deg, n_det: int) -> np.ndarray:
+    """Exact line integrals of the continuous phantom along the rays of the
+    detector grid, in pixel units (physical value times N/2).
+
+    For one ellipse the chord length through it at normal angle theta and
+    offset s' from the centre is 2ab*sqrt(q - s'^2)/q with
+    q = a^2 cos^2(theta-phi) + b^2 sin^2(theta-phi) (zero when s'^2 > q).
+    Returns float64 [n_angles, n_det]."""
+    th = np.radians(np.asarray(angles_deg, dtype=np.float64))[:, None]
+    u = (np.arange(n_det, dtype=np.float64) - (n_det - 1) / 2.0)[None, :]
+    S = u * (2.0 / N)
+    out = np.zeros((th.shape[0], n_det), dtype=np.float64)
+    for cx, cy, a, b, phi, rho in zip(e.cx, e.cy, e.a, e.b, e.phi_deg, e.rho):
+        sp = S - (cx * np.cos(th) + cy * np.sin(th))
+        d = th - math.radians(phi)
+        q = (a * np.cos(d)) ** 2 + (b * np.sin(d)) ** 2
+        rad = np.clip(q - sp * sp, 0.0, None)
+        out += rho * 2.0 * a * b * np.sqrt(rad) / q
+    return out * (N / 2.0)
+
+
+def disk_sinogram(radius_px: float, n_angles: int, n_det: int) -> np.ndarray:
+    """Line integrals of a centred unit-intensity disk of radius R (pixel
+    units): 2*sqrt(R^2 - u^2), independent of the angle."""
+    u = np.arange(n_det, dtype=np.float64) - (n_det - 1) / 2.0
+    row = 2.0 * np.sqrt(np.clip(radius_px * radius_px - u * u, 0.0, None))
+    return np.repeat(row[None, :], n_angles, axis=0)
+
+
+def noisy_sinogram(y_clean: np.ndarray, N: int, seed: int, I0: float = 1e5,
+                   sigma: float = 0.01) -> np.ndarray:
+    """Poisson photon noise at I0 plus Gaussian noise of std sigma in physical
+    post-log units.  y_clean is in pixel units; kappa = 2/N converts."""
+    rng = np.random.default_rng(seed)
+    kappa = 2.0 / N
+    counts = rng.poisson(I0 * np.exp(-kappa * y_clean))
+    post_log = -np.log(np.maximum(counts, 1) / I0)
+    post_log = post_log + sigma * rng.standard_normal(y_clean.shape)
+    return post_log / kappa
+
+
+def uniform_angles(n_angles: int) -> np.ndarray:
+    """theta_a = 180 a / n_angles degrees, a = 0..n_angles-1."""
+    return 180.0 * np.arange(n_angles, dtype=np.float64) / n_angles
+
+
+def sketch_indices(n_angles: int, m: int, offset: int) -> np.ndarray:
+    """Interleaved angle subset S_k = {offset + j*stride}, stride = n_angles/m
+    (Sec. 4.2.1: the operator is split into N interleaved minibatches)."""
+    if m <= 0 or n_angles % m != 0:
+        raise ValueError("sketch size must divide the angle count")
+    stride = n_angles // m
+    if not 0 <= offset < stride:
+        raise ValueError("offset must lie in [0, stride)")
+    return (offset + stride * np.arange(m)).astype(np.int32)
+
+
+def random_sketch_offset(rng: np.random.Generator, n_angles: int, m: int) -> int:
+    return int(rng.integers(0, n_angles // m))
+
+
+def rotation_angles(rng: np.random.Generator, B: int, G: int) -> np.ndarray:
+    """G rotation angles per sample, U[0, 360) degrees, float64 [B, G]."""
+    return rng.uniform(0.0, 360.0, size=(B, G))
+
+
+def step_rng(step: int) -> np.random.Generator:
+    """Per-iteration randomness (sketch offset, rotations)."""
+    return np.random.default_rng(1000 + int(step))
