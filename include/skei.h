@@ -1,0 +1,240 @@
+/*
+ * skei.h - C ABI of the GB300 (sm_103a) operators inside one sketched
+ * Equivariant Imaging (SkEI) step for parallel-beam CT.
+ *
+ * Paper: "Equivariant Test-Time Training with Operator Sketching for Imaging
+ * Inverse Problems" (arXiv 2411.05771).  The operators are those of
+ *   Sec. 2.1           y ~ A x; network input A^dagger y (FBP for CT)
+ *   Eq. (e:eiloss)     MC term ||y - A F(A^dagger y)||^2 and EI term
+ *                      ||T_g F(.) - F(A^dagger A T_g F(.))||^2
+ *   Eq. (e:skeiloss), Eq. (e:skeilossttt)
+ *                      the same with A_S = S A, y_S = S y, A_S^dagger
+ *   Sec. 4.1.1, 4.1.3, 4.2.1
+ *                      discrete Radon transform, rotations as the group,
+ *                      interleaved angle subsets as the sketch.
+ *
+ * Discretisation (the paper leaves it open; these readings are fixed here):
+ *   image x: N x N, row-major, row 0 at the top; pixel centre
+ *     x_j = j - (N-1)/2, y_i = (N-1)/2 - i (pixel units, y up).
+ *   detector: n_det unit bins, u_k = k - (n_det-1)/2; ray (theta, k) is the
+ *     line x cos(theta) + y sin(theta) = u_k.
+ *   A: Joseph's method - along rows when (theta mod 180) lies in [0,45] or
+ *     (135,180), along columns otherwise; linear interpolation between the
+ *     two nearest pixels of each row (column), zero outside the image,
+ *     weighted by 1/|cos| (1/|sin|).
+ *   H: Ram-Lak filter h(0)=1/4, h(odd n)=-1/(pi^2 n^2), h(even n)=0, linear
+ *     convolution over the detector (zero outside).
+ *   B: pixel-driven back-projection, linear interpolation on the bins at
+ *     t = x_j cos + y_i sin + (n_det-1)/2.
+ *   A_S^dagger = (pi/m) B_S H with m the number of angles in S (FBP).
+ *   T_g: counter-clockwise rotation by g degrees about the image centre,
+ *     bilinear, zero outside.
+ *
+ * Conventions for every entry point:
+ *   - returns SKEI_OK (0) or a negative status; never throws, never aborts;
+ *     skei_last_error() gives a message for the calling thread.
+ *   - asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream); no entry point synchronises unless it says so.
+ *   - every image / sinogram pointer is a DEVICE pointer owned by the caller,
+ *     16-byte aligned, densely packed in the layout stated; `dtype` says how
+ *     those buffers are stored (SKEI_F32 = float, SKEI_BF16 = bfloat16
+ *     round-to-nearest-even).  Arithmetic is FP32 in every case; loss
+ *     reductions are FP64.
+ *   - angle index lists (`idx`) are DEVICE int32 arrays of m entries into the
+ *     plan's angle list; idx == NULL means all angles in order (then m must
+ *     equal n_angles).  Entries outside [0, n_angles) are not dereferenced:
+ *     the kernel zeroes that row and records the fault in the plan's status
+ *     word (skei_plan_status).
+ *   - the library owns only plan objects (angle tables on the device) and
+ *     allocates nothing else; callers pass workspaces sized by the
+ *     *_workspace_size queries.
+ *   - results do not depend on the stream or on the launch order of
+ *     independent calls; calls that write the same buffer concurrently race.
+ */
+#ifndef SKEI_H
+#define SKEI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SKEI_OK        0
+#define SKEI_EINVAL   (-1)  /* bad shape, pointer, alignment, dtype or size   */
+#define SKEI_ENOMEM   (-2)  /* plan allocation failed                          */
+#define SKEI_ECUDA    (-3)  /* a CUDA runtime call or kernel launch failed     */
+#define SKEI_ETIMEOUT (-4)  /* a bounded device wait gave up                   */
+
+#define SKEI_F32  0
+#define SKEI_BF16 1
+
+/* Maximum image side and detector size accepted by a plan. */
+#define SKEI_MAX_N     4096
+#define SKEI_MAX_NDET  5800
+#define SKEI_MAX_ANGLES 65535
+
+typedef struct skei_plan_s *skei_plan;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int skei_version(void);
+
+/* Message describing the last failing call on this thread ("" if none).
+ * The string stays valid until the next call on this thread. */
+const char *skei_last_error(void);
+
+/* ---------------------------------------------------------------- plans --
+ * A plan fixes the geometry of A: image side N, detector bins n_det and the
+ * full angle list (Sec. 4.1.1: n uniformly spaced views).
+ *   N          1..SKEI_MAX_N
+ *   n_det      0 selects the smallest odd integer >= N*sqrt(2); otherwise
+ *              1..SKEI_MAX_NDET
+ *   n_angles   1..SKEI_MAX_ANGLES
+ *   angles_deg HOST array of n_angles degrees (any real values), or NULL for
+ *              theta_a = 180 a / n_angles.
+ * The plan copies the angles, derives its per-angle constants in FP64 and
+ * uploads them to the CURRENT device; use it only with that device.
+ * Errors: EINVAL for bad sizes or a NULL `out`; ENOMEM / ECUDA on device
+ * allocation or copy failure (nothing is leaked). */
+int skei_plan_create(int N, int n_det, int n_angles, const double *angles_deg,
+                     skei_plan *out);
+int skei_plan_destroy(skei_plan plan);
+int skei_plan_geometry(skei_plan plan, int *N, int *n_det, int *n_angles);
+
+/* Reads (and, if reset != 0, clears) the plan's device status word: bit 0 is
+ * set when a kernel met an angle index outside [0, n_angles).  SYNCHRONISES
+ * the device. */
+int skei_plan_status(skei_plan plan, int reset, int *word);
+
+/* --------------------------------------------------------------- A, A^T --
+ * skei_proj_fwd: sinogram of x on the angle subset S (Sec. 2.3 and 3.1:
+ * A_S = S A; Sec. 4.2.1: S selects interleaved angles).
+ *   x    [B][N][N]                      (dtype)
+ *   out  [B][m][n_det]                  (dtype)
+ *        out[b][a][k] = (A x_b)[idx[a]][k]                     if y == NULL
+ *        out[b][a][k] = y[b][idx[a]][k] - (A x_b)[idx[a]][k]   otherwise
+ *   y    NULL or the FULL measurement [B][n_angles][n_det] (dtype): the
+ *        measurement-consistency residual S y - A_S x of Eq. (e:skeiloss).
+ * B >= 1, 1 <= m <= n_angles.  x and out must not overlap. */
+int skei_proj_fwd(skei_plan plan, int dtype, const void *x, int B,
+                  const int *idx, int m, const void *y, void *out, void *stream);
+
+/* skei_proj_adj: x = alpha * A_S^T sino + beta * x, the exact transpose of
+ * skei_proj_fwd (the same interpolation weights, gathered per pixel; needed
+ * for the gradient of the MC and EI terms, Algorithm 2's update).
+ *   sino [B][m][n_det] (dtype);  x [B][N][N] (dtype), read only if beta != 0. */
+int skei_proj_adj(skei_plan plan, int dtype, const void *sino, int B,
+                  const int *idx, int m, float alpha, float beta, void *x,
+                  void *stream);
+
+/* ---------------------------------------------------- H, B, B^T, FBP --
+ * skei_filter: q = scale * H p for `rows` rows of n_det bins (dtype).
+ * H is the Ram-Lak ramp of filtered back-projection (Sec. 2.1, 4.1.1); it is
+ * symmetric, so it is also its own transpose. */
+int skei_filter(skei_plan plan, int dtype, const void *p, int rows, float scale,
+                void *q, void *stream);
+
+/* skei_backproject: x = alpha * B_S q + beta * x (unscaled back-projection).
+ *   q [B][m][n_det] (dtype);  x [B][N][N] (dtype). */
+int skei_backproject(skei_plan plan, int dtype, const void *q, int B,
+                     const int *idx, int m, float alpha, float beta, void *x,
+                     void *stream);
+
+/* skei_backproject_adj: q = alpha * B_S^T x, the exact transpose of
+ * skei_backproject.  x [B][N][N];  q [B][m][n_det]. */
+int skei_backproject_adj(skei_plan plan, int dtype, const void *x, int B,
+                         const int *idx, int m, float alpha, void *q,
+                         void *stream);
+
+/* Workspace (bytes) for skei_fbp / skei_fbp_adj on B images and m angles. */
+size_t skei_fbp_workspace_size(skei_plan plan, int dtype, int B, int m);
+
+/* skei_fbp: x = A_S^dagger sino = (pi/m) B_S H sino - the FBP approximation
+ * of the pseudo-inverse (Sec. 2.1; Sec. 3.1 uses it on the sketch).
+ *   sino [B][m][n_det];  x [B][N][N];  work >= skei_fbp_workspace_size. */
+int skei_fbp(skei_plan plan, int dtype, const void *sino, int B, const int *idx,
+             int m, void *x, void *work, size_t work_bytes, void *stream);
+
+/* skei_fbp_adj: sino = (A_S^dagger)^T x = (pi/m) H B_S^T x. */
+int skei_fbp_adj(skei_plan plan, int dtype, const void *x, int B,
+                 const int *idx, int m, void *sino, void *work,
+                 size_t work_bytes, void *stream);
+
+/* ------------------------------------------------------------ rotations --
+ * skei_rotate: out[b][g] = T_{g_deg[b][g]} x[b] (Sec. 4.1.3: the transform
+ * group of CT is rotations; Eq. (e:eiloss) applies T_i to F(A^dagger y)).
+ *   x [B][N][N]; out [B][G][N][N] (dtype); g_deg DEVICE double [B][G]. */
+int skei_rotate(int dtype, const void *x, int B, int N, const double *g_deg,
+                int G, void *out, void *stream);
+
+/* skei_rotate_adj: gx[b] = alpha * sum_g T_{g_deg[b][g]}^T gout[b][g]
+ *                          + beta * gx[b]   (exact transpose, gathered). */
+int skei_rotate_adj(int dtype, const void *gout, int B, int N,
+                    const double *g_deg, int G, float alpha, float beta,
+                    void *gx, void *stream);
+
+/* ------------------------------------------------- fused EI / SkEI loss --
+ * The loss of Eq. (e:skeiloss) / (e:skeilossttt), split around the caller's
+ * network F, for B measurements and G rotations each:
+ *   x1 = F(A^dagger y)                              (caller)
+ *   skei_ei_loss_fwd:    r  = S_mc y - A_mc x1      [B][mc_m][n_det]
+ *                        x2 = T_g x1                [B][G][N][N]
+ *                        z  = A_S^dagger A_S x2     [B][G][N][N]
+ *   x3 = F(z)                                       (caller)
+ *   skei_ei_loss_finish: mc_b  = mc_scale ||r_b||^2
+ *                        ei_bg = ||x2_bg - x3_bg||^2
+ *                        loss  = (1/B) sum_b [mc_b + (lambda/G) sum_g ei_bg]
+ *                        g_x2 = dloss/dx2 = 2 lambda/(B G) (x2 - x3) = -g_x3
+ *   g_z = (dF/dz)^T g_x3                            (caller)
+ *   skei_ei_loss_bwd:    g_x1 = -2 mc_coef A_mc^T r
+ *                               + sum_g T_g^T [g_x2 + (pi/m) A_S^T H B_S^T g_z]
+ * mc_idx/mc_m select the angles of the MC term (NULL = all), sk_idx/sk_m the
+ * sketch S of the EI term (NULL = all: plain EI).  mc_scale multiplies a
+ * sketched MC term (n/m makes it unbiased, Sec. 3.1's E(S^T S) = I).  With
+ * loss as above, mc_coef = mc_scale / B.  All outputs are in `dtype` except
+ * mc_out [B], ei_out [B][G] and loss_out [1], which are DEVICE doubles. */
+size_t skei_ei_workspace_size(skei_plan plan, int dtype, int B, int G, int mc_m,
+                              int sk_m);
+
+int skei_ei_loss_fwd(skei_plan plan, int dtype, const void *x1, const void *y,
+                     int B, const int *mc_idx, int mc_m, const int *sk_idx,
+                     int sk_m, const double *g_deg, int G, void *r, void *x2,
+                     void *z, void *work, size_t work_bytes, void *stream);
+
+int skei_ei_loss_finish(int dtype, const void *x2, const void *x3,
+                        const void *r, int B, int G, int N, int r_len,
+                        double lambda, double mc_scale, double *mc_out,
+                        double *ei_out, double *loss_out, void *g_x2, void *g_x3,
+                        void *work, size_t work_bytes, void *stream);
+
+/* g_x2 and g_z may be NULL (treated as zero). */
+int skei_ei_loss_bwd(skei_plan plan, int dtype, const void *r, const void *g_x2,
+                     const void *g_z, int B, const int *mc_idx, int mc_m,
+                     const int *sk_idx, int sk_m, const double *g_deg, int G,
+                     double mc_coef, void *g_x1, void *work, size_t work_bytes,
+                     void *stream);
+
+/* ------------------------------------------ stand-in network utilities --
+ * Not operators of the paper: the residual stand-in network
+ * F_theta(u) = u + theta used by the benchmark's test-time-training loop,
+ * and the Adam update of Algorithm 2 (Sec. 4.1.3: Adam, lr 5e-4).
+ *
+ * skei_residual_add: out[c][i] = u[c][i] + theta[i], c < count, i < n.
+ *   u, out: dtype; theta: float. */
+int skei_residual_add(int dtype, const void *u, const float *theta, int count,
+                      int64_t n, void *out, void *stream);
+
+/* skei_adam_step: g[i] = sum_{c<c1} g1[c][i] + sum_{c<c2} g2[c][i] (g1, g2 in
+ * dtype; g2 may be NULL with c2 = 0), then one Adam update of theta, m, v
+ * (float, n entries) with bias correction for the step number *step (DEVICE
+ * int, >= 1; read, not modified). */
+int skei_adam_step(float *theta, int64_t n, int dtype, const void *g1, int c1,
+                   const void *g2, int c2, float *m, float *v, const int *step,
+                   double lr, double beta1, double beta2, double eps,
+                   void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SKEI_H */

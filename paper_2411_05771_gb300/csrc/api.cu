@@ -1,0 +1,524 @@
+// C-ABI entry points of libskei: argument validation, dtype dispatch and the
+// composition of the EI / SkEI loss (Eq. (e:skeiloss), Algorithm 2) from the
+// operator kernels, plus the FP64 loss reductions and the stand-in network's
+// helpers (residual add, Adam).
+#include <cmath>
+
+#include "common.cuh"
+
+using bf16 = __nv_bfloat16;
+
+namespace skei {
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kChunk = 8192;     // elements per partial sum of the loss
+constexpr int kRedThreads = 256;
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// ------------------------------------------------------ loss reductions --
+// Pass 1: one CTA per chunk of one segment.  Image segments (b, g) hold
+// d = x2 - x3 and also emit g_x2 = kappa d, g_x3 = -kappa d; residual
+// segments b hold r.  Each CTA writes sum d^2 (FP64) of its chunk.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads)
+    ei_partials_kernel(const T *x2, const T *x3, const T *r, int64_t n_img, int n_imgseg,
+                       int cpi, int64_t r_len, int cpr, float kappa, T *g_x2, T *g_x3,
+                       double *partial) {
+  __shared__ double red[kRedThreads / 32];
+  const int blk = blockIdx.x;
+  double s = 0.0;
+  if (blk < n_imgseg * cpi) {
+    const int seg = blk / cpi, ch = blk - seg * cpi;
+    const int64_t base = (int64_t)seg * n_img;
+    const int64_t e0 = (int64_t)ch * kChunk, e1 = min(e0 + kChunk, n_img);
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += kRedThreads) {
+      const float d = ldg_f(x2 + base + e) - ldg_f(x3 + base + e);
+      s += (double)d * (double)d;
+      if (g_x2) st_f(g_x2 + base + e, kappa * d);
+      if (g_x3) st_f(g_x3 + base + e, -kappa * d);
+    }
+  } else {
+    const int rb = blk - n_imgseg * cpi;
+    const int seg = rb / cpr, ch = rb - seg * cpr;
+    const int64_t base = (int64_t)seg * r_len;
+    const int64_t e0 = (int64_t)ch * kChunk, e1 = min(e0 + kChunk, r_len);
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += kRedThreads) {
+      const float v = ldg_f(r + base + e);
+      s += (double)v * (double)v;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kRedThreads / 32; ++w) t += red[w];
+    partial[blk] = t;
+  }
+}
+
+// Pass 2 (one CTA): segment sums in a fixed order, then
+// loss = (1/B) sum_b [mc_scale ||r_b||^2 + (lambda/G) sum_g ||x2 - x3||^2].
+__global__ void __launch_bounds__(kRedThreads)
+    ei_final_kernel(const double *partial, int B, int G, int cpi, int cpr, double lambda,
+                    double mc_scale, double *mc_out, double *ei_out, double *loss_out) {
+  extern __shared__ double seg_sum[];  // [B*G + B]
+  const int nseg = B * G + B;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int sgi = warp; sgi < nseg; sgi += kRedThreads / 32) {
+    const bool img = sgi < B * G;
+    const int nch = img ? cpi : cpr;
+    const double *src = img ? partial + (size_t)sgi * cpi
+                            : partial + (size_t)B * G * cpi + (size_t)(sgi - B * G) * cpr;
+    double s = 0.0;
+    for (int c = lane; c < nch; c += 32) s += src[c];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) seg_sum[sgi] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double loss = 0.0;
+    for (int b = 0; b < B; ++b) {
+      const double mc = mc_scale * seg_sum[B * G + b];
+      double ei = 0.0;
+      for (int g = 0; g < G; ++g) {
+        const double e = seg_sum[b * G + g];
+        if (ei_out) ei_out[b * G + g] = e;
+        ei += e;
+      }
+      if (mc_out) mc_out[b] = mc;
+      loss += mc + lambda / G * ei;
+    }
+    if (loss_out) *loss_out = loss / B;
+  }
+}
+
+// --------------------------------------------------- stand-in network --
+template <typename T>
+__global__ void residual_add_kernel(const T *u, const float *theta, int count, int64_t n,
+                                    T *out) {
+  const int64_t total = (int64_t)count * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x)
+    st_f(out + e, ldg_f(u + e) + __ldg(theta + e % n));
+}
+
+template <typename T>
+__global__ void adam_kernel(float *theta, int64_t n, const T *g1, int c1, const T *g2, int c2,
+                            float *m, float *v, const int *step, float lr, float b1, float b2,
+                            float eps) {
+  __shared__ float bc[2];
+  if (threadIdx.x == 0) {
+    const int t = max(*step, 1);
+    bc[0] = (float)(1.0 - pow((double)b1, (double)t));
+    bc[1] = (float)(1.0 - pow((double)b2, (double)t));
+  }
+  __syncthreads();
+  const float bc1 = bc[0], bc2 = bc[1];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float g = 0.0f;
+    for (int c = 0; c < c1; ++c) g += ldg_f(g1 + (int64_t)c * n + i);
+    for (int c = 0; c < c2; ++c) g += ldg_f(g2 + (int64_t)c * n + i);
+    const float mi = fmaf(b1, m[i], (1.0f - b1) * g);
+    const float vi = fmaf(b2, v[i], (1.0f - b2) * g * g);
+    m[i] = mi;
+    v[i] = vi;
+    theta[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+  }
+}
+
+int grid_for(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  return (int)std::min<int64_t>(std::max<int64_t>(g, 1), 152 * 32);
+}
+
+// ------------------------------------------------------------ FBP helpers --
+template <typename T>
+int fbp_impl(skei_plan p, const T *sino, int B, const int *idx, int m, T *x, float *work,
+             cudaStream_t st) {
+  if (int rc = launch_filter<T, float>(p, sino, B * m, (float)(kPi / m), work, st)) return rc;
+  return launch_backproject<float, T, T>(p, work, B, idx, m, 1.0f, 0.0f, nullptr, x, st);
+}
+
+template <typename T>
+int fbp_adj_impl(skei_plan p, const T *x, int B, const int *idx, int m, T *sino, float *work,
+                 cudaStream_t st) {
+  if (int rc = launch_backproject_adj<T, float>(p, x, B, idx, m, 1.0f, work, st)) return rc;
+  return launch_filter<float, T>(p, work, B * m, (float)(kPi / m), sino, st);
+}
+
+// -------------------------------------------------------------- EI loss --
+struct EiWork {
+  size_t p_bytes, img_bytes, part_bytes, total;
+  int cpi, cpr;
+};
+
+EiWork ei_work(skei_plan p, int B, int G, int mc_m, int sk_m) {
+  EiWork w;
+  const size_t bg = (size_t)B * G;
+  w.p_bytes = align256(bg * sk_m * p->n_det * sizeof(float));
+  w.img_bytes = align256(bg * p->N * p->N * sizeof(float));
+  w.cpi = (int)ceil_div((size_t)p->N * p->N, kChunk);
+  w.cpr = (int)ceil_div((size_t)mc_m * p->n_det, kChunk);
+  w.part_bytes = align256((bg * w.cpi + (size_t)B * w.cpr) * sizeof(double));
+  const size_t fwd = 2 * w.p_bytes;
+  const size_t bwd = 2 * w.p_bytes + w.img_bytes;
+  w.total = std::max(std::max(fwd, bwd), w.part_bytes);
+  return w;
+}
+
+template <typename T>
+int ei_fwd_impl(skei_plan p, const T *x1, const T *y, int B, const int *mc_idx, int mc_m,
+                const int *sk_idx, int sk_m, const double *g_deg, int G, T *r, T *x2, T *z,
+                char *work, cudaStream_t st) {
+  const EiWork w = ei_work(p, B, G, mc_m, sk_m);
+  float *pbuf = reinterpret_cast<float *>(work);
+  float *qbuf = reinterpret_cast<float *>(work + w.p_bytes);
+  const int BG = B * G;
+  int rc;
+  if ((rc = launch_proj_fwd<T, T>(p, x1, B, mc_idx, mc_m, y, r, st))) return rc;
+  if ((rc = launch_rotate<T, T>(x1, B, p->N, g_deg, G, x2, st))) return rc;
+  if ((rc = launch_proj_fwd<T, float>(p, x2, BG, sk_idx, sk_m, nullptr, pbuf, st))) return rc;
+  if ((rc = launch_filter<float, float>(p, pbuf, BG * sk_m, (float)(kPi / sk_m), qbuf, st)))
+    return rc;
+  return launch_backproject<float, T, T>(p, qbuf, BG, sk_idx, sk_m, 1.0f, 0.0f, nullptr, z, st);
+}
+
+template <typename T>
+int ei_bwd_impl(skei_plan p, const T *r, const T *g_x2, const T *g_z, int B, const int *mc_idx,
+                int mc_m, const int *sk_idx, int sk_m, const double *g_deg, int G,
+                double mc_coef, T *g_x1, char *work, cudaStream_t st) {
+  const EiWork w = ei_work(p, B, G, mc_m, sk_m);
+  float *ubuf = reinterpret_cast<float *>(work);
+  float *vbuf = reinterpret_cast<float *>(work + w.p_bytes);
+  float *gtot = reinterpret_cast<float *>(work + 2 * w.p_bytes);
+  const int BG = B * G;
+  int rc;
+  // MC term: g_x1 = -2 mc_coef A_mc^T r
+  if ((rc = launch_proj_adj<T, T, T>(p, r, B, mc_idx, mc_m, (float)(-2.0 * mc_coef), 0.0f,
+                                     nullptr, g_x1, st)))
+    return rc;
+  if (g_z) {
+    // through z = (pi/m) B_S H A_S x2:  g_x2 + (pi/m) A_S^T H B_S^T g_z
+    if ((rc = launch_backproject_adj<T, float>(p, g_z, BG, sk_idx, sk_m, 1.0f, ubuf, st)))
+      return rc;
+    if ((rc = launch_filter<float, float>(p, ubuf, BG * sk_m, (float)(kPi / sk_m), vbuf, st)))
+      return rc;
+    if ((rc = launch_proj_adj<float, T, float>(p, vbuf, BG, sk_idx, sk_m, 1.0f,
+                                               g_x2 ? 1.0f : 0.0f, g_x2, gtot, st)))
+      return rc;
+    return launch_rotate_adj<float, T>(gtot, B, p->N, g_deg, G, 1.0f, 1.0f, g_x1, st);
+  }
+  if (g_x2) return launch_rotate_adj<T, T>(g_x2, B, p->N, g_deg, G, 1.0f, 1.0f, g_x1, st);
+  return SKEI_OK;
+}
+
+template <typename T>
+int ei_finish_impl(const T *x2, const T *x3, const T *r, int B, int G, int N, int r_len,
+                   double lambda, double mc_scale, double *mc_out, double *ei_out,
+                   double *loss_out, T *g_x2, T *g_x3, char *work, cudaStream_t st) {
+  const int64_t n_img = (int64_t)N * N;
+  const int cpi = (int)ceil_div((size_t)n_img, kChunk);
+  const int cpr = (int)ceil_div((size_t)r_len, kChunk);
+  double *partial = reinterpret_cast<double *>(work);
+  const int nblk = B * G * cpi + B * cpr;
+  const float kappa = (float)(2.0 * lambda / ((double)B * G));
+  ei_partials_kernel<T><<<nblk, kRedThreads, 0, st>>>(x2, x3, r, n_img, B * G, cpi, r_len, cpr,
+                                                      kappa, g_x2, g_x3, partial);
+  if (int rc = check_launch("loss partial sums launch")) return rc;
+  const size_t smem = sizeof(double) * (size_t)(B * G + B);
+  if (smem > 48 * 1024) return set_error(SKEI_EINVAL, "B*G + B = %d segments is too many", B * G + B);
+  ei_final_kernel<<<1, kRedThreads, smem, st>>>(partial, B, G, cpi, cpr, lambda, mc_scale,
+                                                mc_out, ei_out, loss_out);
+  return check_launch("loss final reduction launch");
+}
+
+// --------------------------------------------------------- validation --
+#define SKEI_TRY(expr)                     \
+  do {                                     \
+    if (int rc_ = (expr)) return rc_;      \
+  } while (0)
+
+cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int check_common(skei_plan p, int dtype, int B) {
+  SKEI_TRY(check_plan(p));
+  SKEI_TRY(check_dtype(dtype));
+  return check_batch(B);
+}
+
+int check_work(void *work, size_t have, size_t need) {
+  if (need == 0) return SKEI_OK;
+  SKEI_TRY(check_dev_ptr(work, "work"));
+  if (have < need)
+    return set_error(SKEI_EINVAL, "workspace of %zu bytes is smaller than the %zu needed", have,
+                     need);
+  return SKEI_OK;
+}
+
+int check_rot(int dtype, int B, int N, const double *g_deg, int G) {
+  SKEI_TRY(check_dtype(dtype));
+  SKEI_TRY(check_batch(B));
+  if (N < 1 || N > SKEI_MAX_N) return set_error(SKEI_EINVAL, "N=%d outside [1, %d]", N, SKEI_MAX_N);
+  if (G < 1 || (int64_t)B * G > 65535)
+    return set_error(SKEI_EINVAL, "G=%d with B=%d: need G >= 1 and B*G <= 65535", G, B);
+  return check_dev_ptr(g_deg, "g_deg");
+}
+
+}  // namespace
+}  // namespace skei
+
+using namespace skei;
+
+extern "C" {
+
+int skei_proj_fwd(skei_plan plan, int dtype, const void *x, int B, const int *idx, int m,
+                  const void *y, void *out, void *stream) {
+  SKEI_TRY(check_common(plan, dtype, B));
+  SKEI_TRY(check_dev_ptr(x, "x"));
+  SKEI_TRY(check_dev_ptr(out, "out"));
+  if (y) SKEI_TRY(check_dev_ptr(y, "y"));
+  SKEI_TRY(check_idx(plan, idx, m));
+  if (dtype == SKEI_F32)
+    return launch_proj_fwd<float, float>(plan, (const float *)x, B, idx, m, (const float *)y,
+                                         (float *)out, as_stream(stream));
+  return launch_proj_fwd<bf16, bf16>(plan, (const bf16 *)x, B, idx, m, (const bf16 *)y,
+                                     (bf16 *)out, as_stream(stream));
+}
+
+int skei_proj_adj(skei_plan plan, int dtype, const void *sino, int B, const int *idx, int m,
+                  float alpha, float beta, void *x, void *stream) {
+  SKEI_TRY(check_common(plan, dtype, B));
+  SKEI_TRY(check_dev_ptr(sino, "sino"));
+  SKEI_TRY(check_dev_ptr(x, "x"));
+  SKEI_TRY(check_idx(plan, idx, m));
+  if (dtype == SKEI_F32)
+    return launch_proj_adj<float, float, float>(plan, (const float *)sino, B, idx, m, alpha, beta,
+                                                (const float *)x, (float *)x, as_stream(stream));
+  return launch_proj_adj<bf16, bf16, bf16>(plan, (const bf16 *)sino, B, idx, m, alpha, beta,
+                                           (const bf16 *)x, (bf16 *)x, as_stream(stream));
+}
+
+int skei_filter(skei_plan plan, int dtype, const void *p, int rows, float scale, void *q,
+                void *stream) {
+  SKEI_TRY(check_plan(plan));
+  SKEI_TRY(check_dtype(dtype));
+  if (rows < 1) return set_error(SKEI_EINVAL, "rows=%d must be >= 1", rows);
+  SKEI_TRY(check_dev_ptr(p, "p"));
+  SKEI_TRY(check_dev_ptr(q, "q"));
+  if (dtype == SKEI_F32)
+    return launch_filter<float, float>(plan, (const float *)p, rows, scale, (float *)q,
+                                       as_stream(stream));
+  return launch_filter<bf16, bf16>(plan, (const bf16 *)p, rows, scale, (bf16 *)q,
+                                   as_stream(stream));
+}
+
+int skei_backproject(skei_plan plan, int dtype, const void *q, int B, const int *idx, int m,
+                     float alpha, float beta, void *x, void *stream) {
+  SKEI_TRY(check_common(plan, dtype, B));
+  SKEI_TRY(check_dev_ptr(q, "q"));
+  SKEI_TRY(check_dev_ptr(x, "x"));
+  SKEI_TRY(check_idx(plan, idx, m));
+  if (dtype == SKEI_F32)
+    return launch_backproject<float, float, float>(plan, (const float *)q, B, idx, m, alpha, beta,
+                                                   (const float *)x, (float *)x,
+                                                   as_stream(stream));
+  return launch_backproject<bf16, bf16, bf16>(plan, (const bf16 *)q, B, idx, m, alpha, beta,
+                                              (const bf16 *)x, (bf16 *)x, as_stream(stream));
+}
+
+int skei_backproject_adj(skei_plan plan, int dtype, const void *x, int B, const int *idx, int m,
+                         float alpha, void *q, void *stream) {
+  SKEI_TRY(check_common(plan, dtype, B));
+  SKEI_TRY(check_dev_ptr(x, "x"));
+  SKEI_TRY(check_dev_ptr(q, "q"));
+  SKEI_TRY(check_idx(plan, idx, m));
+  if (dtype == SKEI_F32)
+    return launch_backproject_adj<float, float>(plan, (const float *)x, B, idx, m, alpha,
+                                                (float *)q, as_stream(stream));
+  return launch_backproject_adj<bf16, bf16>(plan, (const bf16 *)x, B, idx, m, alpha, (bf16 *)q,
+                                            as_stream(stream));
+}
+
+size_t skei_fbp_workspace_size(skei_plan plan, int dtype, int B, int m) {
+  if (check_plan(plan) || check_dtype(dtype) || B < 1 || m < 1) return 0;
+  return align256((size_t)B * m * plan->n_det * sizeof(float));
+}
+
+int skei_fbp(skei_plan plan, int dtype, const void *sino, int B, const int *idx, int m, void *x,
+             void *work, size_t work_bytes, void *stream) {
+  SKEI_TRY(check_common(plan, dtype, B));
+  SKEI_TRY(check_dev_ptr(sino, "sino"));
+  SKEI_TRY(check_dev_ptr(x, "x"));
+  SKEI_TRY(check_idx(plan, idx, m));
+  SKEI_TRY(check_work(work, work_bytes, skei_fbp_workspace_size(plan, dtype, B, m)));
+  if (dtype == SKEI_F32)
+    return fbp_impl<float>(plan, (const float *)sino, B, idx, m, (float *)x, (float *)work,
+                           as_stream(stream));
+  return fbp_impl<bf16>(plan, (const bf16 *)sino, B, idx, m, (bf16 *)x, (float *)work,
+                        as_stream(stream));
+}
+
+int skei_fbp_adj(skei_plan plan, int dtype, const void *x, int B, const int *idx, int m,
+                 void *sino, void *work, size_t work_bytes, void *stream) {
+  SKEI_TRY(check_common(plan, dtype, B));
+  SKEI_TRY(check_dev_ptr(x, "x"));
+  SKEI_TRY(check_dev_ptr(sino, "sino"));
+  SKEI_TRY(check_idx(plan, idx, m));
+  SKEI_TRY(check_work(work, work_bytes, skei_fbp_workspace_size(plan, dtype, B, m)));
+  if (dtype == SKEI_F32)
+    return fbp_adj_impl<float>(plan, (const float *)x, B, idx, m, (float *)sino, (float *)work,
+                               as_stream(stream));
+  return fbp_adj_impl<bf16>(plan, (const bf16 *)x, B, idx, m, (bf16 *)sino, (float *)work,
+                            as_stream(stream));
+}
+
+int skei_rotate(int dtype, const void *x, int B, int N, const double *g_deg, int G, void *out,
+                void *stream) {
+  SKEI_TRY(check_rot(dtype, B, N, g_deg, G));
+  SKEI_TRY(check_dev_ptr(x, "x"));
+  SKEI_TRY(check_dev_ptr(out, "out"));
+  if (dtype == SKEI_F32)
+    return launch_rotate<float, float>((const float *)x, B, N, g_deg, G, (float *)out,
+                                       as_stream(stream));
+  return launch_rotate<bf16, bf16>((const bf16 *)x, B, N, g_deg, G, (bf16 *)out,
+                                   as_stream(stream));
+}
+
+int skei_rotate_adj(int dtype, const void *gout, int B, int N, const double *g_deg, int G,
+                    float alpha, float beta, void *gx, void *stream) {
+  SKEI_TRY(check_rot(dtype, B, N, g_deg, G));
+  SKEI_TRY(check_dev_ptr(gout, "gout"));
+  SKEI_TRY(check_dev_ptr(gx, "gx"));
+  if (dtype == SKEI_F32)
+    return launch_rotate_adj<float, float>((const float *)gout, B, N, g_deg, G, alpha, beta,
+                                           (float *)gx, as_stream(stream));
+  return launch_rotate_adj<bf16, bf16>((const bf16 *)gout, B, N, g_deg, G, alpha, beta,
+                                       (bf16 *)gx, as_stream(stream));
+}
+
+size_t skei_ei_workspace_size(skei_plan plan, int dtype, int B, int G, int mc_m, int sk_m) {
+  if (check_plan(plan) || check_dtype(dtype) || B < 1 || G < 1 || mc_m < 1 || sk_m < 1) return 0;
+  return ei_work(plan, B, G, mc_m, sk_m).total;
+}
+
+int skei_ei_loss_fwd(skei_plan plan, int dtype, const void *x1, const void *y, int B,
+                     const int *mc_idx, int mc_m, const int *sk_idx, int sk_m,
+                     const double *g_deg, int G, void *r, void *x2, void *z, void *work,
+                     size_t work_bytes, void *stream) {
+  SKEI_TRY(check_common(plan, dtype, B));
+  SKEI_TRY(check_rot(dtype, B, plan->N, g_deg, G));
+  SKEI_TRY(check_dev_ptr(x1, "x1"));
+  SKEI_TRY(check_dev_ptr(y, "y"));
+  SKEI_TRY(check_dev_ptr(r, "r"));
+  SKEI_TRY(check_dev_ptr(x2, "x2"));
+  SKEI_TRY(check_dev_ptr(z, "z"));
+  SKEI_TRY(check_idx(plan, mc_idx, mc_m));
+  SKEI_TRY(check_idx(plan, sk_idx, sk_m));
+  SKEI_TRY(check_work(work, work_bytes, skei_ei_workspace_size(plan, dtype, B, G, mc_m, sk_m)));
+  if (dtype == SKEI_F32)
+    return ei_fwd_impl<float>(plan, (const float *)x1, (const float *)y, B, mc_idx, mc_m, sk_idx,
+                              sk_m, g_deg, G, (float *)r, (float *)x2, (float *)z, (char *)work,
+                              as_stream(stream));
+  return ei_fwd_impl<bf16>(plan, (const bf16 *)x1, (const bf16 *)y, B, mc_idx, mc_m, sk_idx, sk_m,
+                           g_deg, G, (bf16 *)r, (bf16 *)x2, (bf16 *)z, (char *)work,
+                           as_stream(stream));
+}
+
+int skei_ei_loss_finish(int dtype, const void *x2, const void *x3, const void *r, int B, int G,
+                        int N, int r_len, double lambda, double mc_scale, double *mc_out,
+                        double *ei_out, double *loss_out, void *g_x2, void *g_x3, void *work,
+                        size_t work_bytes, void *stream) {
+  SKEI_TRY(check_dtype(dtype));
+  SKEI_TRY(check_batch(B));
+  if (G < 1 || (int64_t)B * G > 65535) return set_error(SKEI_EINVAL, "bad G=%d", G);
+  if (N < 1 || N > SKEI_MAX_N) return set_error(SKEI_EINVAL, "N=%d outside [1, %d]", N, SKEI_MAX_N);
+  if (r_len < 1) return set_error(SKEI_EINVAL, "r_len=%d must be >= 1", r_len);
+  SKEI_TRY(check_dev_ptr(x2, "x2"));
+  SKEI_TRY(check_dev_ptr(x3, "x3"));
+  SKEI_TRY(check_dev_ptr(r, "r"));
+  if (g_x2) SKEI_TRY(check_dev_ptr(g_x2, "g_x2"));
+  if (g_x3) SKEI_TRY(check_dev_ptr(g_x3, "g_x3"));
+  if (mc_out && (reinterpret_cast<uintptr_t>(mc_out) % 8)) return set_error(SKEI_EINVAL, "mc_out misaligned");
+  if (ei_out && (reinterpret_cast<uintptr_t>(ei_out) % 8)) return set_error(SKEI_EINVAL, "ei_out misaligned");
+  if (loss_out && (reinterpret_cast<uintptr_t>(loss_out) % 8)) return set_error(SKEI_EINVAL, "loss_out misaligned");
+  const size_t need = align256(((size_t)B * G * ceil_div((size_t)N * N, kChunk) +
+                                (size_t)B * ceil_div((size_t)r_len, kChunk)) * sizeof(double));
+  SKEI_TRY(check_work(work, work_bytes, need));
+  if (dtype == SKEI_F32)
+    return ei_finish_impl<float>((const float *)x2, (const float *)x3, (const float *)r, B, G, N,
+                                 r_len, lambda, mc_scale, mc_out, ei_out, loss_out, (float *)g_x2,
+                                 (float *)g_x3, (char *)work, as_stream(stream));
+  return ei_finish_impl<bf16>((const bf16 *)x2, (const bf16 *)x3, (const bf16 *)r, B, G, N, r_len,
+                              lambda, mc_scale, mc_out, ei_out, loss_out, (bf16 *)g_x2,
+                              (bf16 *)g_x3, (char *)work, as_stream(stream));
+}
+
+int skei_ei_loss_bwd(skei_plan plan, int dtype, const void *r, const void *g_x2, const void *g_z,
+                     int B, const int *mc_idx, int mc_m, const int *sk_idx, int sk_m,
+                     const double *g_deg, int G, double mc_coef, void *g_x1, void *work,
+                     size_t work_bytes, void *stream) {
+  SKEI_TRY(check_common(plan, dtype, B));
+  SKEI_TRY(check_rot(dtype, B, plan->N, g_deg, G));
+  SKEI_TRY(check_dev_ptr(r, "r"));
+  SKEI_TRY(check_dev_ptr(g_x1, "g_x1"));
+  if (g_x2) SKEI_TRY(check_dev_ptr(g_x2, "g_x2"));
+  if (g_z) SKEI_TRY(check_dev_ptr(g_z, "g_z"));
+  SKEI_TRY(check_idx(plan, mc_idx, mc_m));
+  SKEI_TRY(check_idx(plan, sk_idx, sk_m));
+  SKEI_TRY(check_work(work, work_bytes, skei_ei_workspace_size(plan, dtype, B, G, mc_m, sk_m)));
+  if (dtype == SKEI_F32)
+    return ei_bwd_impl<float>(plan, (const float *)r, (const float *)g_x2, (const float *)g_z, B,
+                              mc_idx, mc_m, sk_idx, sk_m, g_deg, G, mc_coef, (float *)g_x1,
+                              (char *)work, as_stream(stream));
+  return ei_bwd_impl<bf16>(plan, (const bf16 *)r, (const bf16 *)g_x2, (const bf16 *)g_z, B, mc_idx,
+                           mc_m, sk_idx, sk_m, g_deg, G, mc_coef, (bf16 *)g_x1, (char *)work,
+                           as_stream(stream));
+}
+
+int skei_residual_add(int dtype, const void *u, const float *theta, int count, int64_t n,
+                      void *out, void *stream) {
+  SKEI_TRY(check_dtype(dtype));
+  if (count < 1 || n < 1) return set_error(SKEI_EINVAL, "count=%d, n=%lld must be >= 1", count, (long long)n);
+  SKEI_TRY(check_dev_ptr(u, "u"));
+  SKEI_TRY(check_dev_ptr(theta, "theta"));
+  SKEI_TRY(check_dev_ptr(out, "out"));
+  const int grid = grid_for((int64_t)count * n, 256);
+  if (dtype == SKEI_F32)
+    residual_add_kernel<float><<<grid, 256, 0, as_stream(stream)>>>((const float *)u, theta, count,
+                                                                    n, (float *)out);
+  else
+    residual_add_kernel<bf16><<<grid, 256, 0, as_stream(stream)>>>((const bf16 *)u, theta, count,
+                                                                   n, (bf16 *)out);
+  return check_launch("residual add launch");
+}
+
+int skei_adam_step(float *theta, int64_t n, int dtype, const void *g1, int c1, const void *g2,
+                   int c2, float *m, float *v, const int *step, double lr, double beta1,
+                   double beta2, double eps, void *stream) {
+  SKEI_TRY(check_dtype(dtype));
+  if (n < 1 || c1 < 1 || c2 < 0) return set_error(SKEI_EINVAL, "bad sizes n=%lld c1=%d c2=%d", (long long)n, c1, c2);
+  SKEI_TRY(check_dev_ptr(theta, "theta"));
+  SKEI_TRY(check_dev_ptr(g1, "g1"));
+  if (c2 > 0) SKEI_TRY(check_dev_ptr(g2, "g2"));
+  SKEI_TRY(check_dev_ptr(m, "m"));
+  SKEI_TRY(check_dev_ptr(v, "v"));
+  if (!step || reinterpret_cast<uintptr_t>(step) % 4) return set_error(SKEI_EINVAL, "step is NULL or misaligned");
+  const int grid = grid_for(n, 256);
+  if (dtype == SKEI_F32)
+    adam_kernel<float><<<grid, 256, 0, as_stream(stream)>>>(theta, n, (const float *)g1, c1,
+                                                            (const float *)g2, c2, m, v, step,
+                                                            (float)lr, (float)beta1, (float)beta2,
+                                                            (float)eps);
+  else
+    adam_kernel<bf16><<<grid, 256, 0, as_stream(stream)>>>(theta, n, (const bf16 *)g1, c1,
+                                                           (const bf16 *)g2, c2, m, v, step,
+                                                           (float)lr, (float)beta1, (float)beta2,
+                                                           (float)eps);
+  return check_launch("adam launch");
+}
+
+}  // extern "C"

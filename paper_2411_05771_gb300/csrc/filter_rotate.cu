@@ -1,0 +1,244 @@
+// Ram-Lak filtering H of FBP (Sec. 2.1 / 4.1.1: FBP as the stable
+// approximation of A^dagger) and the bilinear rotations T_g of the CT
+// transform group (Sec. 4.1.3) with their exact gathered transposes.
+#include <cmath>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace skei {
+
+// Ram-Lak taps h(n) for n = 0..SKEI_MAX_NDET-1 (unit bins): h(0) = 1/4,
+// h(odd n) = -1/(pi^2 n^2), h(even n) = 0.  They do not depend on the plan,
+// so one copy lives in constant memory, where a warp-uniform read is a
+// broadcast that costs no shared-memory bandwidth.
+__constant__ float c_ramlak[SKEI_MAX_NDET];
+
+// Uploads the taps once per device (called by skei_plan_create, so never
+// inside a stream capture).
+int ensure_ramlak_taps() {
+  static std::mutex mu;
+  static bool done[64] = {false};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+    return set_error(SKEI_ECUDA, "ramlak taps: no current device");
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return SKEI_OK;
+  std::vector<float> taps(SKEI_MAX_NDET);
+  for (int n = 0; n < SKEI_MAX_NDET; ++n)
+    taps[n] = n == 0 ? 0.25f
+                     : (n % 2 == 0 ? 0.0f : (float)(-1.0 / (M_PI * M_PI * (double)n * (double)n)));
+  cudaError_t e = cudaMemcpyToSymbol(c_ramlak, taps.data(), sizeof(float) * SKEI_MAX_NDET);
+  if (e != cudaSuccess) return cuda_error(e, "ramlak taps upload");
+  done[dev] = true;
+  return SKEI_OK;
+}
+
+namespace {
+
+// ------------------------------------------------------------- Ram-Lak --
+// CTA (row, chunk): the row sits in shared memory between n_det zeros on
+// each side; thread t forms output k = chunk*128 + t as
+//   q[k] = scale (h0 p[k] + sum_{n odd} h(n) (p[k-n] + p[k+n])),
+// the even taps of the Ram-Lak kernel being zero.
+constexpr int kFilterThreads = 128;
+
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(kFilterThreads)
+    ramlak_kernel(const Tin *in, Tout *out, int nd, float scale) {
+  extern __shared__ float4 smem4[];
+  float *pb = reinterpret_cast<float *>(smem4);  // [3 nd]
+  const size_t row = blockIdx.x;
+  const Tin *pr = in + row * nd;
+  for (int e = threadIdx.x; e < 3 * nd; e += kFilterThreads) {
+    const int k = e - nd;
+    pb[e] = (k >= 0 && k < nd) ? ldg_f(pr + k) : 0.0f;
+  }
+  __syncthreads();
+  const int k = blockIdx.y * kFilterThreads + threadIdx.x;
+  if (k >= nd) return;
+  const float *pc = pb + nd + k;
+  float acc0 = c_ramlak[0] * pc[0], acc1 = 0.0f;
+  int n = 1;
+  for (; n + 2 < nd; n += 4) {
+    acc0 = fmaf(c_ramlak[n], pc[-n] + pc[n], acc0);
+    acc1 = fmaf(c_ramlak[n + 2], pc[-n - 2] + pc[n + 2], acc1);
+  }
+  for (; n < nd; n += 2) acc0 = fmaf(c_ramlak[n], pc[-n] + pc[n], acc0);
+  st_f(out + row * nd + k, scale * (acc0 + acc1));
+}
+
+// ------------------------------------------------------------ rotation --
+// Output pixel (i, j) samples the input at R(-g)(x_j, y_i), in fixed point
+//   row = R0 + j s + i c,   col = C0 + j c - i s,
+// R0 = h(1 - s - c), C0 = h(1 + s - c), h = (N-1)/2; bilinear weights
+// (1-fr)(1-fc), (1-fr)fc, fr(1-fc), fr fc; taps outside the image are 0.
+constexpr int kRotX = 32, kRotY = 8, kRotQ = 8;  // CTA tile 32 x 64, 8 pixels/thread
+constexpr int kRotThreads = kRotX * kRotY;
+
+struct RotConst {
+  long long c, s, C0, R0;  // 32.32
+  float cf, sf, C0f, R0f;  // FP32 copies to choose candidates
+};
+
+__device__ __forceinline__ RotConst rot_const(double deg, int N) {
+  double c, s;
+  trig_deg(deg, &c, &s);
+  const double h = 0.5 * (N - 1);
+  const double C0 = h * (1.0 + s - c), R0 = h * (1.0 - s - c);
+  return RotConst{to_fx(c), to_fx(s), to_fx(C0), to_fx(R0),
+                  (float)c, (float)s, (float)C0, (float)R0};
+}
+
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(kRotThreads)
+    rotate_kernel(const Tin *x, int N, int G, const double *g_deg, Tout *out) {
+  __shared__ RotConst rc;
+  const int bg = blockIdx.z, b = bg / G;
+  if (threadIdx.x == 0) rc = rot_const(g_deg[bg], N);
+  __syncthreads();
+  const int tx = threadIdx.x % kRotX, ty = threadIdx.x / kRotX;
+  const int j = blockIdx.x * kRotX + tx;
+  const int i_first = blockIdx.y * kRotY * kRotQ + ty;
+  if (j >= N) return;
+  const Tin *xb = x + (size_t)b * N * N;
+  long long row = rc.R0 + (long long)j * rc.s + (long long)i_first * rc.c;
+  long long col = rc.C0 + (long long)j * rc.c - (long long)i_first * rc.s;
+  const long long drow = rc.c * kRotY, dcol = -rc.s * kRotY;
+#pragma unroll 2
+  for (int q = 0; q < kRotQ; ++q, row += drow, col += dcol) {
+    const int i = i_first + kRotY * q;
+    if (i >= N) break;
+    const int i0 = ipart(row), j0 = ipart(col);
+    const float fr = frac23(row), fc = frac23(col);
+    const float gr = 1.0f - fr, gc = 1.0f - fc;
+    const bool r0 = i0 >= 0 && i0 < N, r1 = i0 + 1 >= 0 && i0 + 1 < N;
+    const bool c0 = j0 >= 0 && j0 < N, c1 = j0 + 1 >= 0 && j0 + 1 < N;
+    float v = 0.0f;
+    if (r0 && c0) v = fmaf(gr * gc, ldg_f(xb + (size_t)i0 * N + j0), v);
+    if (r0 && c1) v = fmaf(gr * fc, ldg_f(xb + (size_t)i0 * N + j0 + 1), v);
+    if (r1 && c0) v = fmaf(fr * gc, ldg_f(xb + (size_t)(i0 + 1) * N + j0), v);
+    if (r1 && c1) v = fmaf(fr * fc, ldg_f(xb + (size_t)(i0 + 1) * N + j0 + 1), v);
+    st_f(out + ((size_t)bg * N + i) * N + j, v);
+  }
+}
+
+// Transpose, gathered per input pixel (a, bb): the output pixels whose
+// sample lands in (a-1, a+1) x (bb-1, bb+1) lie within sqrt 2 of the
+// rotated position of (a, bb), i.e. among 3x3 candidates; each candidate's
+// sample is recomputed exactly in the forward's fixed-point form and
+// weighted with tap_weight, reproducing the forward's weights bitwise.
+constexpr int kAdjT = 16, kAdjQ = 2;  // CTA tile 16 x 32, 2 pixels/thread
+constexpr int kMaxG = 64;
+
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(kAdjT *kAdjT)
+    rotate_adj_kernel(const Tin *gout, int N, int G, const double *g_deg, float alpha,
+                      float beta, Tout *gx) {
+  __shared__ RotConst rc[kMaxG];
+  const int b = blockIdx.z;
+  const int t = threadIdx.y * kAdjT + threadIdx.x;
+  const int bb = blockIdx.x * kAdjT + threadIdx.x;
+  float acc[kAdjQ];
+#pragma unroll
+  for (int q = 0; q < kAdjQ; ++q) acc[q] = 0.0f;
+  for (int g0 = 0; g0 < G; g0 += kMaxG) {
+    const int ng = min(kMaxG, G - g0);
+    __syncthreads();
+    if (t < ng) rc[t] = rot_const(g_deg[(size_t)b * G + g0 + t], N);
+    __syncthreads();
+    if (bb >= N) continue;
+    for (int g = 0; g < ng; ++g) {
+      const RotConst r = rc[g];
+      const Tin *gb = gout + ((size_t)b * G + g0 + g) * N * N;
+#pragma unroll
+      for (int q = 0; q < kAdjQ; ++q) {
+        const int a = (blockIdx.y * kAdjQ + q) * kAdjT + threadIdx.y;
+        if (a >= N) continue;
+        const float dc = (float)bb - r.C0f, dr = (float)a - r.R0f;
+        const int ri = round_int(fmaf(-r.sf, dc, r.cf * dr));
+        const int rj = round_int(fmaf(r.cf, dc, r.sf * dr));
+        // candidate (ri-1, rj-1); i steps add (c, -s), j steps add (s, c)
+        const long long row0 = r.R0 + (long long)(rj - 1) * r.s + (long long)(ri - 1) * r.c;
+        const long long col0 = r.C0 + (long long)(rj - 1) * r.c - (long long)(ri - 1) * r.s;
+        float s = acc[q];
+#pragma unroll
+        for (int di = 0; di < 3; ++di) {
+          const int i = ri - 1 + di;
+          if (i < 0 || i >= N) continue;
+#pragma unroll
+          for (int dj = 0; dj < 3; ++dj) {
+            const int j = rj - 1 + dj;
+            if (j < 0 || j >= N) continue;
+            const long long row = row0 + (long long)di * r.c + (long long)dj * r.s;
+            const long long col = col0 - (long long)di * r.s + (long long)dj * r.c;
+            const float w = tap_weight(row, a) * tap_weight(col, bb);
+            if (w != 0.0f) s = fmaf(w, ldg_f(gb + (size_t)i * N + j), s);
+          }
+        }
+        acc[q] = s;
+      }
+    }
+  }
+  if (bb >= N) return;
+#pragma unroll
+  for (int q = 0; q < kAdjQ; ++q) {
+    const int a = (blockIdx.y * kAdjQ + q) * kAdjT + threadIdx.y;
+    if (a >= N) continue;
+    const size_t o = ((size_t)b * N + a) * N + bb;
+    float v = alpha * acc[q];
+    if (beta != 0.0f) v = fmaf(beta, ldg_f(gx + o), v);
+    st_f(gx + o, v);
+  }
+}
+
+}  // namespace
+
+template <typename Tin, typename Tout>
+int launch_filter(skei_plan p, const Tin *in, int rows, float scale, Tout *out,
+                  cudaStream_t st) {
+  const int nd = p->n_det;
+  const size_t smem = (size_t)3 * nd * sizeof(float);
+  auto kern = ramlak_kernel<Tin, Tout>;
+  static size_t configured = 0;
+  if (smem > 48 * 1024 && smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return cuda_error(e, "ramlak: shared memory attribute");
+    configured = smem;
+  }
+  dim3 grid(rows, (nd + kFilterThreads - 1) / kFilterThreads);
+  kern<<<grid, kFilterThreads, smem, st>>>(in, out, nd, scale);
+  return check_launch("ramlak filter launch");
+}
+
+template <typename Tin, typename Tout>
+int launch_rotate(const Tin *x, int B, int N, const double *g_deg, int G, Tout *out,
+                  cudaStream_t st) {
+  dim3 grid((N + kRotX - 1) / kRotX, (N + kRotY * kRotQ - 1) / (kRotY * kRotQ), B * G);
+  rotate_kernel<Tin, Tout><<<grid, kRotThreads, 0, st>>>(x, N, G, g_deg, out);
+  return check_launch("rotation launch");
+}
+
+template <typename Tin, typename Tout>
+int launch_rotate_adj(const Tin *gout, int B, int N, const double *g_deg, int G,
+                      float alpha, float beta, Tout *gx, cudaStream_t st) {
+  dim3 grid((N + kAdjT - 1) / kAdjT, (N + kAdjT * kAdjQ - 1) / (kAdjT * kAdjQ), B);
+  rotate_adj_kernel<Tin, Tout>
+      <<<grid, dim3(kAdjT, kAdjT), 0, st>>>(gout, N, G, g_deg, alpha, beta, gx);
+  return check_launch("rotation transpose launch");
+}
+
+#define SKEI_FR_INST(TI, TO)                                                                  \
+  template int launch_filter<TI, TO>(skei_plan, const TI *, int, float, TO *, cudaStream_t);  \
+  template int launch_rotate<TI, TO>(const TI *, int, int, const double *, int, TO *,         \
+                                     cudaStream_t);                                          \
+  template int launch_rotate_adj<TI, TO>(const TI *, int, int, const double *, int, float,    \
+                                         float, TO *, cudaStream_t);
+SKEI_FR_INST(float, float)
+SKEI_FR_INST(__nv_bfloat16, __nv_bfloat16)
+SKEI_FR_INST(float, __nv_bfloat16)
+SKEI_FR_INST(__nv_bfloat16, float)
+#undef SKEI_FR_INST
+
+}  // namespace skei

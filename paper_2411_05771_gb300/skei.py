@@ -1,0 +1,410 @@
+"""Thin Python binding of libskei (include/skei.h).
+
+Every function here marshals torch tensors into the C ABI of the same name
+(``proj_fwd`` -> ``skei_proj_fwd`` and so on) and launches on the current
+torch CUDA stream; all arithmetic runs in the library's CUDA kernels.  There
+is no fallback: importing this module fails if libskei.so is missing, and
+every call fails on non-CUDA tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+__all__ = [
+    "F32", "BF16", "Plan", "last_error", "version",
+    "proj_fwd", "proj_adj", "filter", "backproject", "backproject_adj",
+    "fbp_workspace_size", "fbp", "fbp_adj", "rotate", "rotate_adj",
+    "ei_workspace_size", "ei_loss_fwd", "ei_loss_finish", "ei_loss_bwd",
+    "residual_add", "adam_step", "library_path",
+]
+
+F32, BF16 = 0, 1
+
+library_path = _build.LIB
+if not os.path.exists(library_path):
+    raise ImportError(
+        f"libskei.so not found at {library_path}; build it with "
+        "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+_lib = ctypes.CDLL(library_path)
+
+_vp, _i, _f, _d, _sz, _i64 = (ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_double,
+                              ctypes.c_size_t, ctypes.c_int64)
+_PLAN = ctypes.c_void_p
+_SIGS = {
+    "skei_version": ([], _i),
+    "skei_last_error": ([], ctypes.c_char_p),
+    "skei_plan_create": ([_i, _i, _i, _vp, ctypes.POINTER(_PLAN)], _i),
+    "skei_plan_destroy": ([_PLAN], _i),
+    "skei_plan_geometry": ([_PLAN, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)], _i),
+    "skei_plan_status": ([_PLAN, _i, ctypes.POINTER(_i)], _i),
+    "skei_proj_fwd": ([_PLAN, _i, _vp, _i, _vp, _i, _vp, _vp, _vp], _i),
+    "skei_proj_adj": ([_PLAN, _i, _vp, _i, _vp, _i, _f, _f, _vp, _vp], _i),
+    "skei_filter": ([_PLAN, _i, _vp, _i, _f, _vp, _vp], _i),
+    "skei_backproject": ([_PLAN, _i, _vp, _i, _vp, _i, _f, _f, _vp, _vp], _i),
+    "skei_backproject_adj": ([_PLAN, _i, _vp, _i, _vp, _i, _f, _vp, _vp], _i),
+    "skei_fbp_workspace_size": ([_PLAN, _i, _i, _i], _sz),
+    "skei_fbp": ([_PLAN, _i, _vp, _i, _vp, _i, _vp, _vp, _sz, _vp], _i),
+    "skei_fbp_adj": ([_PLAN, _i, _vp, _i, _vp, _i, _vp, _vp, _sz, _vp], _i),
+    "skei_rotate": ([_i, _vp, _i, _i, _vp, _i, _vp, _vp], _i),
+    "skei_rotate_adj": ([_i, _vp, _i, _i, _vp, _i, _f, _f, _vp, _vp], _i),
+    "skei_ei_workspace_size": ([_PLAN, _i, _i, _i, _i, _i], _sz),
+    "skei_ei_loss_fwd": ([_PLAN, _i, _vp, _vp, _i, _vp, _i, _vp, _i, _vp, _i, _vp, _vp, _vp,
+                          _vp, _sz, _vp], _i),
+    "skei_ei_loss_finish": ([_i, _vp, _vp, _vp, _i, _i, _i, _i, _d, _d, _vp, _vp, _vp, _vp,
+                             _vp, _vp, _sz, _vp], _i),
+    "skei_ei_loss_bwd": ([_PLAN, _i, _vp, _vp, _vp, _i, _vp, _i, _vp, _i, _vp, _i, _d, _vp,
+                          _vp, _sz, _vp], _i),
+    "skei_residual_add": ([_i, _vp, _vp, _i, _i64, _vp, _vp], _i),
+    "skei_adam_step": ([_vp, _i64, _i, _vp, _i, _vp, _i, _vp, _vp, _vp, _d, _d, _d, _d, _vp], _i),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = _res
+
+
+def last_error() -> str:
+    return _lib.skei_last_error().decode()
+
+
+def version() -> int:
+    return _lib.skei_version()
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise RuntimeError(f"{what} failed ({rc}): {last_error()}")
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.bfloat16:
+        return BF16
+    raise TypeError(f"unsupported dtype {t.dtype}: use float32 or bfloat16")
+
+
+def _dev(t, name, dtype=None, shape=None):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """Geometry of A: image side N, detector bins n_det (0 = smallest odd
+    >= N sqrt 2) and the full angle list in degrees (default 180 a / n)."""
+
+    def __init__(self, N: int, n_angles: int, angles_deg=None, n_det: int = 0):
+        self._h = _PLAN()
+        ang = None
+        if angles_deg is not None:
+            ang = np.ascontiguousarray(np.asarray(angles_deg, dtype=np.float64).ravel())
+            if ang.size != n_angles:
+                raise ValueError("angles_deg must hold n_angles values")
+        p = None if ang is None else ang.ctypes.data_as(ctypes.c_void_p)
+        _check(_lib.skei_plan_create(int(N), int(n_det), int(n_angles), p, ctypes.byref(self._h)),
+               "skei_plan_create")
+        n, d, a = _i(), _i(), _i()
+        _check(_lib.skei_plan_geometry(self._h, ctypes.byref(n), ctypes.byref(d), ctypes.byref(a)),
+               "skei_plan_geometry")
+        self.N, self.n_det, self.n_angles = n.value, d.value, a.value
+        self.angles_deg = (ang.copy() if ang is not None
+                           else 180.0 * np.arange(n_angles, dtype=np.float64) / n_angles)
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("plan is closed")
+        return self._h
+
+    def status(self, reset: bool = True) -> int:
+        w = _i()
+        _check(_lib.skei_plan_status(self.handle, int(reset), ctypes.byref(w)), "skei_plan_status")
+        return w.value
+
+    def close(self):
+        if self._h:
+            _lib.skei_plan_destroy(self._h)
+            self._h = _PLAN()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _idx(plan: Plan, idx):
+    if idx is None:
+        return None, plan.n_angles
+    _dev(idx, "idx", torch.int32)
+    return ctypes.c_void_p(idx.data_ptr()), int(idx.numel())
+
+
+def proj_fwd(plan: Plan, x: torch.Tensor, idx=None, y=None, out=None) -> torch.Tensor:
+    """A_S x (or S y - A_S x when y is given); x [B, N, N] -> [B, m, n_det]."""
+    B = x.shape[0]
+    ip, m = _idx(plan, idx)
+    _dev(x, "x", shape=(B, plan.N, plan.N))
+    if y is not None:
+        _dev(y, "y", x.dtype, (B, plan.n_angles, plan.n_det))
+    if out is None:
+        out = torch.empty((B, m, plan.n_det), device=x.device, dtype=x.dtype)
+    _dev(out, "out", x.dtype, (B, m, plan.n_det))
+    _check(_lib.skei_proj_fwd(plan.handle, _dtype_code(x), _ptr(x), B, ip, m, _ptr(y), _ptr(out),
+                              _stream()), "skei_proj_fwd")
+    return out
+
+
+def proj_adj(plan: Plan, sino, idx=None, alpha=1.0, beta=0.0, out=None) -> torch.Tensor:
+    """alpha A_S^T sino + beta out; sino [B, m, n_det] -> [B, N, N]."""
+    B = sino.shape[0]
+    ip, m = _idx(plan, idx)
+    _dev(sino, "sino", shape=(B, m, plan.n_det))
+    if out is None:
+        if beta != 0.0:
+            raise ValueError("beta != 0 needs out")
+        out = torch.empty((B, plan.N, plan.N), device=sino.device, dtype=sino.dtype)
+    _dev(out, "out", sino.dtype, (B, plan.N, plan.N))
+    _check(_lib.skei_proj_adj(plan.handle, _dtype_code(sino), _ptr(sino), B, ip, m, float(alpha),
+                              float(beta), _ptr(out), _stream()), "skei_proj_adj")
+    return out
+
+
+def filter(plan: Plan, p, scale=1.0, out=None) -> torch.Tensor:  # noqa: A001
+    """scale * H p along the last (detector) axis."""
+    if p.shape[-1] != plan.n_det:
+        raise ValueError("last axis must hold n_det bins")
+    _dev(p, "p")
+    out = torch.empty_like(p) if out is None else out
+    _dev(out, "out", p.dtype, p.shape)
+    rows = p.numel() // plan.n_det
+    _check(_lib.skei_filter(plan.handle, _dtype_code(p), _ptr(p), rows, float(scale), _ptr(out),
+                            _stream()), "skei_filter")
+    return out
+
+
+def backproject(plan: Plan, q, idx=None, alpha=1.0, beta=0.0, out=None) -> torch.Tensor:
+    B = q.shape[0]
+    ip, m = _idx(plan, idx)
+    _dev(q, "q", shape=(B, m, plan.n_det))
+    if out is None:
+        if beta != 0.0:
+            raise ValueError("beta != 0 needs out")
+        out = torch.empty((B, plan.N, plan.N), device=q.device, dtype=q.dtype)
+    _dev(out, "out", q.dtype, (B, plan.N, plan.N))
+    _check(_lib.skei_backproject(plan.handle, _dtype_code(q), _ptr(q), B, ip, m, float(alpha),
+                                 float(beta), _ptr(out), _stream()), "skei_backproject")
+    return out
+
+
+def backproject_adj(plan: Plan, x, idx=None, alpha=1.0, out=None) -> torch.Tensor:
+    B = x.shape[0]
+    ip, m = _idx(plan, idx)
+    _dev(x, "x", shape=(B, plan.N, plan.N))
+    if out is None:
+        out = torch.empty((B, m, plan.n_det), device=x.device, dtype=x.dtype)
+    _dev(out, "out", x.dtype, (B, m, plan.n_det))
+    _check(_lib.skei_backproject_adj(plan.handle, _dtype_code(x), _ptr(x), B, ip, m, float(alpha),
+                                     _ptr(out), _stream()), "skei_backproject_adj")
+    return out
+
+
+def fbp_workspace_size(plan: Plan, dtype: int, B: int, m: int) -> int:
+    return int(_lib.skei_fbp_workspace_size(plan.handle, dtype, B, m))
+
+
+def _work(nbytes: int, device, work=None):
+    if work is not None:
+        if work.numel() * work.element_size() < nbytes:
+            raise ValueError("workspace too small")
+        return work
+    return torch.empty(max(nbytes, 16), dtype=torch.uint8, device=device)
+
+
+def fbp(plan: Plan, sino, idx=None, out=None, work=None) -> torch.Tensor:
+    """A_S^dagger sino = (pi/m) B_S H sino; [B, m, n_det] -> [B, N, N]."""
+    B = sino.shape[0]
+    ip, m = _idx(plan, idx)
+    _dev(sino, "sino", shape=(B, m, plan.n_det))
+    out = torch.empty((B, plan.N, plan.N), device=sino.device, dtype=sino.dtype) if out is None else out
+    _dev(out, "out", sino.dtype, (B, plan.N, plan.N))
+    code = _dtype_code(sino)
+    nb = fbp_workspace_size(plan, code, B, m)
+    w = _work(nb, sino.device, work)
+    _check(_lib.skei_fbp(plan.handle, code, _ptr(sino), B, ip, m, _ptr(out), _ptr(w), nb,
+                         _stream()), "skei_fbp")
+    return out
+
+
+def fbp_adj(plan: Plan, x, idx=None, out=None, work=None) -> torch.Tensor:
+    B = x.shape[0]
+    ip, m = _idx(plan, idx)
+    _dev(x, "x", shape=(B, plan.N, plan.N))
+    out = torch.empty((B, m, plan.n_det), device=x.device, dtype=x.dtype) if out is None else out
+    _dev(out, "out", x.dtype, (B, m, plan.n_det))
+    code = _dtype_code(x)
+    nb = fbp_workspace_size(plan, code, B, m)
+    w = _work(nb, x.device, work)
+    _check(_lib.skei_fbp_adj(plan.handle, code, _ptr(x), B, ip, m, _ptr(out), _ptr(w), nb,
+                             _stream()), "skei_fbp_adj")
+    return out
+
+
+def rotate(x, g_deg, out=None) -> torch.Tensor:
+    """T_g x for every (b, g): x [B, N, N], g_deg float64 [B, G] -> [B, G, N, N]."""
+    B, N = x.shape[0], x.shape[-1]
+    G = g_deg.shape[1]
+    _dev(x, "x", shape=(B, N, N))
+    _dev(g_deg, "g_deg", torch.float64, (B, G))
+    out = torch.empty((B, G, N, N), device=x.device, dtype=x.dtype) if out is None else out
+    _dev(out, "out", x.dtype, (B, G, N, N))
+    _check(_lib.skei_rotate(_dtype_code(x), _ptr(x), B, N, _ptr(g_deg), G, _ptr(out), _stream()),
+           "skei_rotate")
+    return out
+
+
+def rotate_adj(gout, g_deg, alpha=1.0, beta=0.0, out=None) -> torch.Tensor:
+    """alpha sum_g T_g^T gout[:, g] + beta out; [B, G, N, N] -> [B, N, N]."""
+    B, G, N = gout.shape[0], gout.shape[1], gout.shape[-1]
+    _dev(gout, "gout", shape=(B, G, N, N))
+    _dev(g_deg, "g_deg", torch.float64, (B, G))
+    if out is None:
+        if beta != 0.0:
+            raise ValueError("beta != 0 needs out")
+        out = torch.empty((B, N, N), device=gout.device, dtype=gout.dtype)
+    _dev(out, "out", gout.dtype, (B, N, N))
+    _check(_lib.skei_rotate_adj(_dtype_code(gout), _ptr(gout), B, N, _ptr(g_deg), G, float(alpha),
+                                float(beta), _ptr(out), _stream()), "skei_rotate_adj")
+    return out
+
+
+def ei_workspace_size(plan: Plan, dtype: int, B: int, G: int, mc_m: int, sk_m: int) -> int:
+    return int(_lib.skei_ei_workspace_size(plan.handle, dtype, B, G, mc_m, sk_m))
+
+
+def ei_loss_fwd(plan: Plan, x1, y, g_deg, mc_idx=None, sk_idx=None, work=None, out=None):
+    """Stage 1 of the (sketched) EI loss.  Returns (r, x2, z)."""
+    B, G = x1.shape[0], g_deg.shape[1]
+    mp, mc_m = _idx(plan, mc_idx)
+    sp, sk_m = _idx(plan, sk_idx)
+    N, nd = plan.N, plan.n_det
+    _dev(x1, "x1", shape=(B, N, N))
+    _dev(y, "y", x1.dtype, (B, plan.n_angles, nd))
+    _dev(g_deg, "g_deg", torch.float64, (B, G))
+    if out is None:
+        out = (torch.empty((B, mc_m, nd), device=x1.device, dtype=x1.dtype),
+               torch.empty((B, G, N, N), device=x1.device, dtype=x1.dtype),
+               torch.empty((B, G, N, N), device=x1.device, dtype=x1.dtype))
+    r, x2, z = out
+    _dev(r, "r", x1.dtype, (B, mc_m, nd))
+    _dev(x2, "x2", x1.dtype, (B, G, N, N))
+    _dev(z, "z", x1.dtype, (B, G, N, N))
+    code = _dtype_code(x1)
+    nb = ei_workspace_size(plan, code, B, G, mc_m, sk_m)
+    w = _work(nb, x1.device, work)
+    _check(_lib.skei_ei_loss_fwd(plan.handle, code, _ptr(x1), _ptr(y), B, mp, mc_m, sp, sk_m,
+                                 _ptr(g_deg), G, _ptr(r), _ptr(x2), _ptr(z), _ptr(w), nb,
+                                 _stream()), "skei_ei_loss_fwd")
+    return r, x2, z
+
+
+def ei_loss_finish(x2, x3, r, lam: float, mc_scale: float, want_grads=True, work=None,
+                   out=None):
+    """Returns (loss[1], mc[B], ei[B, G], g_x2, g_x3) with FP64 sums on the device."""
+    B, G, N = x2.shape[0], x2.shape[1], x2.shape[-1]
+    _dev(x2, "x2", shape=(B, G, N, N))
+    _dev(x3, "x3", x2.dtype, (B, G, N, N))
+    _dev(r, "r", x2.dtype)
+    r_len = r.numel() // B
+    dev = x2.device
+    if out is None:
+        out = (torch.empty(1, dtype=torch.float64, device=dev),
+               torch.empty(B, dtype=torch.float64, device=dev),
+               torch.empty((B, G), dtype=torch.float64, device=dev),
+               torch.empty_like(x2) if want_grads else None,
+               torch.empty_like(x2) if want_grads else None)
+    loss, mc, ei, g_x2, g_x3 = out
+    chunks = B * G * -(-N * N // 8192) + B * -(-r_len // 8192)
+    nb = ((chunks * 8) + 255) // 256 * 256
+    w = _work(nb, dev, work)
+    _check(_lib.skei_ei_loss_finish(_dtype_code(x2), _ptr(x2), _ptr(x3), _ptr(r), B, G, N, r_len,
+                                    float(lam), float(mc_scale), _ptr(mc), _ptr(ei), _ptr(loss),
+                                    _ptr(g_x2), _ptr(g_x3), _ptr(w), nb, _stream()),
+           "skei_ei_loss_finish")
+    return loss, mc, ei, g_x2, g_x3
+
+
+def ei_loss_bwd(plan: Plan, r, g_x2, g_z, g_deg, mc_coef: float, mc_idx=None, sk_idx=None,
+                work=None, out=None):
+    """g_x1 = -2 mc_coef A_mc^T r + sum_g T_g^T [g_x2 + (pi/m) A_S^T H B_S^T g_z]."""
+    B, G = g_deg.shape
+    mp, mc_m = _idx(plan, mc_idx)
+    sp, sk_m = _idx(plan, sk_idx)
+    N, nd = plan.N, plan.n_det
+    _dev(r, "r", shape=(B, mc_m, nd))
+    _dev(g_x2, "g_x2", r.dtype, (B, G, N, N))
+    _dev(g_z, "g_z", r.dtype, (B, G, N, N))
+    _dev(g_deg, "g_deg", torch.float64, (B, G))
+    out = torch.empty((B, N, N), device=r.device, dtype=r.dtype) if out is None else out
+    _dev(out, "out", r.dtype, (B, N, N))
+    code = _dtype_code(r)
+    nb = ei_workspace_size(plan, code, B, G, mc_m, sk_m)
+    w = _work(nb, r.device, work)
+    _check(_lib.skei_ei_loss_bwd(plan.handle, code, _ptr(r), _ptr(g_x2), _ptr(g_z), B, mp, mc_m,
+                                 sp, sk_m, _ptr(g_deg), G, float(mc_coef), _ptr(out), _ptr(w), nb,
+                                 _stream()), "skei_ei_loss_bwd")
+    return out
+
+
+def residual_add(u, theta, out=None) -> torch.Tensor:
+    """u + theta, theta (float32, n elements) broadcast over the leading dims of u."""
+    n = theta.numel()
+    if u.numel() % n:
+        raise ValueError("u.numel() must be a multiple of theta.numel()")
+    _dev(u, "u")
+    _dev(theta, "theta", torch.float32)
+    out = torch.empty_like(u) if out is None else out
+    _dev(out, "out", u.dtype, u.shape)
+    _check(_lib.skei_residual_add(_dtype_code(u), _ptr(u), _ptr(theta), u.numel() // n, n,
+                                  _ptr(out), _stream()), "skei_residual_add")
+    return out
+
+
+def adam_step(theta, m, v, step_dev, g1, g2=None, lr=5e-4, beta1=0.9, beta2=0.999, eps=1e-8):
+    """In-place Adam on theta/m/v (float32) with g = sum over leading dims of
+    g1 (and g2); step_dev is a CUDA int32 scalar tensor (>= 1)."""
+    n = theta.numel()
+    for t, nm in ((theta, "theta"), (m, "m"), (v, "v")):
+        _dev(t, nm, torch.float32)
+    _dev(step_dev, "step", torch.int32)
+    _dev(g1, "g1")
+    c1 = g1.numel() // n
+    c2 = 0 if g2 is None else g2.numel() // n
+    if g2 is not None:
+        _dev(g2, "g2", g1.dtype)
+    _check(_lib.skei_adam_step(_ptr(theta), n, _dtype_code(g1), _ptr(g1), c1, _ptr(g2), c2,
+                               _ptr(m), _ptr(v), _ptr(step_dev), lr, beta1, beta2, eps, _stream()),
+           "skei_adam_step")
