@@ -161,6 +161,33 @@ int skei_fbp_adj(skei_plan plan, int dtype, const void *x, int B,
                  const int *idx, int m, void *sino, void *work,
                  size_t work_bytes, void *stream);
 
+/* -------------------------------------------- FBP without allocation --
+ * No counterpart in the paper.  skei_fbp_noalloc computes what skei_fbp
+ * computes, but takes no workspace.  It is for callers that cannot call
+ * cudaMalloc and so cannot hand skei_fbp its workspace: code whose device
+ * memory is all owned by someone else's fixed pool, real-time loops that
+ * forbid allocation once they are running, or plugin hosts that give a
+ * plugin no allocator.
+ *
+ * Its scratch (the filtered sinogram, FP32) lives in one static device
+ * array inside the library: SKEI_FBP_NOALLOC_MAX_FLOATS floats (4 MiB),
+ * held by every GPU that loads the library until the process exits.
+ *   - B * m * n_det must not exceed SKEI_FBP_NOALLOC_MAX_FLOATS; a larger
+ *     call returns SKEI_EINVAL and launches nothing.
+ *   - The first call on a device looks the array's device address up once,
+ *     with that device current; make that first call before any stream
+ *     capture.
+ *   - Nothing is allocated: no cudaMalloc, cudaFree or allocating library
+ *     routine runs in this call.
+ *   - All calls share the one array and it keeps the last call's contents;
+ *     each call writes the part it uses before reading it, so nothing needs
+ *     clearing.  Calls that overlap on the GPU (other streams, other host
+ *     threads) race on the array: serialise them.
+ * Arguments, layouts and other errors are those of skei_fbp. */
+#define SKEI_FBP_NOALLOC_MAX_FLOATS 1048576
+int skei_fbp_noalloc(skei_plan plan, int dtype, const void *sino, int B,
+                     const int *idx, int m, void *x, void *stream);
+
 /* ------------------------------------------------------------ rotations --
  * skei_rotate: out[b][g] = T_{g_deg[b][g]} x[b] (Sec. 4.1.3: the transform
  * group of CT is rotations; Eq. (e:eiloss) applies T_i to F(A^dagger y)).

@@ -19,7 +19,7 @@ from . import build as _build
 __all__ = [
     "F32", "BF16", "Plan", "last_error", "version",
     "proj_fwd", "proj_adj", "filter", "backproject", "backproject_adj",
-    "fbp_workspace_size", "fbp", "fbp_adj", "rotate", "rotate_adj",
+    "fbp_workspace_size", "fbp", "fbp_adj", "fbp_noalloc", "rotate", "rotate_adj",
     "ei_workspace_size", "ei_loss_fwd", "ei_loss_finish", "ei_loss_bwd",
     "residual_add", "adam_step", "library_path",
 ]
@@ -51,6 +51,7 @@ _SIGS = {
     "skei_fbp_workspace_size": ([_PLAN, _i, _i, _i], _sz),
     "skei_fbp": ([_PLAN, _i, _vp, _i, _vp, _i, _vp, _vp, _sz, _vp], _i),
     "skei_fbp_adj": ([_PLAN, _i, _vp, _i, _vp, _i, _vp, _vp, _sz, _vp], _i),
+    "skei_fbp_noalloc": ([_PLAN, _i, _vp, _i, _vp, _i, _vp, _vp], _i),
     "skei_rotate": ([_i, _vp, _i, _i, _vp, _i, _vp, _vp], _i),
     "skei_rotate_adj": ([_i, _vp, _i, _i, _vp, _i, _f, _f, _vp, _vp], _i),
     "skei_ei_workspace_size": ([_PLAN, _i, _i, _i, _i, _i], _sz),
@@ -270,6 +271,25 @@ def fbp_adj(plan: Plan, x, idx=None, out=None, work=None) -> torch.Tensor:
     w = _work(nb, x.device, work)
     _check(_lib.skei_fbp_adj(plan.handle, code, _ptr(x), B, ip, m, _ptr(out), _ptr(w), nb,
                              _stream()), "skei_fbp_adj")
+    return out
+
+
+FBP_NOALLOC_MAX_FLOATS = 1048576
+
+
+def fbp_noalloc(plan: Plan, sino, idx=None, out=None) -> torch.Tensor:
+    """skei_fbp_noalloc: the FBP of `fbp` without a workspace, for callers
+    that cannot allocate device memory (its scratch is a static 4 MiB array
+    inside the library; B * m * n_det <= FBP_NOALLOC_MAX_FLOATS; calls that
+    overlap on the GPU race on that array).  `out` must be given by a caller
+    that allocates nothing."""
+    B = sino.shape[0]
+    ip, m = _idx(plan, idx)
+    _dev(sino, "sino", shape=(B, m, plan.n_det))
+    out = torch.empty((B, plan.N, plan.N), device=sino.device, dtype=sino.dtype) if out is None else out
+    _dev(out, "out", sino.dtype, (B, plan.N, plan.N))
+    _check(_lib.skei_fbp_noalloc(plan.handle, _dtype_code(sino), _ptr(sino), B, ip, m, _ptr(out),
+                                 _stream()), "skei_fbp_noalloc")
     return out
 
 
