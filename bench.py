@@ -140,7 +140,7 @@ class Arm:
         # dL/dtheta = dL/dx1 + sum_g dL/dx3 (F's Jacobian is the identity)
         S.adam_step(self.theta, self.m1, self.v1, self.step_no, self.gx1, self.gx3, lr=LR)
 
-    launches_per_step = 15  # 1 + 5 + 1 + 2 + 5 + 1 kernels, see step()
+    launches_per_step = 13  # 1 + 4 + 1 + 2 + 4 + 1 kernels, see step()
 
     def reset(self):
         self.theta.zero_()
@@ -209,49 +209,64 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_breakdown(S, arm, reps=20):
-    """Average device time of each kernel of one step, launched one by one
-    on the stream with CUDA events around each (same arguments as the fused
-    calls issue internally)."""
+def kernel_breakdown(S, arm, stream, reps=20):
+    """Device time of every kernel launch of one step, each re-issued with
+    the step's own arguments: `reps` copies are captured in a CUDA graph and
+    the replay is timed with CUDA events on the launching stream."""
     import torch
     p = arm.plan
     mc_idx = arm.idx if arm.sketched else None
     sk_idx = arm.idx if arm.sketched else None
     BG, m = BATCH * G_ROT, arm.m
-    pbuf = torch.empty((BG, m, p.n_det), dtype=torch.float32, device="cuda")
+    f32 = dict(dtype=torch.float32, device="cuda")
+    pbuf = torch.empty((BG, m, p.n_det), **f32)
     qbuf = torch.empty_like(pbuf)
-    gtot = torch.empty((BG, N_IMG, N_IMG), dtype=torch.float32, device="cuda")
-    x2f = arm.x2.float().reshape(BG, N_IMG, N_IMG) if arm.tdt != torch.float32 else \
-        arm.x2.reshape(BG, N_IMG, N_IMG)
-    gzf = arm.gx3.float().reshape(BG, N_IMG, N_IMG) if arm.tdt != torch.float32 else \
-        arm.gx3.reshape(BG, N_IMG, N_IMG)
+    gtot = torch.empty((BATCH, G_ROT, N_IMG, N_IMG), **f32)
+    x2 = arm.x2.reshape(BG, N_IMG, N_IMG)
+    gx3 = arm.gx3.reshape(BG, N_IMG, N_IMG)
+    gx2 = arm.gx2.reshape(BG, N_IMG, N_IMG)
+    z = arm.z.reshape(BG, N_IMG, N_IMG)
     ops = {
-        "joseph_fwd(MC, x1)": lambda: S.proj_fwd(p, arm.x1, mc_idx, y=arm.y, out=arm.r),
+        "residual_add(x1)": lambda: S.residual_add(arm.x0, arm.theta, out=arm.x1),
         "rotate": lambda: S.rotate(arm.x1, arm.g, out=arm.x2),
-        "joseph_fwd(EI, x2)": lambda: S.proj_fwd(p, x2f, sk_idx, out=pbuf),
-        "ramlak(EI fwd)": lambda: S.filter(p, pbuf, np.pi / m, out=qbuf),
-        "backproject(EI)": lambda: S.backproject(p, qbuf, sk_idx, out=gtot),
-        "backproject_adj(EI)": lambda: S.backproject_adj(p, gzf, sk_idx, out=pbuf),
-        "ramlak(EI bwd)": lambda: S.filter(p, pbuf, np.pi / m, out=qbuf),
-        "joseph_adj(EI)": lambda: S.proj_adj(p, qbuf, sk_idx, out=gtot),
-        "joseph_adj(MC)": lambda: S.proj_adj(p, arm.r, mc_idx, out=arm.gx1),
-        "rotate_adj": lambda: S.rotate_adj(gtot.reshape(BATCH, G_ROT, N_IMG, N_IMG).to(arm.tdt)
-                                           if arm.tdt != torch.float32 else
-                                           gtot.reshape(BATCH, G_ROT, N_IMG, N_IMG), arm.g,
-                                           beta=1.0, out=arm.gx1),
+        "joseph_fwd(MC+EI)": lambda: S.proj_fwd_multi(
+            p, [S.Job(arm.x1, arm.r, mc_idx, aux=arm.y), S.Job(x2, pbuf, sk_idx)]),
+        "ramlak(fwd)": lambda: S.filter(p, pbuf, np.pi / m, out=qbuf),
+        "backproject": lambda: S.backproject(p, qbuf.to(arm.tdt) if arm.tdt != torch.float32
+                                             else qbuf, sk_idx, out=z),
+        "residual_add(x3)": lambda: S.residual_add(arm.z, arm.theta, out=arm.x3),
+        "loss_finish(2 kernels)": lambda: S.ei_loss_finish(
+            arm.x2, arm.x3, arm.r, LAM, arm.mc_scale, work=arm.work,
+            out=(arm.loss, arm.mc, arm.ei, arm.gx2, arm.gx3)),
+        "backproject_adj": lambda: S.backproject_adj(p, gx3, sk_idx, out=pbuf),
+        "ramlak(bwd)": lambda: S.filter(p, pbuf, np.pi / m, out=qbuf),
+        "joseph_adj(MC+EI)": lambda: S.proj_adj_multi(
+            p, [S.Job(arm.r, arm.gx1, mc_idx, alpha=-2.0 * arm.mc_scale / BATCH),
+                S.Job(qbuf, gtot.reshape(BG, N_IMG, N_IMG), sk_idx, aux=gx2, beta=1.0)]),
+        "rotate_adj": lambda: S.rotate_adj(gtot if arm.tdt == torch.float32 else gtot.to(arm.tdt),
+                                           arm.g, beta=1.0, out=arm.gx1),
+        "adam": lambda: S.adam_step(arm.theta, arm.m1, arm.v1, arm.step_no, arm.gx1, arm.gx3,
+                                    lr=LR),
     }
     times = {}
-    for name, fn in ops.items():
-        for _ in range(3):
-            fn()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(reps)]
-        for a, b in evs:
-            a.record()
-            fn()
-            b.record()
-        torch.cuda.synchronize()
-        times[name] = 1e3 * sum(a.elapsed_time(b) for a, b in evs) / reps  # microseconds
+    with torch.cuda.stream(stream):
+        for name, fn in ops.items():
+            for _ in range(2):
+                fn()
+            stream.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=stream):
+                for _ in range(reps):
+                    fn()
+            graph.replay()
+            stream.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            graph.replay()
+            e1.record(stream)
+            stream.synchronize()
+            times[name] = 1e3 * e0.elapsed_time(e1) / reps  # microseconds per launch
     return times
 
 
@@ -445,8 +460,7 @@ def main():
     d2h = 8
 
     # per-kernel device times and the roofline of the dominant kernel
-    with torch.cuda.stream(stream):
-        bd = kernel_breakdown(S, sk)
+    bd = kernel_breakdown(S, sk, stream)
     dom = max(bd, key=bd.get)
     peaks = {}
     try:
@@ -458,8 +472,9 @@ def main():
     fp32_peak_tflops = sm_count * 128 * 2 * max_mhz * 1e6 / 1e12
     idx_now = sk.idx.cpu().numpy()
     if dom.startswith("joseph"):
-        n_img = BATCH * (G_ROT if "EI" in dom else 1)
-        work = joseph_samples(plan, n_img, idx_now) * 7.0  # FP32 flops per sample
+        # the fused launch projects x1 (MC angles) and the G rotated copies
+        work = 7.0 * (joseph_samples(plan, BATCH, idx_now)
+                      + joseph_samples(plan, BATCH * G_ROT, idx_now))
     else:
         work = None
     roof = None

@@ -128,6 +128,32 @@ int skei_proj_adj(skei_plan plan, int dtype, const void *sino, int B,
                   const int *idx, int m, float alpha, float beta, void *x,
                   void *stream);
 
+/* Batched forms: up to SKEI_MAX_JOBS image sets, each with its own
+ * buffers, storage types and angle subset, in ONE kernel launch (e.g. the
+ * MC-term projection of x1 and the EI-term projection of x2 of a SkEI step).
+ * For skei_proj_fwd_multi a job computes out = A_S in, or aux_S - A_S in
+ * when aux != NULL (aux = full measurement [B][n_angles][n_det]); alpha and
+ * beta are ignored.  For skei_proj_adj_multi a job computes
+ * out = alpha A_S^T in + beta aux (aux may alias out; read only if beta != 0).
+ * Layouts as for skei_proj_fwd / skei_proj_adj.  The sum of the jobs' B
+ * must not exceed 65535. */
+#define SKEI_MAX_JOBS 2
+typedef struct {
+  int dtype_in, dtype_aux, dtype_out;   /* SKEI_F32 or SKEI_BF16 per buffer */
+  const void *in;
+  const void *aux;
+  void *out;
+  const int *idx;                       /* DEVICE angle list or NULL (all) */
+  int m;                                /* angles in idx */
+  int B;                                /* images */
+  float alpha, beta;
+} skei_job;
+
+int skei_proj_fwd_multi(skei_plan plan, const skei_job *jobs, int njobs,
+                        void *stream);
+int skei_proj_adj_multi(skei_plan plan, const skei_job *jobs, int njobs,
+                        void *stream);
+
 /* ---------------------------------------------------- H, B, B^T, FBP --
  * skei_filter: q = scale * H p for `rows` rows of n_det bins (dtype).
  * H is the Ram-Lak ramp of filtered back-projection (Sec. 2.1, 4.1.1); it is
@@ -228,6 +254,10 @@ int skei_ei_loss_fwd(skei_plan plan, int dtype, const void *x1, const void *y,
                      int B, const int *mc_idx, int mc_m, const int *sk_idx,
                      int sk_m, const double *g_deg, int G, void *r, void *x2,
                      void *z, void *work, size_t work_bytes, void *stream);
+
+/* Workspace (bytes) of skei_ei_loss_finish; skei_ei_workspace_size(...)
+ * with the same B, G and sizes is never smaller. */
+size_t skei_ei_finish_workspace_size(int B, int G, int N, int r_len);
 
 int skei_ei_loss_finish(int dtype, const void *x2, const void *x3,
                         const void *r, int B, int G, int N, int r_len,

@@ -12,7 +12,7 @@ namespace skei {
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
-constexpr int kChunk = 8192;     // elements per partial sum of the loss
+constexpr int kChunk = 2048;     // elements per partial sum of the loss
 constexpr int kRedThreads = 256;
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -33,7 +33,23 @@ __global__ void __launch_bounds__(kRedThreads)
     const int seg = blk / cpi, ch = blk - seg * cpi;
     const int64_t base = (int64_t)seg * n_img;
     const int64_t e0 = (int64_t)ch * kChunk, e1 = min(e0 + kChunk, n_img);
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += kRedThreads) {
+    int64_t e = e0 + threadIdx.x;
+    if (!is_bf16<T>() && n_img % 4 == 0) {
+      // four elements per access; chunks start on multiples of kChunk
+      const float4 *a4 = reinterpret_cast<const float4 *>(x2 + base);
+      const float4 *b4 = reinterpret_cast<const float4 *>(x3 + base);
+      float4 *g2 = reinterpret_cast<float4 *>(g_x2 + base);
+      float4 *g3 = reinterpret_cast<float4 *>(g_x3 + base);
+      for (int64_t e4 = e0 / 4 + threadIdx.x; e4 < e1 / 4; e4 += kRedThreads) {
+        const float4 a = __ldg(a4 + e4), c = __ldg(b4 + e4);
+        const float4 d = make_float4(a.x - c.x, a.y - c.y, a.z - c.z, a.w - c.w);
+        s += (double)d.x * d.x + (double)d.y * d.y + (double)d.z * d.z + (double)d.w * d.w;
+        if (g_x2) g2[e4] = make_float4(kappa * d.x, kappa * d.y, kappa * d.z, kappa * d.w);
+        if (g_x3) g3[e4] = make_float4(-kappa * d.x, -kappa * d.y, -kappa * d.z, -kappa * d.w);
+      }
+      e = e1;
+    }
+    for (; e < e1; e += kRedThreads) {
       const float d = ldg_f(x2 + base + e) - ldg_f(x3 + base + e);
       s += (double)d * (double)d;
       if (g_x2) st_f(g_x2 + base + e, kappa * d);
@@ -97,26 +113,30 @@ __global__ void __launch_bounds__(kRedThreads)
 
 // --------------------------------------------------- stand-in network --
 template <typename T>
-__global__ void residual_add_kernel(const T *u, const float *theta, int count, int64_t n,
-                                    T *out) {
-  const int64_t total = (int64_t)count * n;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x)
-    st_f(out + e, ldg_f(u + e) + __ldg(theta + e % n));
+__global__ void residual_add_kernel(const T *u, const float *theta, int n, T *out) {
+  // blockIdx.y selects the image, so no division or modulo per element
+  const size_t base = (size_t)blockIdx.y * n;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
+    st_f(out + base + e, ldg_f(u + base + e) + __ldg(theta + e));
 }
 
+// FP32, n % 4 == 0: four elements per thread and access.
+__global__ void residual_add4_kernel(const float4 *u, const float4 *theta, int n4, float4 *out) {
+  const size_t base = (size_t)blockIdx.y * n4;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n4; e += gridDim.x * blockDim.x) {
+    const float4 a = __ldg(u + base + e), t = __ldg(theta + e);
+    out[base + e] = make_float4(a.x + t.x, a.y + t.y, a.z + t.z, a.w + t.w);
+  }
+}
+
+// Bias corrections 1 - beta^t evaluated as -expm1(t ln beta) with ln beta
+// from FP64 on the host: no cancellation, so FP32 keeps them to ~1e-7.
 template <typename T>
 __global__ void adam_kernel(float *theta, int64_t n, const T *g1, int c1, const T *g2, int c2,
                             float *m, float *v, const int *step, float lr, float b1, float b2,
-                            float eps) {
-  __shared__ float bc[2];
-  if (threadIdx.x == 0) {
-    const int t = max(*step, 1);
-    bc[0] = (float)(1.0 - pow((double)b1, (double)t));
-    bc[1] = (float)(1.0 - pow((double)b2, (double)t));
-  }
-  __syncthreads();
-  const float bc1 = bc[0], bc2 = bc[1];
+                            float eps, float lnb1, float lnb2) {
+  const float t = (float)max(__ldg(step), 1);
+  const float bc1 = -expm1f(t * lnb1), bc2 = -expm1f(t * lnb2);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     float g = 0.0f;
@@ -127,6 +147,37 @@ __global__ void adam_kernel(float *theta, int64_t n, const T *g1, int c1, const 
     m[i] = mi;
     v[i] = vi;
     theta[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+  }
+}
+
+// FP32 gradients, n % 4 == 0: four elements per thread and access.
+__global__ void adam4_kernel(float4 *theta, int n4, const float4 *g1, int c1, const float4 *g2,
+                             int c2, float4 *m, float4 *v, const int *step, float lr, float b1,
+                             float b2, float eps, float lnb1, float lnb2) {
+  const float t = (float)max(__ldg(step), 1);
+  const float bc1 = -expm1f(t * lnb1), bc2 = -expm1f(t * lnb2);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += gridDim.x * blockDim.x) {
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int c = 0; c < c1; ++c) {
+      const float4 a = __ldg(g1 + (size_t)c * n4 + i);
+      g.x += a.x; g.y += a.y; g.z += a.z; g.w += a.w;
+    }
+    for (int c = 0; c < c2; ++c) {
+      const float4 a = __ldg(g2 + (size_t)c * n4 + i);
+      g.x += a.x; g.y += a.y; g.z += a.z; g.w += a.w;
+    }
+    float4 mi = m[i], vi = v[i], th = theta[i];
+    float *pm = &mi.x, *pv = &vi.x, *pt = &th.x;
+    const float *pg = &g.x;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      pm[q] = fmaf(b1, pm[q], (1.0f - b1) * pg[q]);
+      pv[q] = fmaf(b2, pv[q], (1.0f - b2) * pg[q] * pg[q]);
+      pt[q] -= lr * (pm[q] / bc1) / (sqrtf(pv[q] / bc2) + eps);
+    }
+    m[i] = mi;
+    v[i] = vi;
+    theta[i] = th;
   }
 }
 
@@ -178,10 +229,15 @@ int ei_fwd_impl(skei_plan p, const T *x1, const T *y, int B, const int *mc_idx, 
   float *pbuf = reinterpret_cast<float *>(work);
   float *qbuf = reinterpret_cast<float *>(work + w.p_bytes);
   const int BG = B * G;
+  const int tb = is_bf16<T>();
   int rc;
-  if ((rc = launch_proj_fwd<T, T>(p, x1, B, mc_idx, mc_m, y, r, st))) return rc;
   if ((rc = launch_rotate<T, T>(x1, B, p->N, g_deg, G, x2, st))) return rc;
-  if ((rc = launch_proj_fwd<T, float>(p, x2, BG, sk_idx, sk_m, nullptr, pbuf, st))) return rc;
+  // one launch: r = S_mc y - A_mc x1 (MC term) and p = A_S x2 (EI term)
+  Jobs J{};
+  J.njobs = 2;
+  J.j[0] = Job{x1, y, r, mc_idx, mc_m, B, 1.0f, 0.0f, tb, tb, tb};
+  J.j[1] = Job{x2, nullptr, pbuf, sk_idx, sk_m, BG, 1.0f, 0.0f, tb, 0, 0};
+  if ((rc = launch_band_jobs(p, OP_JOSEPH, J, st))) return rc;
   if ((rc = launch_filter<float, float>(p, pbuf, BG * sk_m, (float)(kPi / sk_m), qbuf, st)))
     return rc;
   return launch_backproject<float, T, T>(p, qbuf, BG, sk_idx, sk_m, 1.0f, 0.0f, nullptr, z, st);
@@ -196,22 +252,27 @@ int ei_bwd_impl(skei_plan p, const T *r, const T *g_x2, const T *g_z, int B, con
   float *vbuf = reinterpret_cast<float *>(work + w.p_bytes);
   float *gtot = reinterpret_cast<float *>(work + 2 * w.p_bytes);
   const int BG = B * G;
+  const int tb = is_bf16<T>();
+  const float amc = (float)(-2.0 * mc_coef);
   int rc;
-  // MC term: g_x1 = -2 mc_coef A_mc^T r
-  if ((rc = launch_proj_adj<T, T, T>(p, r, B, mc_idx, mc_m, (float)(-2.0 * mc_coef), 0.0f,
-                                     nullptr, g_x1, st)))
-    return rc;
   if (g_z) {
     // through z = (pi/m) B_S H A_S x2:  g_x2 + (pi/m) A_S^T H B_S^T g_z
     if ((rc = launch_backproject_adj<T, float>(p, g_z, BG, sk_idx, sk_m, 1.0f, ubuf, st)))
       return rc;
     if ((rc = launch_filter<float, float>(p, ubuf, BG * sk_m, (float)(kPi / sk_m), vbuf, st)))
       return rc;
-    if ((rc = launch_proj_adj<float, T, float>(p, vbuf, BG, sk_idx, sk_m, 1.0f,
-                                               g_x2 ? 1.0f : 0.0f, g_x2, gtot, st)))
-      return rc;
+    // one launch: g_x1 = -2 mc_coef A_mc^T r (MC term) and
+    // gtot = g_x2 + A_S^T v (EI term)
+    Jobs J{};
+    J.njobs = 2;
+    J.j[0] = Job{r, nullptr, g_x1, mc_idx, mc_m, B, amc, 0.0f, tb, tb, tb};
+    J.j[1] = Job{vbuf, g_x2, gtot, sk_idx, sk_m, BG, 1.0f, g_x2 ? 1.0f : 0.0f, 0, tb, 0};
+    if ((rc = launch_tile_jobs(p, OP_JOSEPH_ADJ, J, st))) return rc;
     return launch_rotate_adj<float, T>(gtot, B, p->N, g_deg, G, 1.0f, 1.0f, g_x1, st);
   }
+  // MC term: g_x1 = -2 mc_coef A_mc^T r
+  if ((rc = launch_proj_adj<T, T, T>(p, r, B, mc_idx, mc_m, amc, 0.0f, nullptr, g_x1, st)))
+    return rc;
   if (g_x2) return launch_rotate_adj<T, T>(g_x2, B, p->N, g_deg, G, 1.0f, 1.0f, g_x1, st);
   return SKEI_OK;
 }
@@ -259,6 +320,33 @@ int check_work(void *work, size_t have, size_t need) {
   return SKEI_OK;
 }
 
+int to_jobs(skei_plan plan, const skei_job *jobs, int njobs, bool fwd, Jobs *J) {
+  if (!jobs || njobs < 1 || njobs > SKEI_MAX_JOBS)
+    return set_error(SKEI_EINVAL, "njobs=%d outside [1, %d]", njobs, SKEI_MAX_JOBS);
+  int total = 0;
+  J->njobs = njobs;
+  for (int q = 0; q < njobs; ++q) {
+    const skei_job &s = jobs[q];
+    SKEI_TRY(check_dtype(s.dtype_in));
+    SKEI_TRY(check_dtype(s.dtype_out));
+    SKEI_TRY(check_batch(s.B));
+    SKEI_TRY(check_dev_ptr(s.in, "job.in"));
+    SKEI_TRY(check_dev_ptr(s.out, "job.out"));
+    SKEI_TRY(check_idx(plan, s.idx, s.m));
+    const bool use_aux = fwd ? s.aux != nullptr : (s.aux != nullptr && s.beta != 0.0f);
+    if (use_aux) {
+      SKEI_TRY(check_dtype(s.dtype_aux));
+      SKEI_TRY(check_dev_ptr(s.aux, "job.aux"));
+    }
+    total += s.B;
+    J->j[q] = Job{s.in, use_aux ? s.aux : nullptr, s.out, s.idx, s.m, s.B,
+                  fwd ? 1.0f : s.alpha, fwd ? 0.0f : (use_aux ? s.beta : 0.0f),
+                  s.dtype_in == SKEI_BF16, s.dtype_aux == SKEI_BF16, s.dtype_out == SKEI_BF16};
+  }
+  if (total > 65535) return set_error(SKEI_EINVAL, "jobs hold %d images (max 65535)", total);
+  return SKEI_OK;
+}
+
 int check_rot(int dtype, int B, int N, const double *g_deg, int G) {
   SKEI_TRY(check_dtype(dtype));
   SKEI_TRY(check_batch(B));
@@ -287,6 +375,20 @@ int skei_proj_fwd(skei_plan plan, int dtype, const void *x, int B, const int *id
                                          (float *)out, as_stream(stream));
   return launch_proj_fwd<bf16, bf16>(plan, (const bf16 *)x, B, idx, m, (const bf16 *)y,
                                      (bf16 *)out, as_stream(stream));
+}
+
+int skei_proj_fwd_multi(skei_plan plan, const skei_job *jobs, int njobs, void *stream) {
+  SKEI_TRY(check_plan(plan));
+  Jobs J{};
+  SKEI_TRY(to_jobs(plan, jobs, njobs, true, &J));
+  return launch_band_jobs(plan, OP_JOSEPH, J, as_stream(stream));
+}
+
+int skei_proj_adj_multi(skei_plan plan, const skei_job *jobs, int njobs, void *stream) {
+  SKEI_TRY(check_plan(plan));
+  Jobs J{};
+  SKEI_TRY(to_jobs(plan, jobs, njobs, false, &J));
+  return launch_tile_jobs(plan, OP_JOSEPH_ADJ, J, as_stream(stream));
 }
 
 int skei_proj_adj(skei_plan plan, int dtype, const void *sino, int B, const int *idx, int m,
@@ -428,6 +530,12 @@ int skei_ei_loss_fwd(skei_plan plan, int dtype, const void *x1, const void *y, i
                            as_stream(stream));
 }
 
+size_t skei_ei_finish_workspace_size(int B, int G, int N, int r_len) {
+  if (B < 1 || G < 1 || N < 1 || r_len < 1) return 0;
+  return align256(((size_t)B * G * ceil_div((size_t)N * N, kChunk) +
+                   (size_t)B * ceil_div((size_t)r_len, kChunk)) * sizeof(double));
+}
+
 int skei_ei_loss_finish(int dtype, const void *x2, const void *x3, const void *r, int B, int G,
                         int N, int r_len, double lambda, double mc_scale, double *mc_out,
                         double *ei_out, double *loss_out, void *g_x2, void *g_x3, void *work,
@@ -445,9 +553,7 @@ int skei_ei_loss_finish(int dtype, const void *x2, const void *x3, const void *r
   if (mc_out && (reinterpret_cast<uintptr_t>(mc_out) % 8)) return set_error(SKEI_EINVAL, "mc_out misaligned");
   if (ei_out && (reinterpret_cast<uintptr_t>(ei_out) % 8)) return set_error(SKEI_EINVAL, "ei_out misaligned");
   if (loss_out && (reinterpret_cast<uintptr_t>(loss_out) % 8)) return set_error(SKEI_EINVAL, "loss_out misaligned");
-  const size_t need = align256(((size_t)B * G * ceil_div((size_t)N * N, kChunk) +
-                                (size_t)B * ceil_div((size_t)r_len, kChunk)) * sizeof(double));
-  SKEI_TRY(check_work(work, work_bytes, need));
+  SKEI_TRY(check_work(work, work_bytes, skei_ei_finish_workspace_size(B, G, N, r_len)));
   if (dtype == SKEI_F32)
     return ei_finish_impl<float>((const float *)x2, (const float *)x3, (const float *)r, B, G, N,
                                  r_len, lambda, mc_scale, mc_out, ei_out, loss_out, (float *)g_x2,
@@ -486,13 +592,19 @@ int skei_residual_add(int dtype, const void *u, const float *theta, int count, i
   SKEI_TRY(check_dev_ptr(u, "u"));
   SKEI_TRY(check_dev_ptr(theta, "theta"));
   SKEI_TRY(check_dev_ptr(out, "out"));
-  const int grid = grid_for((int64_t)count * n, 256);
-  if (dtype == SKEI_F32)
-    residual_add_kernel<float><<<grid, 256, 0, as_stream(stream)>>>((const float *)u, theta, count,
-                                                                    n, (float *)out);
+  if (n > (int64_t)1 << 30 || count > 65535)
+    return set_error(SKEI_EINVAL, "residual add: n=%lld or count=%d too large", (long long)n, count);
+  const dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 1024), (unsigned)count);
+  if (dtype == SKEI_F32 && n % 4 == 0) {
+    const dim3 grid4((unsigned)std::min<int64_t>((n / 4 + 255) / 256, 1024), (unsigned)count);
+    residual_add4_kernel<<<grid4, 256, 0, as_stream(stream)>>>(
+        (const float4 *)u, (const float4 *)theta, (int)(n / 4), (float4 *)out);
+  } else if (dtype == SKEI_F32)
+    residual_add_kernel<float><<<grid, 256, 0, as_stream(stream)>>>((const float *)u, theta,
+                                                                    (int)n, (float *)out);
   else
-    residual_add_kernel<bf16><<<grid, 256, 0, as_stream(stream)>>>((const bf16 *)u, theta, count,
-                                                                   n, (bf16 *)out);
+    residual_add_kernel<bf16><<<grid, 256, 0, as_stream(stream)>>>((const bf16 *)u, theta,
+                                                                   (int)n, (bf16 *)out);
   return check_launch("residual add launch");
 }
 
@@ -507,17 +619,27 @@ int skei_adam_step(float *theta, int64_t n, int dtype, const void *g1, int c1, c
   SKEI_TRY(check_dev_ptr(m, "m"));
   SKEI_TRY(check_dev_ptr(v, "v"));
   if (!step || reinterpret_cast<uintptr_t>(step) % 4) return set_error(SKEI_EINVAL, "step is NULL or misaligned");
+  if (!(beta1 > 0.0 && beta1 < 1.0 && beta2 > 0.0 && beta2 < 1.0))
+    return set_error(SKEI_EINVAL, "Adam betas must lie in (0, 1)");
   const int grid = grid_for(n, 256);
-  if (dtype == SKEI_F32)
+  const float lnb1 = (float)std::log(beta1), lnb2 = (float)std::log(beta2);
+  const bool vec = dtype == SKEI_F32 && n % 4 == 0 && n / 4 < (int64_t)1 << 30 &&
+                   ((reinterpret_cast<uintptr_t>(g2) & 15) == 0);
+  if (vec)
+    adam4_kernel<<<grid_for(n / 4, 256), 256, 0, as_stream(stream)>>>(
+        (float4 *)theta, (int)(n / 4), (const float4 *)g1, c1, (const float4 *)g2, c2,
+        (float4 *)m, (float4 *)v, step, (float)lr, (float)beta1, (float)beta2, (float)eps, lnb1,
+        lnb2);
+  else if (dtype == SKEI_F32)
     adam_kernel<float><<<grid, 256, 0, as_stream(stream)>>>(theta, n, (const float *)g1, c1,
                                                             (const float *)g2, c2, m, v, step,
                                                             (float)lr, (float)beta1, (float)beta2,
-                                                            (float)eps);
+                                                            (float)eps, lnb1, lnb2);
   else
     adam_kernel<bf16><<<grid, 256, 0, as_stream(stream)>>>(theta, n, (const bf16 *)g1, c1,
                                                            (const bf16 *)g2, c2, m, v, step,
                                                            (float)lr, (float)beta1, (float)beta2,
-                                                           (float)eps);
+                                                           (float)eps, lnb1, lnb2);
   return check_launch("adam launch");
 }
 

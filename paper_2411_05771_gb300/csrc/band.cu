@@ -1,17 +1,24 @@
-// Ray-driven operators over image bands: Joseph's forward projector A
-// (Sec. 4.1.1: the discrete Radon transform; Eq. (e:skeiloss): A_S = S A)
+// Operators that sum over image "lines" (rows when |cos| >= |sin|, columns
+// otherwise) for every detector bin: Joseph's forward projector A
+// (Sec. 4.1.1, the discrete Radon transform; Eq. (e:skeiloss): A_S = S A)
 // and the transpose B_S^T of pixel-driven back-projection (needed to
 // differentiate through A_S^dagger = (pi/m) B_S H, Algorithm 2's update).
 //
-// Both sum, for every detector bin (a, k), contributions from every image
-// "line" (a row when |cos| >= |sin|, a column otherwise).  A cluster of 8
-// CTAs covers one image and a block of AB angles; CTA r stages lines
-// [r R, (r+1) R) (R = ceil(N/8)) in shared memory - rows as they are,
-// columns transposed - sub-band by sub-band, accumulates per-bin partial
-// sums in its own shared memory, and after a cluster barrier reduces 1/8 of
-// the bins over the 8 CTAs' partials through distributed shared memory.  The
-// reduction order is fixed, so results are deterministic; there are no
-// atomics and no global scratch.
+// A cluster of 8 CTAs covers one image and a block of AB angles; CTA r
+// stages lines [r R, (r+1) R) (R = ceil(N/8)) in shared memory - rows as
+// they are, columns transposed - sub-band by sub-band, and accumulates
+// per-bin partial sums in its own shared memory.  After a cluster barrier
+// each CTA reduces 1/8 of the bins over the 8 CTAs' partials through
+// distributed shared memory, in a fixed order: deterministic, no atomics, no
+// global scratch.
+//
+//   A:    one thread per ray gathers the linear interpolation on each line.
+//   B^T:  one thread per bin gathers, on each line, the (at most 3) pixels
+//         whose bin coordinate lies within one bin of it, with exactly the
+//         back-projector's weights.
+//
+// Up to two jobs share a launch (grid.z spans the images of both), e.g. the
+// MC projection of x1 and the EI projection of x2 of one SkEI step.
 #include <cooperative_groups.h>
 
 #include <cmath>
@@ -24,61 +31,110 @@ namespace skei {
 namespace {
 
 constexpr int kBands = 8;    // cluster size = number of line bands
-constexpr int kPad = 2;      // zero columns on each side of a staged line
+constexpr int kPad = 4;      // zero columns on each side of a staged line
 constexpr int kMaxAB = 8;    // angles per cluster
 constexpr int kThreads = 256;
-
-enum { OP_JOSEPH = 0, OP_BP_ADJ = 1 };
+constexpr int kWarps = kThreads / 32;
 
 struct BandGeom {
   int N, n_det, n_angles;
-  int R;   // lines per band
-  int SB;  // lines per staged sub-band
-  int P;   // pitch of a staged line (odd, >= N + 2 kPad)
-  int AB;  // angles per cluster
+  int R;       // lines per band
+  int SB;      // lines per staged sub-band
+  int Prow;    // pitch of staged rows (multiple of 4: 16-byte aligned rows)
+  int Pcol;    // pitch of staged columns (= 2 mod 8: conflict-free transposed writes)
+  int AB;      // angles per cluster
+  int C;       // OP_BP_ADJ: warps (partial rows) per angle = kWarps / AB
+  int fast;    // N % 8 == 0: vectorised staging
 };
 
-template <typename Tin, typename Tout>
 struct BandArgs {
-  const Tin *x;        // [B][N][N]
-  const Tout *y;       // OP_JOSEPH residual source [B][n_angles][n_det] or null
-  Tout *out;           // [B][m][n_det]
-  const int *idx;      // [m] or null
-  int m;
+  Jobs jobs;
   const AngleConst *ang;
   int *status;
-  float alpha;         // OP_BP_ADJ output scale
   BandGeom g;
 };
 
+// 4 consecutive image values at element offset i as floats (16-byte aligned
+// for float, 8-byte for bfloat16).
+__device__ __forceinline__ float4 load4(const void *x, size_t i, int bf16) {
+  if (bf16) {
+    const uint2 u = __ldg(reinterpret_cast<const uint2 *>(static_cast<const __nv_bfloat16 *>(x) + i));
+    return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                       __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+  }
+  return __ldg(reinterpret_cast<const float4 *>(static_cast<const float *>(x) + i));
+}
+
+// Stages lines [s0, s0 + nl) of image xb (element offset xo in x) into buf
+// (pitch P): mode 1 copies rows, mode 0 copies columns transposed.  kPad
+// zero columns on each side.
+__device__ __forceinline__ void stage(const void *x, size_t xo, int bf16, int N, int mode,
+                                      int s0, int nl, float *buf, int P, bool fast) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (mode == 1) {
+    if (fast) {
+      for (int r = warp; r < nl; r += kWarps) {
+        const size_t src = xo + (size_t)(s0 + r) * N;
+        float *dst = buf + r * P + kPad;
+        for (int c = 4 * lane; c < N; c += 128)
+          *reinterpret_cast<float4 *>(dst + c) = load4(x, src + c, bf16);
+      }
+    } else {
+      for (int r = warp; r < nl; r += kWarps) {
+        const size_t src = xo + (size_t)(s0 + r) * N;
+        float *dst = buf + r * P + kPad;
+        for (int c = lane; c < N; c += 32) dst[c] = ld_any(x, src + c, bf16);
+      }
+    }
+  } else {
+    if (fast && nl == 16 && (s0 & 3) == 0) {
+      // lane = 4 * (position within a group of 8) + quarter of the 16 lines;
+      // 4 consecutive lines of a column start 16-byte aligned (N % 8 == 0)
+      const int q = lane & 3;
+      for (int p = warp * 8 + (lane >> 2); p < N; p += kWarps * 8) {
+        const float4 v = load4(x, xo + (size_t)p * N + s0 + 4 * q, bf16);
+        float *dst = buf + (4 * q) * P + kPad + p;
+        dst[0] = v.x;
+        dst[P] = v.y;
+        dst[2 * P] = v.z;
+        dst[3 * P] = v.w;
+      }
+    } else {
+      for (int p = warp; p < N; p += kWarps)
+        for (int l = lane; l < nl; l += 32)
+          buf[l * P + kPad + p] = ld_any(x, xo + (size_t)p * N + s0 + l, bf16);
+    }
+  }
+  const int npad = P - N;
+  for (int r = warp; r < nl; r += kWarps)
+    for (int c = lane; c < npad; c += 32) buf[r * P + (c < kPad ? c : N + c)] = 0.0f;
+}
+
 // Line range [lo, hi) within [s0, s1) on which lam0 + L * lam1 lies in
-// (lo_bound, hi_bound).
-__device__ __forceinline__ void line_range(float lam0, float lam1, float lo_bound,
-                                           float hi_bound, int s0, int s1, int *lo,
-                                           int *hi) {
+// (lo_bound, hi_bound); inv1 = 1 / lam1.
+__device__ __forceinline__ void line_range(float lam0, float lam1, float inv1, float lo_bound,
+                                           float hi_bound, int s0, int s1, int *lo, int *hi) {
   if (fabsf(lam1) < 1e-20f) {
-    bool in = lam0 > lo_bound && lam0 < hi_bound;
+    const bool in = lam0 > lo_bound && lam0 < hi_bound;
     *lo = s0;
     *hi = in ? s1 : s0;
     return;
   }
-  float inv = 1.0f / lam1;
-  float la = (lo_bound - lam0) * inv, lb = (hi_bound - lam0) * inv;
-  float lmin = fmaxf(fminf(la, lb), (float)s0);
-  float lmax = fminf(fmaxf(la, lb), (float)(s1 - 1));
+  const float la = (lo_bound - lam0) * inv1, lb = (hi_bound - lam0) * inv1;
+  const float lmin = fmaxf(fminf(la, lb), (float)s0);
+  const float lmax = fminf(fmaxf(la, lb), (float)(s1 - 1));
   *lo = (int)ceilf(lmin);
   *hi = (int)floorf(lmax) + 1;
 }
 
 // Joseph: sum over lines [s0,s1) of the linear interpolation at the
 // fixed-point crossing pos(L, k) = G + k A + L T on the staged band.
-__device__ __forceinline__ float joseph_partial(const AngleConst &C, int k, int s0,
-                                                int s1, int N, const float *buf,
-                                                int P) {
+__device__ __forceinline__ float joseph_partial(const AngleConst &C, int k, int s0, int s1,
+                                                int N, const float *buf, int P) {
   int lo, hi;
   // taps are nonzero only for pos in (-1, N); the relaxed window keeps every
   // such line and never reads beyond the kPad zero columns
-  line_range(fmaf((float)k, C.Af, C.Gf), C.Tf, -1.5f, (float)N + 0.5f, s0, s1, &lo, &hi);
+  line_range(fmaf((float)k, C.Af, C.Gf), C.Tf, C.invT, -1.5f, (float)N + 0.5f, s0, s1, &lo, &hi);
   float acc = 0.0f;
   if (lo < hi) {
     const long long T = C.T;
@@ -97,45 +153,48 @@ __device__ __forceinline__ float joseph_partial(const AngleConst &C, int k, int 
   return acc;
 }
 
-// B^T: for bin k, sum over lines of the pixels whose bin coordinate
+// B^T for bin k: the pixels of lines [s0, s1) whose bin coordinate
 // t(L, P) = t00 + L bline + P bstep lies in (k-1, k+1), weighted exactly as
 // the back-projector weights them.  At most 3 pixels per line
-// (|bstep| >= 1/sqrt 2), found around P = (k - t(L, 0)) / bstep.
-__device__ __forceinline__ float bpadj_partial(const AngleConst &C, int k, int s0,
-                                               int s1, int N, const float *buf,
-                                               int P) {
+// (|bstep| >= 1/sqrt 2): the nearest one, r, and its two neighbours.  r and
+// its exact offset D = t(L, r) - k (32-bit fixed point, |D| <= |bstep|/2)
+// are carried from line to line: D grows by bline (|bline| <= |bstep|), and
+// one step of r re-centres it.
+__device__ __forceinline__ float bpadj_partial(const AngleConst &C, int k, int s0, int s1,
+                                               int N, const float *buf, int P) {
   const float kf = (float)k;
   const float inv = C.inv_bstep;
   int lo, hi;
-  // the candidate centre must come within sqrt(2) of [0, N-1]; relaxed window
-  line_range((kf - C.t00f) * inv, -C.blinef * inv, -2.5f, (float)N + 1.5f, s0, s1, &lo, &hi);
+  // the nearest pixel must come within sqrt(2) of [0, N-1]; relaxed window,
+  // so that r stays in [-3, N+2] and its neighbours in the kPad zero columns
+  line_range((kf - C.t00f) * inv, -C.blinef * inv, -C.bstepf * C.inv_bline, -2.5f,
+             (float)N + 1.5f, s0, s1, &lo, &hi);
   float acc = 0.0f;
   if (lo < hi) {
-    const long long bstep = C.bstep, bline = C.bline;
-    long long tl = C.t00 + (long long)lo * bline;
-    float tlf = fmaf((float)lo, C.blinef, C.t00f);
+    const int bs = (int)(unsigned)C.bstep, bl = (int)(unsigned)C.bline;
+    const int abs_bs = abs(bs), half = abs_bs >> 1, sgn = bs < 0 ? -1 : 1;
+    int r = round_int((kf - fmaf((float)lo, C.blinef, C.t00f)) * inv);
+    // D = t(lo, r) - k on the low words (exact: |D| < 2^31)
+    int D = (int)((unsigned)(C.t00 + (long long)lo * C.bline) + (unsigned)r * (unsigned)bs -
+                  ((unsigned)k << kFxBits));
     const float *row = buf + (lo - s0) * P + kPad;
     for (int l = lo; l < hi; ++l) {
-      int r = round_int((kf - tlf) * inv);
-      r = min(max(r, -1), N);
-      long long t = tl + (long long)(r - 1) * bstep;
+      if (D > half) { r -= sgn; D -= abs_bs; }
+      else if (D < -half) { r += sgn; D += abs_bs; }
       const float *q = row + r;
-      acc = fmaf(tap_weight(t, k), q[-1], acc);
-      t += bstep;
-      acc = fmaf(tap_weight(t, k), q[0], acc);
-      t += bstep;
-      acc = fmaf(tap_weight(t, k), q[1], acc);
+      acc = fmaf(w23_to_float(tap_w23(D - bs)), q[-1], acc);
+      acc = fmaf(w23_to_float(tap_w23(D)), q[0], acc);
+      acc = fmaf(w23_to_float(tap_w23(D + bs)), q[1], acc);
+      D += bl;
       row += P;
-      tl += bline;
-      tlf += C.blinef;
     }
   }
   return acc;
 }
 
-template <int OP, typename Tin, typename Tout>
+template <int OP>
 __global__ void __cluster_dims__(kBands, 1, 1) __launch_bounds__(kThreads)
-    band_kernel(const BandArgs<Tin, Tout> args) {
+    band_kernel(const BandArgs args) {
   extern __shared__ float4 smem4[];
   float *smem = reinterpret_cast<float *>(smem4);
   __shared__ AngleConst sc[kMaxAB];
@@ -143,19 +202,25 @@ __global__ void __cluster_dims__(kBands, 1, 1) __launch_bounds__(kThreads)
 
   cg::cluster_group cluster = cg::this_cluster();
   const BandGeom g = args.g;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int band = (int)cluster.block_rank();
-  const int b = blockIdx.z;
+  // the job and image of this cluster
+  const int z = blockIdx.z;
+  const int jn = (args.jobs.njobs > 1 && z >= args.jobs.j[0].nimg) ? 1 : 0;
+  const Job &J = args.jobs.j[jn];
+  const int b = z - (jn ? args.jobs.j[0].nimg : 0);
   const int a_begin = blockIdx.y * g.AB;
-  const int na = min(g.AB, args.m - a_begin);
-  const int nd = g.n_det, N = g.N, P = g.P;
-  float *part = smem;                 // [AB][n_det]
-  float *buf = smem + g.AB * nd;      // [SB][P]
+  if (a_begin >= J.m) return;  // uniform over the cluster: no peer waits for it
+  const int na = min(g.AB, J.m - a_begin);
+  const int nd = g.n_det, N = g.N;
+  const int nrows = g.AB;                              // rows of partial bins
+  float *part = smem;                                  // [nrows][n_det]
+  float *buf = smem + ((nrows * nd + 3) & ~3);         // [SB][P], 16-byte aligned
 
   if (tid < kMaxAB) {
     int ai = -1;
     if (tid < na) {
-      ai = args.idx ? args.idx[a_begin + tid] : a_begin + tid;
+      ai = J.idx ? J.idx[a_begin + tid] : a_begin + tid;
       if (ai < 0 || ai >= g.n_angles) {
         if (band == 0) atomicOr(args.status, 1);
         ai = -1;
@@ -164,41 +229,26 @@ __global__ void __cluster_dims__(kBands, 1, 1) __launch_bounds__(kThreads)
     sai[tid] = ai;
     if (ai >= 0) sc[tid] = args.ang[ai];
   }
-  for (int e = tid; e < na * nd; e += kThreads) part[e] = 0.0f;
+  for (int e = tid; e < nrows * nd; e += kThreads) part[e] = 0.0f;
   __syncthreads();
 
-  const Tin *xb = args.x + (size_t)b * N * N;
+  const size_t xo = (size_t)b * N * N;
   const int L0 = band * g.R, L1 = min(N, L0 + g.R);
   for (int mode = 1; mode >= 0; --mode) {
     bool any = false;
     for (int a = 0; a < na; ++a) any |= (sai[a] >= 0 && sc[a].mode == mode);
     if (!any) continue;
+    const int P = mode ? g.Prow : g.Pcol;
     for (int s0 = L0; s0 < L1; s0 += g.SB) {
       const int s1 = min(L1, s0 + g.SB), nl = s1 - s0;
       __syncthreads();  // the previous sub-band is no longer read
-      if (mode == 1) {
-        for (int e = tid; e < nl * N; e += kThreads) {
-          const int l = e / N, p = e - l * N;
-          buf[l * P + kPad + p] = ldg_f(xb + (size_t)(s0 + l) * N + p);
-        }
-      } else {
-        for (int e = tid; e < nl * N; e += kThreads) {
-          const int p = e / nl, l = e - p * nl;
-          buf[l * P + kPad + p] = ldg_f(xb + (size_t)p * N + s0 + l);
-        }
-      }
-      const int npad = P - N;
-      for (int e = tid; e < nl * npad; e += kThreads) {
-        const int l = e / npad, q = e - l * npad;
-        buf[l * P + (q < kPad ? q : N + q)] = 0.0f;
-      }
+      stage(J.in, xo, J.in_bf16, N, mode, s0, nl, buf, P, g.fast != 0);
       __syncthreads();
-      for (int it = tid; it < na * nd; it += kThreads) {
-        const int a = it / nd, k = it - a * nd;
+      for (int a = 0; a < na; ++a) {
         if (sai[a] < 0 || sc[a].mode != mode) continue;
-        const float v = OP == OP_JOSEPH ? joseph_partial(sc[a], k, s0, s1, N, buf, P)
-                                        : bpadj_partial(sc[a], k, s0, s1, N, buf, P);
-        part[it] += v;
+        for (int k = tid; k < nd; k += kThreads)
+          part[a * nd + k] += OP == OP_JOSEPH ? joseph_partial(sc[a], k, s0, s1, N, buf, P)
+                                              : bpadj_partial(sc[a], k, s0, s1, N, buf, P);
       }
     }
   }
@@ -206,22 +256,22 @@ __global__ void __cluster_dims__(kBands, 1, 1) __launch_bounds__(kThreads)
   cluster.sync();
   const int n_items = na * nd;
   for (int it = band * kThreads + tid; it < n_items; it += kBands * kThreads) {
+    const int a = it / nd, k = it - a * nd;
     float s = 0.0f;
 #pragma unroll
     for (int q = 0; q < kBands; ++q) s += cluster.map_shared_rank(part, q)[it];
-    const int a = it / nd, k = it - a * nd;
     const int ai = sai[a];
-    Tout *o = args.out + ((size_t)b * args.m + a_begin + a) * nd + k;
+    const size_t o = ((size_t)b * J.m + a_begin + a) * nd + k;
     float v;
     if (ai < 0) {
       v = 0.0f;
     } else if (OP == OP_JOSEPH) {
       v = s * sc[a].W;
-      if (args.y) v = ldg_f(args.y + ((size_t)b * g.n_angles + ai) * nd + k) - v;
+      if (J.aux) v = ld_any(J.aux, ((size_t)b * g.n_angles + ai) * nd + k, J.aux_bf16) - v;
     } else {
-      v = s * args.alpha;
+      v = s * J.alpha;
     }
-    st_f(o, v);
+    st_any(J.out, o, v, J.out_bf16);
   }
   cluster.sync();  // keep this CTA's partials alive until every peer has read them
 }
@@ -239,39 +289,54 @@ int sm_count() {
   return count[dev];
 }
 
-template <int OP, typename Tin, typename Tout>
-int launch_band(skei_plan p, const Tin *x, int B, const int *idx, int m,
-                const Tout *y, float alpha, Tout *out, cudaStream_t st) {
+template <int OP>
+int launch_band(skei_plan p, const Jobs &jobs, cudaStream_t st) {
   BandGeom g;
   g.N = p->N;
   g.n_det = p->n_det;
   g.n_angles = p->n_angles;
   g.R = (g.N + kBands - 1) / kBands;
-  g.P = g.N + 2 * kPad;
-  if (g.P % 2 == 0) g.P += 1;  // odd pitch: transposed staging writes hit distinct banks
-  g.SB = min(g.R, 32);
-  while (g.SB > 1 && (size_t)g.SB * g.P * 4 > 96 * 1024) --g.SB;
+  g.Prow = (g.N + 2 * kPad + 3) & ~3;
+  g.Pcol = ((g.N + 2 * kPad - 2 + 7) & ~7) + 2;
+  g.fast = (g.N % 8 == 0) ? 1 : 0;
+  const int Pmax = g.Prow > g.Pcol ? g.Prow : g.Pcol;
+  // 16 staged lines keep the band at ~33 KB for N = 512: several CTAs per SM
+  g.SB = min(g.R, 16);
+  while (g.SB > 1 && (size_t)g.SB * Pmax * 4 > 96 * 1024) --g.SB;
+  const size_t band_bytes = (size_t)g.SB * Pmax * 4;
+  int m_max = 0, nimg = 0;
+  for (int q = 0; q < jobs.njobs; ++q) {
+    m_max = max(m_max, jobs.j[q].m);
+    nimg += jobs.j[q].nimg;
+  }
+  if (nimg > 65535) return set_error(SKEI_EINVAL, "too many images (%d) in one launch", nimg);
 
   // angles per cluster: fewest waves x angles per CTA (the per-CTA time),
-  // ties to the larger block (less staging)
-  int ab_max = min(kMaxAB, m);
-  while (ab_max > 1 && (size_t)ab_max * g.n_det * 4 > 48 * 1024) --ab_max;
-  const size_t band_bytes = (size_t)g.SB * g.P * 4;
+  // ties to the larger block (less staging); B^T needs AB | kWarps
+  const int ab_max = min(kMaxAB, m_max);
   int best_ab = 1;
   double best_cost = 1e300;
   for (int ab = 1; ab <= ab_max; ++ab) {
-    const size_t bytes = band_bytes + (size_t)ab * g.n_det * 4;
+    const int rows = ab;
+    const size_t bytes = band_bytes + (size_t)((rows * g.n_det + 3) & ~3) * 4;
+    if (bytes > 200 * 1024) continue;
     int per_sm = (int)((227 * 1024) / (bytes + 1024));
     per_sm = max(1, min(per_sm, 8));
     const double slots = (double)sm_count() * per_sm;
-    const double ctas = (double)kBands * ((m + ab - 1) / ab) * B;
+    double ctas = 0.0;
+    for (int q = 0; q < jobs.njobs; ++q)
+      ctas += (double)kBands * ((jobs.j[q].m + ab - 1) / ab) * jobs.j[q].nimg;
     const double cost = std::ceil(ctas / slots) * ab;
     if (cost <= best_cost) { best_cost = cost; best_ab = ab; }
   }
   g.AB = best_ab;
-  const size_t smem = band_bytes + (size_t)g.AB * g.n_det * 4;
+  g.C = 1;
+  const int rows = g.AB;
+  const size_t smem = band_bytes + (size_t)((rows * g.n_det + 3) & ~3) * 4;
+  if (smem > 227 * 1024)
+    return set_error(SKEI_EINVAL, "detector of %d bins needs too much shared memory", g.n_det);
 
-  auto kern = band_kernel<OP, Tin, Tout>;
+  auto kern = band_kernel<OP>;
   static size_t configured = 0;
   if (smem > 48 * 1024 && smem > configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -279,34 +344,18 @@ int launch_band(skei_plan p, const Tin *x, int B, const int *idx, int m,
     if (e != cudaSuccess) return cuda_error(e, "band kernel: shared memory attribute");
     configured = smem;
   }
-  BandArgs<Tin, Tout> a{x, y, out, idx, m, p->d_ang, p->d_status, alpha, g};
-  dim3 grid(kBands, (m + g.AB - 1) / g.AB, B);
+  BandArgs a{jobs, p->d_ang, p->d_status, g};
+  dim3 grid(kBands, (m_max + g.AB - 1) / g.AB, nimg);
   kern<<<grid, kThreads, smem, st>>>(a);
   return check_launch(OP == OP_JOSEPH ? "joseph forward launch" : "back-projection transpose launch");
 }
 
 }  // namespace
 
-template <typename Tin, typename Tout>
-int launch_proj_fwd(skei_plan p, const Tin *x, int B, const int *idx, int m,
-                    const Tout *y, Tout *out, cudaStream_t st) {
-  return launch_band<OP_JOSEPH, Tin, Tout>(p, x, B, idx, m, y, 1.0f, out, st);
+int launch_band_jobs(skei_plan p, int op, const Jobs &jobs, cudaStream_t st) {
+  if (op == OP_JOSEPH) return launch_band<OP_JOSEPH>(p, jobs, st);
+  if (op == OP_BP_ADJ) return launch_band<OP_BP_ADJ>(p, jobs, st);
+  return set_error(SKEI_EINVAL, "band launch: unknown operator %d", op);
 }
-
-template <typename Tin, typename Tout>
-int launch_backproject_adj(skei_plan p, const Tin *x, int B, const int *idx, int m,
-                           float alpha, Tout *q, cudaStream_t st) {
-  return launch_band<OP_BP_ADJ, Tin, Tout>(p, x, B, idx, m, nullptr, alpha, q, st);
-}
-
-#define SKEI_BAND_INST(TI, TO)                                                              \
-  template int launch_proj_fwd<TI, TO>(skei_plan, const TI *, int, const int *, int,        \
-                                       const TO *, TO *, cudaStream_t);                     \
-  template int launch_backproject_adj<TI, TO>(skei_plan, const TI *, int, const int *, int, \
-                                              float, TO *, cudaStream_t);
-SKEI_BAND_INST(float, float)
-SKEI_BAND_INST(__nv_bfloat16, __nv_bfloat16)
-SKEI_BAND_INST(__nv_bfloat16, float)
-#undef SKEI_BAND_INST
 
 }  // namespace skei

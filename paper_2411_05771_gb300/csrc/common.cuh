@@ -13,11 +13,13 @@
 namespace skei {
 
 // Per-angle constants, derived in FP64 on the host.  Positions are kept in
-// 32.32 fixed point (int64: integer part in the high word, fraction in the
-// low word), so that every kernel evaluates them EXACTLY, in any order:
-// forward operators and their gathered transposes then see bitwise the same
-// positions and interpolation weights, and the weights are accurate to
-// ~1e-7 (FP32 positions near 512 would only be good to ~3e-5).
+// 36.28 fixed point (int64: value * 2^28), so that every kernel evaluates
+// them EXACTLY, in any order: forward operators and their gathered
+// transposes then see bitwise the same positions and interpolation weights.
+// Constants are rounded to 2^-29, so a position is within (k + L + 1) 2^-29
+// (~2e-6 px at 512^2) of its FP64 value; FP32 positions near 512 would only
+// be good to ~3e-5.  Differences of positions that are known to be small
+// (|D| < 8) are exact in 32-bit wrapping arithmetic on the low words.
 //
 // Joseph's projector (Sec. 4.1.1, discrete Radon transform): ray k crosses
 // "line" L (an image row in row mode, a column in column mode) at
@@ -30,26 +32,48 @@ namespace skei {
 //     t(i, j) = t00 + j tj + i ti                    (fixed point)
 // and B_S^T walks lines L with position P: (L, P) = (i, j) in row mode,
 // (j, i) in column mode, i.e. t = t00 + L bline + P bstep.
+constexpr int kFxBits = 28;
+constexpr long long kFxOne = 1LL << kFxBits;
 struct AngleConst {
-  long long T, A, G;             // Joseph, 32.32
-  long long t00, bline, bstep;   // back-projection, 32.32
-  long long tj, ti;              // back-projection per column / per row, 32.32
+  long long T, A, G;             // Joseph, fixed point
+  long long t00, bline, bstep;   // back-projection, fixed point
+  long long tj, ti;              // back-projection per column / per row, fixed point
   float Tf, Af, Gf;              // FP32 copies, only to choose candidates
   float W;                       // 1/|cos| (row mode) or 1/|sin| (column mode)
   float invA;                    // 1/A
   float t00f, blinef, bstepf, inv_bstep;
   float tjf, tif;
+  float invT;                    // 1/T (0 when T == 0)
+  float inv_bline;               // 1/bline (0 when bline == 0)
   int mode;                      // 1: lines are rows (position = column j)
+  int pad0;
 };
-static_assert(sizeof(AngleConst) == 112, "AngleConst layout");
+static_assert(sizeof(AngleConst) == 128, "AngleConst layout");
 
-// The fraction of a 32.32 position, truncated to 23 bits: an exact multiple
-// of 2^-23 in [0, 1), so that 1 - f is exact too.
+// The fraction of a fixed-point position, truncated to 23 bits: an exact
+// multiple of 2^-23 in [0, 1), so that 1 - f is exact too.
 __device__ __forceinline__ float frac23(long long pos) {
   const unsigned lo = (unsigned)pos;
-  return __uint_as_float(0x3F800000u | (lo >> 9)) - 1.0f;
+  return __uint_as_float(0x3F800000u | ((lo >> (kFxBits - 23)) & 0x7FFFFFu)) - 1.0f;
 }
-__device__ __forceinline__ int ipart(long long pos) { return (int)(pos >> 32); }
+__device__ __forceinline__ float frac23(int d) { return frac23((long long)d); }
+__device__ __forceinline__ int ipart(long long pos) { return (int)(pos >> kFxBits); }
+__device__ __forceinline__ int ipart(int d) { return d >> kFxBits; }
+
+// Linear-interpolation weight of a sample at fixed-point offset D (|D| < 8,
+// 32-bit) from an integer position q, D = pos - q: 1-f if floor(pos) == q,
+// f if floor(pos) == q-1, else 0, with f the 23-bit fraction of pos.  With
+// a = D >> 5 (floor division), both cases are 2^23 - |a| in units of 2^-23:
+// for D >= 0, a is f's 23 bits; for D < 0, f's bits are a + 2^23.
+__device__ __forceinline__ int tap_w23(int D) {
+  const int a = D >> (kFxBits - 23);
+  return max((1 << 23) - abs(a), 0);
+}
+
+// A weight w23 * 2^-23 (0 <= w23 <= 2^23) as an exact float.
+__device__ __forceinline__ float w23_to_float(int w23) {
+  return __int_as_float(0x3F800000 + w23) - 1.0f;
+}
 
 // Weight with which a sample at fixed-point position `pos` reaches integer
 // position q under linear interpolation between floor(pos) and
@@ -111,8 +135,8 @@ __device__ __forceinline__ int round_int(float x) {
   return __float_as_int(__fadd_rn(x, M)) - 0x4B400000;
 }
 
-// 32.32 fixed point of a double (|v| < 2^30).
-__device__ __forceinline__ long long to_fx(double v) { return __double2ll_rn(v * 4294967296.0); }
+// Fixed point of a double (|v| < 2^34).
+__device__ __forceinline__ long long to_fx(double v) { return __double2ll_rn(v * (double)kFxOne); }
 
 // cos and sin in FP64 of an angle in degrees, reduced exactly to
 // [-45, 45] first (exact 0/+-1 at multiples of 90 degrees).
@@ -130,25 +154,91 @@ __device__ __forceinline__ void trig_deg(double deg, double *c, double *s) {
 
 inline size_t ceil_div(size_t a, size_t b) { return (a + b - 1) / b; }
 
+// --------------------------------------------- dtype-erased device data --
+// Loads/stores of image and sinogram buffers whose storage type (float or
+// bfloat16) is a runtime flag; kernels branch on it only where the branch is
+// uniform across a CTA (staging, window fills, final stores).
+__device__ __forceinline__ float ld_any(const void *p, size_t i, int bf16) {
+  return bf16 ? __bfloat162float(__ldg(static_cast<const __nv_bfloat16 *>(p) + i))
+              : __ldg(static_cast<const float *>(p) + i);
+}
+__device__ __forceinline__ void st_any(void *p, size_t i, float v, int bf16) {
+  if (bf16) static_cast<__nv_bfloat16 *>(p)[i] = __float2bfloat16_rn(v);
+  else static_cast<float *>(p)[i] = v;
+}
+template <typename T> __host__ __device__ constexpr int is_bf16() { return 0; }
+template <> __host__ __device__ constexpr int is_bf16<__nv_bfloat16>() { return 1; }
+
+// One operator application over a batch of images, as the band and tile
+// kernels see it.  Up to kMaxJobs jobs share a launch (grid.z spans the
+// images of all of them): the fused EI step projects x1 (MC term) and x2
+// (EI term) in one launch, and back-projects r and the EI gradient in one.
+//   band (A, B^T):   in = images [nimg][N][N]; out = [nimg][m][n_det];
+//                    aux = NULL or full measurement y [nimg][n_angles][n_det]
+//                    (A only: out = S y - A_S x)
+//   tile (A^T, B):   in = sinograms [nimg][m][n_det]; out = [nimg][N][N];
+//                    out = alpha * op(in) + beta * aux (aux may alias out)
+struct Job {
+  const void *in;
+  const void *aux;
+  void *out;
+  const int *idx;     // device angle list [m] or NULL (all angles)
+  int m, nimg;
+  float alpha, beta;
+  int in_bf16, aux_bf16, out_bf16;
+};
+constexpr int kMaxJobs = 2;
+struct Jobs {
+  Job j[kMaxJobs];
+  int njobs;
+};
+
+enum { OP_JOSEPH = 0, OP_BP_ADJ = 1, OP_JOSEPH_ADJ = 2, OP_BACKPROJECT = 3 };
+
+int launch_band_jobs(skei_plan p, int op, const Jobs &jobs, cudaStream_t st);
+int launch_tile_jobs(skei_plan p, int op, const Jobs &jobs, cudaStream_t st);
+
 // ------------------------------------------------------ internal launches --
-// Joseph forward on a batch: out[b][a][k] = (A_S x_b) (or y_S - A_S x_b).
+// Single-job conveniences over the two above.
 template <typename Tin, typename Tout>
 int launch_proj_fwd(skei_plan p, const Tin *x, int B, const int *idx, int m,
-                    const Tout *y, Tout *out, cudaStream_t st);
+                    const Tout *y, Tout *out, cudaStream_t st) {
+  Jobs J{};
+  J.njobs = 1;
+  J.j[0] = Job{x, y, out, idx, m, B, 1.0f, 0.0f, is_bf16<Tin>(), is_bf16<Tout>(), is_bf16<Tout>()};
+  return launch_band_jobs(p, OP_JOSEPH, J, st);
+}
 // Joseph adjoint: out = alpha A_S^T sino + beta add (add may alias out).
 template <typename Tin, typename Tadd, typename Tout>
 int launch_proj_adj(skei_plan p, const Tin *sino, int B, const int *idx, int m,
                     float alpha, float beta, const Tadd *add, Tout *out,
-                    cudaStream_t st);
+                    cudaStream_t st) {
+  Jobs J{};
+  J.njobs = 1;
+  J.j[0] = Job{sino, add, out, idx, m, B, alpha, beta, is_bf16<Tin>(), is_bf16<Tadd>(),
+               is_bf16<Tout>()};
+  return launch_tile_jobs(p, OP_JOSEPH_ADJ, J, st);
+}
 // Back-projection: out = alpha B_S q + beta add.
 template <typename Tin, typename Tadd, typename Tout>
 int launch_backproject(skei_plan p, const Tin *q, int B, const int *idx, int m,
                        float alpha, float beta, const Tadd *add, Tout *out,
-                       cudaStream_t st);
+                       cudaStream_t st) {
+  Jobs J{};
+  J.njobs = 1;
+  J.j[0] = Job{q, add, out, idx, m, B, alpha, beta, is_bf16<Tin>(), is_bf16<Tadd>(),
+               is_bf16<Tout>()};
+  return launch_tile_jobs(p, OP_BACKPROJECT, J, st);
+}
 // Back-projection transpose: q = alpha B_S^T x.
 template <typename Tin, typename Tout>
 int launch_backproject_adj(skei_plan p, const Tin *x, int B, const int *idx,
-                           int m, float alpha, Tout *q, cudaStream_t st);
+                           int m, float alpha, Tout *q, cudaStream_t st) {
+  Jobs J{};
+  J.njobs = 1;
+  J.j[0] = Job{x, nullptr, q, idx, m, B, alpha, 0.0f, is_bf16<Tin>(), 0, is_bf16<Tout>()};
+  return launch_band_jobs(p, OP_BP_ADJ, J, st);
+}
 // Ram-Lak: q = scale H p, `rows` rows.
 template <typename Tin, typename Tout>
 int launch_filter(skei_plan p, const Tin *in, int rows, float scale, Tout *out,

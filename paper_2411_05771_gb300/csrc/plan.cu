@@ -73,7 +73,7 @@ static void host_trig(double deg, double *c, double *s) {
   else { *c = sr; *s = -cr; }
 }
 
-static long long fx(double v) { return std::llround(v * 4294967296.0); }
+static long long fx(double v) { return std::llround(std::ldexp(v, kFxBits)); }
 
 // Derives the constants documented on AngleConst for one angle.
 static AngleConst make_angle(double deg, int N, int n_det) {
@@ -121,6 +121,9 @@ static AngleConst make_angle(double deg, int N, int n_det) {
   a.blinef = (float)(row ? ti : tj);
   a.bstepf = (float)(row ? tj : ti);
   a.inv_bstep = (float)(1.0 / (row ? tj : ti));
+  a.invT = T != 0.0 ? (float)(1.0 / T) : 0.0f;
+  const double bl = row ? ti : tj;
+  a.inv_bline = bl != 0.0 ? (float)(1.0 / bl) : 0.0f;
   a.mode = row ? 1 : 0;
   return a;
 }

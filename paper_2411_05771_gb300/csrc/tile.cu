@@ -1,70 +1,84 @@
-// Pixel-driven gathers over 32x32 image tiles: the exact transpose A_S^T of
-// Joseph's projector (the gradient of the MC and EI terms, Algorithm 2) and
-// the back-projection B_S of FBP (A_S^dagger = (pi/m) B_S H, Sec. 2.1 and
-// 3.1).
+// Pixel-driven gathers over 8 x 128 image tiles: the exact transpose A_S^T
+// of Joseph's projector (the gradient of the MC and EI terms, Algorithm 2)
+// and the back-projection B_S of FBP (A_S^dagger = (pi/m) B_S H, Sec. 2.1
+// and 3.1).
 //
-// A CTA owns one tile of one image and walks the angle list in chunks; for
-// each angle it stages in shared memory only the window of detector bins
-// that the tile projects onto (at most ~50 bins).  Every thread accumulates
-// 4 pixels in registers and writes each once, so no atomics are needed.
+// A CTA owns one tile of one image (one warp per tile row, 4 consecutive
+// pixels per thread) and walks the angle list in chunks; for each angle it
+// stages in shared memory only the window of detector bins the tile projects
+// onto.  Every thread accumulates its 4 pixels in registers and writes each
+// once: no atomics.  Up to two jobs share a launch (grid.z spans the images
+// of both), e.g. the MC-term and EI-term adjoints of one SkEI step.
 //
-// A^T: pixel (L, P) (line, position) receives, for each angle, from the rays
-// whose crossing with line L lies in (P-1, P+1) - at most 3 candidates
-// around k = (P - G - L T) / A.  The crossing is recomputed exactly in the
-// forward's fixed-point form and weighted with tap_weight(), so the gathered
-// weights equal bitwise the forward's interpolation weights.
+// A^T: pixel (L, P) (line, position) receives, for each angle, from the two
+// rays whose crossing with line L has integer part P (weight 1-f) and P-1
+// (weight f).  With u = P - G - L T and r the ray nearest to P
+// (r = round(u / A)), the exact fixed-point offset D = pos(L, r) - P =
+// r A - u lies in (-1, 1); its sign says whether r is the "1-f" or the "f"
+// ray, and the other one is r's neighbour on the opposite side, at
+// D -+ |A|.  Both offsets are small, so they are exact in 32-bit wrapping
+// arithmetic on the low words of the fixed-point values, and their 23-bit
+// fractions are bitwise the forward's interpolation weights.
 #include "common.cuh"
 
 namespace skei {
 namespace {
 
-constexpr int kTile = 32;
-constexpr int kRows = 8;   // thread rows; each thread owns kTile/kRows pixels
-constexpr int kWin = 64;   // staged bins per angle
-constexpr int kAC = 16;    // angles per chunk
-constexpr int kThreads = kTile * kRows;
+constexpr int kTW = 128;                 // tile width (columns)
+constexpr int kTH = 8;                   // tile height (rows) = warps per CTA
+constexpr int kPPT = 4;                  // consecutive pixels per thread
+constexpr int kThreads = 32 * kTH;
+constexpr int kWin = 192;                // staged bins per angle
+constexpr int kAC = 8;                   // angles per chunk
 
-enum { OP_JOSEPH_ADJ = 0, OP_BACKPROJECT = 1 };
-
-template <typename Tin, typename Tadd, typename Tout>
 struct TileArgs {
-  const Tin *sino;    // [B][m][n_det]
-  const Tadd *add;    // [B][N][N] or null
-  Tout *out;          // [B][N][N]
-  const int *idx;
-  int m, N, n_det, n_angles;
-  float alpha, beta;
+  Jobs jobs;
+  int N, n_det, n_angles;
   const AngleConst *ang;
   int *status;
 };
 
-template <int OP, typename Tin, typename Tadd, typename Tout>
-__global__ void __launch_bounds__(kThreads)
-    tile_kernel(const TileArgs<Tin, Tadd, Tout> args) {
+// Stores up to 4 consecutive pixels at element offset o.
+__device__ __forceinline__ void store4(void *out, size_t o, const float *v, int n_valid,
+                                       int bf16) {
+  if (!bf16) {
+    float *p = static_cast<float *>(out) + o;
+    if (n_valid == 4 && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+      *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+      return;
+    }
+  }
+  for (int q = 0; q < n_valid; ++q) st_any(out, o + q, v[q], bf16);
+}
+
+template <int OP>
+__global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs args) {
   __shared__ float win[kAC][kWin];
   __shared__ AngleConst sc[kAC];
-  __shared__ long long c0w[kAC];   // Joseph: G + kw0 A, the window's first ray at line 0
   __shared__ int sai[kAC];
   __shared__ int kw0[kAC];
 
   const int tid = threadIdx.x;
-  const int tx = tid % kTile, ty = tid / kTile;
+  const int lane = tid & 31, warp = tid >> 5;
   const int N = args.N, nd = args.n_det;
-  const int i0 = blockIdx.y * kTile, j0 = blockIdx.x * kTile;
-  const int b = blockIdx.z;
-  const int i_last = min(i0 + kTile, N) - 1, j_last = min(j0 + kTile, N) - 1;
+  const int i0 = blockIdx.y * kTH, j0 = blockIdx.x * kTW;
+  const int z = blockIdx.z;
+  const int jn = (args.jobs.njobs > 1 && z >= args.jobs.j[0].nimg) ? 1 : 0;
+  const Job &J = args.jobs.j[jn];
+  const int b = z - (jn ? args.jobs.j[0].nimg : 0);
+  const int i_last = min(i0 + kTH, N) - 1, j_last = min(j0 + kTW, N) - 1;
+  const int i = i0 + warp;                 // this thread's row
+  const int jb = j0 + kPPT * lane;         // its first column
 
-  float acc[kTile / kRows];
+  float acc[kPPT];
 #pragma unroll
-  for (int q = 0; q < kTile / kRows; ++q) acc[q] = 0.0f;
-  const int j = j0 + tx;
-  const float fj = (float)j;
+  for (int q = 0; q < kPPT; ++q) acc[q] = 0.0f;
 
-  for (int c0 = 0; c0 < args.m; c0 += kAC) {
-    const int nac = min(kAC, args.m - c0);
+  for (int c0 = 0; c0 < J.m; c0 += kAC) {
+    const int nac = min(kAC, J.m - c0);
     __syncthreads();  // previous chunk no longer read
     if (tid < nac) {
-      int ai = args.idx ? args.idx[c0 + tid] : c0 + tid;
+      int ai = J.idx ? J.idx[c0 + tid] : c0 + tid;
       if (ai < 0 || ai >= args.n_angles) {
         if (blockIdx.x == 0 && blockIdx.y == 0) atomicOr(args.status, 1);
         ai = -1;
@@ -81,12 +95,10 @@ __global__ void __launch_bounds__(kThreads)
             const float L = C.mode ? fi_ : fj_, Pp = C.mode ? fj_ : fi_;
             float v;
             if (OP == OP_JOSEPH_ADJ) v = (Pp - fmaf(L, C.Tf, C.Gf)) * C.invA;
-            else v = fmaf(Pp, C.bstepf, fmaf(L, C.blinef, C.t00f));
+            else v = fmaf(fj_, C.tjf, fmaf(fi_, C.tif, C.t00f));
             lo = fminf(lo, v);
           }
-        const int k0 = (int)floorf(lo) - (OP == OP_JOSEPH_ADJ ? 2 : 1);
-        kw0[tid] = k0;
-        c0w[tid] = C.G + (long long)k0 * C.A;
+        kw0[tid] = (int)floorf(lo) - 3;
       }
     }
     __syncthreads();
@@ -97,7 +109,7 @@ __global__ void __launch_bounds__(kThreads)
       if (ai >= 0) {
         const int k = kw0[a] + w;
         if (k >= 0 && k < nd) {
-          v = ldg_f(args.sino + ((size_t)b * args.m + c0 + a) * nd + k);
+          v = ld_any(J.in, ((size_t)b * J.m + c0 + a) * nd + k, J.in_bf16);
           if (OP == OP_JOSEPH_ADJ) v *= sc[a].W;
         }
       }
@@ -108,88 +120,82 @@ __global__ void __launch_bounds__(kThreads)
     for (int a = 0; a < nac; ++a) {
       if (sai[a] < 0) continue;
       const AngleConst &C = sc[a];
-      const int base = kw0[a];
       const float *wa = win[a];
+      const int base = kw0[a];
       if (OP == OP_JOSEPH_ADJ) {
-        const long long A = C.A, T = C.T;
-        const long long c0 = c0w[a];
+        const bool row = C.mode != 0;
+        const unsigned A32 = (unsigned)C.A;
+        const int absA32 = (int)(unsigned)(C.A < 0 ? -C.A : C.A);
+        const int sA = C.A < 0 ? -1 : 1;
+        // u = P - G - L T for the first pixel (low word; exact modulo 2^32);
+        // per step along the row, row mode (P = j) adds 1, column mode
+        // (L = j) subtracts T
+        const int L0 = row ? i : jb, P0 = row ? jb : i;
+        unsigned u = (unsigned)(((long long)P0 << kFxBits) - C.G - (long long)L0 * C.T);
+        const unsigned du = row ? (unsigned)kFxOne : (unsigned)(-C.T);
+        float kc = ((float)P0 - fmaf((float)L0, C.Tf, C.Gf)) * C.invA;
+        const float dkc = row ? C.invA : -C.Tf * C.invA;
 #pragma unroll
-        for (int q = 0; q < kTile / kRows; ++q) {
-          const int i = i0 + ty + kRows * q;
-          const int L = C.mode ? i : j, Pp = C.mode ? j : i;
-          const float kc = ((float)Pp - fmaf((float)L, C.Tf, C.Gf)) * C.invA;
-          int r = round_int(kc) - 1 - base;       // window slot of the first candidate
-          r = min(max(r, 0), kWin - 3);
-          long long pos = c0 + (long long)r * A + (long long)L * T;
-          float s = acc[q];
-          s = fmaf(tap_weight(pos, Pp), wa[r], s);
-          pos += A;
-          s = fmaf(tap_weight(pos, Pp), wa[r + 1], s);
-          pos += A;
-          s = fmaf(tap_weight(pos, Pp), wa[r + 2], s);
-          acc[q] = s;
+        for (int q = 0; q < kPPT; ++q) {
+          const int r = round_int(kc);
+          const int D = (int)((unsigned)r * A32 - u);   // pos(L, r) - P, in (-1, 1)
+          const bool right = D >= 0;                     // r is the "1-f" ray
+          const int D2 = right ? D - absA32 : D + absA32;
+          const int w1 = tap_w23(D), w2 = tap_w23(D2);
+          const int r2 = right ? r - sA : r + sA;
+          const unsigned s1 = min((unsigned)(r - base), (unsigned)(kWin - 1));
+          const unsigned s2 = min((unsigned)(r2 - base), (unsigned)(kWin - 1));
+          acc[q] = fmaf(w23_to_float(w1), wa[s1], fmaf(w23_to_float(w2), wa[s2], acc[q]));
+          u += du;
+          kc += dkc;
         }
       } else {
-        const long long step = C.ti * kRows;
-        long long t = C.t00 + (long long)j * C.tj + (long long)(i0 + ty) * C.ti;
+        // t(i, j) = t00 + j tj + i ti, stepping along the row by tj
+        long long t = C.t00 + (long long)jb * C.tj + (long long)i * C.ti;
+        const long long tj = C.tj;
 #pragma unroll
-        for (int q = 0; q < kTile / kRows; ++q) {
+        for (int q = 0; q < kPPT; ++q) {
           int k0 = ipart(t) - base;
           k0 = min(max(k0, 0), kWin - 2);
           const float w = frac23(t);
           const float v0 = wa[k0], v1 = wa[k0 + 1];
           acc[q] += fmaf(w, v1 - v0, v0);
-          t += step;
+          t += tj;
         }
       }
     }
   }
 
-  if (j >= N) return;
+  if (i >= N || jb >= N) return;
+  const int n_valid = min(kPPT, N - jb);
+  const size_t o = ((size_t)b * N + i) * N + jb;
+  float v[kPPT];
 #pragma unroll
-  for (int q = 0; q < kTile / kRows; ++q) {
-    const int i = i0 + ty + kRows * q;
-    if (i >= N) continue;
-    const size_t o = ((size_t)b * N + i) * N + j;
-    float v = args.alpha * acc[q];
-    if (args.beta != 0.0f && args.add) v = fmaf(args.beta, ldg_f(args.add + o), v);
-    st_f(args.out + o, v);
+  for (int q = 0; q < kPPT; ++q) {
+    v[q] = J.alpha * acc[q];
+    if (J.beta != 0.0f && J.aux && q < n_valid)
+      v[q] = fmaf(J.beta, ld_any(J.aux, o + q, J.aux_bf16), v[q]);
   }
+  store4(J.out, o, v, n_valid, J.out_bf16);
 }
 
-template <int OP, typename Tin, typename Tadd, typename Tout>
-int launch_tile(skei_plan p, const Tin *sino, int B, const int *idx, int m, float alpha,
-                float beta, const Tadd *add, Tout *out, cudaStream_t st) {
-  TileArgs<Tin, Tadd, Tout> a{sino, add, out, idx, m, p->N, p->n_det, p->n_angles,
-                              alpha, beta, p->d_ang, p->d_status};
-  dim3 grid((p->N + kTile - 1) / kTile, (p->N + kTile - 1) / kTile, B);
-  tile_kernel<OP, Tin, Tadd, Tout><<<grid, kThreads, 0, st>>>(a);
+template <int OP>
+int launch_tile(skei_plan p, const Jobs &jobs, cudaStream_t st) {
+  int nimg = 0;
+  for (int q = 0; q < jobs.njobs; ++q) nimg += jobs.j[q].nimg;
+  if (nimg > 65535) return set_error(SKEI_EINVAL, "too many images (%d) in one launch", nimg);
+  TileArgs a{jobs, p->N, p->n_det, p->n_angles, p->d_ang, p->d_status};
+  dim3 grid((p->N + kTW - 1) / kTW, (p->N + kTH - 1) / kTH, nimg);
+  tile_kernel<OP><<<grid, kThreads, 0, st>>>(a);
   return check_launch(OP == OP_JOSEPH_ADJ ? "joseph adjoint launch" : "back-projection launch");
 }
 
 }  // namespace
 
-template <typename Tin, typename Tadd, typename Tout>
-int launch_proj_adj(skei_plan p, const Tin *sino, int B, const int *idx, int m,
-                    float alpha, float beta, const Tadd *add, Tout *out, cudaStream_t st) {
-  return launch_tile<OP_JOSEPH_ADJ>(p, sino, B, idx, m, alpha, beta, add, out, st);
+int launch_tile_jobs(skei_plan p, int op, const Jobs &jobs, cudaStream_t st) {
+  if (op == OP_JOSEPH_ADJ) return launch_tile<OP_JOSEPH_ADJ>(p, jobs, st);
+  if (op == OP_BACKPROJECT) return launch_tile<OP_BACKPROJECT>(p, jobs, st);
+  return set_error(SKEI_EINVAL, "tile launch: unknown operator %d", op);
 }
-
-template <typename Tin, typename Tadd, typename Tout>
-int launch_backproject(skei_plan p, const Tin *q, int B, const int *idx, int m,
-                       float alpha, float beta, const Tadd *add, Tout *out, cudaStream_t st) {
-  return launch_tile<OP_BACKPROJECT>(p, q, B, idx, m, alpha, beta, add, out, st);
-}
-
-#define SKEI_TILE_INST(TI, TA, TO)                                                           \
-  template int launch_proj_adj<TI, TA, TO>(skei_plan, const TI *, int, const int *, int,     \
-                                           float, float, const TA *, TO *, cudaStream_t);    \
-  template int launch_backproject<TI, TA, TO>(skei_plan, const TI *, int, const int *, int,  \
-                                              float, float, const TA *, TO *, cudaStream_t);
-SKEI_TILE_INST(float, float, float)
-SKEI_TILE_INST(__nv_bfloat16, __nv_bfloat16, __nv_bfloat16)
-SKEI_TILE_INST(float, __nv_bfloat16, float)
-SKEI_TILE_INST(float, __nv_bfloat16, __nv_bfloat16)
-#undef SKEI_TILE_INST
 
 }  // namespace skei

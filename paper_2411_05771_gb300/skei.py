@@ -18,7 +18,8 @@ from . import build as _build
 
 __all__ = [
     "F32", "BF16", "Plan", "last_error", "version",
-    "proj_fwd", "proj_adj", "filter", "backproject", "backproject_adj",
+    "proj_fwd", "proj_adj", "proj_fwd_multi", "proj_adj_multi", "Job",
+    "filter", "backproject", "backproject_adj",
     "fbp_workspace_size", "fbp", "fbp_adj", "fbp_noalloc", "rotate", "rotate_adj",
     "ei_workspace_size", "ei_loss_fwd", "ei_loss_finish", "ei_loss_bwd",
     "residual_add", "adam_step", "library_path",
@@ -36,6 +37,15 @@ _lib = ctypes.CDLL(library_path)
 _vp, _i, _f, _d, _sz, _i64 = (ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_double,
                               ctypes.c_size_t, ctypes.c_int64)
 _PLAN = ctypes.c_void_p
+
+
+class _Job(ctypes.Structure):
+    _fields_ = [("dtype_in", ctypes.c_int), ("dtype_aux", ctypes.c_int),
+                ("dtype_out", ctypes.c_int), ("in_", ctypes.c_void_p), ("aux", ctypes.c_void_p),
+                ("out", ctypes.c_void_p), ("idx", ctypes.c_void_p), ("m", ctypes.c_int),
+                ("B", ctypes.c_int), ("alpha", ctypes.c_float), ("beta", ctypes.c_float)]
+
+
 _SIGS = {
     "skei_version": ([], _i),
     "skei_last_error": ([], ctypes.c_char_p),
@@ -46,6 +56,8 @@ _SIGS = {
     "skei_proj_fwd": ([_PLAN, _i, _vp, _i, _vp, _i, _vp, _vp, _vp], _i),
     "skei_proj_adj": ([_PLAN, _i, _vp, _i, _vp, _i, _f, _f, _vp, _vp], _i),
     "skei_filter": ([_PLAN, _i, _vp, _i, _f, _vp, _vp], _i),
+    "skei_proj_fwd_multi": ([_PLAN, ctypes.POINTER(_Job), _i, _vp], _i),
+    "skei_proj_adj_multi": ([_PLAN, ctypes.POINTER(_Job), _i, _vp], _i),
     "skei_backproject": ([_PLAN, _i, _vp, _i, _vp, _i, _f, _f, _vp, _vp], _i),
     "skei_backproject_adj": ([_PLAN, _i, _vp, _i, _vp, _i, _f, _vp, _vp], _i),
     "skei_fbp_workspace_size": ([_PLAN, _i, _i, _i], _sz),
@@ -55,6 +67,7 @@ _SIGS = {
     "skei_rotate": ([_i, _vp, _i, _i, _vp, _i, _vp, _vp], _i),
     "skei_rotate_adj": ([_i, _vp, _i, _i, _vp, _i, _f, _f, _vp, _vp], _i),
     "skei_ei_workspace_size": ([_PLAN, _i, _i, _i, _i, _i], _sz),
+    "skei_ei_finish_workspace_size": ([_i, _i, _i, _i], _sz),
     "skei_ei_loss_fwd": ([_PLAN, _i, _vp, _vp, _i, _vp, _i, _vp, _i, _vp, _i, _vp, _vp, _vp,
                           _vp, _sz, _vp], _i),
     "skei_ei_loss_finish": ([_i, _vp, _vp, _vp, _i, _i, _i, _i, _d, _d, _vp, _vp, _vp, _vp,
@@ -192,6 +205,49 @@ def proj_adj(plan: Plan, sino, idx=None, alpha=1.0, beta=0.0, out=None) -> torch
     _check(_lib.skei_proj_adj(plan.handle, _dtype_code(sino), _ptr(sino), B, ip, m, float(alpha),
                               float(beta), _ptr(out), _stream()), "skei_proj_adj")
     return out
+
+
+class Job:
+    """One image set of a batched projector launch (see skei_job)."""
+
+    def __init__(self, inp, out, idx=None, aux=None, alpha=1.0, beta=0.0):
+        self.inp, self.out, self.idx, self.aux = inp, out, idx, aux
+        self.alpha, self.beta = alpha, beta
+
+
+def _jobs(plan: Plan, jobs, fwd: bool):
+    arr = (_Job * len(jobs))()
+    for q, jb in enumerate(jobs):
+        _dev(jb.inp, "job.inp")
+        _dev(jb.out, "job.out")
+        ip, m = _idx(plan, jb.idx)
+        use_aux = jb.aux is not None
+        if use_aux:
+            _dev(jb.aux, "job.aux")
+        B = jb.inp.shape[0]
+        if fwd:
+            if tuple(jb.inp.shape) != (B, plan.N, plan.N) or tuple(jb.out.shape) != (B, m, plan.n_det):
+                raise ValueError("job shapes: in [B,N,N], out [B,m,n_det]")
+        else:
+            if tuple(jb.inp.shape) != (B, m, plan.n_det) or tuple(jb.out.shape) != (B, plan.N, plan.N):
+                raise ValueError("job shapes: in [B,m,n_det], out [B,N,N]")
+        arr[q] = _Job(_dtype_code(jb.inp), _dtype_code(jb.aux) if use_aux else 0,
+                      _dtype_code(jb.out), jb.inp.data_ptr(),
+                      jb.aux.data_ptr() if use_aux else None, jb.out.data_ptr(),
+                      ip.value if ip is not None else None, m, B, float(jb.alpha), float(jb.beta))
+    return arr
+
+
+def proj_fwd_multi(plan: Plan, jobs) -> None:
+    """Several A_S (or S y - A_S x) applications in one launch."""
+    arr = _jobs(plan, jobs, True)
+    _check(_lib.skei_proj_fwd_multi(plan.handle, arr, len(jobs), _stream()), "skei_proj_fwd_multi")
+
+
+def proj_adj_multi(plan: Plan, jobs) -> None:
+    """Several alpha A_S^T in + beta aux applications in one launch."""
+    arr = _jobs(plan, jobs, False)
+    _check(_lib.skei_proj_adj_multi(plan.handle, arr, len(jobs), _stream()), "skei_proj_adj_multi")
 
 
 def filter(plan: Plan, p, scale=1.0, out=None) -> torch.Tensor:  # noqa: A001
@@ -367,8 +423,7 @@ def ei_loss_finish(x2, x3, r, lam: float, mc_scale: float, want_grads=True, work
                torch.empty_like(x2) if want_grads else None,
                torch.empty_like(x2) if want_grads else None)
     loss, mc, ei, g_x2, g_x3 = out
-    chunks = B * G * -(-N * N // 8192) + B * -(-r_len // 8192)
-    nb = ((chunks * 8) + 255) // 256 * 256
+    nb = int(_lib.skei_ei_finish_workspace_size(B, G, N, r_len))
     w = _work(nb, dev, work)
     _check(_lib.skei_ei_loss_finish(_dtype_code(x2), _ptr(x2), _ptr(x3), _ptr(r), B, G, N, r_len,
                                     float(lam), float(mc_scale), _ptr(mc), _ptr(ei), _ptr(loss),
