@@ -39,7 +39,8 @@ UNIT = "steps/s"
 # workload
 N_IMG, N_VIEWS, SKETCH, G_ROT, BATCH = 512, 60, 30, 4, 1
 LAM, LR = 1.0, 5e-4
-PSNR_ITERS = 200
+PSNR_ITERS = 1000          # iterations of each arm's PSNR trajectory
+PSNR_REF_ITERS = 200       # the TTT run length of the equal-PSNR comparison
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -53,6 +54,9 @@ def parse():
                     help="storage type of the sketched arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=0, help="oracle steps (0 = auto, ~15 s)")
+    ap.add_argument("--profile", action="store_true",
+                    help="set up the sketched arm, run one warm and one more step, and exit "
+                         "(a short, untimed run for ncu: 2 launches of set-up, then 13 per step)")
     return ap.parse_args()
 
 
@@ -148,19 +152,61 @@ class Arm:
         self.v1.zero_()
 
 
-def run_psnr(arm, x_gt, iters):
-    """Algorithm 2 for `iters` iterations from theta = 0; PSNR of F(x0)."""
+def psnr_curve(arm, x_gt, iters, every=25):
+    """Algorithm 2 for `iters` iterations from theta = 0; PSNR of F(x0) =
+    x0 + theta against the phantom every `every` iterations (untimed)."""
     import torch
     arm.reset()
     idx_all, g_all = step_params(iters, arm.sketched)
-    for s in range(iters):
+    rngv = float(x_gt.max() - x_gt.min())
+    curve = {}
+    for s in range(iters + 1):
+        if s % every == 0:
+            torch.cuda.synchronize()
+            rec = (arm.x0.double() + arm.theta.double()).cpu().numpy()[0]
+            curve[s] = 10 * np.log10(rngv * rngv / float(np.mean((rec - x_gt) ** 2)))
+        if s == iters:
+            break
         arm.load_params(idx_all[s], g_all[s], s + 1)
         arm.step()
-    torch.cuda.synchronize()
-    rec = (arm.x0.double() + arm.theta.double()).cpu().numpy()[0]
-    mse = float(np.mean((rec - x_gt) ** 2))
-    rngv = float(x_gt.max() - x_gt.min())
-    return 10 * np.log10(rngv * rngv / mse)
+    return curve
+
+
+def psnr_block(c_sk, c_pl, ms_sk, ms_pl):
+    """Equal-PSNR comparison: the sketched arm's time to reach the plain
+    arm's PSNR after PSNR_REF_ITERS iterations, and to reach the plain arm's
+    best PSNR over the whole trajectory."""
+    ref = c_pl[PSNR_REF_ITERS]
+    best_it = max(c_pl, key=c_pl.get)
+    best = c_pl[best_it]
+    out = {"iters_run": PSNR_ITERS, "fbp_x0": c_pl[0],
+           "at_ref_iters": {"iters": PSNR_REF_ITERS, "plain": ref, "sketched": c_sk[PSNR_REF_ITERS],
+                            "delta_db": c_sk[PSNR_REF_ITERS] - ref},
+           "plain_best": {"psnr": best, "iters": best_it},
+           "sketched_final": c_sk[max(c_sk)]}
+    for key, target, it_pl in (("to_plain_ref", ref, PSNR_REF_ITERS), ("to_plain_best", best, best_it)):
+        it_sk = iters_to_reach(c_sk, target)
+        if it_sk is None:
+            out[key] = {"target_db": target, "sketched_iters": None}
+            continue
+        t_pl, t_sk = it_pl * ms_pl, it_sk * ms_sk
+        out[key] = {"target_db": target, "plain_iters": it_pl, "sketched_iters": it_sk,
+                    "plain_ms": t_pl, "sketched_ms": t_sk, "speedup": t_pl / t_sk}
+    out["curve_every_100"] = {"plain": {k: round(v, 3) for k, v in c_pl.items() if k % 100 == 0},
+                              "sketched": {k: round(v, 3) for k, v in c_sk.items() if k % 100 == 0}}
+    return out
+
+
+def iters_to_reach(curve, target):
+    """First iteration (linearly interpolated between samples) at which the
+    curve reaches `target`, or None."""
+    its = sorted(curve)
+    for a, b in zip(its, its[1:]):
+        if curve[a] >= target:
+            return float(a)
+        if curve[b] >= target:
+            return a + (b - a) * (target - curve[a]) / (curve[b] - curve[a])
+    return None
 
 
 class Clocks:
@@ -290,6 +336,76 @@ def joseph_samples(plan, n_img, m_angles_idx):
     return total * n_img
 
 
+FLOPS_PER_SAMPLE = 7  # position, fraction, lerp (sub + fma), accumulate
+
+
+def pixel_angles(plan, n_img, n_ang):
+    return n_img * plan.N * plan.N * n_ang
+
+
+def algorithmic_flops(plan, arm, name):
+    """FP32 flops a kernel of the step must do at the least: 7 per nonzero
+    of its operator (Joseph crossings inside the image for A and A^T; pixel
+    x angle for B and B^T), 3 per (output, odd tap) pair for the filter."""
+    idx = arm.idx.cpu().numpy()
+    m = len(idx)
+    BG = BATCH * G_ROT
+    if name.startswith("joseph"):
+        return FLOPS_PER_SAMPLE * (joseph_samples(plan, BATCH, idx)
+                                   + joseph_samples(plan, BG, idx))
+    if name.startswith("backproject"):
+        return FLOPS_PER_SAMPLE * pixel_angles(plan, BG, m)
+    if name.startswith("ramlak"):
+        nd = plan.n_det
+        return 3.0 * BG * m * nd * (nd // 2)
+    return None
+
+
+def csrc_digest():
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2411_05771_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None if the kernels have changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    digest = csrc_digest()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) == 3 and parts[0] == kernel and parts[2] == digest:
+            return float(parts[1])
+    return None
+
+
+def roofline_entry(plan, arm, bd, dom, dev):
+    import torch
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    work = algorithmic_flops(plan, arm, dom)
+    if not work:
+        return {"bound": "hbm", "kernel": dom, "achieved": None, "peak": peaks.get("hbm_gbs"),
+                "unit": "GB/s", "frac": None, "traffic": measured_traffic(dom)}
+    peak = sm_count * 128 * 2 * max_mhz * 1e6 / 1e12
+    achieved = work / (bd[dom] * 1e-6) / 1e12
+    return {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": measured_traffic(dom),
+            "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 flop x {max_mhz:.0f} MHz",
+            "work": f"{FLOPS_PER_SAMPLE} flop per operator nonzero", "launch_us": bd[dom]}
+
+
 def cpu_oracle_steps(prob, n_steps, sketched):
     """The FP64 oracle (single-threaded C loops + numpy) on the same step."""
     import oracle as O
@@ -358,17 +474,19 @@ def main():
 
     prob = make_problem()
     plan = S.Plan(N_IMG, N_VIEWS, prob["angs"])
+    if args.profile:
+        arm = Arm(S, plan, prob, True, args.dtype, dev)
+        arm.step()
+        arm.step()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_run": "ok", "launches": 2 + 2 * Arm.launches_per_step}))
+        return
     sk = Arm(S, plan, prob, True, args.dtype, dev)
     pl = Arm(S, plan, prob, False, "f32", dev)
 
     # reconstruction quality: both arms, same start, same draws
-    psnr_fbp = None
-    psnr_sk = run_psnr(sk, prob["x_gt"], PSNR_ITERS)
-    psnr_pl = run_psnr(pl, prob["x_gt"], PSNR_ITERS)
-    rec0 = sk.x0.double().cpu().numpy()[0]
-    mse0 = float(np.mean((rec0 - prob["x_gt"]) ** 2))
-    rng_gt = float(prob["x_gt"].max() - prob["x_gt"].min())
-    psnr_fbp = 10 * np.log10(rng_gt ** 2 / mse0)
+    curve_sk = psnr_curve(sk, prob["x_gt"], PSNR_ITERS)
+    curve_pl = psnr_curve(pl, prob["x_gt"], PSNR_ITERS)
 
     K, W = args.steps, max(args.warmup, 3)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -376,7 +494,7 @@ def main():
 
     def timed(arm, use_graph):
         arm.reset()
-        idx_all, g_all = step_params(W + K, arm.sketched, first=PSNR_ITERS)
+        idx_all, g_all = step_params(W + K, arm.sketched, first=PSNR_ITERS + 1)
         with torch.cuda.stream(stream):
             graph = None
             if use_graph:
@@ -433,7 +551,7 @@ def main():
     if sk.tdt != torch.float32:
         host_y = host_y.to(sk.tdt).pin_memory()
     host_loss = torch.empty(1, dtype=torch.float64).pin_memory()
-    idx_all, g_all = step_params(K, True, first=PSNR_ITERS + W + K)
+    idx_all, g_all = step_params(K, True, first=PSNR_ITERS + 1 + W + K)
     h_idx = torch.from_numpy(idx_all).pin_memory()
     h_g = torch.from_numpy(g_all).pin_memory()
     h_step = torch.arange(1, K + 1, dtype=torch.int32).pin_memory()
@@ -462,28 +580,12 @@ def main():
     # per-kernel device times and the roofline of the dominant kernel
     bd = kernel_breakdown(S, sk, stream)
     dom = max(bd, key=bd.get)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak_tflops = sm_count * 128 * 2 * max_mhz * 1e6 / 1e12
-    idx_now = sk.idx.cpu().numpy()
-    if dom.startswith("joseph"):
-        # the fused launch projects x1 (MC angles) and the G rotated copies
-        work = 7.0 * (joseph_samples(plan, BATCH, idx_now)
-                      + joseph_samples(plan, BATCH * G_ROT, idx_now))
-    else:
-        work = None
-    roof = None
-    if work is not None:
-        achieved = work / (bd[dom] * 1e-6) / 1e12
-        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
-                "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {max_mhz:.0f} MHz",
-                "flops_per_sample": 7, "launch_us": bd[dom]}
+    roof = roofline_entry(plan, sk, bd, dom, dev)
+    kernels = {k: {"us": round(v, 2)} for k, v in bd.items()}
+    for k in kernels:
+        w = algorithmic_flops(plan, sk, k)
+        if w:
+            kernels[k]["tflops"] = round(w / (bd[k] * 1e-6) / 1e12, 3)
 
     total_ms = torch.tensor([sk_ms], dtype=torch.float64, device=dev)
     if world > 1:
@@ -517,13 +619,12 @@ def main():
                        "l2": "flushed between timed steps (256 MiB write, untimed)"},
             "plain": {"value": K / (pl_ms * 1e-3), "ms_per_step": pl_ms / K, "dtype": "f32"},
             "speedup_vs_plain": pl_ms / sk_ms,
-            "psnr": {"iters": PSNR_ITERS, "sketched": psnr_sk, "plain": psnr_pl,
-                     "delta_db": psnr_sk - psnr_pl, "fbp_x0": psnr_fbp},
+            "psnr": psnr_block(curve_sk, curve_pl, sk_ms / K, pl_ms / K),
             "e2e": {"value": K / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": Arm.launches_per_step * K,
             "roofline": roof,
-            "kernels_us": {k: round(v, 2) for k, v in bd.items()},
+            "kernels": kernels,
             "clocks": clk,
             "cpu_baseline": cpu,
             "wall_s_timed": sk_wall,

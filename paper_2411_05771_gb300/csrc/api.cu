@@ -28,7 +28,9 @@ __global__ void __launch_bounds__(kRedThreads)
                        double *partial) {
   __shared__ double red[kRedThreads / 32];
   const int blk = blockIdx.x;
-  double s = 0.0;
+  // each thread sums its few elements in FP32, the block adds the threads'
+  // sums in FP64 in a fixed order
+  float s = 0.0f;
   if (blk < n_imgseg * cpi) {
     const int seg = blk / cpi, ch = blk - seg * cpi;
     const int64_t base = (int64_t)seg * n_img;
@@ -43,7 +45,7 @@ __global__ void __launch_bounds__(kRedThreads)
       for (int64_t e4 = e0 / 4 + threadIdx.x; e4 < e1 / 4; e4 += kRedThreads) {
         const float4 a = __ldg(a4 + e4), c = __ldg(b4 + e4);
         const float4 d = make_float4(a.x - c.x, a.y - c.y, a.z - c.z, a.w - c.w);
-        s += (double)d.x * d.x + (double)d.y * d.y + (double)d.z * d.z + (double)d.w * d.w;
+        s = fmaf(d.x, d.x, fmaf(d.y, d.y, fmaf(d.z, d.z, fmaf(d.w, d.w, s))));
         if (g_x2) g2[e4] = make_float4(kappa * d.x, kappa * d.y, kappa * d.z, kappa * d.w);
         if (g_x3) g3[e4] = make_float4(-kappa * d.x, -kappa * d.y, -kappa * d.z, -kappa * d.w);
       }
@@ -51,7 +53,7 @@ __global__ void __launch_bounds__(kRedThreads)
     }
     for (; e < e1; e += kRedThreads) {
       const float d = ldg_f(x2 + base + e) - ldg_f(x3 + base + e);
-      s += (double)d * (double)d;
+      s = fmaf(d, d, s);
       if (g_x2) st_f(g_x2 + base + e, kappa * d);
       if (g_x3) st_f(g_x3 + base + e, -kappa * d);
     }
@@ -62,11 +64,12 @@ __global__ void __launch_bounds__(kRedThreads)
     const int64_t e0 = (int64_t)ch * kChunk, e1 = min(e0 + kChunk, r_len);
     for (int64_t e = e0 + threadIdx.x; e < e1; e += kRedThreads) {
       const float v = ldg_f(r + base + e);
-      s += (double)v * (double)v;
+      s = fmaf(v, v, s);
     }
   }
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  double sd = (double)s;
+  for (int o = 16; o > 0; o >>= 1) sd += __shfl_xor_sync(0xffffffffu, sd, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sd;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;

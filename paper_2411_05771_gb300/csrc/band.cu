@@ -41,7 +41,7 @@ struct BandGeom {
   int R;       // lines per band
   int SB;      // lines per staged sub-band
   int Prow;    // pitch of staged rows (multiple of 4: 16-byte aligned rows)
-  int Pcol;    // pitch of staged columns (= 2 mod 8: conflict-free transposed writes)
+  int Pcol;    // pitch of staged columns (conflict-free transposed writes)
   int AB;      // angles per cluster
   int C;       // OP_BP_ADJ: warps (partial rows) per angle = kWarps / AB
   int fast;    // N % 8 == 0: vectorised staging
@@ -87,11 +87,13 @@ __device__ __forceinline__ void stage(const void *x, size_t xo, int bf16, int N,
       }
     }
   } else {
-    if (fast && nl == 16 && (s0 & 3) == 0) {
-      // lane = 4 * (position within a group of 8) + quarter of the 16 lines;
-      // 4 consecutive lines of a column start 16-byte aligned (N % 8 == 0)
-      const int q = lane & 3;
-      for (int p = warp * 8 + (lane >> 2); p < N; p += kWarps * 8) {
+    if (fast && (nl == 16 || nl == 32) && (s0 & 3) == 0) {
+      // lane = (nl/4) * (position within a group) + quarter of the lines; 4
+      // consecutive lines of a column start 16-byte aligned (N % 8 == 0)
+      const int qn = nl >> 2, qs = nl == 16 ? 2 : 3;
+      const int q = lane & (qn - 1);
+      const int per_warp = 32 / qn;
+      for (int p = warp * per_warp + (lane >> qs); p < N; p += kWarps * per_warp) {
         const float4 v = load4(x, xo + (size_t)p * N + s0 + 4 * q, bf16);
         float *dst = buf + (4 * q) * P + kPad + p;
         dst[0] = v.x;
@@ -297,12 +299,16 @@ int launch_band(skei_plan p, const Jobs &jobs, cudaStream_t st) {
   g.n_angles = p->n_angles;
   g.R = (g.N + kBands - 1) / kBands;
   g.Prow = (g.N + 2 * kPad + 3) & ~3;
-  g.Pcol = ((g.N + 2 * kPad - 2 + 7) & ~7) + 2;
+  // A: 32 staged lines (fewer per-ray range setups); B^T: 16 (its per-bin
+  // work per line is larger, and the smaller band leaves room for more CTAs)
+  g.SB = min(g.R, OP == OP_JOSEPH ? 32 : 16);
+  // transposed staging writes lines 4q..4q+3 of (32 / (SB/4)) positions per
+  // warp: a pitch = 2 mod 8 (16 lines) or odd (32 lines) keeps them in
+  // distinct banks
+  g.Pcol = g.SB == 32 ? ((g.N + 2 * kPad) | 1) : ((g.N + 2 * kPad - 2 + 7) & ~7) + 2;
   g.fast = (g.N % 8 == 0) ? 1 : 0;
   const int Pmax = g.Prow > g.Pcol ? g.Prow : g.Pcol;
-  // 16 staged lines keep the band at ~33 KB for N = 512: several CTAs per SM
-  g.SB = min(g.R, 16);
-  while (g.SB > 1 && (size_t)g.SB * Pmax * 4 > 96 * 1024) --g.SB;
+  while (g.SB > 1 && (size_t)g.SB * Pmax * 4 > 96 * 1024) --g.SB;  // large N: slow staging
   const size_t band_bytes = (size_t)g.SB * Pmax * 4;
   int m_max = 0, nimg = 0;
   for (int q = 0; q < jobs.njobs; ++q) {

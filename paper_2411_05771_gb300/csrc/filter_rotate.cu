@@ -37,35 +37,93 @@ int ensure_ramlak_taps() {
 namespace {
 
 // ------------------------------------------------------------- Ram-Lak --
-// CTA (row, chunk): the row sits in shared memory between n_det zeros on
-// each side; thread t forms output k = chunk*128 + t as
-//   q[k] = scale (h0 p[k] + sum_{n odd} h(n) (p[k-n] + p[k+n])),
-// the even taps of the Ram-Lak kernel being zero.
-constexpr int kFilterThreads = 128;
+// One CTA per sinogram row; the row sits in shared memory between zero
+// margins.  Only odd taps are nonzero besides h(0), so an output k needs
+// p[k -+ n] for odd n; a thread owns the 4 same-parity outputs
+// k0, k0+2, k0+4, k0+6 and slides one window of 4 left and 4 right inputs
+// from tap n to n+2: two shared loads serve 4 output-taps.  The taps are
+// split into kSeg segments handled by different warps (short dependency
+// chains, 4x the warps), whose partial sums are added in a fixed order.
+// Shared memory is skewed (one pad word per 8) so the lanes' loads hit
+// distinct banks.
+//   q[k] = scale (h0 p[k] + sum_{n odd} h(n) (p[k-n] + p[k+n]))
+constexpr int kSeg = 4;                        // tap segments
+constexpr int kGroupWarps = 6;                 // 6 warps x 128 outputs per pass
+constexpr int kFilterThreads = 32 * kGroupWarps * kSeg;
+constexpr int kFilterOuts = 4 * 32 * kGroupWarps;
+
+__host__ __device__ constexpr int skew(int e) { return e + (e >> 3); }
 
 template <typename Tin, typename Tout>
 __global__ void __launch_bounds__(kFilterThreads)
     ramlak_kernel(const Tin *in, Tout *out, int nd, float scale) {
   extern __shared__ float4 smem4[];
-  float *pb = reinterpret_cast<float *>(smem4);  // [3 nd]
+  float *red = reinterpret_cast<float *>(smem4);        // [kSeg][kFilterOuts]
+  float *pb = red + kSeg * kFilterOuts;
+  // zero margins: before the row, the farthest left tap (n <= nd-1, plus the
+  // window's 2 extra); after it, the last pass's outputs (rounded up to
+  // kFilterOuts) plus the farthest right tap
+  const int lp = nd + 8;
+  const int len = lp + ((nd + kFilterOuts - 1) / kFilterOuts) * kFilterOuts + nd + 16;
   const size_t row = blockIdx.x;
   const Tin *pr = in + row * nd;
-  for (int e = threadIdx.x; e < 3 * nd; e += kFilterThreads) {
-    const int k = e - nd;
-    pb[e] = (k >= 0 && k < nd) ? ldg_f(pr + k) : 0.0f;
+  for (int e = threadIdx.x; e < len; e += kFilterThreads) {
+    const int k = e - lp;
+    pb[skew(e)] = (k >= 0 && k < nd) ? ldg_f(pr + k) : 0.0f;
   }
-  __syncthreads();
-  const int k = blockIdx.y * kFilterThreads + threadIdx.x;
-  if (k >= nd) return;
-  const float *pc = pb + nd + k;
-  float acc0 = c_ramlak[0] * pc[0], acc1 = 0.0f;
-  int n = 1;
-  for (; n + 2 < nd; n += 4) {
-    acc0 = fmaf(c_ramlak[n], pc[-n] + pc[n], acc0);
-    acc1 = fmaf(c_ramlak[n + 2], pc[-n - 2] + pc[n + 2], acc1);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gw = warp % kGroupWarps, seg = warp / kGroupWarps;
+  // odd taps 1, 3, ..., n_last, split into kSeg runs of whole 4-tap groups
+  const int n_odd = nd / 2;                       // number of odd n < nd
+  const int groups = (n_odd + 3) / 4;
+  const int g0 = (groups * seg) / kSeg, g1 = (groups * (seg + 1)) / kSeg;
+  for (int kb = 0; kb < nd; kb += kFilterOuts) {
+    __syncthreads();                              // staging done / red reusable
+    const int ko = gw * 128 + 8 * (lane >> 1) + (lane & 1);   // offset in the pass
+    const int e0 = lp + kb + ko;
+    float acc[4], L[4], R[4];
+    const int nfirst = 1 + 8 * g0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      acc[j] = (seg == 0) ? c_ramlak[0] * pb[skew(e0 + 2 * j)] : 0.0f;
+      L[j] = pb[skew(e0 + 2 * j - nfirst)];
+      R[j] = pb[skew(e0 + 2 * j + nfirst)];
+    }
+    // skewed addresses of the next left / right loads, per tap t = 0..3 of a
+    // group; a group moves them by -8 / +8 elements, i.e. -9 / +9 words
+    int aL[4], aR[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      aL[t] = skew(e0 - (nfirst + 2 * t) - 2);
+      aR[t] = skew(e0 + 6 + (nfirst + 2 * t) + 2);
+    }
+    for (int gi = g0; gi < g1; ++gi) {
+      const int n0 = 1 + 8 * gi;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int n = n0 + 2 * t;
+        const float h = n < nd ? c_ramlak[n] : 0.0f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[j] = fmaf(h, L[j] + R[j], acc[j]);
+        const float l_new = pb[aL[t]], r_new = pb[aR[t]];
+        aL[t] -= 9;
+        aR[t] += 9;
+        L[3] = L[2]; L[2] = L[1]; L[1] = L[0]; L[0] = l_new;
+        R[0] = R[1]; R[1] = R[2]; R[2] = R[3]; R[3] = r_new;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) red[seg * kFilterOuts + ko + 2 * j] = acc[j];
+    __syncthreads();
+    for (int o = threadIdx.x; o < kFilterOuts; o += kFilterThreads) {
+      const int k = kb + o;
+      if (k >= nd) continue;
+      float v = red[o];
+#pragma unroll
+      for (int sg = 1; sg < kSeg; ++sg) v += red[sg * kFilterOuts + o];
+      st_f(out + row * nd + k, scale * v);
+    }
   }
-  for (; n < nd; n += 2) acc0 = fmaf(c_ramlak[n], pc[-n] + pc[n], acc0);
-  st_f(out + row * nd + k, scale * (acc0 + acc1));
 }
 
 // ------------------------------------------------------------ rotation --
@@ -158,22 +216,26 @@ __global__ void __launch_bounds__(kAdjT *kAdjT)
         const float dc = (float)bb - r.C0f, dr = (float)a - r.R0f;
         const int ri = round_int(fmaf(-r.sf, dc, r.cf * dr));
         const int rj = round_int(fmaf(r.cf, dc, r.sf * dr));
-        // candidate (ri-1, rj-1); i steps add (c, -s), j steps add (s, c)
-        const long long row0 = r.R0 + (long long)(rj - 1) * r.s + (long long)(ri - 1) * r.c;
-        const long long col0 = r.C0 + (long long)(rj - 1) * r.c - (long long)(ri - 1) * r.s;
+        // exact offsets of candidate (ri-1, rj-1)'s sample from (a, bb); an
+        // i step adds (c, -s), a j step (s, c); all within a few pixels, so
+        // exact in 32-bit wrapping arithmetic on the low words
+        const unsigned c32 = (unsigned)r.c, s32 = (unsigned)r.s;
+        const unsigned dr0 = (unsigned)(r.R0 + (long long)(rj - 1) * r.s +
+                                        (long long)(ri - 1) * r.c) - ((unsigned)a << kFxBits);
+        const unsigned dc0 = (unsigned)(r.C0 + (long long)(rj - 1) * r.c -
+                                        (long long)(ri - 1) * r.s) - ((unsigned)bb << kFxBits);
         float s = acc[q];
 #pragma unroll
         for (int di = 0; di < 3; ++di) {
           const int i = ri - 1 + di;
-          if (i < 0 || i >= N) continue;
 #pragma unroll
           for (int dj = 0; dj < 3; ++dj) {
             const int j = rj - 1 + dj;
-            if (j < 0 || j >= N) continue;
-            const long long row = row0 + (long long)di * r.c + (long long)dj * r.s;
-            const long long col = col0 - (long long)di * r.s + (long long)dj * r.c;
-            const float w = tap_weight(row, a) * tap_weight(col, bb);
-            if (w != 0.0f) s = fmaf(w, ldg_f(gb + (size_t)i * N + j), s);
+            const int Dr = (int)(dr0 + di * c32 + dj * s32);
+            const int Dc = (int)(dc0 - di * s32 + dj * c32);
+            const int wr = tap_w23(Dr), wc = tap_w23(Dc);
+            if ((wr != 0) & (wc != 0) & (i >= 0) & (i < N) & (j >= 0) & (j < N))
+              s = fmaf(w23_to_float(wr) * w23_to_float(wc), ldg_f(gb + (size_t)i * N + j), s);
           }
         }
         acc[q] = s;
@@ -198,7 +260,8 @@ template <typename Tin, typename Tout>
 int launch_filter(skei_plan p, const Tin *in, int rows, float scale, Tout *out,
                   cudaStream_t st) {
   const int nd = p->n_det;
-  const size_t smem = (size_t)3 * nd * sizeof(float);
+  const int len = (nd + 8) + ((nd + kFilterOuts - 1) / kFilterOuts) * kFilterOuts + nd + 16;
+  const size_t smem = (size_t)(kSeg * kFilterOuts + skew(len + 16) + 1) * sizeof(float);
   auto kern = ramlak_kernel<Tin, Tout>;
   static size_t configured = 0;
   if (smem > 48 * 1024 && smem > configured) {
@@ -207,8 +270,7 @@ int launch_filter(skei_plan p, const Tin *in, int rows, float scale, Tout *out,
     if (e != cudaSuccess) return cuda_error(e, "ramlak: shared memory attribute");
     configured = smem;
   }
-  dim3 grid(rows, (nd + kFilterThreads - 1) / kFilterThreads);
-  kern<<<grid, kFilterThreads, smem, st>>>(in, out, nd, scale);
+  kern<<<rows, kFilterThreads, smem, st>>>(in, out, nd, scale);
   return check_launch("ramlak filter launch");
 }
 

@@ -1,9 +1,9 @@
-// Pixel-driven gathers over 8 x 128 image tiles: the exact transpose A_S^T
+// Pixel-driven gathers over 8 x 256 image tiles: the exact transpose A_S^T
 // of Joseph's projector (the gradient of the MC and EI terms, Algorithm 2)
 // and the back-projection B_S of FBP (A_S^dagger = (pi/m) B_S H, Sec. 2.1
 // and 3.1).
 //
-// A CTA owns one tile of one image (one warp per tile row, 4 consecutive
+// A CTA owns one tile of one image (one warp per tile row, 8 consecutive
 // pixels per thread) and walks the angle list in chunks; for each angle it
 // stages in shared memory only the window of detector bins the tile projects
 // onto.  Every thread accumulates its 4 pixels in registers and writes each
@@ -24,11 +24,11 @@
 namespace skei {
 namespace {
 
-constexpr int kTW = 128;                 // tile width (columns)
+constexpr int kPPT = 8;                  // consecutive pixels per thread
+constexpr int kTW = 32 * kPPT;           // tile width (columns)
 constexpr int kTH = 8;                   // tile height (rows) = warps per CTA
-constexpr int kPPT = 4;                  // consecutive pixels per thread
 constexpr int kThreads = 32 * kTH;
-constexpr int kWin = 192;                // staged bins per angle
+constexpr int kWin = 288;                // staged bins per angle (>= kTW + kTH + 6)
 constexpr int kAC = 8;                   // angles per chunk
 
 struct TileArgs {
@@ -38,13 +38,15 @@ struct TileArgs {
   int *status;
 };
 
-// Stores up to 4 consecutive pixels at element offset o.
-__device__ __forceinline__ void store4(void *out, size_t o, const float *v, int n_valid,
-                                       int bf16) {
+// Stores up to kPPT consecutive pixels at element offset o.
+__device__ __forceinline__ void store_run(void *out, size_t o, const float *v, int n_valid,
+                                          int bf16) {
   if (!bf16) {
     float *p = static_cast<float *>(out) + o;
-    if (n_valid == 4 && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
-      *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    if (n_valid == kPPT && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+#pragma unroll
+      for (int q = 0; q < kPPT; q += 4)
+        *reinterpret_cast<float4 *>(p + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
       return;
     }
   }
@@ -124,27 +126,31 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs args) {
       const int base = kw0[a];
       if (OP == OP_JOSEPH_ADJ) {
         const bool row = C.mode != 0;
-        const unsigned A32 = (unsigned)C.A;
-        const int absA32 = (int)(unsigned)(C.A < 0 ? -C.A : C.A);
-        const int sA = C.A < 0 ? -1 : 1;
+        const long long A = C.A, T = C.T, G = C.G;
+        const unsigned A32 = (unsigned)A;
+        const int absA32 = (int)(unsigned)(A < 0 ? -A : A);
+        const int sA = A < 0 ? -1 : 1;
+        const float Tf = C.Tf, Gf = C.Gf, invA = C.invA;
         // u = P - G - L T for the first pixel (low word; exact modulo 2^32);
         // per step along the row, row mode (P = j) adds 1, column mode
         // (L = j) subtracts T
         const int L0 = row ? i : jb, P0 = row ? jb : i;
-        unsigned u = (unsigned)(((long long)P0 << kFxBits) - C.G - (long long)L0 * C.T);
-        const unsigned du = row ? (unsigned)kFxOne : (unsigned)(-C.T);
-        float kc = ((float)P0 - fmaf((float)L0, C.Tf, C.Gf)) * C.invA;
-        const float dkc = row ? C.invA : -C.Tf * C.invA;
+        unsigned u = (unsigned)(((long long)P0 << kFxBits) - G - (long long)L0 * T);
+        const unsigned du = row ? (unsigned)kFxOne : (unsigned)(-T);
+        float kc = ((float)P0 - fmaf((float)L0, Tf, Gf)) * invA;
+        const float dkc = row ? invA : -Tf * invA;
 #pragma unroll
         for (int q = 0; q < kPPT; ++q) {
           const int r = round_int(kc);
           const int D = (int)((unsigned)r * A32 - u);   // pos(L, r) - P, in (-1, 1)
           const bool right = D >= 0;                     // r is the "1-f" ray
           const int D2 = right ? D - absA32 : D + absA32;
-          const int w1 = tap_w23(D), w2 = tap_w23(D2);
-          const int r2 = right ? r - sA : r + sA;
-          const unsigned s1 = min((unsigned)(r - base), (unsigned)(kWin - 1));
-          const unsigned s2 = min((unsigned)(r2 - base), (unsigned)(kWin - 1));
+          // window slots; the tile's bins lie inside the window by
+          // construction, the clamp only bounds the read
+          const int s1 = min(max(r - base, 1), kWin - 2);
+          const int s2 = s1 + (right ? -sA : sA);
+          const int w1 = (1 << 23) - abs(D >> (kFxBits - 23));   // |D| < 1: no clamp
+          const int w2 = tap_w23(D2);
           acc[q] = fmaf(w23_to_float(w1), wa[s1], fmaf(w23_to_float(w2), wa[s2], acc[q]));
           u += du;
           kc += dkc;
@@ -176,7 +182,7 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs args) {
     if (J.beta != 0.0f && J.aux && q < n_valid)
       v[q] = fmaf(J.beta, ld_any(J.aux, o + q, J.aux_bf16), v[q]);
   }
-  store4(J.out, o, v, n_valid, J.out_bf16);
+  store_run(J.out, o, v, n_valid, J.out_bf16);
 }
 
 template <int OP>
