@@ -268,6 +268,12 @@ def kernel_breakdown(S, arm, stream, reps=20):
     pbuf = torch.empty((BG, m, p.n_det), **f32)
     qbuf = torch.empty_like(pbuf)
     gtot = torch.empty((BATCH, G_ROT, N_IMG, N_IMG), **f32)
+    # the public calls want one storage type per call, where the step's own
+    # launches mix BF16 images with FP32 sinogram buffers: with BF16 storage
+    # these stand-ins read BF16 copies instead
+    q_t = qbuf if arm.tdt == torch.float32 else qbuf.to(arm.tdt)
+    p_t = pbuf if arm.tdt == torch.float32 else pbuf.to(arm.tdt)
+    gtot_t = gtot if arm.tdt == torch.float32 else gtot.to(arm.tdt)
     x2 = arm.x2.reshape(BG, N_IMG, N_IMG)
     gx3 = arm.gx3.reshape(BG, N_IMG, N_IMG)
     gx2 = arm.gx2.reshape(BG, N_IMG, N_IMG)
@@ -278,19 +284,17 @@ def kernel_breakdown(S, arm, stream, reps=20):
         "joseph_fwd(MC+EI)": lambda: S.proj_fwd_multi(
             p, [S.Job(arm.x1, arm.r, mc_idx, aux=arm.y), S.Job(x2, pbuf, sk_idx)]),
         "ramlak(fwd)": lambda: S.filter(p, pbuf, np.pi / m, out=qbuf),
-        "backproject": lambda: S.backproject(p, qbuf.to(arm.tdt) if arm.tdt != torch.float32
-                                             else qbuf, sk_idx, out=z),
+        "backproject": lambda: S.backproject(p, q_t, sk_idx, out=z),
         "residual_add(x3)": lambda: S.residual_add(arm.z, arm.theta, out=arm.x3),
-        "loss_finish(2 kernels)": lambda: S.ei_loss_finish(
+        "loss_finish": lambda: S.ei_loss_finish(
             arm.x2, arm.x3, arm.r, LAM, arm.mc_scale, work=arm.work,
             out=(arm.loss, arm.mc, arm.ei, arm.gx2, arm.gx3)),
-        "backproject_adj": lambda: S.backproject_adj(p, gx3, sk_idx, out=pbuf),
+        "backproject_adj": lambda: S.backproject_adj(p, gx3, sk_idx, out=p_t),
         "ramlak(bwd)": lambda: S.filter(p, pbuf, np.pi / m, out=qbuf),
         "joseph_adj(MC+EI)": lambda: S.proj_adj_multi(
             p, [S.Job(arm.r, arm.gx1, mc_idx, alpha=-2.0 * arm.mc_scale / BATCH),
                 S.Job(qbuf, gtot.reshape(BG, N_IMG, N_IMG), sk_idx, aux=gx2, beta=1.0)]),
-        "rotate_adj": lambda: S.rotate_adj(gtot if arm.tdt == torch.float32 else gtot.to(arm.tdt),
-                                           arm.g, beta=1.0, out=arm.gx1),
+        "rotate_adj": lambda: S.rotate_adj(gtot_t, arm.g, beta=1.0, out=arm.gx1),
         "adam": lambda: S.adam_step(arm.theta, arm.m1, arm.v1, arm.step_no, arm.gx1, arm.gx3,
                                     lr=LR),
     }
