@@ -46,7 +46,8 @@
  *     the kernel zeroes that row and records the fault in the plan's status
  *     word (skei_plan_status).
  *   - the library owns only plan objects (angle tables on the device) and
- *     allocates nothing else; callers pass workspaces sized by the
+ *     batch objects (task lists, work queues, the batched FBP's workspace)
+ *     and allocates nothing else; callers pass workspaces sized by the
  *     *_workspace_size queries.
  *   - results do not depend on the stream or on the launch order of
  *     independent calls; calls that write the same buffer concurrently race.
@@ -290,6 +291,72 @@ int skei_adam_step(float *theta, int64_t n, int dtype, const void *g1, int c1,
                    const void *g2, int c2, float *m, float *v, const int *step,
                    double lr, double beta1, double beta2, double eps,
                    void *stream);
+
+/* ------------------------------------------------ batched schedule --
+ * One operator applied to many instances in one persistent launch per
+ * kernel: images of different sizes (each item its own plan), each with its
+ * own sketch S_k and its own storage type.  Eq. (e:skeiloss) and Algorithm 2
+ * draw a sketch per sample and step; a batch runs all of them at once.
+ *
+ *   SKEI_BATCH_PROJ_FWD        out = scale A_S in      in [B][N][N], out [B][m][n_det]
+ *   SKEI_BATCH_PROJ_ADJ        out = scale A_S^T in    in [B][m][n_det], out [B][N][N]
+ *   SKEI_BATCH_BACKPROJECT     out = scale B_S in      in [B][m][n_det], out [B][N][N]
+ *   SKEI_BATCH_BACKPROJECT_ADJ out = scale B_S^T in    in [B][N][N], out [B][m][n_det]
+ *   SKEI_BATCH_FILTER          out = scale H in        in, out [B][m][n_det]
+ *   SKEI_BATCH_FBP             out = scale (pi/m) B_S H in  (Sec. 2.1), two
+ *                              persistent launches (filter, back-projection)
+ *
+ * Results are bitwise equal to the single-instance entry points on the same
+ * item (each output element is computed by one task, in the same order).
+ *
+ * skei_batch_create validates every item (as the single-instance calls do)
+ * and uploads the task list; it allocates the task list, a 2-int work queue
+ * per launch and, for SKEI_BATCH_FBP, an FP32 workspace of sum(B m n_det)
+ * floats.  It synchronises (host-to-device copies).  The item pointers are
+ * baked into the batch: the buffers and plans must outlive it, and their
+ * contents may change between runs.
+ * skei_batch_run issues the launches on `stream` (asynchronous; it may be
+ * captured in a CUDA graph and replayed).  Runs of one batch must not
+ * overlap: each launch takes tasks from the batch's own work queue, which
+ * its last worker resets for the next run.
+ * skei_batch_tune(b, reps, stream) runs every candidate shape (angles per
+ * task 1..8 for A and B^T; 1..max resident CTAs per SM for the others)
+ * reps + 1 times on the items' own buffers (overwriting the outputs), times
+ * them with events on `stream`, and keeps the fastest.  It synchronises and
+ * returns SKEI_EINVAL inside a stream capture.
+ * skei_batch_info(b, phase, ...) reports launch `phase` (0, or 1 for the
+ * back-projection of SKEI_BATCH_FBP): the number of launches, tasks, workers
+ * (CTAs, or 8-CTA clusters for A and B^T) and the block (angles per task for
+ * A and B^T, CTAs per SM otherwise, 0 = all that fit).
+ */
+#define SKEI_BATCH_PROJ_FWD 0
+#define SKEI_BATCH_PROJ_ADJ 1
+#define SKEI_BATCH_BACKPROJECT 2
+#define SKEI_BATCH_BACKPROJECT_ADJ 3
+#define SKEI_BATCH_FILTER 4
+#define SKEI_BATCH_FBP 5
+#define SKEI_MAX_BATCH_ITEMS 65536
+
+typedef struct {
+  skei_plan plan;      /* geometry of this item; several items may share one */
+  int dtype_in;        /* SKEI_F32 / SKEI_BF16 storage of in */
+  int dtype_out;       /* ... of out */
+  const void *in;      /* device, layout per operator above */
+  void *out;           /* device, must not overlap another item's out */
+  const int *idx;      /* device int32[m] rows of the plan's angles, or NULL */
+  int m;               /* sketch size (n_angles when idx is NULL) */
+  int B;               /* images in this item */
+  float scale;         /* output scale (1 for the plain operator) */
+} skei_batch_item;
+
+typedef struct skei_batch_s *skei_batch;
+
+int skei_batch_create(int op, const skei_batch_item *items, int n_items, skei_batch *out);
+int skei_batch_run(skei_batch batch, void *stream);
+int skei_batch_tune(skei_batch batch, int reps, void *stream);
+int skei_batch_info(skei_batch batch, int phase, int *n_phases, int *n_tasks, int *workers,
+                    int *block);
+int skei_batch_destroy(skei_batch batch);
 
 #ifdef __cplusplus
 }

@@ -301,10 +301,6 @@ int ei_finish_impl(const T *x2, const T *x3, const T *r, int B, int G, int N, in
 }
 
 // --------------------------------------------------------- validation --
-#define SKEI_TRY(expr)                     \
-  do {                                     \
-    if (int rc_ = (expr)) return rc_;      \
-  } while (0)
 
 cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
 

@@ -54,6 +54,38 @@ struct BandArgs {
   BandGeom g;
 };
 
+// Staging geometry of one image size and operator with AB angles per task.
+__host__ __device__ __forceinline__ BandGeom band_geom(int N, int n_det, int n_angles, int op,
+                                                       int AB) {
+  BandGeom g;
+  g.N = N;
+  g.n_det = n_det;
+  g.n_angles = n_angles;
+  g.R = (N + kBands - 1) / kBands;
+  g.Prow = (N + 2 * kPad + 3) & ~3;
+  // A: 32 staged lines (fewer per-ray range setups); B^T: 16 (its per-bin
+  // work per line is larger, and the smaller band leaves room for more CTAs)
+  const int sb = op == OP_JOSEPH ? 32 : 16;
+  g.SB = g.R < sb ? g.R : sb;
+  // transposed staging writes lines 4q..4q+3 of (32 / (SB/4)) positions per
+  // warp: a pitch = 2 mod 8 (16 lines) or odd (32 lines) keeps them in
+  // distinct banks
+  g.Pcol = g.SB == 32 ? ((N + 2 * kPad) | 1) : ((N + 2 * kPad - 2 + 7) & ~7) + 2;
+  g.fast = (N % 8 == 0) ? 1 : 0;
+  const int Pmax = g.Prow > g.Pcol ? g.Prow : g.Pcol;
+  while (g.SB > 1 && g.SB * Pmax * 4 > 96 * 1024) --g.SB;  // large N: slow staging
+  g.AB = AB;
+  g.C = 1;
+  return g;
+}
+
+// Dynamic shared memory of a band task: AB rows of partial bins, then the
+// staged sub-band.
+inline size_t band_smem(const BandGeom &g) {
+  const int Pmax = g.Prow > g.Pcol ? g.Prow : g.Pcol;
+  return (size_t)g.SB * Pmax * 4 + (size_t)((g.AB * g.n_det + 3) & ~3) * 4;
+}
+
 // 4 consecutive image values at element offset i as floats (16-byte aligned
 // for float, 8-byte for bfloat16).
 __device__ __forceinline__ float4 load4(const void *x, size_t i, int bf16) {
@@ -194,24 +226,15 @@ __device__ __forceinline__ float bpadj_partial(const AngleConst &C, int k, int s
   return acc;
 }
 
+// One task: image b of job J, angles [a_begin, a_begin + g.AB) of its list,
+// computed by the 8 CTAs of this cluster.  Ends with a cluster barrier, after
+// which the CTA's shared memory may be reused.
 template <int OP>
-__global__ void __cluster_dims__(kBands, 1, 1) __launch_bounds__(kThreads)
-    band_kernel(const BandArgs args) {
-  extern __shared__ float4 smem4[];
-  float *smem = reinterpret_cast<float *>(smem4);
-  __shared__ AngleConst sc[kMaxAB];
-  __shared__ int sai[kMaxAB];
-
-  cg::cluster_group cluster = cg::this_cluster();
-  const BandGeom g = args.g;
-  const int tid = threadIdx.x, warp = tid >> 5;
+__device__ __forceinline__ void band_task(const Job &J, int b, int a_begin, const BandGeom &g,
+                                          const AngleConst *ang, int *status, float *smem,
+                                          AngleConst *sc, int *sai, cg::cluster_group &cluster) {
+  const int tid = threadIdx.x;
   const int band = (int)cluster.block_rank();
-  // the job and image of this cluster
-  const int z = blockIdx.z;
-  const int jn = (args.jobs.njobs > 1 && z >= args.jobs.j[0].nimg) ? 1 : 0;
-  const Job &J = args.jobs.j[jn];
-  const int b = z - (jn ? args.jobs.j[0].nimg : 0);
-  const int a_begin = blockIdx.y * g.AB;
   if (a_begin >= J.m) return;  // uniform over the cluster: no peer waits for it
   const int na = min(g.AB, J.m - a_begin);
   const int nd = g.n_det, N = g.N;
@@ -224,12 +247,12 @@ __global__ void __cluster_dims__(kBands, 1, 1) __launch_bounds__(kThreads)
     if (tid < na) {
       ai = J.idx ? J.idx[a_begin + tid] : a_begin + tid;
       if (ai < 0 || ai >= g.n_angles) {
-        if (band == 0) atomicOr(args.status, 1);
+        if (band == 0) atomicOr(status, 1);
         ai = -1;
       }
     }
     sai[tid] = ai;
-    if (ai >= 0) sc[tid] = args.ang[ai];
+    if (ai >= 0) sc[tid] = ang[ai];
   }
   for (int e = tid; e < nrows * nd; e += kThreads) part[e] = 0.0f;
   __syncthreads();
@@ -270,12 +293,60 @@ __global__ void __cluster_dims__(kBands, 1, 1) __launch_bounds__(kThreads)
     } else if (OP == OP_JOSEPH) {
       v = s * sc[a].W;
       if (J.aux) v = ld_any(J.aux, ((size_t)b * g.n_angles + ai) * nd + k, J.aux_bf16) - v;
+      v *= J.alpha;
     } else {
       v = s * J.alpha;
     }
     st_any(J.out, o, v, J.out_bf16);
   }
   cluster.sync();  // keep this CTA's partials alive until every peer has read them
+}
+
+template <int OP>
+__global__ void __cluster_dims__(kBands, 1, 1) __launch_bounds__(kThreads)
+    band_kernel(const BandArgs args) {
+  extern __shared__ float4 smem4[];
+  __shared__ AngleConst sc[kMaxAB];
+  __shared__ int sai[kMaxAB];
+  cg::cluster_group cluster = cg::this_cluster();
+  // the job and image of this cluster
+  const int z = blockIdx.z;
+  const int jn = (args.jobs.njobs > 1 && z >= args.jobs.j[0].nimg) ? 1 : 0;
+  const Job &J = args.jobs.j[jn];
+  const int b = z - (jn ? args.jobs.j[0].nimg : 0);
+  band_task<OP>(J, b, blockIdx.y * args.g.AB, args.g, args.ang, args.status,
+                reinterpret_cast<float *>(smem4), sc, sai, cluster);
+}
+
+// Persistent form over the tasks of a batch of instances (plans of their
+// own): each cluster takes the next task from a global counter (tasks come
+// in decreasing cost order) until none is left; the last cluster to finish
+// resets the counter for the next launch.
+template <int OP>
+__global__ void __cluster_dims__(kBands, 1, 1) __launch_bounds__(kThreads)
+    band_batch_kernel(const BatchItem *items, const int4 *tasks, int n_tasks, int AB,
+                      int *queue) {
+  extern __shared__ float4 smem4[];
+  __shared__ AngleConst sc[kMaxAB];
+  __shared__ int sai[kMaxAB];
+  __shared__ int s_task;
+  cg::cluster_group cluster = cg::this_cluster();
+  const bool leader = cluster.block_rank() == 0 && threadIdx.x == 0;
+  for (;;) {
+    if (leader) s_task = atomicAdd(queue, 1);
+    cluster.sync();
+    const int t = *cluster.map_shared_rank(&s_task, 0);
+    cluster.sync();  // every CTA has read it: the leader may overwrite it, or exit
+    if (t >= n_tasks) break;
+    const int4 tk = tasks[t];
+    const BatchItem &it = items[tk.x];
+    const Job J{it.in, nullptr, it.out, it.idx, it.m, it.B, it.alpha, 0.0f,
+                it.in_bf16, 0, it.out_bf16};
+    const BandGeom g = band_geom(it.N, it.n_det, it.n_angles, OP, AB);
+    band_task<OP>(J, tk.y, tk.z, g, it.ang, it.status, reinterpret_cast<float *>(smem4), sc,
+                  sai, cluster);
+  }
+  if (leader) queue_retire(queue, gridDim.x / kBands);
 }
 
 int sm_count() {
@@ -292,24 +363,25 @@ int sm_count() {
 }
 
 template <int OP>
+int set_band_smem(size_t smem) {
+  static size_t configured[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (smem > 48 * 1024 && smem > configured[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(band_kernel<OP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(band_batch_kernel<OP>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_error(e, "band kernel: shared memory attribute");
+    configured[dev] = smem;
+  }
+  return SKEI_OK;
+}
+
+template <int OP>
 int launch_band(skei_plan p, const Jobs &jobs, cudaStream_t st) {
-  BandGeom g;
-  g.N = p->N;
-  g.n_det = p->n_det;
-  g.n_angles = p->n_angles;
-  g.R = (g.N + kBands - 1) / kBands;
-  g.Prow = (g.N + 2 * kPad + 3) & ~3;
-  // A: 32 staged lines (fewer per-ray range setups); B^T: 16 (its per-bin
-  // work per line is larger, and the smaller band leaves room for more CTAs)
-  g.SB = min(g.R, OP == OP_JOSEPH ? 32 : 16);
-  // transposed staging writes lines 4q..4q+3 of (32 / (SB/4)) positions per
-  // warp: a pitch = 2 mod 8 (16 lines) or odd (32 lines) keeps them in
-  // distinct banks
-  g.Pcol = g.SB == 32 ? ((g.N + 2 * kPad) | 1) : ((g.N + 2 * kPad - 2 + 7) & ~7) + 2;
-  g.fast = (g.N % 8 == 0) ? 1 : 0;
-  const int Pmax = g.Prow > g.Pcol ? g.Prow : g.Pcol;
-  while (g.SB > 1 && (size_t)g.SB * Pmax * 4 > 96 * 1024) --g.SB;  // large N: slow staging
-  const size_t band_bytes = (size_t)g.SB * Pmax * 4;
   int m_max = 0, nimg = 0;
   for (int q = 0; q < jobs.njobs; ++q) {
     m_max = max(m_max, jobs.j[q].m);
@@ -318,13 +390,12 @@ int launch_band(skei_plan p, const Jobs &jobs, cudaStream_t st) {
   if (nimg > 65535) return set_error(SKEI_EINVAL, "too many images (%d) in one launch", nimg);
 
   // angles per cluster: fewest waves x angles per CTA (the per-CTA time),
-  // ties to the larger block (less staging); B^T needs AB | kWarps
+  // ties to the larger block (less staging)
   const int ab_max = min(kMaxAB, m_max);
   int best_ab = 1;
   double best_cost = 1e300;
   for (int ab = 1; ab <= ab_max; ++ab) {
-    const int rows = ab;
-    const size_t bytes = band_bytes + (size_t)((rows * g.n_det + 3) & ~3) * 4;
+    const size_t bytes = band_smem(band_geom(p->N, p->n_det, p->n_angles, OP, ab));
     if (bytes > 200 * 1024) continue;
     int per_sm = (int)((227 * 1024) / (bytes + 1024));
     per_sm = max(1, min(per_sm, 8));
@@ -335,25 +406,44 @@ int launch_band(skei_plan p, const Jobs &jobs, cudaStream_t st) {
     const double cost = std::ceil(ctas / slots) * ab;
     if (cost <= best_cost) { best_cost = cost; best_ab = ab; }
   }
-  g.AB = best_ab;
-  g.C = 1;
-  const int rows = g.AB;
-  const size_t smem = band_bytes + (size_t)((rows * g.n_det + 3) & ~3) * 4;
+  const BandGeom g = band_geom(p->N, p->n_det, p->n_angles, OP, best_ab);
+  const size_t smem = band_smem(g);
   if (smem > 227 * 1024)
     return set_error(SKEI_EINVAL, "detector of %d bins needs too much shared memory", g.n_det);
-
-  auto kern = band_kernel<OP>;
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return cuda_error(e, "band kernel: shared memory attribute");
-    configured = smem;
-  }
+  SKEI_TRY(set_band_smem<OP>(smem));
   BandArgs a{jobs, p->d_ang, p->d_status, g};
   dim3 grid(kBands, (m_max + g.AB - 1) / g.AB, nimg);
-  kern<<<grid, kThreads, smem, st>>>(a);
+  band_kernel<OP><<<grid, kThreads, smem, st>>>(a);
   return check_launch(OP == OP_JOSEPH ? "joseph forward launch" : "back-projection transpose launch");
+}
+
+// The persistent launch of a batch: `clusters` clusters of kBands CTAs over
+// `n_tasks` tasks; smem is the largest task's dynamic shared memory.
+template <int OP>
+int launch_band_batch(const BatchItem *items, const int4 *tasks, int n_tasks, int AB,
+                      size_t smem, int clusters, int *queue, cudaStream_t st) {
+  SKEI_TRY(set_band_smem<OP>(smem));
+  band_batch_kernel<OP><<<clusters * kBands, kThreads, smem, st>>>(items, tasks, n_tasks, AB,
+                                                                 queue);
+  return check_launch(OP == OP_JOSEPH ? "batched joseph forward launch"
+                                      : "batched back-projection transpose launch");
+}
+
+template <int OP>
+int band_batch_clusters(size_t smem, int *clusters) {
+  SKEI_TRY(set_band_smem<OP>(smem));
+  // the kernel's cluster shape is compiled in (__cluster_dims__)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kBands * 64, 1, 1);
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.attrs = nullptr;
+  cfg.numAttrs = 0;
+  int n = 0;
+  cudaError_t e = cudaOccupancyMaxActiveClusters(&n, band_batch_kernel<OP>, &cfg);
+  if (e != cudaSuccess) return cuda_error(e, "band kernel: cluster occupancy");
+  *clusters = n > 0 ? n : 1;
+  return SKEI_OK;
 }
 
 }  // namespace
@@ -362,6 +452,25 @@ int launch_band_jobs(skei_plan p, int op, const Jobs &jobs, cudaStream_t st) {
   if (op == OP_JOSEPH) return launch_band<OP_JOSEPH>(p, jobs, st);
   if (op == OP_BP_ADJ) return launch_band<OP_BP_ADJ>(p, jobs, st);
   return set_error(SKEI_EINVAL, "band launch: unknown operator %d", op);
+}
+
+size_t band_batch_smem(int op, int N, int n_det, int n_angles, int AB) {
+  return band_smem(band_geom(N, n_det, n_angles, op, AB));
+}
+
+int band_batch_occupancy(int op, size_t smem, int *clusters) {
+  if (op == OP_JOSEPH) return band_batch_clusters<OP_JOSEPH>(smem, clusters);
+  if (op == OP_BP_ADJ) return band_batch_clusters<OP_BP_ADJ>(smem, clusters);
+  return set_error(SKEI_EINVAL, "band batch: unknown operator %d", op);
+}
+
+int launch_band_batch_op(int op, const BatchItem *items, const int4 *tasks, int n_tasks, int AB,
+                         size_t smem, int clusters, int *queue, cudaStream_t st) {
+  if (op == OP_JOSEPH)
+    return launch_band_batch<OP_JOSEPH>(items, tasks, n_tasks, AB, smem, clusters, queue, st);
+  if (op == OP_BP_ADJ)
+    return launch_band_batch<OP_BP_ADJ>(items, tasks, n_tasks, AB, smem, clusters, queue, st);
+  return set_error(SKEI_EINVAL, "band batch: unknown operator %d", op);
 }
 
 }  // namespace skei

@@ -98,6 +98,10 @@ namespace skei {
 // ---------------------------------------------------------------- errors --
 int set_error(int code, const char *fmt, ...);
 int cuda_error(cudaError_t e, const char *where);
+#define SKEI_TRY(expr)                     \
+  do {                                     \
+    if (int rc_ = (expr)) return rc_;      \
+  } while (0)
 inline int check_launch(const char *where) {
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SKEI_OK : cuda_error(e, where);
@@ -197,6 +201,50 @@ enum { OP_JOSEPH = 0, OP_BP_ADJ = 1, OP_JOSEPH_ADJ = 2, OP_BACKPROJECT = 3 };
 
 int launch_band_jobs(skei_plan p, int op, const Jobs &jobs, cudaStream_t st);
 int launch_tile_jobs(skei_plan p, int op, const Jobs &jobs, cudaStream_t st);
+
+// ------------------------------------------------- batched (persistent) --
+// One instance of a batch - images of one size and angle list, with its own
+// sketch - as the persistent kernels see it: out = alpha op_S(in).
+struct BatchItem {
+  const AngleConst *ang;   // the instance's plan
+  int *status;
+  const void *in;
+  void *out;
+  const int *idx;          // sketch rows [m] or NULL
+  int N, n_det, n_angles, m, B;
+  float alpha;
+  int in_bf16, out_bf16;
+};
+
+// A persistent launch hands out tasks through queue[0] and counts finished
+// workers in queue[1]; the last worker to finish resets both, so the next
+// launch (stream-ordered after this one) starts from zero.  Called by one
+// thread per worker after its last atomicAdd on queue[0].
+__device__ __forceinline__ void queue_retire(int *queue, int workers) {
+  __threadfence();
+  if (atomicAdd(queue + 1, 1) == workers - 1) {
+    atomicExch(queue, 0);
+    atomicExch(queue + 1, 0);
+  }
+}
+
+// Band operators (A: OP_JOSEPH, B^T: OP_BP_ADJ): AB angles per task.
+size_t band_batch_smem(int op, int N, int n_det, int n_angles, int AB);
+int band_batch_occupancy(int op, size_t smem, int *clusters);
+int launch_band_batch_op(int op, const BatchItem *items, const int4 *tasks, int n_tasks, int AB,
+                         size_t smem, int clusters, int *queue, cudaStream_t st);
+// Tile operators (A^T: OP_JOSEPH_ADJ, B: OP_BACKPROJECT): one 8 x 256 tile
+// per task; tile_batch_shape gives the tile size for task lists.
+void tile_batch_shape(int *rows, int *cols);
+int tile_batch_occupancy(int op, int *ctas_per_sm);
+int launch_tile_batch_op(int op, const BatchItem *items, const int4 *tasks, int n_tasks,
+                         int ctas, int *queue, cudaStream_t st);
+// Ram-Lak rows: one row per task (items' in/out are sinograms, alpha the
+// filter's scale).
+size_t filter_batch_smem(int n_det_max);
+int filter_batch_occupancy(size_t smem, int *ctas_per_sm);
+int launch_filter_batch(const BatchItem *items, const int4 *tasks, int n_tasks, size_t smem,
+                        int ctas, int *queue, cudaStream_t st);
 
 // ------------------------------------------------------ internal launches --
 // Single-job conveniences over the two above.

@@ -54,19 +54,17 @@ constexpr int kFilterOuts = 4 * 32 * kGroupWarps;
 
 __host__ __device__ constexpr int skew(int e) { return e + (e >> 3); }
 
+// Filters one row: po[k] = scale (H pr)[k], k < nd.
 template <typename Tin, typename Tout>
-__global__ void __launch_bounds__(kFilterThreads)
-    ramlak_kernel(const Tin *in, Tout *out, int nd, float scale) {
-  extern __shared__ float4 smem4[];
-  float *red = reinterpret_cast<float *>(smem4);        // [kSeg][kFilterOuts]
+__device__ __forceinline__ void ramlak_row(const Tin *pr, Tout *po, int nd, float scale,
+                                           float *smem) {
+  float *red = smem;                                    // [kSeg][kFilterOuts]
   float *pb = red + kSeg * kFilterOuts;
   // zero margins: before the row, the farthest left tap (n <= nd-1, plus the
   // window's 2 extra); after it, the last pass's outputs (rounded up to
   // kFilterOuts) plus the farthest right tap
   const int lp = nd + 8;
   const int len = lp + ((nd + kFilterOuts - 1) / kFilterOuts) * kFilterOuts + nd + 16;
-  const size_t row = blockIdx.x;
-  const Tin *pr = in + row * nd;
   for (int e = threadIdx.x; e < len; e += kFilterThreads) {
     const int k = e - lp;
     pb[skew(e)] = (k >= 0 && k < nd) ? ldg_f(pr + k) : 0.0f;
@@ -121,9 +119,48 @@ __global__ void __launch_bounds__(kFilterThreads)
       float v = red[o];
 #pragma unroll
       for (int sg = 1; sg < kSeg; ++sg) v += red[sg * kFilterOuts + o];
-      st_f(out + row * nd + k, scale * v);
+      st_f(po + k, scale * v);
     }
   }
+}
+
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(kFilterThreads)
+    ramlak_kernel(const Tin *in, Tout *out, int nd, float scale) {
+  extern __shared__ float4 smem4[];
+  const size_t row = blockIdx.x;
+  ramlak_row<Tin, Tout>(in + row * nd, out + row * nd, nd, scale,
+                        reinterpret_cast<float *>(smem4));
+}
+
+// Persistent form over the rows of a batch of instances (task = item, row;
+// rows come in decreasing n_det order).
+__global__ void __launch_bounds__(kFilterThreads)
+    ramlak_batch_kernel(const BatchItem *items, const int4 *tasks, int n_tasks, int *queue) {
+  extern __shared__ float4 smem4[];
+  float *smem = reinterpret_cast<float *>(smem4);
+  __shared__ int s_task;
+  for (;;) {
+    __syncthreads();  // the previous row's shared memory and s_task are no longer read
+    if (threadIdx.x == 0) s_task = atomicAdd(queue, 1);
+    __syncthreads();
+    const int t = s_task;
+    if (t >= n_tasks) break;
+    const int4 tk = tasks[t];
+    const BatchItem &it = items[tk.x];
+    const int nd = it.n_det;
+    const size_t o = (size_t)tk.y * nd;
+    if (it.in_bf16) {
+      const __nv_bfloat16 *pi = static_cast<const __nv_bfloat16 *>(it.in) + o;
+      if (it.out_bf16) ramlak_row(pi, static_cast<__nv_bfloat16 *>(it.out) + o, nd, it.alpha, smem);
+      else ramlak_row(pi, static_cast<float *>(it.out) + o, nd, it.alpha, smem);
+    } else {
+      const float *pi = static_cast<const float *>(it.in) + o;
+      if (it.out_bf16) ramlak_row(pi, static_cast<__nv_bfloat16 *>(it.out) + o, nd, it.alpha, smem);
+      else ramlak_row(pi, static_cast<float *>(it.out) + o, nd, it.alpha, smem);
+    }
+  }
+  if (threadIdx.x == 0) queue_retire(queue, gridDim.x);
 }
 
 // ------------------------------------------------------------ rotation --
@@ -256,19 +293,61 @@ __global__ void __launch_bounds__(kAdjT *kAdjT)
 
 }  // namespace
 
+// Dynamic shared memory of a filter CTA for rows of nd bins: the segment
+// partials, then the skewed row between its zero margins.
+static size_t filter_smem(int nd) {
+  const int len = (nd + 8) + ((nd + kFilterOuts - 1) / kFilterOuts) * kFilterOuts + nd + 16;
+  return (size_t)(kSeg * kFilterOuts + skew(len + 16) + 1) * sizeof(float);
+}
+
+static int set_filter_batch_smem(size_t smem) {
+  static size_t configured[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (smem > 48 * 1024 && smem > configured[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(ramlak_batch_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_error(e, "batched ramlak: shared memory attribute");
+    configured[dev] = smem;
+  }
+  return SKEI_OK;
+}
+
+size_t filter_batch_smem(int n_det_max) { return filter_smem(n_det_max); }
+
+int filter_batch_occupancy(size_t smem, int *ctas_per_sm) {
+  SKEI_TRY(set_filter_batch_smem(smem));
+  int n = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ramlak_batch_kernel,
+                                                                kFilterThreads, smem);
+  if (e != cudaSuccess) return cuda_error(e, "batched ramlak: occupancy");
+  *ctas_per_sm = n > 0 ? n : 1;
+  return SKEI_OK;
+}
+
+int launch_filter_batch(const BatchItem *items, const int4 *tasks, int n_tasks, size_t smem,
+                        int ctas, int *queue, cudaStream_t st) {
+  SKEI_TRY(set_filter_batch_smem(smem));
+  ramlak_batch_kernel<<<ctas, kFilterThreads, smem, st>>>(items, tasks, n_tasks, queue);
+  return check_launch("batched ramlak filter launch");
+}
+
 template <typename Tin, typename Tout>
 int launch_filter(skei_plan p, const Tin *in, int rows, float scale, Tout *out,
                   cudaStream_t st) {
   const int nd = p->n_det;
-  const int len = (nd + 8) + ((nd + kFilterOuts - 1) / kFilterOuts) * kFilterOuts + nd + 16;
-  const size_t smem = (size_t)(kSeg * kFilterOuts + skew(len + 16) + 1) * sizeof(float);
+  const size_t smem = filter_smem(nd);
   auto kern = ramlak_kernel<Tin, Tout>;
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
+  static size_t configured[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (smem > 48 * 1024 && smem > configured[dev]) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return cuda_error(e, "ramlak: shared memory attribute");
-    configured = smem;
+    configured[dev] = smem;
   }
   kern<<<rows, kFilterThreads, smem, st>>>(in, out, nd, scale);
   return check_launch("ramlak filter launch");

@@ -53,21 +53,24 @@ __device__ __forceinline__ void store_run(void *out, size_t o, const float *v, i
   for (int q = 0; q < n_valid; ++q) st_any(out, o + q, v[q], bf16);
 }
 
-template <int OP>
-__global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs args) {
-  __shared__ float win[kAC][kWin];
-  __shared__ AngleConst sc[kAC];
-  __shared__ int sai[kAC];
-  __shared__ int kw0[kAC];
+// Shared memory of a tile task.
+struct TileSmem {
+  float win[kAC][kWin];
+  AngleConst sc[kAC];
+  int sai[kAC];
+  int kw0[kAC];
+};
 
+// One task: the tile at (i0, j0) of image b of job J.
+template <int OP>
+__device__ __forceinline__ void tile_task(const Job &J, int b, int i0, int j0, int N, int nd,
+                                          int n_angles, const AngleConst *ang, int *status,
+                                          bool report, TileSmem &sm) {
+  float (*win)[kWin] = sm.win;
+  AngleConst *sc = sm.sc;
+  int *sai = sm.sai, *kw0 = sm.kw0;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  const int N = args.N, nd = args.n_det;
-  const int i0 = blockIdx.y * kTH, j0 = blockIdx.x * kTW;
-  const int z = blockIdx.z;
-  const int jn = (args.jobs.njobs > 1 && z >= args.jobs.j[0].nimg) ? 1 : 0;
-  const Job &J = args.jobs.j[jn];
-  const int b = z - (jn ? args.jobs.j[0].nimg : 0);
   const int i_last = min(i0 + kTH, N) - 1, j_last = min(j0 + kTW, N) - 1;
   const int i = i0 + warp;                 // this thread's row
   const int jb = j0 + kPPT * lane;         // its first column
@@ -81,13 +84,13 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs args) {
     __syncthreads();  // previous chunk no longer read
     if (tid < nac) {
       int ai = J.idx ? J.idx[c0 + tid] : c0 + tid;
-      if (ai < 0 || ai >= args.n_angles) {
-        if (blockIdx.x == 0 && blockIdx.y == 0) atomicOr(args.status, 1);
+      if (ai < 0 || ai >= n_angles) {
+        if (report) atomicOr(status, 1);
         ai = -1;
       }
       sai[tid] = ai;
       if (ai >= 0) {
-        const AngleConst C = args.ang[ai];
+        const AngleConst C = ang[ai];
         sc[tid] = C;
         // bin range of the tile: extremes of an affine function at corners
         float lo = 3.0e38f;
@@ -186,6 +189,41 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs args) {
 }
 
 template <int OP>
+__global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs args) {
+  __shared__ TileSmem sm;
+  const int z = blockIdx.z;
+  const int jn = (args.jobs.njobs > 1 && z >= args.jobs.j[0].nimg) ? 1 : 0;
+  const Job &J = args.jobs.j[jn];
+  const int b = z - (jn ? args.jobs.j[0].nimg : 0);
+  tile_task<OP>(J, b, blockIdx.y * kTH, blockIdx.x * kTW, args.N, args.n_det, args.n_angles,
+                args.ang, args.status, blockIdx.x == 0 && blockIdx.y == 0, sm);
+}
+
+// Persistent form over the tile tasks of a batch of instances: each CTA takes
+// the next task from a global counter (tasks come in decreasing cost order)
+// until none is left.
+template <int OP>
+__global__ void __launch_bounds__(kThreads)
+    tile_batch_kernel(const BatchItem *items, const int4 *tasks, int n_tasks, int *queue) {
+  __shared__ TileSmem sm;
+  __shared__ int s_task;
+  for (;;) {
+    __syncthreads();  // the previous task's reads of s_task and shared memory are done
+    if (threadIdx.x == 0) s_task = atomicAdd(queue, 1);
+    __syncthreads();
+    const int t = s_task;
+    if (t >= n_tasks) break;
+    const int4 tk = tasks[t];
+    const BatchItem &it = items[tk.x];
+    const Job J{it.in, nullptr, it.out, it.idx, it.m, it.B, it.alpha, 0.0f,
+                it.in_bf16, 0, it.out_bf16};
+    tile_task<OP>(J, tk.y, tk.z * kTH, tk.w * kTW, it.N, it.n_det, it.n_angles, it.ang,
+                  it.status, tk.z == 0 && tk.w == 0, sm);
+  }
+  if (threadIdx.x == 0) queue_retire(queue, gridDim.x);
+}
+
+template <int OP>
 int launch_tile(skei_plan p, const Jobs &jobs, cudaStream_t st) {
   int nimg = 0;
   for (int q = 0; q < jobs.njobs; ++q) nimg += jobs.j[q].nimg;
@@ -202,6 +240,33 @@ int launch_tile_jobs(skei_plan p, int op, const Jobs &jobs, cudaStream_t st) {
   if (op == OP_JOSEPH_ADJ) return launch_tile<OP_JOSEPH_ADJ>(p, jobs, st);
   if (op == OP_BACKPROJECT) return launch_tile<OP_BACKPROJECT>(p, jobs, st);
   return set_error(SKEI_EINVAL, "tile launch: unknown operator %d", op);
+}
+
+void tile_batch_shape(int *rows, int *cols) {
+  *rows = kTH;
+  *cols = kTW;
+}
+
+int tile_batch_occupancy(int op, int *ctas_per_sm) {
+  int n = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &n, op == OP_JOSEPH_ADJ ? tile_batch_kernel<OP_JOSEPH_ADJ> : tile_batch_kernel<OP_BACKPROJECT>,
+      kThreads, 0);
+  if (e != cudaSuccess) return cuda_error(e, "tile kernel: occupancy");
+  *ctas_per_sm = n > 0 ? n : 1;
+  return SKEI_OK;
+}
+
+int launch_tile_batch_op(int op, const BatchItem *items, const int4 *tasks, int n_tasks,
+                         int ctas, int *queue, cudaStream_t st) {
+  if (op == OP_JOSEPH_ADJ)
+    tile_batch_kernel<OP_JOSEPH_ADJ><<<ctas, kThreads, 0, st>>>(items, tasks, n_tasks, queue);
+  else if (op == OP_BACKPROJECT)
+    tile_batch_kernel<OP_BACKPROJECT><<<ctas, kThreads, 0, st>>>(items, tasks, n_tasks, queue);
+  else
+    return set_error(SKEI_EINVAL, "tile batch: unknown operator %d", op);
+  return check_launch(op == OP_JOSEPH_ADJ ? "batched joseph adjoint launch"
+                                          : "batched back-projection launch");
 }
 
 }  // namespace skei

@@ -23,6 +23,8 @@ __all__ = [
     "fbp_workspace_size", "fbp", "fbp_adj", "fbp_noalloc", "rotate", "rotate_adj",
     "ei_workspace_size", "ei_loss_fwd", "ei_loss_finish", "ei_loss_bwd",
     "residual_add", "adam_step", "library_path",
+    "Batch", "BatchItem", "PROJ_FWD", "PROJ_ADJ", "BACKPROJECT", "BACKPROJECT_ADJ", "FILTER",
+    "FBP",
 ]
 
 F32, BF16 = 0, 1
@@ -45,6 +47,15 @@ class _Job(ctypes.Structure):
                 ("out", ctypes.c_void_p), ("idx", ctypes.c_void_p), ("m", ctypes.c_int),
                 ("B", ctypes.c_int), ("alpha", ctypes.c_float), ("beta", ctypes.c_float)]
 
+
+class _BatchItemC(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("dtype_in", ctypes.c_int),
+                ("dtype_out", ctypes.c_int), ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("idx", ctypes.c_void_p), ("m", ctypes.c_int), ("B", ctypes.c_int),
+                ("scale", ctypes.c_float)]
+
+
+_BATCH = ctypes.c_void_p
 
 _SIGS = {
     "skei_version": ([], _i),
@@ -76,6 +87,12 @@ _SIGS = {
                           _vp, _sz, _vp], _i),
     "skei_residual_add": ([_i, _vp, _vp, _i, _i64, _vp, _vp], _i),
     "skei_adam_step": ([_vp, _i64, _i, _vp, _i, _vp, _i, _vp, _vp, _vp, _d, _d, _d, _d, _vp], _i),
+    "skei_batch_create": ([_i, ctypes.POINTER(_BatchItemC), _i, ctypes.POINTER(_BATCH)], _i),
+    "skei_batch_run": ([_BATCH, _vp], _i),
+    "skei_batch_tune": ([_BATCH, _i, _vp], _i),
+    "skei_batch_info": ([_BATCH, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
+                         ctypes.POINTER(_i)], _i),
+    "skei_batch_destroy": ([_BATCH], _i),
 }
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -483,3 +500,75 @@ def adam_step(theta, m, v, step_dev, g1, g2=None, lr=5e-4, beta1=0.9, beta2=0.99
     _check(_lib.skei_adam_step(_ptr(theta), n, _dtype_code(g1), _ptr(g1), c1, _ptr(g2), c2,
                                _ptr(m), _ptr(v), _ptr(step_dev), lr, beta1, beta2, eps, _stream()),
            "skei_adam_step")
+
+
+# ------------------------------------------------------- batched schedule
+PROJ_FWD, PROJ_ADJ, BACKPROJECT, BACKPROJECT_ADJ, FILTER, FBP = range(6)
+_BATCH_NAMES = ["proj_fwd", "proj_adj", "backproject", "backproject_adj", "filter", "fbp"]
+
+
+class BatchItem:
+    """One instance of a batch: `inp` -> `out` under the batch's operator with
+    the plan's geometry and the sketch `idx` (int32 CUDA tensor, None = all
+    angles); out = scale * op(inp)."""
+
+    def __init__(self, plan: Plan, inp, out, idx=None, scale: float = 1.0):
+        self.plan, self.inp, self.out, self.idx, self.scale = plan, inp, out, idx, float(scale)
+
+
+class Batch:
+    """skei_batch_*: one operator over many instances (different plans,
+    sketches and storage types) in one persistent launch per kernel.  The
+    tensors are baked in at creation: write new inputs into them and call
+    run() again (also inside a captured CUDA graph)."""
+
+    def __init__(self, op: int, items):
+        if op not in range(6):
+            raise ValueError(f"unknown batch operator {op}")
+        self.op, self.items = op, list(items)
+        arr = (_BatchItemC * len(self.items))()
+        for q, it in enumerate(self.items):
+            p = it.plan
+            idx_p, m = _idx(p, it.idx)
+            B = int(it.inp.shape[0]) if it.inp.dim() >= 1 else 0
+            img, sino = (B, p.N, p.N), (B, m, p.n_det)
+            shp_in, shp_out = {
+                PROJ_FWD: (img, sino), PROJ_ADJ: (sino, img), BACKPROJECT: (sino, img),
+                BACKPROJECT_ADJ: (img, sino), FILTER: (sino, sino), FBP: (sino, img)}[op]
+            _dev(it.inp, f"items[{q}].inp", shape=shp_in)
+            _dev(it.out, f"items[{q}].out", shape=shp_out)
+            arr[q] = _BatchItemC(p.handle.value, _dtype_code(it.inp), _dtype_code(it.out),
+                                 it.inp.data_ptr(), it.out.data_ptr(),
+                                 None if idx_p is None else idx_p.value, m, B, it.scale)
+        self._h = _BATCH()
+        _check(_lib.skei_batch_create(int(op), arr, len(self.items), ctypes.byref(self._h)),
+               "skei_batch_create")
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("batch is closed")
+        return self._h
+
+    def run(self) -> None:
+        _check(_lib.skei_batch_run(self.handle, _stream()), "skei_batch_run")
+
+    def tune(self, reps: int = 5) -> None:
+        _check(_lib.skei_batch_tune(self.handle, int(reps), _stream()), "skei_batch_tune")
+
+    def info(self, phase: int = 0) -> dict:
+        n_ph, n_t, w, blk = _i(), _i(), _i(), _i()
+        _check(_lib.skei_batch_info(self.handle, int(phase), ctypes.byref(n_ph), ctypes.byref(n_t),
+                                    ctypes.byref(w), ctypes.byref(blk)), "skei_batch_info")
+        return {"phases": n_ph.value, "tasks": n_t.value, "workers": w.value, "block": blk.value}
+
+    def close(self):
+        if self._h:
+            _lib.skei_batch_destroy(self._h)
+            self._h = _BATCH()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

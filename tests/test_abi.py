@@ -86,3 +86,23 @@ def test_binding_rejects_host_tensors():
     from paper_2411_05771_gb300 import skei as S
     with pytest.raises(TypeError):
         S.rotate(torch.zeros(1, 8, 8), torch.zeros(1, 1, dtype=torch.float64))
+
+
+def test_batch_validation_needs_no_gpu(lib):
+    vp = ctypes.c_void_p
+    lib.skei_last_error.restype = ctypes.c_char_p
+    lib.skei_batch_create.argtypes = [ctypes.c_int, vp, ctypes.c_int, ctypes.POINTER(vp)]
+    lib.skei_batch_run.argtypes = [vp, vp]
+    lib.skei_batch_tune.argtypes = [vp, ctypes.c_int, vp]
+    lib.skei_batch_destroy.argtypes = [vp]
+    h = vp()
+    assert lib.skei_batch_create(0, vp(64), 1, None) == EINVAL
+    assert lib.skei_batch_create(6, vp(64), 1, ctypes.byref(h)) == EINVAL
+    assert b"operator" in lib.skei_last_error()
+    assert lib.skei_batch_create(-1, vp(64), 1, ctypes.byref(h)) == EINVAL
+    assert lib.skei_batch_create(0, None, 1, ctypes.byref(h)) == EINVAL
+    assert lib.skei_batch_create(0, vp(64), 0, ctypes.byref(h)) == EINVAL
+    assert not h.value
+    assert lib.skei_batch_run(None, None) == EINVAL
+    assert lib.skei_batch_tune(None, 3, None) == EINVAL
+    assert lib.skei_batch_destroy(None) == 0
