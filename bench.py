@@ -47,13 +47,17 @@ L2_FLUSH_BYTES = 256 << 20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="skei", choices=["skei", "reference"])
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"],
                     help="storage type of the sketched arm")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=0, help="oracle steps (0 = auto, ~15 s)")
+    ap.add_argument("--suite", action="store_true",
+                    help="instead of the headline line, print one JSON line per measurement "
+                         "of the other workloads: single operators at 64^2 and 8 x 256^2, the "
+                         "differentiated EI step at 8 x 4 x 256^2, the 16-instance batch")
     ap.add_argument("--profile", action="store_true",
                     help="set up the sketched arm, run one warm and one more step, and exit "
                          "(a short, untimed run for ncu: 2 launches of set-up, then 13 per step)")
@@ -61,26 +65,61 @@ def parse():
 
 
 # --------------------------------------------------------------------- inputs
-def make_problem(seed=0):
+class Workload:
+    """Shape of one TTT step: B images of N^2, `views` angles, EI term on an
+    m-angle interleaved sketch (m = views: no sketch), MC term on the same
+    sketch or on all views, G rotations per image."""
+
+    def __init__(self, N=N_IMG, views=N_VIEWS, m=SKETCH, G=G_ROT, B=BATCH, mc_sketched=True,
+                 noisy=True, draw_m=None):
+        self.N, self.views, self.m, self.G, self.B = N, views, m, G, B
+        self.mc_sketched = mc_sketched and m < views
+        self.noisy = noisy
+        # sketch size of the per-step offset draw: the plain arm draws as the
+        # sketched one does, so both see the same rotations
+        self.draw_m = draw_m or m
+
+    @property
+    def sketched(self):
+        return self.m < self.views
+
+    @property
+    def mc_m(self):
+        return self.m if self.mc_sketched else self.views
+
+    @property
+    def mc_scale(self):
+        return self.views / self.m if self.mc_sketched else 1.0
+
+
+SKETCHED = Workload()                                   # the headline arm
+PLAIN = Workload(m=N_VIEWS, mc_sketched=False, draw_m=SKETCH)   # full operators
+
+
+def make_problem(wl=SKETCHED, seed=0):
     from paper_2411_05771_gb300 import inputs as I
-    e = I.random_ellipses(seed)
-    x_gt = I.rasterize(e, N_IMG)
-    angs = I.uniform_angles(N_VIEWS)
-    n_det = int(np.ceil(N_IMG * np.sqrt(2.0))) | 1
-    y_clean = I.analytic_sinogram(e, N_IMG, angs, n_det)
-    y = I.noisy_sinogram(y_clean, N_IMG, seed=seed + 77)
-    return dict(x_gt=x_gt, angs=angs, n_det=n_det, y=y)
+    angs = I.uniform_angles(wl.views)
+    n_det = int(np.ceil(wl.N * np.sqrt(2.0))) | 1
+    xs, ys = [], []
+    for b in range(wl.B):
+        e = I.random_ellipses(seed + b)
+        xs.append(I.rasterize(e, wl.N))
+        y = I.analytic_sinogram(e, wl.N, angs, n_det)
+        ys.append(I.noisy_sinogram(y, wl.N, seed=seed + b + 77) if wl.noisy else y)
+    return dict(x_gt=xs[0], x_all=np.stack(xs), angs=angs, n_det=n_det, y=ys[0], y_all=np.stack(ys))
 
 
-def step_params(n_steps, sketched, first=0):
+def step_params(n_steps, wl, first=0):
+    """Per-step draws (Algorithm 2): one sketch offset and B x G rotation
+    angles from default_rng(1000 + step)."""
     from paper_2411_05771_gb300 import inputs as I
     idx, g = [], []
     for s in range(first, first + n_steps):
         rng = I.step_rng(s)
-        off = I.random_sketch_offset(rng, N_VIEWS, SKETCH)
-        idx.append(I.sketch_indices(N_VIEWS, SKETCH, off) if sketched
-                   else np.arange(N_VIEWS, dtype=np.int32))
-        g.append(I.rotation_angles(rng, BATCH, G_ROT))
+        off = I.random_sketch_offset(rng, wl.views, wl.draw_m)
+        idx.append(I.sketch_indices(wl.views, wl.m, off) if wl.sketched
+                   else np.arange(wl.views, dtype=np.int32))
+        g.append(I.rotation_angles(rng, wl.B, wl.G))
     return np.stack(idx).astype(np.int32), np.stack(g)
 
 
@@ -89,38 +128,39 @@ class Arm:
     """One TTT problem on the GPU with all buffers resident; `step()` issues
     Algorithm 2's iteration through the C ABI on the current stream."""
 
-    def __init__(self, S, plan, prob, sketched, dtype, device):
+    def __init__(self, S, plan, prob, wl, dtype, device):
         import torch
-        self.S, self.plan, self.sketched = S, plan, sketched
+        self.S, self.plan, self.wl = S, plan, wl
+        self.sketched = wl.sketched
         self.tdt = torch.float32 if dtype == "f32" else torch.bfloat16
-        N, nd = N_IMG, plan.n_det
-        self.m = SKETCH if sketched else N_VIEWS
-        self.mc_scale = (N_VIEWS / SKETCH) if sketched else 1.0
+        N, nd, B, G = wl.N, plan.n_det, wl.B, wl.G
+        self.m, self.mc_m = wl.m, wl.mc_m
+        self.mc_scale = wl.mc_scale
         d = device
-        self.y = torch.tensor(prob["y"][None], dtype=self.tdt, device=d)
-        y32 = torch.tensor(prob["y"][None], dtype=torch.float32, device=d)
+        self.y = torch.tensor(prob["y_all"], dtype=self.tdt, device=d)
+        y32 = torch.tensor(prob["y_all"], dtype=torch.float32, device=d)
         self.x0 = S.fbp(plan, y32).to(self.tdt).contiguous()
         self.theta = torch.zeros((N, N), dtype=torch.float32, device=d)
         self.m1 = torch.zeros_like(self.theta)
         self.v1 = torch.zeros_like(self.theta)
         self.step_no = torch.zeros(1, dtype=torch.int32, device=d)
         self.idx = torch.zeros(self.m, dtype=torch.int32, device=d)
-        self.g = torch.zeros((BATCH, G_ROT), dtype=torch.float64, device=d)
-        self.x1 = torch.empty((BATCH, N, N), dtype=self.tdt, device=d)
-        self.r = torch.empty((BATCH, self.m, nd), dtype=self.tdt, device=d)
-        self.x2 = torch.empty((BATCH, G_ROT, N, N), dtype=self.tdt, device=d)
+        self.g = torch.zeros((B, G), dtype=torch.float64, device=d)
+        self.x1 = torch.empty((B, N, N), dtype=self.tdt, device=d)
+        self.r = torch.empty((B, self.mc_m, nd), dtype=self.tdt, device=d)
+        self.x2 = torch.empty((B, G, N, N), dtype=self.tdt, device=d)
         self.z = torch.empty_like(self.x2)
         self.x3 = torch.empty_like(self.x2)
         self.gx2 = torch.empty_like(self.x2)
         self.gx3 = torch.empty_like(self.x2)
         self.gx1 = torch.empty_like(self.x1)
         self.loss = torch.empty(1, dtype=torch.float64, device=d)
-        self.mc = torch.empty(BATCH, dtype=torch.float64, device=d)
-        self.ei = torch.empty((BATCH, G_ROT), dtype=torch.float64, device=d)
+        self.mc = torch.empty(B, dtype=torch.float64, device=d)
+        self.ei = torch.empty((B, G), dtype=torch.float64, device=d)
         code = S.F32 if dtype == "f32" else S.BF16
-        self.work = torch.empty(max(S.ei_workspace_size(plan, code, BATCH, G_ROT, self.m, self.m),
+        self.work = torch.empty(max(S.ei_workspace_size(plan, code, B, G, self.mc_m, self.m),
                                     16), dtype=torch.uint8, device=d)
-        idx_all, g_all = step_params(1, sketched)
+        idx_all, g_all = step_params(1, wl)
         self.load_params(idx_all[0], g_all[0], 1)
 
     def load_params(self, idx, g, step_no):
@@ -131,7 +171,7 @@ class Arm:
 
     def step(self):
         S, p = self.S, self.plan
-        mc_idx = self.idx if self.sketched else None
+        mc_idx = self.idx if self.wl.mc_sketched else None
         sk_idx = self.idx if self.sketched else None
         S.residual_add(self.x0, self.theta, out=self.x1)                      # x1 = F(x0)
         S.ei_loss_fwd(p, self.x1, self.y, self.g, mc_idx, sk_idx, work=self.work,
@@ -139,7 +179,7 @@ class Arm:
         S.residual_add(self.z, self.theta, out=self.x3)                       # x3 = F(z)
         S.ei_loss_finish(self.x2, self.x3, self.r, LAM, self.mc_scale, work=self.work,
                          out=(self.loss, self.mc, self.ei, self.gx2, self.gx3))
-        S.ei_loss_bwd(p, self.r, self.gx2, self.gx3, self.g, self.mc_scale / BATCH, mc_idx,
+        S.ei_loss_bwd(p, self.r, self.gx2, self.gx3, self.g, self.mc_scale / self.wl.B, mc_idx,
                       sk_idx, work=self.work, out=self.gx1)
         # dL/dtheta = dL/dx1 + sum_g dL/dx3 (F's Jacobian is the identity)
         S.adam_step(self.theta, self.m1, self.v1, self.step_no, self.gx1, self.gx3, lr=LR)
@@ -157,7 +197,7 @@ def psnr_curve(arm, x_gt, iters, every=25):
     x0 + theta against the phantom every `every` iterations (untimed)."""
     import torch
     arm.reset()
-    idx_all, g_all = step_params(iters, arm.sketched)
+    idx_all, g_all = step_params(iters, arm.wl)
     rngv = float(x_gt.max() - x_gt.min())
     curve = {}
     for s in range(iters + 1):
@@ -220,10 +260,19 @@ class Clocks:
         try:
             self.f = open(self.path, "w")
             self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_id}", f"--query-gpu={q}",
-                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+            return
+        # start timing only once samples flow (nvidia-smi takes a moment)
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 5.0 and self.p.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.01)
+        self.f.flush()
+        self.skip = sum(1 for _ in open(self.path))   # samples taken before the timed region
 
     def stop(self):
         if not self.p:
@@ -236,7 +285,9 @@ class Clocks:
         self.f.close()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for n, line in enumerate(open(self.path)):
+            if n < getattr(self, "skip", 0):
+                continue
             parts = [t.strip() for t in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -263,21 +314,22 @@ def kernel_breakdown(S, arm, stream, reps=20):
     p = arm.plan
     mc_idx = arm.idx if arm.sketched else None
     sk_idx = arm.idx if arm.sketched else None
-    BG, m = BATCH * G_ROT, arm.m
+    wl = arm.wl
+    N, BG, m = wl.N, wl.B * wl.G, arm.m
     f32 = dict(dtype=torch.float32, device="cuda")
     pbuf = torch.empty((BG, m, p.n_det), **f32)
     qbuf = torch.empty_like(pbuf)
-    gtot = torch.empty((BATCH, G_ROT, N_IMG, N_IMG), **f32)
+    gtot = torch.empty((wl.B, wl.G, N, N), **f32)
     # the public calls want one storage type per call, where the step's own
     # launches mix BF16 images with FP32 sinogram buffers: with BF16 storage
     # these stand-ins read BF16 copies instead
     q_t = qbuf if arm.tdt == torch.float32 else qbuf.to(arm.tdt)
     p_t = pbuf if arm.tdt == torch.float32 else pbuf.to(arm.tdt)
     gtot_t = gtot if arm.tdt == torch.float32 else gtot.to(arm.tdt)
-    x2 = arm.x2.reshape(BG, N_IMG, N_IMG)
-    gx3 = arm.gx3.reshape(BG, N_IMG, N_IMG)
-    gx2 = arm.gx2.reshape(BG, N_IMG, N_IMG)
-    z = arm.z.reshape(BG, N_IMG, N_IMG)
+    x2 = arm.x2.reshape(BG, N, N)
+    gx3 = arm.gx3.reshape(BG, N, N)
+    gx2 = arm.gx2.reshape(BG, N, N)
+    z = arm.z.reshape(BG, N, N)
     ops = {
         "residual_add(x1)": lambda: S.residual_add(arm.x0, arm.theta, out=arm.x1),
         "rotate": lambda: S.rotate(arm.x1, arm.g, out=arm.x2),
@@ -292,8 +344,8 @@ def kernel_breakdown(S, arm, stream, reps=20):
         "backproject_adj": lambda: S.backproject_adj(p, gx3, sk_idx, out=p_t),
         "ramlak(bwd)": lambda: S.filter(p, pbuf, np.pi / m, out=qbuf),
         "joseph_adj(MC+EI)": lambda: S.proj_adj_multi(
-            p, [S.Job(arm.r, arm.gx1, mc_idx, alpha=-2.0 * arm.mc_scale / BATCH),
-                S.Job(qbuf, gtot.reshape(BG, N_IMG, N_IMG), sk_idx, aux=gx2, beta=1.0)]),
+            p, [S.Job(arm.r, arm.gx1, mc_idx, alpha=-2.0 * arm.mc_scale / wl.B),
+                S.Job(qbuf, gtot.reshape(BG, N, N), sk_idx, aux=gx2, beta=1.0)]),
         "rotate_adj": lambda: S.rotate_adj(gtot_t, arm.g, beta=1.0, out=arm.gx1),
         "adam": lambda: S.adam_step(arm.theta, arm.m1, arm.v1, arm.step_no, arm.gx1, arm.gx3,
                                     lr=LR),
@@ -348,14 +400,17 @@ def pixel_angles(plan, n_img, n_ang):
 
 
 def algorithmic_flops(plan, arm, name):
-    """FP32 flops a kernel of the step must do at the least: 7 per nonzero
-    of its operator (Joseph crossings inside the image for A and A^T; pixel
-    x angle for B and B^T), 3 per (output, odd tap) pair for the filter."""
+    """FP32 flops a kernel of the step must do at the least: 7 per
+    interpolation sample of its operator (a Joseph crossing inside the image
+    for A and A^T; a pixel x angle for B and B^T), 3 per (output, odd tap)
+    pair for the filter."""
+    wl = arm.wl
     idx = arm.idx.cpu().numpy()
+    mc_idx = idx if wl.mc_sketched else np.arange(wl.views)
     m = len(idx)
-    BG = BATCH * G_ROT
+    BG = wl.B * wl.G
     if name.startswith("joseph"):
-        return FLOPS_PER_SAMPLE * (joseph_samples(plan, BATCH, idx)
+        return FLOPS_PER_SAMPLE * (joseph_samples(plan, wl.B, mc_idx)
                                    + joseph_samples(plan, BG, idx))
     if name.startswith("backproject"):
         return FLOPS_PER_SAMPLE * pixel_angles(plan, BG, m)
@@ -407,7 +462,7 @@ def roofline_entry(plan, arm, bd, dom, dev):
     return {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": measured_traffic(dom),
             "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 flop x {max_mhz:.0f} MHz",
-            "work": f"{FLOPS_PER_SAMPLE} flop per operator nonzero", "launch_us": bd[dom]}
+            "work": f"{FLOPS_PER_SAMPLE} flop per interpolation sample", "launch_us": bd[dom]}
 
 
 def cpu_oracle_steps(prob, n_steps, sketched):
@@ -419,7 +474,7 @@ def cpu_oracle_steps(prob, n_steps, sketched):
     theta = np.zeros((N_IMG, N_IMG))
     mom = np.zeros_like(theta)
     vel = np.zeros_like(theta)
-    idx_all, g_all = step_params(n_steps, sketched)
+    idx_all, g_all = step_params(n_steps, SKETCHED if sketched else PLAIN)
     mcs = (N_VIEWS / SKETCH) if sketched else 1.0
     t0 = time.perf_counter()
     for s in range(n_steps):
@@ -452,6 +507,154 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ suite
+def time_graph(fn, stream, reps=20):
+    """Microseconds per call of `fn`: `reps` calls captured in a CUDA graph,
+    one warm replay, one timed replay (CUDA events on the launching stream)."""
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            fn()
+        stream.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            for _ in range(reps):
+                fn()
+        graph.replay()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+        stream.synchronize()
+    return 1e3 * e0.elapsed_time(e1) / reps
+
+
+def fp32_peak(dev):
+    import torch
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    return sm * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+
+
+def op_line(workload, op, us, samples, peak, **extra):
+    flops = FLOPS_PER_SAMPLE * samples
+    line = {"suite": workload, "op": op, "us": round(us, 2), "samples": int(samples),
+            "tflops": round(flops / (us * 1e-6) / 1e12, 3),
+            "roofline_frac": round(flops / (us * 1e-6) / 1e12 / peak, 4)}
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+
+
+def suite(S, dev, stream):
+    """The measurements behind the per-workload table: single operators
+    (64^2 with 60 views; 8 x 256^2 with 180 views, full and a 45-angle
+    sketch), the differentiated EI step at 8 x 4 x 256^2 (MC term on all
+    180 views, EI term on the sketch), and the 16-instance batch of 256^2 /
+    512^2 instances with sketches of 45-360 angles."""
+    import torch
+    from paper_2411_05771_gb300 import inputs as I
+    peak = fp32_peak(dev)
+    for name, N, views, B, m in (("64x64-60views", 64, 60, 1, None),
+                                 ("8x256x256-180views-363bins", 256, 180, 8, 45)):
+        plan = S.Plan(N, views)
+        x = torch.tensor(np.stack([I.rasterize(I.random_ellipses(b), N) for b in range(B)]),
+                         dtype=torch.float32, device=dev)
+        sets = [("full", None, np.arange(views))]
+        if m:
+            off = I.random_sketch_offset(np.random.default_rng(0), views, m)
+            sk = I.sketch_indices(views, m, off)
+            sets.append((f"sketch{m}", torch.tensor(sk, dtype=torch.int32, device=dev), sk))
+        for tag, idx, idx_np in sets:
+            mm = len(idx_np)
+            y = S.proj_fwd(plan, x, idx)
+            xo = torch.empty_like(x)
+            yo = torch.empty_like(y)
+            work = torch.empty(max(S.fbp_workspace_size(plan, S.F32, B, mm), 16),
+                               dtype=torch.uint8, device=dev)
+            js = joseph_samples(plan, B, idx_np)
+            pa = pixel_angles(plan, B, mm)
+            ops = [("A", lambda: S.proj_fwd(plan, x, idx, out=yo), js),
+                   ("A^T", lambda: S.proj_adj(plan, y, idx, out=xo), js),
+                   ("H", lambda: S.filter(plan, y, 1.0, out=yo), None),
+                   ("B", lambda: S.backproject(plan, y, idx, out=xo), pa),
+                   ("B^T", lambda: S.backproject_adj(plan, x, idx, out=yo), pa),
+                   ("FBP", lambda: S.fbp(plan, y, idx, out=xo, work=work), pa)]
+            for op, fn, smp in ops:
+                us = time_graph(fn, stream)
+                if smp is None:
+                    nd = plan.n_det
+                    macs = B * mm * nd * (nd // 2)
+                    print(json.dumps({"suite": name, "op": op, "angles": tag, "us": round(us, 2),
+                                      "tflops": round(3.0 * macs / (us * 1e-6) / 1e12, 3),
+                                      "roofline_frac": round(3.0 * macs / (us * 1e-6) / 1e12
+                                                             / peak, 4)}), flush=True)
+                else:
+                    op_line(name, op, us, smp, peak, angles=tag, B=B)
+
+    # the differentiated EI step, MC on all views, EI on a 45-angle sketch
+    wl = Workload(N=256, views=180, m=45, G=4, B=8, mc_sketched=False, noisy=False)
+    wp = Workload(N=256, views=180, m=180, G=4, B=8, mc_sketched=False, noisy=False, draw_m=45)
+    prob = make_problem(wl)
+    plan = S.Plan(256, 180, prob["angs"])
+    res = {}
+    for tag, w in (("sketched", wl), ("plain", wp)):
+        arm = Arm(S, plan, prob, w, "f32", dev)
+        idx_all, g_all = step_params(1, w)
+        arm.load_params(idx_all[0], g_all[0], 1)
+        res[tag] = time_graph(arm.step, stream)
+    print(json.dumps({"suite": "ei-step-8x4x256x256-180views-sketch45", "G": 4, "B": 8,
+                      "mc": "all 180 views", "ei": "45-angle sketch",
+                      "sketched_steps_per_s": round(1e6 / res["sketched"], 1),
+                      "plain_steps_per_s": round(1e6 / res["plain"], 1),
+                      "speedup": round(res["plain"] / res["sketched"], 3),
+                      "operator_work_ratio_bound": 3.0}), flush=True)
+
+    # 16 instances mixing 256^2 / 360 angles and 512^2 / 720 angles
+    rng = np.random.default_rng(4)
+    sizes = [(256, 360), (512, 720)] * 8
+    ms = rng.choice([45, 90, 180, 360], size=16)
+    plans = {k: S.Plan(*k) for k in set(sizes)}
+    for dt in (torch.float32, torch.bfloat16):
+        for opname in ("PROJ_FWD", "PROJ_ADJ", "FBP"):
+            op = getattr(S, opname)
+            items, singles, samples = [], [], 0
+            for q, ((N, n), m) in enumerate(zip(sizes, ms)):
+                p = plans[(N, n)]
+                off = I.random_sketch_offset(np.random.default_rng(q), n, int(m))
+                sk = I.sketch_indices(n, int(m), off)
+                idx = torch.tensor(sk, dtype=torch.int32, device=dev)
+                img = torch.randn((1, N, N), device=dev).to(dt)
+                sino = torch.randn((1, int(m), p.n_det), device=dev).to(dt)
+                inp, out = (img, torch.empty_like(sino)) if op == S.PROJ_FWD else \
+                    (sino, torch.empty_like(img))
+                items.append(S.BatchItem(p, inp, out, idx))
+                if op == S.PROJ_FWD:
+                    singles.append(lambda p=p, inp=inp, idx=idx, out=out:
+                                   S.proj_fwd(p, inp, idx, out=out))
+                    samples += joseph_samples(p, 1, sk)
+                elif op == S.PROJ_ADJ:
+                    singles.append(lambda p=p, inp=inp, idx=idx, out=out:
+                                   S.proj_adj(p, inp, idx, out=out))
+                    samples += joseph_samples(p, 1, sk)
+                else:
+                    singles.append(lambda p=p, inp=inp, idx=idx, out=out: S.fbp(p, inp, idx, out=out))
+                    samples += pixel_angles(p, 1, int(m))
+            batch = S.Batch(op, items)
+            us_default = time_graph(batch.run, stream, reps=5)
+            batch.tune(reps=3)
+            us_tuned = time_graph(batch.run, stream, reps=5)
+            us_single = time_graph(lambda: [f() for f in singles], stream, reps=5)
+            op_line("batch-16-mixed-256-512", opname, us_tuned, samples, peak,
+                    dtype="f32" if dt == torch.float32 else "bf16",
+                    us_untuned=round(us_default, 2), us_16_single_launches=round(us_single, 2),
+                    tuned=batch.info(batch.info(0)["phases"] - 1))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -476,17 +679,20 @@ def main():
     except Exception:
         gpu_id = str(local)
 
+    if args.suite:
+        suite(S, dev, torch.cuda.Stream(device=dev))
+        return
     prob = make_problem()
     plan = S.Plan(N_IMG, N_VIEWS, prob["angs"])
     if args.profile:
-        arm = Arm(S, plan, prob, True, args.dtype, dev)
+        arm = Arm(S, plan, prob, SKETCHED, args.dtype, dev)
         arm.step()
         arm.step()
         torch.cuda.synchronize()
         print(json.dumps({"profile_run": "ok", "launches": 2 + 2 * Arm.launches_per_step}))
         return
-    sk = Arm(S, plan, prob, True, args.dtype, dev)
-    pl = Arm(S, plan, prob, False, "f32", dev)
+    sk = Arm(S, plan, prob, SKETCHED, args.dtype, dev)
+    pl = Arm(S, plan, prob, PLAIN, "f32", dev)
 
     # reconstruction quality: both arms, same start, same draws
     curve_sk = psnr_curve(sk, prob["x_gt"], PSNR_ITERS)
@@ -498,7 +704,7 @@ def main():
 
     def timed(arm, use_graph):
         arm.reset()
-        idx_all, g_all = step_params(W + K, arm.sketched, first=PSNR_ITERS + 1)
+        idx_all, g_all = step_params(W + K, arm.wl, first=PSNR_ITERS + 1)
         with torch.cuda.stream(stream):
             graph = None
             if use_graph:
@@ -555,7 +761,7 @@ def main():
     if sk.tdt != torch.float32:
         host_y = host_y.to(sk.tdt).pin_memory()
     host_loss = torch.empty(1, dtype=torch.float64).pin_memory()
-    idx_all, g_all = step_params(K, True, first=PSNR_ITERS + 1 + W + K)
+    idx_all, g_all = step_params(K, SKETCHED, first=PSNR_ITERS + 1 + W + K)
     h_idx = torch.from_numpy(idx_all).pin_memory()
     h_g = torch.from_numpy(g_all).pin_memory()
     h_step = torch.arange(1, K + 1, dtype=torch.int32).pin_memory()
