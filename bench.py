@@ -507,6 +507,19 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+# -------------------------------------------------------------- ranks
+def whole_job(ms, steps, world, device):
+    """Max of the timed interval over the ranks (each runs its own replica)
+    and the whole-job throughput: the steps all ranks ran / that max."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, world * steps / (ms_max * 1e-3)
+
+
 # ------------------------------------------------------------------ suite
 def time_graph(fn, stream, reps=20):
     """Microseconds per call of `fn`: `reps` calls captured in a CUDA graph,
@@ -797,10 +810,7 @@ def main():
         if w:
             kernels[k]["tflops"] = round(w / (bd[k] * 1e-6) / 1e12, 3)
 
-    total_ms = torch.tensor([sk_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(total_ms, op=dist.ReduceOp.MAX)
-    sk_ms_max = float(total_ms.item())
+    sk_ms_max, value = whole_job(sk_ms, K, world, dev)
 
     if rank == 0:
         cpu = None
@@ -811,7 +821,7 @@ def main():
                    "sample": f"{n_cpu} sketched TTT steps at 512^2 (FP64 C oracle, 1 thread)"}
         line = {
             "metric": METRIC,
-            "value": world * K / (sk_ms_max * 1e-3),
+            "value": value,
             "unit": UNIT,
             "n_gpus": world,
             "steps": K,
