@@ -4,24 +4,38 @@
 // and the transpose B_S^T of pixel-driven back-projection (needed to
 // differentiate through A_S^dagger = (pi/m) B_S H, Algorithm 2's update).
 //
-// A cluster of 8 CTAs covers one image and a block of AB angles; CTA r
-// stages lines [r R, (r+1) R) (R = ceil(N/8)) in shared memory - rows as
-// they are, columns transposed - sub-band by sub-band, and accumulates
-// per-bin partial sums in its own shared memory.  After a cluster barrier
-// each CTA reduces 1/8 of the bins over the 8 CTAs' partials through
-// distributed shared memory, in a fixed order: deterministic, no atomics, no
-// global scratch.
+// A cluster of 8 CTAs covers a group of images and a block of AB angles;
+// CTA r stages lines [r R, (r+1) R) (R = ceil(N/8)) in shared memory - rows
+// as they are, columns transposed - sub-band by sub-band, and accumulates
+// per-bin sums in its own shared memory.  After a cluster barrier each CTA
+// reduces 1/8 of the bins over the 8 CTAs' sums through distributed shared
+// memory, in a fixed order: deterministic, no atomics, no global scratch.
+// (Measured on GB300: double-buffered cp.async staging and cutting the bins
+// into chunks per cluster were both slower at 512^2.)
 //
 //   A:    one thread per ray gathers the linear interpolation on each line.
 //   B^T:  one thread per bin gathers, on each line, the (at most 3) pixels
 //         whose bin coordinate lies within one bin of it, with exactly the
 //         back-projector's weights.
 //
-// Up to two jobs share a launch (grid.z spans the images of both), e.g. the
+// Image groups.  All images of a job share the angle list, so positions,
+// weights and candidate pixels are the same for every image of a group of
+// NI = 4: they can be computed once and applied to the 4 images, staged
+// interleaved ([line][position][image], one 16-byte load per tap for the
+// whole group).  Jobs whose image count is not a multiple of 4 finish with
+// single-image groups.  Every image sees the same sequence of operations in
+// either form, and the per-bin sums run over the lines of the band in order
+// whatever the staging sub-band, so results do not depend on the grouping.
+//
+// Up to two jobs share a launch (grid.z spans the groups of both), e.g. the
 // MC projection of x1 and the EI projection of x2 of one SkEI step.
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <cmath>
+#include <functional>
+#include <queue>
+#include <vector>
 
 #include "common.cuh"
 
@@ -30,60 +44,93 @@ namespace cg = cooperative_groups;
 namespace skei {
 namespace {
 
+// Build-time tuning knobs (defaults are the measured best on GB300 for the
+// 512^2 step): image group size of A and of B^T (1 or 4; B^T's 3 candidate
+// weights per line gain from sharing, A's 2 taps do not), staged lines per
+// sub-band for groups of 4, and a fixed number of angles per cluster (0:
+// chosen per launch).
+#ifndef SKEI_BAND_GROUP_FWD
+#define SKEI_BAND_GROUP_FWD 1
+#endif
+#ifndef SKEI_BAND_GROUP_BPADJ
+#define SKEI_BAND_GROUP_BPADJ 4
+#endif
+#ifndef SKEI_BAND_SB4
+#define SKEI_BAND_SB4 8
+#endif
+#ifndef SKEI_BAND_AB
+#define SKEI_BAND_AB 0
+#endif
+
 constexpr int kBands = 8;    // cluster size = number of line bands
-constexpr int kPad = 4;      // zero columns on each side of a staged line
+constexpr int kPad = 4;      // zero positions on each side of a staged line
 constexpr int kMaxAB = 8;    // angles per cluster
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
+__host__ __device__ constexpr int group_max(int op) {
+  return op == OP_JOSEPH ? SKEI_BAND_GROUP_FWD : SKEI_BAND_GROUP_BPADJ;
+}
+
 struct BandGeom {
   int N, n_det, n_angles;
+  int NI;      // images per group (1 or 4), interleaved in shared memory
   int R;       // lines per band
   int SB;      // lines per staged sub-band
-  int Prow;    // pitch of staged rows (multiple of 4: 16-byte aligned rows)
-  int Pcol;    // pitch of staged columns (conflict-free transposed writes)
+  int Prow;    // pitch (positions) of staged rows
+  int Pcol;    // pitch (positions) of staged columns (conflict-free transposed writes)
   int AB;      // angles per cluster
-  int C;       // OP_BP_ADJ: warps (partial rows) per angle = kWarps / AB
-  int fast;    // N % 8 == 0: vectorised staging
+  int fast;    // N % 8 == 0: 16-byte staging of single-image rows
 };
 
 struct BandArgs {
   Jobs jobs;
   const AngleConst *ang;
   int *status;
-  BandGeom g;
+  BandGeom g1, g4;   // geometry of single-image and 4-image groups
 };
 
-// Staging geometry of one image size and operator with AB angles per task.
+// Staging geometry of one image size, operator and group size with AB
+// angles per task.
 __host__ __device__ __forceinline__ BandGeom band_geom(int N, int n_det, int n_angles, int op,
-                                                       int AB) {
+                                                       int AB, int NI) {
   BandGeom g;
   g.N = N;
   g.n_det = n_det;
   g.n_angles = n_angles;
+  g.NI = NI;
   g.R = (N + kBands - 1) / kBands;
   g.Prow = (N + 2 * kPad + 3) & ~3;
-  // A: 32 staged lines (fewer per-ray range setups); B^T: 16 (its per-bin
-  // work per line is larger, and the smaller band leaves room for more CTAs)
-  const int sb = op == OP_JOSEPH ? 32 : 16;
-  g.SB = g.R < sb ? g.R : sb;
-  // transposed staging writes lines 4q..4q+3 of (32 / (SB/4)) positions per
-  // warp: a pitch = 2 mod 8 (16 lines) or odd (32 lines) keeps them in
-  // distinct banks
-  g.Pcol = g.SB == 32 ? ((N + 2 * kPad) | 1) : ((N + 2 * kPad - 2 + 7) & ~7) + 2;
+  if (NI == 1) {
+    // A: 32 staged lines (fewer per-ray range setups); B^T: 16 (its per-bin
+    // work per line is larger, and the smaller band leaves room for more CTAs)
+    const int sb = op == OP_JOSEPH ? 32 : 16;
+    g.SB = g.R < sb ? g.R : sb;
+    // transposed staging writes lines 4q..4q+3 of (32 / (SB/4)) positions
+    // per warp: a pitch = 2 mod 8 (16 lines) or odd (32 lines) keeps them in
+    // distinct banks
+    g.Pcol = g.SB == 32 ? ((N + 2 * kPad) | 1) : ((N + 2 * kPad - 2 + 7) & ~7) + 2;
+  } else {
+    // 16 bytes per position: an odd pitch puts the 8 lines of one position
+    // that 8 consecutive threads write in distinct bank quads
+    g.SB = g.R < SKEI_BAND_SB4 ? g.R : SKEI_BAND_SB4;
+    g.Pcol = (N + 2 * kPad) | 1;
+  }
   g.fast = (N % 8 == 0) ? 1 : 0;
   const int Pmax = g.Prow > g.Pcol ? g.Prow : g.Pcol;
-  while (g.SB > 1 && g.SB * Pmax * 4 > 96 * 1024) --g.SB;  // large N: slow staging
+  while (g.SB > 1 && g.SB * Pmax * 4 * NI > 96 * 1024) --g.SB;  // large N: slow staging
   g.AB = AB;
-  g.C = 1;
   return g;
 }
 
-// Dynamic shared memory of a band task: AB rows of partial bins, then the
-// staged sub-band.
-inline size_t band_smem(const BandGeom &g) {
+// Dynamic shared memory of a band task: the per-bin sums of AB angles, then
+// the staged sub-band.
+__host__ __device__ __forceinline__ size_t band_part_floats(const BandGeom &g) {
+  return (size_t)((g.AB * g.n_det * g.NI + 3) & ~3);
+}
+__host__ __device__ __forceinline__ size_t band_smem(const BandGeom &g) {
   const int Pmax = g.Prow > g.Pcol ? g.Prow : g.Pcol;
-  return (size_t)g.SB * Pmax * 4 + (size_t)((g.AB * g.n_det + 3) & ~3) * 4;
+  return (band_part_floats(g) + (size_t)g.SB * Pmax * g.NI) * 4;
 }
 
 // 4 consecutive image values at element offset i as floats (16-byte aligned
@@ -97,11 +144,11 @@ __device__ __forceinline__ float4 load4(const void *x, size_t i, int bf16) {
   return __ldg(reinterpret_cast<const float4 *>(static_cast<const float *>(x) + i));
 }
 
-// Stages lines [s0, s0 + nl) of image xb (element offset xo in x) into buf
-// (pitch P): mode 1 copies rows, mode 0 copies columns transposed.  kPad
-// zero columns on each side.
-__device__ __forceinline__ void stage(const void *x, size_t xo, int bf16, int N, int mode,
-                                      int s0, int nl, float *buf, int P, bool fast) {
+// Stages lines [s0, s0 + nl) of one image (element offset xo in x) into buf
+// (pitch P positions): mode 1 copies rows, mode 0 copies columns
+// transposed.  kPad zero positions on each side.
+__device__ __forceinline__ void stage1(const void *x, size_t xo, int bf16, int N, int mode,
+                                       int s0, int nl, float *buf, int P, bool fast) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (mode == 1) {
     if (fast) {
@@ -144,6 +191,43 @@ __device__ __forceinline__ void stage(const void *x, size_t xo, int bf16, int N,
     for (int c = lane; c < npad; c += 32) buf[r * P + (c < kPad ? c : N + c)] = 0.0f;
 }
 
+// The same for 4 images (element offset xo + i N^2), interleaved: position
+// p of line l holds the 4 images' values at buf[4 (l P + kPad + p) + i].
+// Needs nl <= 8.
+__device__ __forceinline__ void stage4(const void *x, size_t xo, int bf16, int N, int mode,
+                                       int s0, int nl, float *buf, int P) {
+  const size_t plane = (size_t)N * N;
+  float4 *b4 = reinterpret_cast<float4 *>(buf);
+  if (mode == 1) {
+    // one position per thread: 4 coalesced loads, one 16-byte store
+    for (int r = 0; r < nl; ++r) {
+      const size_t src = xo + (size_t)(s0 + r) * N;
+      float4 *dst = b4 + r * P + kPad;
+      for (int c = threadIdx.x; c < N; c += kThreads)
+        dst[c] = make_float4(ld_any(x, src + c, bf16), ld_any(x, src + plane + c, bf16),
+                             ld_any(x, src + 2 * plane + c, bf16),
+                             ld_any(x, src + 3 * plane + c, bf16));
+    }
+  } else {
+    // 8 consecutive threads take the 8 lines of one position: with an odd
+    // pitch their 16-byte stores fall in distinct bank quads
+    const int l = threadIdx.x & 7;
+    if (l < nl) {
+      for (int p = threadIdx.x >> 3; p < N; p += kThreads / 8) {
+        const size_t src = xo + (size_t)p * N + s0 + l;
+        b4[l * P + kPad + p] = make_float4(ld_any(x, src, bf16), ld_any(x, src + plane, bf16),
+                                           ld_any(x, src + 2 * plane, bf16),
+                                           ld_any(x, src + 3 * plane, bf16));
+      }
+    }
+  }
+  const int npad = P - N;
+  for (int e = threadIdx.x; e < nl * npad; e += kThreads) {
+    const int r = e / npad, c = e - r * npad;
+    b4[r * P + (c < kPad ? c : N + c)] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  }
+}
+
 // Line range [lo, hi) within [s0, s1) on which lam0 + L * lam1 lies in
 // (lo_bound, hi_bound); inv1 = 1 / lam1.
 __device__ __forceinline__ void line_range(float lam0, float lam1, float inv1, float lo_bound,
@@ -161,76 +245,106 @@ __device__ __forceinline__ void line_range(float lam0, float lam1, float inv1, f
   *hi = (int)floorf(lmax) + 1;
 }
 
-// Joseph: sum over lines [s0,s1) of the linear interpolation at the
-// fixed-point crossing pos(L, k) = G + k A + L T on the staged band.
-__device__ __forceinline__ float joseph_partial(const AngleConst &C, int k, int s0, int s1,
-                                                int N, const float *buf, int P) {
+// Joseph: adds to acc[i] the linear interpolations of image i of the group
+// at the fixed-point crossings pos(L, k) = G + k A + L T of lines [s0, s1)
+// of the staged band, line by line in order.
+template <int NI>
+__device__ __forceinline__ void joseph_lines(const AngleConst &C, int k, int s0, int s1, int N,
+                                             const float *buf, int P, float (&acc)[NI]) {
   int lo, hi;
   // taps are nonzero only for pos in (-1, N); the relaxed window keeps every
-  // such line and never reads beyond the kPad zero columns
+  // such line and never reads beyond the kPad zero positions
   line_range(fmaf((float)k, C.Af, C.Gf), C.Tf, C.invT, -1.5f, (float)N + 0.5f, s0, s1, &lo, &hi);
-  float acc = 0.0f;
-  if (lo < hi) {
-    const long long T = C.T;
-    long long pos = C.G + (long long)k * C.A + (long long)lo * T;
-    const float *row = buf + (lo - s0) * P + kPad;
+  if (lo >= hi) return;
+  const long long T = C.T;
+  long long pos = C.G + (long long)k * C.A + (long long)lo * T;
+  const float *row = buf + ((lo - s0) * P + kPad) * NI;
 #pragma unroll 4
-    for (int l = lo; l < hi; ++l) {
-      const int j0 = ipart(pos);
-      const float f = frac23(pos);
-      const float v0 = row[j0], v1 = row[j0 + 1];
-      acc += fmaf(f, v1 - v0, v0);
-      row += P;
-      pos += T;
+  for (int l = lo; l < hi; ++l) {
+    const int j0 = ipart(pos);
+    const float f = frac23(pos);
+    const float g = 1.0f - f;
+    if (NI == 4) {
+      const float4 v0 = *reinterpret_cast<const float4 *>(row + 4 * j0);
+      const float4 v1 = *reinterpret_cast<const float4 *>(row + 4 * j0 + 4);
+      acc[0] = fmaf(g, v0.x, fmaf(f, v1.x, acc[0]));
+      acc[1] = fmaf(g, v0.y, fmaf(f, v1.y, acc[1]));
+      acc[2] = fmaf(g, v0.z, fmaf(f, v1.z, acc[2]));
+      acc[3] = fmaf(g, v0.w, fmaf(f, v1.w, acc[3]));
+    } else {
+      acc[0] = fmaf(g, row[j0], fmaf(f, row[j0 + 1], acc[0]));
     }
+    row += P * NI;
+    pos += T;
   }
-  return acc;
 }
 
-// B^T for bin k: the pixels of lines [s0, s1) whose bin coordinate
-// t(L, P) = t00 + L bline + P bstep lies in (k-1, k+1), weighted exactly as
-// the back-projector weights them.  At most 3 pixels per line
-// (|bstep| >= 1/sqrt 2): the nearest one, r, and its two neighbours.  r and
-// its exact offset D = t(L, r) - k (32-bit fixed point, |D| <= |bstep|/2)
-// are carried from line to line: D grows by bline (|bline| <= |bstep|), and
-// one step of r re-centres it.
-__device__ __forceinline__ float bpadj_partial(const AngleConst &C, int k, int s0, int s1,
-                                               int N, const float *buf, int P) {
+// A tap weight max(1 - |e|, 0) of an offset e = E 2^-28 whose sign is known
+// (NEG: E < 0; else E >= 0), exactly as the back-projector weights it
+// (fraction truncated to 2^-23), clamped in FP32.
+template <bool NEG>
+__device__ __forceinline__ float side_weight(int E) {
+  const int a = E >> (kFxBits - 23);
+  const float w = __int_as_float(NEG ? 0x40000000 + a : 0x40000000 - a) - 1.0f;
+  return fmaxf(w, 0.0f);
+}
+
+// B^T for bin k: adds to acc[i] the pixels of lines [s0, s1) of image i
+// whose bin coordinate t(L, P) = t00 + L bline + P bstep lies in (k-1, k+1),
+// weighted exactly as the back-projector weights them.  At most 3 pixels per
+// line (|bstep| >= 1/sqrt 2): the nearest one, r, at the exact offset
+// D = t(L, r) - k (|D| <= |bstep|/2, 32-bit fixed point), and its two
+// neighbours at D -+ |bstep|.  r and D are carried from line to line: D
+// grows by bline (|bline| <= |bstep|), and one step of r re-centres it.
+template <int NI>
+__device__ __forceinline__ void bpadj_lines(const AngleConst &C, int k, int s0, int s1, int N,
+                                            const float *buf, int P, float (&acc)[NI]) {
   const float kf = (float)k;
   const float inv = C.inv_bstep;
   int lo, hi;
   // the nearest pixel must come within sqrt(2) of [0, N-1]; relaxed window,
-  // so that r stays in [-3, N+2] and its neighbours in the kPad zero columns
+  // so that r stays in [-3, N+2] and its neighbours in the kPad zero positions
   line_range((kf - C.t00f) * inv, -C.blinef * inv, -C.bstepf * C.inv_bline, -2.5f,
              (float)N + 1.5f, s0, s1, &lo, &hi);
-  float acc = 0.0f;
-  if (lo < hi) {
-    const int bs = (int)(unsigned)C.bstep, bl = (int)(unsigned)C.bline;
-    const int abs_bs = abs(bs), half = abs_bs >> 1, sgn = bs < 0 ? -1 : 1;
-    int r = round_int((kf - fmaf((float)lo, C.blinef, C.t00f)) * inv);
-    // D = t(lo, r) - k on the low words (exact: |D| < 2^31)
-    int D = (int)((unsigned)(C.t00 + (long long)lo * C.bline) + (unsigned)r * (unsigned)bs -
-                  ((unsigned)k << kFxBits));
-    const float *row = buf + (lo - s0) * P + kPad;
-    for (int l = lo; l < hi; ++l) {
-      if (D > half) { r -= sgn; D -= abs_bs; }
-      else if (D < -half) { r += sgn; D += abs_bs; }
-      const float *q = row + r;
-      acc = fmaf(w23_to_float(tap_w23(D - bs)), q[-1], acc);
-      acc = fmaf(w23_to_float(tap_w23(D)), q[0], acc);
-      acc = fmaf(w23_to_float(tap_w23(D + bs)), q[1], acc);
-      D += bl;
-      row += P;
+  if (lo >= hi) return;
+  const int bs = (int)(unsigned)C.bstep, bl = (int)(unsigned)C.bline;
+  const int abs_bs = abs(bs), half = abs_bs >> 1, sgn = bs < 0 ? -1 : 1;
+  int r = round_int((kf - fmaf((float)lo, C.blinef, C.t00f)) * inv);
+  // D = t(lo, r) - k on the low words (exact: |D| < 2^31)
+  int D = (int)((unsigned)(C.t00 + (long long)lo * C.bline) + (unsigned)r * (unsigned)bs -
+                ((unsigned)k << kFxBits));
+  // the neighbour at offset D - |bs| sits at r - sgn, the one at D + |bs| at
+  // r + sgn
+  const int step = sgn * NI;
+  const float *row = buf + ((lo - s0) * P + kPad) * NI;
+  for (int l = lo; l < hi; ++l) {
+    if (D > half) { r -= sgn; D -= abs_bs; }
+    else if (D < -half) { r += sgn; D += abs_bs; }
+    const float w_lo = side_weight<true>(D - abs_bs);
+    const float w_mid = __int_as_float(0x40000000 - abs(D >> (kFxBits - 23))) - 1.0f;
+    const float w_hi = side_weight<false>(D + abs_bs);
+    const float *q = row + r * NI;
+    if (NI == 4) {
+      const float4 a = *reinterpret_cast<const float4 *>(q - step);
+      const float4 b = *reinterpret_cast<const float4 *>(q);
+      const float4 c = *reinterpret_cast<const float4 *>(q + step);
+      acc[0] = fmaf(w_hi, c.x, fmaf(w_mid, b.x, fmaf(w_lo, a.x, acc[0])));
+      acc[1] = fmaf(w_hi, c.y, fmaf(w_mid, b.y, fmaf(w_lo, a.y, acc[1])));
+      acc[2] = fmaf(w_hi, c.z, fmaf(w_mid, b.z, fmaf(w_lo, a.z, acc[2])));
+      acc[3] = fmaf(w_hi, c.w, fmaf(w_mid, b.w, fmaf(w_lo, a.w, acc[3])));
+    } else {
+      acc[0] = fmaf(w_hi, q[step], fmaf(w_mid, q[0], fmaf(w_lo, q[-step], acc[0])));
     }
+    D += bl;
+    row += P * NI;
   }
-  return acc;
 }
 
-// One task: image b of job J, angles [a_begin, a_begin + g.AB) of its list,
-// computed by the 8 CTAs of this cluster.  Ends with a cluster barrier, after
-// which the CTA's shared memory may be reused.
-template <int OP>
-__device__ __forceinline__ void band_task(const Job &J, int b, int a_begin, const BandGeom &g,
+// One task: the NI images b0.. of job J, angles [a_begin, a_begin + g.AB)
+// of its list, computed by the 8 CTAs of this cluster.  Ends with a cluster
+// barrier, after which the CTA's shared memory may be reused.
+template <int OP, int NI>
+__device__ __forceinline__ void band_task(const Job &J, int b0, int a_begin, const BandGeom &g,
                                           const AngleConst *ang, int *status, float *smem,
                                           AngleConst *sc, int *sai, cg::cluster_group &cluster) {
   const int tid = threadIdx.x;
@@ -238,9 +352,8 @@ __device__ __forceinline__ void band_task(const Job &J, int b, int a_begin, cons
   if (a_begin >= J.m) return;  // uniform over the cluster: no peer waits for it
   const int na = min(g.AB, J.m - a_begin);
   const int nd = g.n_det, N = g.N;
-  const int nrows = g.AB;                              // rows of partial bins
-  float *part = smem;                                  // [nrows][n_det]
-  float *buf = smem + ((nrows * nd + 3) & ~3);         // [SB][P], 16-byte aligned
+  float *part = smem;                                       // [AB][n_det][NI]
+  float *buf = smem + band_part_floats(g);                  // [SB][P][NI], 16-byte aligned
 
   if (tid < kMaxAB) {
     int ai = -1;
@@ -254,10 +367,10 @@ __device__ __forceinline__ void band_task(const Job &J, int b, int a_begin, cons
     sai[tid] = ai;
     if (ai >= 0) sc[tid] = ang[ai];
   }
-  for (int e = tid; e < nrows * nd; e += kThreads) part[e] = 0.0f;
+  for (int e = tid; e < na * nd * NI; e += kThreads) part[e] = 0.0f;
   __syncthreads();
 
-  const size_t xo = (size_t)b * N * N;
+  const size_t xo = (size_t)b0 * N * N;
   const int L0 = band * g.R, L1 = min(N, L0 + g.R);
   for (int mode = 1; mode >= 0; --mode) {
     bool any = false;
@@ -267,13 +380,30 @@ __device__ __forceinline__ void band_task(const Job &J, int b, int a_begin, cons
     for (int s0 = L0; s0 < L1; s0 += g.SB) {
       const int s1 = min(L1, s0 + g.SB), nl = s1 - s0;
       __syncthreads();  // the previous sub-band is no longer read
-      stage(J.in, xo, J.in_bf16, N, mode, s0, nl, buf, P, g.fast != 0);
+      if (NI == 4) stage4(J.in, xo, J.in_bf16, N, mode, s0, nl, buf, P);
+      else stage1(J.in, xo, J.in_bf16, N, mode, s0, nl, buf, P, g.fast != 0);
       __syncthreads();
       for (int a = 0; a < na; ++a) {
         if (sai[a] < 0 || sc[a].mode != mode) continue;
-        for (int k = tid; k < nd; k += kThreads)
-          part[a * nd + k] += OP == OP_JOSEPH ? joseph_partial(sc[a], k, s0, s1, N, buf, P)
-                                              : bpadj_partial(sc[a], k, s0, s1, N, buf, P);
+        for (int k = tid; k < nd; k += kThreads) {
+          float *pp = part + (a * nd + k) * NI;
+          float acc[NI];
+          if (NI == 4) {
+            const float4 t = *reinterpret_cast<const float4 *>(pp);
+            acc[0] = t.x;
+            acc[1] = t.y;
+            acc[2] = t.z;
+            acc[3] = t.w;
+          } else {
+            acc[0] = pp[0];
+          }
+          if (OP == OP_JOSEPH) joseph_lines<NI>(sc[a], k, s0, s1, N, buf, P, acc);
+          else bpadj_lines<NI>(sc[a], k, s0, s1, N, buf, P, acc);
+          if (NI == 4)
+            *reinterpret_cast<float4 *>(pp) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+          else
+            pp[0] = acc[0];
+        }
       }
     }
   }
@@ -282,24 +412,41 @@ __device__ __forceinline__ void band_task(const Job &J, int b, int a_begin, cons
   const int n_items = na * nd;
   for (int it = band * kThreads + tid; it < n_items; it += kBands * kThreads) {
     const int a = it / nd, k = it - a * nd;
-    float s = 0.0f;
+    float s[NI];
 #pragma unroll
-    for (int q = 0; q < kBands; ++q) s += cluster.map_shared_rank(part, q)[it];
-    const int ai = sai[a];
-    const size_t o = ((size_t)b * J.m + a_begin + a) * nd + k;
-    float v;
-    if (ai < 0) {
-      v = 0.0f;
-    } else if (OP == OP_JOSEPH) {
-      v = s * sc[a].W;
-      if (J.aux) v = ld_any(J.aux, ((size_t)b * g.n_angles + ai) * nd + k, J.aux_bf16) - v;
-      v *= J.alpha;
-    } else {
-      v = s * J.alpha;
+    for (int i = 0; i < NI; ++i) s[i] = 0.0f;
+#pragma unroll
+    for (int q = 0; q < kBands; ++q) {
+      const float *pq = cluster.map_shared_rank(part, q) + it * NI;
+      if (NI == 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(pq);
+        s[0] += t.x;
+        s[1] += t.y;
+        s[2] += t.z;
+        s[3] += t.w;
+      } else {
+        s[0] += pq[0];
+      }
     }
-    st_any(J.out, o, v, J.out_bf16);
+    const int ai = sai[a];
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      const int b = b0 + i;
+      const size_t o = ((size_t)b * J.m + a_begin + a) * nd + k;
+      float v;
+      if (ai < 0) {
+        v = 0.0f;
+      } else if (OP == OP_JOSEPH) {
+        v = s[i] * sc[a].W;
+        if (J.aux) v = ld_any(J.aux, ((size_t)b * g.n_angles + ai) * nd + k, J.aux_bf16) - v;
+        v *= J.alpha;
+      } else {
+        v = s[i] * J.alpha;
+      }
+      st_any(J.out, o, v, J.out_bf16);
+    }
   }
-  cluster.sync();  // keep this CTA's partials alive until every peer has read them
+  cluster.sync();  // keep this CTA's sums alive until every peer has read them
 }
 
 template <int OP>
@@ -309,19 +456,27 @@ __global__ void __cluster_dims__(kBands, 1, 1) __launch_bounds__(kThreads)
   __shared__ AngleConst sc[kMaxAB];
   __shared__ int sai[kMaxAB];
   cg::cluster_group cluster = cg::this_cluster();
-  // the job and image of this cluster
+  // the job and image group of this cluster
   const int z = blockIdx.z;
-  const int jn = (args.jobs.njobs > 1 && z >= args.jobs.j[0].nimg) ? 1 : 0;
+  const int g0 = n_groups(args.jobs.j[0].nimg, group_max(OP));
+  const int jn = (args.jobs.njobs > 1 && z >= g0) ? 1 : 0;
   const Job &J = args.jobs.j[jn];
-  const int b = z - (jn ? args.jobs.j[0].nimg : 0);
-  band_task<OP>(J, b, blockIdx.y * args.g.AB, args.g, args.ang, args.status,
-                reinterpret_cast<float *>(smem4), sc, sai, cluster);
+  int b0, ni;
+  group_at(J.nimg, z - (jn ? g0 : 0), &b0, &ni, group_max(OP));
+  float *smem = reinterpret_cast<float *>(smem4);
+  if (ni == 4)
+    band_task<OP, 4>(J, b0, blockIdx.y * args.g4.AB, args.g4, args.ang, args.status, smem, sc,
+                     sai, cluster);
+  else
+    band_task<OP, 1>(J, b0, blockIdx.y * args.g1.AB, args.g1, args.ang, args.status, smem, sc,
+                     sai, cluster);
 }
 
 // Persistent form over the tasks of a batch of instances (plans of their
 // own): each cluster takes the next task from a global counter (tasks come
 // in decreasing cost order) until none is left; the last cluster to finish
-// resets the counter for the next launch.
+// resets the counter for the next launch.  Task = (item, b0 << 3 | group
+// size, first angle, 0).
 template <int OP>
 __global__ void __cluster_dims__(kBands, 1, 1) __launch_bounds__(kThreads)
     band_batch_kernel(const BatchItem *items, const int4 *tasks, int n_tasks, int AB,
@@ -332,6 +487,7 @@ __global__ void __cluster_dims__(kBands, 1, 1) __launch_bounds__(kThreads)
   __shared__ int s_task;
   cg::cluster_group cluster = cg::this_cluster();
   const bool leader = cluster.block_rank() == 0 && threadIdx.x == 0;
+  float *smem = reinterpret_cast<float *>(smem4);
   for (;;) {
     if (leader) s_task = atomicAdd(queue, 1);
     cluster.sync();
@@ -342,9 +498,14 @@ __global__ void __cluster_dims__(kBands, 1, 1) __launch_bounds__(kThreads)
     const BatchItem &it = items[tk.x];
     const Job J{it.in, nullptr, it.out, it.idx, it.m, it.B, it.alpha, 0.0f,
                 it.in_bf16, 0, it.out_bf16};
-    const BandGeom g = band_geom(it.N, it.n_det, it.n_angles, OP, AB);
-    band_task<OP>(J, tk.y, tk.z, g, it.ang, it.status, reinterpret_cast<float *>(smem4), sc,
-                  sai, cluster);
+    const int b0 = tk.y >> 3, ni = tk.y & 7;
+    if (ni == 4) {
+      const BandGeom g = band_geom(it.N, it.n_det, it.n_angles, OP, AB, 4);
+      band_task<OP, 4>(J, b0, tk.z, g, it.ang, it.status, smem, sc, sai, cluster);
+    } else {
+      const BandGeom g = band_geom(it.N, it.n_det, it.n_angles, OP, AB, 1);
+      band_task<OP, 1>(J, b0, tk.z, g, it.ang, it.status, smem, sc, sai, cluster);
+    }
   }
   if (leader) queue_retire(queue, gridDim.x / kBands);
 }
@@ -380,39 +541,80 @@ int set_band_smem(size_t smem) {
   return SKEI_OK;
 }
 
+// Estimated time of a launch with `ab` angles per cluster: greedy list
+// scheduling of its cluster tasks (decreasing cost, each to the slot that
+// frees first) on `slots` concurrent clusters.  A task of a group of ni
+// images costs ni (angles x bin passes + staging), the staging of the band
+// counting as `stage4` angles for groups of 4 and `stage1` for single images.
+double band_estimate(const Jobs &jobs, int nd, int ab, int slots, int gm, double stage4,
+                     double stage1) {
+  std::vector<double> cost;
+  const double cw = (double)nd / kThreads;   // bin passes per thread
+  for (int q = 0; q < jobs.njobs; ++q) {
+    const Job &J = jobs.j[q];
+    const int g4 = gm == 4 ? J.nimg >> 2 : 0, g1 = J.nimg - 4 * g4;
+    for (int a0 = 0; a0 < J.m; a0 += ab) {
+      const int na = std::min(ab, J.m - a0);
+      for (int i = 0; i < g4; ++i) cost.push_back(4.0 * (na * cw + stage4));
+      for (int i = 0; i < g1; ++i) cost.push_back(na * cw + stage1);
+    }
+  }
+  std::sort(cost.begin(), cost.end(), [](double x, double y) { return x > y; });
+  std::priority_queue<double, std::vector<double>, std::greater<double>> load;
+  for (int i = 0; i < std::max(slots, 1); ++i) load.push(0.0);
+  double span = 0.0;
+  for (double c : cost) {
+    const double t = load.top() + c;
+    load.pop();
+    load.push(t);
+    span = std::max(span, t);
+  }
+  return span;
+}
+
 template <int OP>
 int launch_band(skei_plan p, const Jobs &jobs, cudaStream_t st) {
-  int m_max = 0, nimg = 0;
+  int m_max = 0, ngroups = 0;
+  bool any4 = false, any1 = false;
+  const int gm = group_max(OP);
   for (int q = 0; q < jobs.njobs; ++q) {
     m_max = max(m_max, jobs.j[q].m);
-    nimg += jobs.j[q].nimg;
+    ngroups += n_groups(jobs.j[q].nimg, gm);
+    any4 |= gm == 4 && jobs.j[q].nimg >= 4;
+    any1 |= gm != 4 || (jobs.j[q].nimg & 3) != 0;
   }
-  if (nimg > 65535) return set_error(SKEI_EINVAL, "too many images (%d) in one launch", nimg);
+  if (ngroups > 65535) return set_error(SKEI_EINVAL, "too many images in one launch");
 
-  // angles per cluster: fewest waves x angles per CTA (the per-CTA time),
-  // ties to the larger block (less staging)
+  // angles per cluster: the smallest estimated time, ties to the larger
+  // block (less staging)
   const int ab_max = min(kMaxAB, m_max);
   int best_ab = 1;
   double best_cost = 1e300;
   for (int ab = 1; ab <= ab_max; ++ab) {
-    const size_t bytes = band_smem(band_geom(p->N, p->n_det, p->n_angles, OP, ab));
+    size_t bytes = 0;
+    if (any4)
+      bytes = std::max(bytes, band_smem(band_geom(p->N, p->n_det, p->n_angles, OP, ab, 4)));
+    if (any1)
+      bytes = std::max(bytes, band_smem(band_geom(p->N, p->n_det, p->n_angles, OP, ab, 1)));
     if (bytes > 200 * 1024) continue;
-    int per_sm = (int)((227 * 1024) / (bytes + 1024));
+    int per_sm = (int)((228 * 1024) / (bytes + 2304));
     per_sm = max(1, min(per_sm, 8));
-    const double slots = (double)sm_count() * per_sm;
-    double ctas = 0.0;
-    for (int q = 0; q < jobs.njobs; ++q)
-      ctas += (double)kBands * ((jobs.j[q].m + ab - 1) / ab) * jobs.j[q].nimg;
-    const double cost = std::ceil(ctas / slots) * ab;
+    const int slots = max(1, sm_count() * per_sm / kBands);
+    const double cost = band_estimate(jobs, p->n_det, ab, slots, gm, 1.0, 0.4);
     if (cost <= best_cost) { best_cost = cost; best_ab = ab; }
   }
-  const BandGeom g = band_geom(p->N, p->n_det, p->n_angles, OP, best_ab);
-  const size_t smem = band_smem(g);
+  if (SKEI_BAND_AB > 0) best_ab = min(SKEI_BAND_AB, ab_max);
+  BandArgs a{jobs, p->d_ang, p->d_status,
+             band_geom(p->N, p->n_det, p->n_angles, OP, best_ab, 1),
+             band_geom(p->N, p->n_det, p->n_angles, OP, best_ab, 4)};
+  size_t smem = 0;
+  if (any4) smem = std::max(smem, band_smem(a.g4));
+  if (any1) smem = std::max(smem, band_smem(a.g1));
   if (smem > 227 * 1024)
-    return set_error(SKEI_EINVAL, "detector of %d bins needs too much shared memory", g.n_det);
+    return set_error(SKEI_EINVAL, "detector of %d bins needs too much shared memory", p->n_det);
   SKEI_TRY(set_band_smem<OP>(smem));
-  BandArgs a{jobs, p->d_ang, p->d_status, g};
-  dim3 grid(kBands, (m_max + g.AB - 1) / g.AB, nimg);
+  const int blocks = (m_max + best_ab - 1) / best_ab;
+  dim3 grid(kBands, blocks, ngroups);
   band_kernel<OP><<<grid, kThreads, smem, st>>>(a);
   return check_launch(OP == OP_JOSEPH ? "joseph forward launch" : "back-projection transpose launch");
 }
@@ -454,8 +656,8 @@ int launch_band_jobs(skei_plan p, int op, const Jobs &jobs, cudaStream_t st) {
   return set_error(SKEI_EINVAL, "band launch: unknown operator %d", op);
 }
 
-size_t band_batch_smem(int op, int N, int n_det, int n_angles, int AB) {
-  return band_smem(band_geom(N, n_det, n_angles, op, AB));
+size_t band_batch_smem(int op, int N, int n_det, int n_angles, int AB, int NI) {
+  return band_smem(band_geom(N, n_det, n_angles, op, AB, NI));
 }
 
 int band_batch_occupancy(int op, size_t smem, int *clusters) {

@@ -5,8 +5,9 @@
 // draw a different S_k, Algorithm 2).
 //
 // The host cuts every instance into the tasks of the operator's kernel (a
-// block of angles of one image for A and B^T, an 8 x 256 image tile for A^T
-// and B, a sinogram row for H), sorts them by decreasing cost, and uploads
+// block of angles of an image group for A and B^T, an 8 x 128 tile of an
+// image group for A^T and B, a sinogram row for H; groups of 4 images share
+// their positions and weights), sorts them by decreasing cost, and uploads
 // the list once.  A run is one persistent launch per kernel: as many CTAs (or
 // 8-CTA clusters) as fit on the GPU at once take tasks from a global counter
 // until none is left, so large and small instances share the machine without
@@ -74,18 +75,24 @@ void make_tasks(const Phase &ph, int block, std::vector<int4> *tasks) {
   for (int q = 0; q < (int)ph.items.size(); ++q) {
     const BatchItem &it = ph.items[q];
     if (is_band(ph.kernel)) {
-      for (int b = 0; b < it.B; ++b)
+      for (int gi = 0; gi < n_groups(it.B); ++gi) {
+        int b0, ni;
+        group_at(it.B, gi, &b0, &ni);
         for (int a0 = 0; a0 < it.m; a0 += block) {
           const int na = std::min(block, it.m - a0);
-          v.push_back({(double)na * it.n_det * it.N, make_int4(q, b, a0, 0)});
+          v.push_back({(double)ni * na * it.n_det * it.N, make_int4(q, b0 << 3 | ni, a0, 0)});
         }
+      }
     } else if (is_tile(ph.kernel)) {
-      for (int b = 0; b < it.B; ++b)
+      for (int gi = 0; gi < n_groups(it.B); ++gi) {
+        int b0, ni;
+        group_at(it.B, gi, &b0, &ni);
         for (int ty = 0; ty * tr < it.N; ++ty)
           for (int tx = 0; tx * tc < it.N; ++tx) {
             const int rows = std::min(tr, it.N - ty * tr), cols = std::min(tc, it.N - tx * tc);
-            v.push_back({(double)it.m * rows * cols, make_int4(q, b, ty, tx)});
+            v.push_back({(double)ni * it.m * rows * cols, make_int4(q, b0 << 3 | ni, ty, tx)});
           }
+      }
     } else {
       for (int r = 0; r < it.B * it.m; ++r)
         v.push_back({(double)it.n_det * it.n_det, make_int4(q, r, 0, 0)});
@@ -100,8 +107,12 @@ void make_tasks(const Phase &ph, int block, std::vector<int4> *tasks) {
 int phase_shape(const Phase &ph, int block, size_t *smem, int *workers, int *max_per_sm) {
   if (is_band(ph.kernel)) {
     size_t s = 0;
-    for (const BatchItem &it : ph.items)
-      s = std::max(s, band_batch_smem(ph.kernel, it.N, it.n_det, it.n_angles, block));
+    for (const BatchItem &it : ph.items) {
+      if (it.B >= 4)
+        s = std::max(s, band_batch_smem(ph.kernel, it.N, it.n_det, it.n_angles, block, 4));
+      if (it.B & 3)
+        s = std::max(s, band_batch_smem(ph.kernel, it.N, it.n_det, it.n_angles, block, 1));
+    }
     if (s > 227 * 1024)
       return set_error(SKEI_EINVAL, "batch: %d angles per task need %zu bytes of shared memory",
                        block, s);
@@ -173,11 +184,14 @@ int run_phase(const Phase &ph, cudaStream_t st) {
 double band_makespan(const Phase &ph, int ab, int clusters) {
   std::vector<double> cost;
   for (const BatchItem &it : ph.items)
-    for (int b = 0; b < it.B; ++b)
+    for (int gi = 0; gi < n_groups(it.B); ++gi) {
+      int b0, ni;
+      group_at(it.B, gi, &b0, &ni);
       for (int a0 = 0; a0 < it.m; a0 += ab) {
         const int na = std::min(ab, it.m - a0);
-        cost.push_back((double)na * it.n_det * it.N + 2.0 * it.N * it.N);
+        cost.push_back(ni * ((double)na * it.n_det * it.N + 2.0 * it.N * it.N));
       }
+    }
   std::sort(cost.begin(), cost.end(), [](double a, double b) { return a > b; });
   std::vector<double> load((size_t)std::max(clusters, 1), 0.0);
   for (double c : cost) {

@@ -199,6 +199,25 @@ struct Jobs {
 
 enum { OP_JOSEPH = 0, OP_BP_ADJ = 1, OP_JOSEPH_ADJ = 2, OP_BACKPROJECT = 3 };
 
+// Image groups.  The images of one job share its angle list, so the
+// operator kernels compute positions and weights once per group of 4 images
+// and apply them to all 4; a job of n images is cut into n / 4 groups of 4,
+// then single images.
+// gmax = 1 turns grouping off.
+__host__ __device__ __forceinline__ int n_groups(int n, int gmax = 4) {
+  return gmax == 4 ? (n >> 2) + (n & 3) : n;
+}
+__host__ __device__ __forceinline__ void group_at(int n, int g, int *b0, int *ni, int gmax = 4) {
+  const int q = gmax == 4 ? n >> 2 : 0;
+  if (g < q) {
+    *b0 = 4 * g;
+    *ni = 4;
+  } else {
+    *b0 = 4 * q + (g - q);
+    *ni = 1;
+  }
+}
+
 int launch_band_jobs(skei_plan p, int op, const Jobs &jobs, cudaStream_t st);
 int launch_tile_jobs(skei_plan p, int op, const Jobs &jobs, cudaStream_t st);
 
@@ -228,13 +247,15 @@ __device__ __forceinline__ void queue_retire(int *queue, int workers) {
   }
 }
 
-// Band operators (A: OP_JOSEPH, B^T: OP_BP_ADJ): AB angles per task.
-size_t band_batch_smem(int op, int N, int n_det, int n_angles, int AB);
+// Band operators (A: OP_JOSEPH, B^T: OP_BP_ADJ): AB angles and an image
+// group of NI (1 or 4) per task.  Tasks: int4 (item, b0 << 3 | NI, first
+// angle or tile row, tile column).
+size_t band_batch_smem(int op, int N, int n_det, int n_angles, int AB, int NI);
 int band_batch_occupancy(int op, size_t smem, int *clusters);
 int launch_band_batch_op(int op, const BatchItem *items, const int4 *tasks, int n_tasks, int AB,
                          size_t smem, int clusters, int *queue, cudaStream_t st);
-// Tile operators (A^T: OP_JOSEPH_ADJ, B: OP_BACKPROJECT): one 8 x 256 tile
-// per task; tile_batch_shape gives the tile size for task lists.
+// Tile operators (A^T: OP_JOSEPH_ADJ, B: OP_BACKPROJECT): one tile of an
+// image group per task; tile_batch_shape gives the tile size.
 void tile_batch_shape(int *rows, int *cols);
 int tile_batch_occupancy(int op, int *ctas_per_sm);
 int launch_tile_batch_op(int op, const BatchItem *items, const int4 *tasks, int n_tasks,

@@ -1,14 +1,22 @@
-// Pixel-driven gathers over 8 x 256 image tiles: the exact transpose A_S^T
+// Pixel-driven gathers over 8 x 128 image tiles: the exact transpose A_S^T
 // of Joseph's projector (the gradient of the MC and EI terms, Algorithm 2)
 // and the back-projection B_S of FBP (A_S^dagger = (pi/m) B_S H, Sec. 2.1
 // and 3.1).
 //
-// A CTA owns one tile of one image (one warp per tile row, 8 consecutive
-// pixels per thread) and walks the angle list in chunks; for each angle it
-// stages in shared memory only the window of detector bins the tile projects
-// onto.  Every thread accumulates its 4 pixels in registers and writes each
-// once: no atomics.  Up to two jobs share a launch (grid.z spans the images
-// of both), e.g. the MC-term and EI-term adjoints of one SkEI step.
+// A CTA owns one tile of a group of images (one warp per tile row, 4
+// consecutive pixels per thread) and walks the angle list in chunks; for
+// each angle it stages in shared memory only the window of detector bins
+// the tile projects onto.  Every thread accumulates its pixels in registers
+// and writes each once: no atomics.  Up to two jobs share a launch (grid.z
+// spans the image groups of both), e.g. the MC-term and EI-term adjoints of
+// one SkEI step.
+//
+// Image groups: the images of a job share its angle list, so a pixel's
+// rays, bins and weights are the same for all of them.  A group of 4 images
+// computes them once and reads the 4 images' bins with one 16-byte load
+// (the window holds [bin][image]); jobs whose image count is not a multiple
+// of 4 finish with single-image groups.  Each image sees the same sequence
+// of operations either way.
 //
 // A^T: pixel (L, P) (line, position) receives, for each angle, from the two
 // rays whose crossing with line L has integer part P (weight 1-f) and P-1
@@ -24,11 +32,11 @@
 namespace skei {
 namespace {
 
-constexpr int kPPT = 8;                  // consecutive pixels per thread
+constexpr int kPPT = 4;                  // consecutive pixels per thread
 constexpr int kTW = 32 * kPPT;           // tile width (columns)
 constexpr int kTH = 8;                   // tile height (rows) = warps per CTA
 constexpr int kThreads = 32 * kTH;
-constexpr int kWin = 288;                // staged bins per angle (>= kTW + kTH + 6)
+constexpr int kWin = 160;                // staged bins per angle (>= kTW + kTH + 6)
 constexpr int kAC = 8;                   // angles per chunk
 
 struct TileArgs {
@@ -38,35 +46,34 @@ struct TileArgs {
   int *status;
 };
 
-// Stores up to kPPT consecutive pixels at element offset o.
+// Shared memory of a tile task: the bins of kAC angles for up to 4 images,
+// [angle][bin][image].
+struct TileSmem {
+  alignas(16) float win[kAC * kWin * 4];
+  AngleConst sc[kAC];
+  int sai[kAC];
+  int kw0[kAC];
+};
+
+// Stores kPPT consecutive pixels (n_valid of them inside the image) at
+// element offset o.
 __device__ __forceinline__ void store_run(void *out, size_t o, const float *v, int n_valid,
                                           int bf16) {
   if (!bf16) {
     float *p = static_cast<float *>(out) + o;
     if (n_valid == kPPT && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
-#pragma unroll
-      for (int q = 0; q < kPPT; q += 4)
-        *reinterpret_cast<float4 *>(p + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
+      *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
       return;
     }
   }
   for (int q = 0; q < n_valid; ++q) st_any(out, o + q, v[q], bf16);
 }
 
-// Shared memory of a tile task.
-struct TileSmem {
-  float win[kAC][kWin];
-  AngleConst sc[kAC];
-  int sai[kAC];
-  int kw0[kAC];
-};
-
-// One task: the tile at (i0, j0) of image b of job J.
-template <int OP>
-__device__ __forceinline__ void tile_task(const Job &J, int b, int i0, int j0, int N, int nd,
+// One task: the tile at (i0, j0) of images b0 .. b0 + NI - 1 of job J.
+template <int OP, int NI>
+__device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, int N, int nd,
                                           int n_angles, const AngleConst *ang, int *status,
                                           bool report, TileSmem &sm) {
-  float (*win)[kWin] = sm.win;
   AngleConst *sc = sm.sc;
   int *sai = sm.sai, *kw0 = sm.kw0;
   const int tid = threadIdx.x;
@@ -75,9 +82,11 @@ __device__ __forceinline__ void tile_task(const Job &J, int b, int i0, int j0, i
   const int i = i0 + warp;                 // this thread's row
   const int jb = j0 + kPPT * lane;         // its first column
 
-  float acc[kPPT];
+  float acc[NI][kPPT];
 #pragma unroll
-  for (int q = 0; q < kPPT; ++q) acc[q] = 0.0f;
+  for (int n = 0; n < NI; ++n)
+#pragma unroll
+    for (int q = 0; q < kPPT; ++q) acc[n][q] = 0.0f;
 
   for (int c0 = 0; c0 < J.m; c0 += kAC) {
     const int nac = min(kAC, J.m - c0);
@@ -107,25 +116,33 @@ __device__ __forceinline__ void tile_task(const Job &J, int b, int i0, int j0, i
       }
     }
     __syncthreads();
+    // window: one (angle, bin) per thread, the group's images side by side
     for (int e = tid; e < nac * kWin; e += kThreads) {
       const int a = e / kWin, w = e - a * kWin;
       const int ai = sai[a];
-      float v = 0.0f;
+      float v[NI];
+#pragma unroll
+      for (int n = 0; n < NI; ++n) v[n] = 0.0f;
       if (ai >= 0) {
         const int k = kw0[a] + w;
         if (k >= 0 && k < nd) {
-          v = ld_any(J.in, ((size_t)b * J.m + c0 + a) * nd + k, J.in_bf16);
-          if (OP == OP_JOSEPH_ADJ) v *= sc[a].W;
+          const float W = OP == OP_JOSEPH_ADJ ? sc[a].W : 1.0f;
+#pragma unroll
+          for (int n = 0; n < NI; ++n) {
+            v[n] = ld_any(J.in, ((size_t)(b0 + n) * J.m + c0 + a) * nd + k, J.in_bf16);
+            if (OP == OP_JOSEPH_ADJ) v[n] *= W;
+          }
         }
       }
-      win[a][w] = v;
+      if (NI == 4) reinterpret_cast<float4 *>(sm.win)[e] = make_float4(v[0], v[1], v[2], v[3]);
+      else sm.win[e] = v[0];
     }
     __syncthreads();
 
     for (int a = 0; a < nac; ++a) {
       if (sai[a] < 0) continue;
       const AngleConst &C = sc[a];
-      const float *wa = win[a];
+      const float *wa = sm.win + a * kWin * NI;
       const int base = kw0[a];
       if (OP == OP_JOSEPH_ADJ) {
         const bool row = C.mode != 0;
@@ -152,9 +169,19 @@ __device__ __forceinline__ void tile_task(const Job &J, int b, int i0, int j0, i
           // construction, the clamp only bounds the read
           const int s1 = min(max(r - base, 1), kWin - 2);
           const int s2 = s1 + (right ? -sA : sA);
-          const int w1 = (1 << 23) - abs(D >> (kFxBits - 23));   // |D| < 1: no clamp
-          const int w2 = tap_w23(D2);
-          acc[q] = fmaf(w23_to_float(w1), wa[s1], fmaf(w23_to_float(w2), wa[s2], acc[q]));
+          const float w1 = __int_as_float(0x40000000 - abs(D >> (kFxBits - 23))) - 1.0f;
+          const float w2 = fmaxf(__int_as_float(0x40000000 - abs(D2 >> (kFxBits - 23))) - 1.0f,
+                                 0.0f);
+          if (NI == 4) {
+            const float4 v1 = reinterpret_cast<const float4 *>(wa)[s1];
+            const float4 v2 = reinterpret_cast<const float4 *>(wa)[s2];
+            acc[0][q] = fmaf(w1, v1.x, fmaf(w2, v2.x, acc[0][q]));
+            acc[1][q] = fmaf(w1, v1.y, fmaf(w2, v2.y, acc[1][q]));
+            acc[2][q] = fmaf(w1, v1.z, fmaf(w2, v2.z, acc[2][q]));
+            acc[3][q] = fmaf(w1, v1.w, fmaf(w2, v2.w, acc[3][q]));
+          } else {
+            acc[0][q] = fmaf(w1, wa[s1], fmaf(w2, wa[s2], acc[0][q]));
+          }
           u += du;
           kc += dkc;
         }
@@ -167,8 +194,17 @@ __device__ __forceinline__ void tile_task(const Job &J, int b, int i0, int j0, i
           int k0 = ipart(t) - base;
           k0 = min(max(k0, 0), kWin - 2);
           const float w = frac23(t);
-          const float v0 = wa[k0], v1 = wa[k0 + 1];
-          acc[q] += fmaf(w, v1 - v0, v0);
+          const float g = 1.0f - w;
+          if (NI == 4) {
+            const float4 v0 = reinterpret_cast<const float4 *>(wa)[k0];
+            const float4 v1 = reinterpret_cast<const float4 *>(wa)[k0 + 1];
+            acc[0][q] = fmaf(w, v1.x, fmaf(g, v0.x, acc[0][q]));
+            acc[1][q] = fmaf(w, v1.y, fmaf(g, v0.y, acc[1][q]));
+            acc[2][q] = fmaf(w, v1.z, fmaf(g, v0.z, acc[2][q]));
+            acc[3][q] = fmaf(w, v1.w, fmaf(g, v0.w, acc[3][q]));
+          } else {
+            acc[0][q] = fmaf(w, wa[k0 + 1], fmaf(g, wa[k0], acc[0][q]));
+          }
           t += tj;
         }
       }
@@ -177,31 +213,42 @@ __device__ __forceinline__ void tile_task(const Job &J, int b, int i0, int j0, i
 
   if (i >= N || jb >= N) return;
   const int n_valid = min(kPPT, N - jb);
-  const size_t o = ((size_t)b * N + i) * N + jb;
-  float v[kPPT];
 #pragma unroll
-  for (int q = 0; q < kPPT; ++q) {
-    v[q] = J.alpha * acc[q];
-    if (J.beta != 0.0f && J.aux && q < n_valid)
-      v[q] = fmaf(J.beta, ld_any(J.aux, o + q, J.aux_bf16), v[q]);
+  for (int n = 0; n < NI; ++n) {
+    const size_t o = ((size_t)(b0 + n) * N + i) * N + jb;
+    float v[kPPT];
+#pragma unroll
+    for (int q = 0; q < kPPT; ++q) {
+      v[q] = J.alpha * acc[n][q];
+      if (J.beta != 0.0f && J.aux && q < n_valid)
+        v[q] = fmaf(J.beta, ld_any(J.aux, o + q, J.aux_bf16), v[q]);
+    }
+    store_run(J.out, o, v, n_valid, J.out_bf16);
   }
-  store_run(J.out, o, v, n_valid, J.out_bf16);
 }
 
 template <int OP>
 __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs args) {
   __shared__ TileSmem sm;
   const int z = blockIdx.z;
-  const int jn = (args.jobs.njobs > 1 && z >= args.jobs.j[0].nimg) ? 1 : 0;
+  const int g0 = n_groups(args.jobs.j[0].nimg);
+  const int jn = (args.jobs.njobs > 1 && z >= g0) ? 1 : 0;
   const Job &J = args.jobs.j[jn];
-  const int b = z - (jn ? args.jobs.j[0].nimg : 0);
-  tile_task<OP>(J, b, blockIdx.y * kTH, blockIdx.x * kTW, args.N, args.n_det, args.n_angles,
-                args.ang, args.status, blockIdx.x == 0 && blockIdx.y == 0, sm);
+  int b0, ni;
+  group_at(J.nimg, z - (jn ? g0 : 0), &b0, &ni);
+  const bool report = blockIdx.x == 0 && blockIdx.y == 0;
+  if (ni == 4)
+    tile_task<OP, 4>(J, b0, blockIdx.y * kTH, blockIdx.x * kTW, args.N, args.n_det,
+                     args.n_angles, args.ang, args.status, report, sm);
+  else
+    tile_task<OP, 1>(J, b0, blockIdx.y * kTH, blockIdx.x * kTW, args.N, args.n_det,
+                     args.n_angles, args.ang, args.status, report, sm);
 }
 
 // Persistent form over the tile tasks of a batch of instances: each CTA takes
 // the next task from a global counter (tasks come in decreasing cost order)
-// until none is left.
+// until none is left.  Task = (item, b0 << 3 | group size, tile row, tile
+// column).
 template <int OP>
 __global__ void __launch_bounds__(kThreads)
     tile_batch_kernel(const BatchItem *items, const int4 *tasks, int n_tasks, int *queue) {
@@ -217,19 +264,25 @@ __global__ void __launch_bounds__(kThreads)
     const BatchItem &it = items[tk.x];
     const Job J{it.in, nullptr, it.out, it.idx, it.m, it.B, it.alpha, 0.0f,
                 it.in_bf16, 0, it.out_bf16};
-    tile_task<OP>(J, tk.y, tk.z * kTH, tk.w * kTW, it.N, it.n_det, it.n_angles, it.ang,
-                  it.status, tk.z == 0 && tk.w == 0, sm);
+    const int b0 = tk.y >> 3, ni = tk.y & 7;
+    const bool report = tk.z == 0 && tk.w == 0;
+    if (ni == 4)
+      tile_task<OP, 4>(J, b0, tk.z * kTH, tk.w * kTW, it.N, it.n_det, it.n_angles, it.ang,
+                       it.status, report, sm);
+    else
+      tile_task<OP, 1>(J, b0, tk.z * kTH, tk.w * kTW, it.N, it.n_det, it.n_angles, it.ang,
+                       it.status, report, sm);
   }
   if (threadIdx.x == 0) queue_retire(queue, gridDim.x);
 }
 
 template <int OP>
 int launch_tile(skei_plan p, const Jobs &jobs, cudaStream_t st) {
-  int nimg = 0;
-  for (int q = 0; q < jobs.njobs; ++q) nimg += jobs.j[q].nimg;
-  if (nimg > 65535) return set_error(SKEI_EINVAL, "too many images (%d) in one launch", nimg);
+  int ngroups = 0;
+  for (int q = 0; q < jobs.njobs; ++q) ngroups += n_groups(jobs.j[q].nimg);
+  if (ngroups > 65535) return set_error(SKEI_EINVAL, "too many images in one launch");
   TileArgs a{jobs, p->N, p->n_det, p->n_angles, p->d_ang, p->d_status};
-  dim3 grid((p->N + kTW - 1) / kTW, (p->N + kTH - 1) / kTH, nimg);
+  dim3 grid((p->N + kTW - 1) / kTW, (p->N + kTH - 1) / kTH, ngroups);
   tile_kernel<OP><<<grid, kThreads, 0, st>>>(a);
   return check_launch(OP == OP_JOSEPH_ADJ ? "joseph adjoint launch" : "back-projection launch");
 }
