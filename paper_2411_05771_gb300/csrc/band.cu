@@ -45,10 +45,11 @@ namespace skei {
 namespace {
 
 // Build-time tuning knobs (defaults are the measured best on GB300 for the
-// 512^2 step): image group size of A and of B^T (1 or 4; B^T's 3 candidate
-// weights per line gain from sharing, A's 2 taps do not), staged lines per
-// sub-band for groups of 4, and a fixed number of angles per cluster (0:
-// chosen per launch).
+// 512^2 steps): largest image group of A and of B^T (1 or 4; B^T's 3
+// candidate weights per line gain from sharing when the launch has clusters
+// to spare, A's 2 taps do not), staged lines per
+// sub-band for groups of 4, a fixed number of angles per cluster (0:
+// chosen per launch), and threads per CTA.
 #ifndef SKEI_BAND_GROUP_FWD
 #define SKEI_BAND_GROUP_FWD 1
 #endif
@@ -61,11 +62,14 @@ namespace {
 #ifndef SKEI_BAND_AB
 #define SKEI_BAND_AB 0
 #endif
+#ifndef SKEI_BAND_THREADS
+#define SKEI_BAND_THREADS 256
+#endif
 
 constexpr int kBands = 8;    // cluster size = number of line bands
 constexpr int kPad = 4;      // zero positions on each side of a staged line
 constexpr int kMaxAB = 8;    // angles per cluster
-constexpr int kThreads = 256;
+constexpr int kThreads = SKEI_BAND_THREADS;
 constexpr int kWarps = kThreads / 32;
 
 __host__ __device__ constexpr int group_max(int op) {
@@ -88,6 +92,7 @@ struct BandArgs {
   const AngleConst *ang;
   int *status;
   BandGeom g1, g4;   // geometry of single-image and 4-image groups
+  int gmax;          // group size of this launch (1 or 4)
 };
 
 // Staging geometry of one image size, operator and group size with AB
@@ -112,9 +117,10 @@ __host__ __device__ __forceinline__ BandGeom band_geom(int N, int n_det, int n_a
     g.Pcol = g.SB == 32 ? ((N + 2 * kPad) | 1) : ((N + 2 * kPad - 2 + 7) & ~7) + 2;
   } else {
     // 16 bytes per position: an odd pitch puts the 8 lines of one position
-    // that 8 consecutive threads write in distinct bank quads
+    // that 8 consecutive threads write in distinct bank quads (both modes)
     g.SB = g.R < SKEI_BAND_SB4 ? g.R : SKEI_BAND_SB4;
     g.Pcol = (N + 2 * kPad) | 1;
+    g.Prow = g.Pcol;
   }
   g.fast = (N % 8 == 0) ? 1 : 0;
   const int Pmax = g.Prow > g.Pcol ? g.Prow : g.Pcol;
@@ -152,10 +158,20 @@ __device__ __forceinline__ void stage1(const void *x, size_t xo, int bf16, int N
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (mode == 1) {
     if (fast) {
+      // 4 loads in flight per thread before their stores
       for (int r = warp; r < nl; r += kWarps) {
         const size_t src = xo + (size_t)(s0 + r) * N;
         float *dst = buf + r * P + kPad;
-        for (int c = 4 * lane; c < N; c += 128)
+        int c = 4 * lane;
+        for (; c + 384 < N; c += 512) {
+          const float4 a = load4(x, src + c, bf16), b = load4(x, src + c + 128, bf16);
+          const float4 d = load4(x, src + c + 256, bf16), e = load4(x, src + c + 384, bf16);
+          *reinterpret_cast<float4 *>(dst + c) = a;
+          *reinterpret_cast<float4 *>(dst + c + 128) = b;
+          *reinterpret_cast<float4 *>(dst + c + 256) = d;
+          *reinterpret_cast<float4 *>(dst + c + 384) = e;
+        }
+        for (; c < N; c += 128)
           *reinterpret_cast<float4 *>(dst + c) = load4(x, src + c, bf16);
       }
     } else {
@@ -172,14 +188,27 @@ __device__ __forceinline__ void stage1(const void *x, size_t xo, int bf16, int N
       const int qn = nl >> 2, qs = nl == 16 ? 2 : 3;
       const int q = lane & (qn - 1);
       const int per_warp = 32 / qn;
-      for (int p = warp * per_warp + (lane >> qs); p < N; p += kWarps * per_warp) {
-        const float4 v = load4(x, xo + (size_t)p * N + s0 + 4 * q, bf16);
+      const int step = kWarps * per_warp;
+      auto put = [&](int p, const float4 &v) {
         float *dst = buf + (4 * q) * P + kPad + p;
         dst[0] = v.x;
         dst[P] = v.y;
         dst[2 * P] = v.z;
         dst[3 * P] = v.w;
+      };
+      int p = warp * per_warp + (lane >> qs);
+      // 4 loads in flight per thread before their stores
+      for (; p + 3 * step < N; p += 4 * step) {
+        const float4 a = load4(x, xo + (size_t)p * N + s0 + 4 * q, bf16);
+        const float4 b = load4(x, xo + (size_t)(p + step) * N + s0 + 4 * q, bf16);
+        const float4 d = load4(x, xo + (size_t)(p + 2 * step) * N + s0 + 4 * q, bf16);
+        const float4 e = load4(x, xo + (size_t)(p + 3 * step) * N + s0 + 4 * q, bf16);
+        put(p, a);
+        put(p + step, b);
+        put(p + 2 * step, d);
+        put(p + 3 * step, e);
       }
+      for (; p < N; p += step) put(p, load4(x, xo + (size_t)p * N + s0 + 4 * q, bf16));
     } else {
       for (int p = warp; p < N; p += kWarps)
         for (int l = lane; l < nl; l += 32)
@@ -193,17 +222,81 @@ __device__ __forceinline__ void stage1(const void *x, size_t xo, int bf16, int N
 
 // The same for 4 images (element offset xo + i N^2), interleaved: position
 // p of line l holds the 4 images' values at buf[4 (l P + kPad + p) + i].
-// Needs nl <= 8.
+// Needs nl <= 8 and an odd pitch P.
+//
+// FP32 fast path (N, s0, nl multiples of 4): every thread loads 4
+// consecutive values of each image with one 16-byte load, transposes the
+// 4 x 4 block in registers and stores 4 positions of 16 bytes; loads are
+// issued in batches of two blocks before the stores.  The thread mapping
+// keeps the stores of each quarter warp in distinct bank quads: rows (mode
+// 1): 8 lines x 4 position groups per warp; columns (mode 0): pairs of
+// 4-line groups x consecutive positions.
+__device__ __forceinline__ void store_block(float4 *dst, int step, const float4 (&v)[4]) {
+  dst[0] = make_float4(v[0].x, v[1].x, v[2].x, v[3].x);
+  dst[step] = make_float4(v[0].y, v[1].y, v[2].y, v[3].y);
+  dst[2 * step] = make_float4(v[0].z, v[1].z, v[2].z, v[3].z);
+  dst[3 * step] = make_float4(v[0].w, v[1].w, v[2].w, v[3].w);
+}
+
 __device__ __forceinline__ void stage4(const void *x, size_t xo, int bf16, int N, int mode,
                                        int s0, int nl, float *buf, int P) {
   const size_t plane = (size_t)N * N;
   float4 *b4 = reinterpret_cast<float4 *>(buf);
-  if (mode == 1) {
+  const int tid = threadIdx.x;
+  const bool fast = !bf16 && (N & 3) == 0 && (s0 & 3) == 0 && (nl & 3) == 0;
+  const float4 *x4 = reinterpret_cast<const float4 *>(static_cast<const float *>(x) + xo);
+  const size_t plane4 = plane >> 2;
+  if (fast && mode == 1) {
+    const int r = tid & 7, pg = tid >> 3;             // line, position group
+    const int ngroups = N >> 2, step_g = kThreads >> 3;
+    if (r < nl) {
+      const size_t row4 = ((size_t)(s0 + r) * N) >> 2;
+      float4 *dst = b4 + r * P + kPad;
+      int g = pg;
+      for (; g + step_g < ngroups; g += 2 * step_g) {
+        float4 va[4], vb[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          va[i] = __ldg(x4 + i * plane4 + row4 + g);
+          vb[i] = __ldg(x4 + i * plane4 + row4 + g + step_g);
+        }
+        store_block(dst + 4 * g, 1, va);
+        store_block(dst + 4 * (g + step_g), 1, vb);
+      }
+      if (g < ngroups) {
+        float4 va[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) va[i] = __ldg(x4 + i * plane4 + row4 + g);
+        store_block(dst + 4 * g, 1, va);
+      }
+    }
+  } else if (fast) {
+    const int lgs = nl >> 2;                          // 4-line groups (1 or 2)
+    const int lg = tid % lgs, p0 = tid / lgs, step_p = kThreads / lgs;
+    float4 *dst = b4 + (4 * lg) * P + kPad;
+    int p = p0;
+    for (; p + step_p < N; p += 2 * step_p) {
+      float4 va[4], vb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        va[i] = __ldg(x4 + i * plane4 + (((size_t)p * N + s0) >> 2) + lg);
+        vb[i] = __ldg(x4 + i * plane4 + (((size_t)(p + step_p) * N + s0) >> 2) + lg);
+      }
+      store_block(dst + p, P, va);
+      store_block(dst + p + step_p, P, vb);
+    }
+    if (p < N) {
+      float4 va[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) va[i] = __ldg(x4 + i * plane4 + (((size_t)p * N + s0) >> 2) + lg);
+      store_block(dst + p, P, va);
+    }
+  } else if (mode == 1) {
     // one position per thread: 4 coalesced loads, one 16-byte store
     for (int r = 0; r < nl; ++r) {
       const size_t src = xo + (size_t)(s0 + r) * N;
       float4 *dst = b4 + r * P + kPad;
-      for (int c = threadIdx.x; c < N; c += kThreads)
+      for (int c = tid; c < N; c += kThreads)
         dst[c] = make_float4(ld_any(x, src + c, bf16), ld_any(x, src + plane + c, bf16),
                              ld_any(x, src + 2 * plane + c, bf16),
                              ld_any(x, src + 3 * plane + c, bf16));
@@ -211,9 +304,9 @@ __device__ __forceinline__ void stage4(const void *x, size_t xo, int bf16, int N
   } else {
     // 8 consecutive threads take the 8 lines of one position: with an odd
     // pitch their 16-byte stores fall in distinct bank quads
-    const int l = threadIdx.x & 7;
+    const int l = tid & 7;
     if (l < nl) {
-      for (int p = threadIdx.x >> 3; p < N; p += kThreads / 8) {
+      for (int p = tid >> 3; p < N; p += kThreads / 8) {
         const size_t src = xo + (size_t)p * N + s0 + l;
         b4[l * P + kPad + p] = make_float4(ld_any(x, src, bf16), ld_any(x, src + plane, bf16),
                                            ld_any(x, src + 2 * plane, bf16),
@@ -222,7 +315,7 @@ __device__ __forceinline__ void stage4(const void *x, size_t xo, int bf16, int N
     }
   }
   const int npad = P - N;
-  for (int e = threadIdx.x; e < nl * npad; e += kThreads) {
+  for (int e = tid; e < nl * npad; e += kThreads) {
     const int r = e / npad, c = e - r * npad;
     b4[r * P + (c < kPad ? c : N + c)] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   }
@@ -458,11 +551,11 @@ __global__ void __cluster_dims__(kBands, 1, 1) __launch_bounds__(kThreads)
   cg::cluster_group cluster = cg::this_cluster();
   // the job and image group of this cluster
   const int z = blockIdx.z;
-  const int g0 = n_groups(args.jobs.j[0].nimg, group_max(OP));
+  const int g0 = n_groups(args.jobs.j[0].nimg, args.gmax);
   const int jn = (args.jobs.njobs > 1 && z >= g0) ? 1 : 0;
   const Job &J = args.jobs.j[jn];
   int b0, ni;
-  group_at(J.nimg, z - (jn ? g0 : 0), &b0, &ni, group_max(OP));
+  group_at(J.nimg, z - (jn ? g0 : 0), &b0, &ni, args.gmax);
   float *smem = reinterpret_cast<float *>(smem4);
   if (ni == 4)
     band_task<OP, 4>(J, b0, blockIdx.y * args.g4.AB, args.g4, args.ang, args.status, smem, sc,
@@ -572,23 +665,20 @@ double band_estimate(const Jobs &jobs, int nd, int ab, int slots, int gm, double
   return span;
 }
 
+// Angles per cluster for group size gm: the smallest estimated time, ties
+// to the larger block (less staging).  Also returns the number of cluster
+// tasks and concurrent cluster slots of that choice.
 template <int OP>
-int launch_band(skei_plan p, const Jobs &jobs, cudaStream_t st) {
-  int m_max = 0, ngroups = 0;
+int choose_ab(skei_plan p, const Jobs &jobs, int gm, int *tasks, int *slots_out) {
+  int m_max = 0;
   bool any4 = false, any1 = false;
-  const int gm = group_max(OP);
   for (int q = 0; q < jobs.njobs; ++q) {
     m_max = max(m_max, jobs.j[q].m);
-    ngroups += n_groups(jobs.j[q].nimg, gm);
     any4 |= gm == 4 && jobs.j[q].nimg >= 4;
     any1 |= gm != 4 || (jobs.j[q].nimg & 3) != 0;
   }
-  if (ngroups > 65535) return set_error(SKEI_EINVAL, "too many images in one launch");
-
-  // angles per cluster: the smallest estimated time, ties to the larger
-  // block (less staging)
   const int ab_max = min(kMaxAB, m_max);
-  int best_ab = 1;
+  int best_ab = 1, best_slots = 1;
   double best_cost = 1e300;
   for (int ab = 1; ab <= ab_max; ++ab) {
     size_t bytes = 0;
@@ -601,19 +691,50 @@ int launch_band(skei_plan p, const Jobs &jobs, cudaStream_t st) {
     per_sm = max(1, min(per_sm, 8));
     const int slots = max(1, sm_count() * per_sm / kBands);
     const double cost = band_estimate(jobs, p->n_det, ab, slots, gm, 1.0, 0.4);
-    if (cost <= best_cost) { best_cost = cost; best_ab = ab; }
+    if (cost <= best_cost) { best_cost = cost; best_ab = ab; best_slots = slots; }
   }
   if (SKEI_BAND_AB > 0) best_ab = min(SKEI_BAND_AB, ab_max);
+  int n = 0;
+  for (int q = 0; q < jobs.njobs; ++q)
+    n += n_groups(jobs.j[q].nimg, gm) * ((jobs.j[q].m + best_ab - 1) / best_ab);
+  *tasks = n;
+  *slots_out = best_slots;
+  return best_ab;
+}
+
+template <int OP>
+int launch_band(skei_plan p, const Jobs &jobs, cudaStream_t st) {
+  // groups of 4 pay only when, with one angle per cluster, they still leave
+  // a cluster task for every concurrent cluster slot: otherwise the launch
+  // runs single images
+  int gm = group_max(OP), tasks = 0, slots = 1;
+  if (gm == 4) {
+    int t1 = 0;
+    for (int q = 0; q < jobs.njobs; ++q) t1 += n_groups(jobs.j[q].nimg, 4) * jobs.j[q].m;
+    const size_t bytes = band_smem(band_geom(p->N, p->n_det, p->n_angles, OP, 1, 4));
+    const int per_sm = max(1, min((int)((228 * 1024) / (bytes + 2304)), 8));
+    if (t1 < max(1, sm_count() * per_sm / kBands)) gm = 1;
+  }
+  const int ab = choose_ab<OP>(p, jobs, gm, &tasks, &slots);
+  int m_max = 0, ngroups = 0;
+  bool any4 = false, any1 = false;
+  for (int q = 0; q < jobs.njobs; ++q) {
+    m_max = max(m_max, jobs.j[q].m);
+    ngroups += n_groups(jobs.j[q].nimg, gm);
+    any4 |= gm == 4 && jobs.j[q].nimg >= 4;
+    any1 |= gm != 4 || (jobs.j[q].nimg & 3) != 0;
+  }
+  if (ngroups > 65535) return set_error(SKEI_EINVAL, "too many images in one launch");
   BandArgs a{jobs, p->d_ang, p->d_status,
-             band_geom(p->N, p->n_det, p->n_angles, OP, best_ab, 1),
-             band_geom(p->N, p->n_det, p->n_angles, OP, best_ab, 4)};
+             band_geom(p->N, p->n_det, p->n_angles, OP, ab, 1),
+             band_geom(p->N, p->n_det, p->n_angles, OP, ab, 4), gm};
   size_t smem = 0;
   if (any4) smem = std::max(smem, band_smem(a.g4));
   if (any1) smem = std::max(smem, band_smem(a.g1));
   if (smem > 227 * 1024)
     return set_error(SKEI_EINVAL, "detector of %d bins needs too much shared memory", p->n_det);
   SKEI_TRY(set_band_smem<OP>(smem));
-  const int blocks = (m_max + best_ab - 1) / best_ab;
+  const int blocks = (m_max + ab - 1) / ab;
   dim3 grid(kBands, blocks, ngroups);
   band_kernel<OP><<<grid, kThreads, smem, st>>>(a);
   return check_launch(OP == OP_JOSEPH ? "joseph forward launch" : "back-projection transpose launch");

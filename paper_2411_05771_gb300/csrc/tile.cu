@@ -32,9 +32,14 @@
 namespace skei {
 namespace {
 
+// Build-time tuning knob: tile height (rows = warps per CTA), 4 or 8.
+#ifndef SKEI_TILE_ROWS
+#define SKEI_TILE_ROWS 8
+#endif
+
 constexpr int kPPT = 4;                  // consecutive pixels per thread
 constexpr int kTW = 32 * kPPT;           // tile width (columns)
-constexpr int kTH = 8;                   // tile height (rows) = warps per CTA
+constexpr int kTH = SKEI_TILE_ROWS;      // tile height (rows) = warps per CTA
 constexpr int kThreads = 32 * kTH;
 constexpr int kWin = 160;                // staged bins per angle (>= kTW + kTH + 6)
 constexpr int kAC = 8;                   // angles per chunk
