@@ -60,7 +60,7 @@ def parse():
                          "differentiated EI step at 8 x 4 x 256^2, the 16-instance batch")
     ap.add_argument("--profile", action="store_true",
                     help="set up the sketched arm, run one warm and one more step, and exit "
-                         "(a short, untimed run for ncu: 2 launches of set-up, then 13 per step)")
+                         "(a short, untimed run for ncu: 2 launches of set-up, then 14 per step)")
     return ap.parse_args()
 
 
@@ -184,7 +184,7 @@ class Arm:
         # dL/dtheta = dL/dx1 + sum_g dL/dx3 (F's Jacobian is the identity)
         S.adam_step(self.theta, self.m1, self.v1, self.step_no, self.gx1, self.gx3, lr=LR)
 
-    launches_per_step = 13  # 1 + 4 + 1 + 2 + 4 + 1 kernels, see step()
+    launches_per_step = 14  # 1 + 4 + 1 + 2 + 5 + 1 kernels, see step()
 
     def reset(self):
         self.theta.zero_()
@@ -307,9 +307,11 @@ class Clocks:
 
 
 def kernel_breakdown(S, arm, stream, reps=20):
-    """Device time of every kernel launch of one step, each re-issued with
-    the step's own arguments: `reps` copies are captured in a CUDA graph and
-    the replay is timed with CUDA events on the launching stream."""
+    """Device time of every operator of one step, each re-issued with the
+    step's own arguments through the public entry point that runs the same
+    kernels (B^T: its workspace form, two launches): `reps`
+    copies are captured in a CUDA graph and the replay is timed with CUDA
+    events on the launching stream."""
     import torch
     p = arm.plan
     mc_idx = arm.idx if arm.sketched else None
@@ -330,18 +332,21 @@ def kernel_breakdown(S, arm, stream, reps=20):
     gx3 = arm.gx3.reshape(BG, N, N)
     gx2 = arm.gx2.reshape(BG, N, N)
     z = arm.z.reshape(BG, N, N)
+    fwd_jobs = [S.Job(arm.x1, arm.r, mc_idx, aux=arm.y), S.Job(x2, pbuf, sk_idx)]
+    bpa_jobs = [S.Job(gx3, p_t, sk_idx)]
+    wsum = torch.empty(max(S.band_sums_workspace_size(p, bpa_jobs), 16), dtype=torch.uint8,
+                       device="cuda")
     ops = {
         "residual_add(x1)": lambda: S.residual_add(arm.x0, arm.theta, out=arm.x1),
         "rotate": lambda: S.rotate(arm.x1, arm.g, out=arm.x2),
-        "joseph_fwd(MC+EI)": lambda: S.proj_fwd_multi(
-            p, [S.Job(arm.x1, arm.r, mc_idx, aux=arm.y), S.Job(x2, pbuf, sk_idx)]),
+        "joseph_fwd(MC+EI)": lambda: S.proj_fwd_multi(p, fwd_jobs),
         "ramlak(fwd)": lambda: S.filter(p, pbuf, np.pi / m, out=qbuf),
         "backproject": lambda: S.backproject(p, q_t, sk_idx, out=z),
         "residual_add(x3)": lambda: S.residual_add(arm.z, arm.theta, out=arm.x3),
         "loss_finish": lambda: S.ei_loss_finish(
             arm.x2, arm.x3, arm.r, LAM, arm.mc_scale, work=arm.work,
             out=(arm.loss, arm.mc, arm.ei, arm.gx2, arm.gx3)),
-        "backproject_adj": lambda: S.backproject_adj(p, gx3, sk_idx, out=p_t),
+        "backproject_adj": lambda: S.backproject_adj_multi_ws(p, bpa_jobs, work=wsum),
         "ramlak(bwd)": lambda: S.filter(p, pbuf, np.pi / m, out=qbuf),
         "joseph_adj(MC+EI)": lambda: S.proj_adj_multi(
             p, [S.Job(arm.r, arm.gx1, mc_idx, alpha=-2.0 * arm.mc_scale / wl.B),
@@ -591,11 +596,17 @@ def suite(S, dev, stream):
                                dtype=torch.uint8, device=dev)
             js = joseph_samples(plan, B, idx_np)
             pa = pixel_angles(plan, B, mm)
+            fj = [S.Job(x, yo, idx)]
+            wsum = torch.empty(max(S.band_sums_workspace_size(plan, fj), 16), dtype=torch.uint8,
+                               device=dev)
             ops = [("A", lambda: S.proj_fwd(plan, x, idx, out=yo), js),
+                   ("A (band sums)", lambda: S.proj_fwd_multi_ws(plan, fj, work=wsum), js),
                    ("A^T", lambda: S.proj_adj(plan, y, idx, out=xo), js),
                    ("H", lambda: S.filter(plan, y, 1.0, out=yo), None),
                    ("B", lambda: S.backproject(plan, y, idx, out=xo), pa),
                    ("B^T", lambda: S.backproject_adj(plan, x, idx, out=yo), pa),
+                   ("B^T (band sums)", lambda: S.backproject_adj_multi_ws(plan, fj, work=wsum),
+                    pa),
                    ("FBP", lambda: S.fbp(plan, y, idx, out=xo, work=work), pa)]
             for op, fn, smp in ops:
                 us = time_graph(fn, stream)

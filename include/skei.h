@@ -155,6 +155,24 @@ int skei_proj_fwd_multi(skei_plan plan, const skei_job *jobs, int njobs,
 int skei_proj_adj_multi(skei_plan plan, const skei_job *jobs, int njobs,
                         void *stream);
 
+/* Workspace forms of the line-summing operators A (skei_proj_fwd_multi_ws,
+ * jobs as for skei_proj_fwd_multi) and B^T (skei_backproject_adj_multi_ws:
+ * a job computes out = alpha B_S^T in, in [B][N][N], out [B][m][n_det];
+ * aux and beta ignored).  Two launches: every CTA sums a thin band of image
+ * lines for a block of angles into `work` (band sums [image][band][angle]
+ * [bin], FP32), then the bands are added in a fixed order.  The image lines
+ * are staged once per angle block instead of once per angle, which makes
+ * these faster than the forms without workspace on large angle sets; the
+ * results agree with them to FP32 rounding (different summation order).
+ * `work` is a DEVICE buffer of at least skei_band_sums_workspace_size(plan,
+ * jobs, njobs) bytes, 16-byte aligned, owned by the caller; calls sharing
+ * it must not overlap. */
+size_t skei_band_sums_workspace_size(skei_plan plan, const skei_job *jobs, int njobs);
+int skei_proj_fwd_multi_ws(skei_plan plan, const skei_job *jobs, int njobs, void *work,
+                           size_t work_bytes, void *stream);
+int skei_backproject_adj_multi_ws(skei_plan plan, const skei_job *jobs, int njobs, void *work,
+                                  size_t work_bytes, void *stream);
+
 /* ---------------------------------------------------- H, B, B^T, FBP --
  * skei_filter: q = scale * H p for `rows` rows of n_det bins (dtype).
  * H is the Ram-Lak ramp of filtered back-projection (Sec. 2.1, 4.1.1); it is

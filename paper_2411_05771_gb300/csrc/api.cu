@@ -206,7 +206,7 @@ int fbp_adj_impl(skei_plan p, const T *x, int B, const int *idx, int m, T *sino,
 
 // -------------------------------------------------------------- EI loss --
 struct EiWork {
-  size_t p_bytes, img_bytes, part_bytes, total;
+  size_t p_bytes, img_bytes, part_bytes, band_off, band_floats, total;
   int cpi, cpr;
 };
 
@@ -220,7 +220,14 @@ EiWork ei_work(skei_plan p, int B, int G, int mc_m, int sk_m) {
   w.part_bytes = align256((bg * w.cpi + (size_t)B * w.cpr) * sizeof(double));
   const size_t fwd = 2 * w.p_bytes;
   const size_t bwd = 2 * w.p_bytes + w.img_bytes;
-  w.total = std::max(std::max(fwd, bwd), w.part_bytes);
+  w.band_off = std::max(std::max(fwd, bwd), w.part_bytes);
+  // band sums of B^T (EI job)
+  Jobs jb{};
+  jb.njobs = 1;
+  jb.j[0].nimg = (int)bg;
+  jb.j[0].m = sk_m;
+  w.band_floats = band_partial_floats(p, jb);
+  w.total = w.band_off + align256(w.band_floats * sizeof(float));
   return w;
 }
 
@@ -240,6 +247,8 @@ int ei_fwd_impl(skei_plan p, const T *x1, const T *y, int B, const int *mc_idx, 
   J.njobs = 2;
   J.j[0] = Job{x1, y, r, mc_idx, mc_m, B, 1.0f, 0.0f, tb, tb, tb};
   J.j[1] = Job{x2, nullptr, pbuf, sk_idx, sk_m, BG, 1.0f, 0.0f, tb, 0, 0};
+  // (the cluster form: for A's 2 taps per line the band-sums form measured
+  // slower at 512^2)
   if ((rc = launch_band_jobs(p, OP_JOSEPH, J, st))) return rc;
   if ((rc = launch_filter<float, float>(p, pbuf, BG * sk_m, (float)(kPi / sk_m), qbuf, st)))
     return rc;
@@ -260,7 +269,12 @@ int ei_bwd_impl(skei_plan p, const T *r, const T *g_x2, const T *g_z, int B, con
   int rc;
   if (g_z) {
     // through z = (pi/m) B_S H A_S x2:  g_x2 + (pi/m) A_S^T H B_S^T g_z
-    if ((rc = launch_backproject_adj<T, float>(p, g_z, BG, sk_idx, sk_m, 1.0f, ubuf, st)))
+    Jobs Jb{};
+    Jb.njobs = 1;
+    Jb.j[0] = Job{g_z, nullptr, ubuf, sk_idx, sk_m, BG, 1.0f, 0.0f, tb, 0, 0};
+    if ((rc = launch_band_partial_jobs(p, OP_BP_ADJ, Jb,
+                                      reinterpret_cast<float *>(work + w.band_off),
+                                      w.band_floats, st)))
       return rc;
     if ((rc = launch_filter<float, float>(p, ubuf, BG * sk_m, (float)(kPi / sk_m), vbuf, st)))
       return rc;
@@ -381,6 +395,44 @@ int skei_proj_fwd_multi(skei_plan plan, const skei_job *jobs, int njobs, void *s
   Jobs J{};
   SKEI_TRY(to_jobs(plan, jobs, njobs, true, &J));
   return launch_band_jobs(plan, OP_JOSEPH, J, as_stream(stream));
+}
+
+size_t skei_band_sums_workspace_size(skei_plan plan, const skei_job *jobs, int njobs) {
+  if (check_plan(plan) || !jobs || njobs < 1 || njobs > SKEI_MAX_JOBS) return 0;
+  Jobs J{};
+  J.njobs = njobs;
+  for (int q = 0; q < njobs; ++q) {
+    if (jobs[q].B < 1 || jobs[q].m < 1) return 0;
+    J.j[q].nimg = jobs[q].B;
+    J.j[q].m = jobs[q].m;
+  }
+  return band_partial_floats(plan, J) * sizeof(float);
+}
+
+int skei_proj_fwd_multi_ws(skei_plan plan, const skei_job *jobs, int njobs, void *work,
+                           size_t work_bytes, void *stream) {
+  SKEI_TRY(check_plan(plan));
+  Jobs J{};
+  SKEI_TRY(to_jobs(plan, jobs, njobs, true, &J));
+  const size_t need = band_partial_floats(plan, J) * sizeof(float);
+  SKEI_TRY(check_work(work, work_bytes, need));
+  return launch_band_partial_jobs(plan, OP_JOSEPH, J, static_cast<float *>(work),
+                                  work_bytes / sizeof(float), as_stream(stream));
+}
+
+int skei_backproject_adj_multi_ws(skei_plan plan, const skei_job *jobs, int njobs, void *work,
+                                  size_t work_bytes, void *stream) {
+  SKEI_TRY(check_plan(plan));
+  Jobs J{};
+  SKEI_TRY(to_jobs(plan, jobs, njobs, false, &J));
+  for (int q = 0; q < J.njobs; ++q) {
+    J.j[q].aux = nullptr;
+    J.j[q].beta = 0.0f;
+  }
+  const size_t need = band_partial_floats(plan, J) * sizeof(float);
+  SKEI_TRY(check_work(work, work_bytes, need));
+  return launch_band_partial_jobs(plan, OP_BP_ADJ, J, static_cast<float *>(work),
+                                  work_bytes / sizeof(float), as_stream(stream));
 }
 
 int skei_proj_adj_multi(skei_plan plan, const skei_job *jobs, int njobs, void *stream) {

@@ -182,10 +182,10 @@ __device__ __forceinline__ void stage1(const void *x, size_t xo, int bf16, int N
       }
     }
   } else {
-    if (fast && (nl == 16 || nl == 32) && (s0 & 3) == 0) {
+    if (fast && (nl == 8 || nl == 16 || nl == 32) && (s0 & 3) == 0) {
       // lane = (nl/4) * (position within a group) + quarter of the lines; 4
       // consecutive lines of a column start 16-byte aligned (N % 8 == 0)
-      const int qn = nl >> 2, qs = nl == 16 ? 2 : 3;
+      const int qn = nl >> 2, qs = nl == 8 ? 1 : (nl == 16 ? 2 : 3);
       const int q = lane & (qn - 1);
       const int per_warp = 32 / qn;
       const int step = kWarps * per_warp;
@@ -769,12 +769,275 @@ int band_batch_clusters(size_t smem, int *clusters) {
   return SKEI_OK;
 }
 
+// ------------------------------------------------ band-partial form --
+// For callers that pass a workspace (the fused SkEI step): a CTA stages a
+// thin band of SBL lines of an image group ONCE and computes every angle of
+// its angle block over it, writing the per-band sums to the workspace,
+// [image][band][angle][bin]; a second kernel adds the bands in order and
+// applies the epilogue.  Each image band is read from L2 once per angle
+// block instead of once per angle, and the CTAs are many and short.
+#ifndef SKEI_PART_SBL1
+#define SKEI_PART_SBL1 16
+#endif
+#ifndef SKEI_PART_SBL4
+#define SKEI_PART_SBL4 8
+#endif
+#ifndef SKEI_PART_GROUP
+#define SKEI_PART_GROUP 4
+#endif
+#ifndef SKEI_PART_CTAS
+#define SKEI_PART_CTAS 3      // target CTAs per SM when choosing the angle block
+#endif
+constexpr int kMaxABP = 32;      // angles per partial CTA
+
+// Staging geometry of one band of SB lines (0: the group size's default).
+// Transposed single-image staging writes 4-line groups of (32 / (SB/4))
+// positions per warp: a column pitch = 4 mod 8 (8 lines), 2 mod 8 (16) or
+// odd (32) keeps them in distinct banks.
+__host__ __device__ __forceinline__ BandGeom part_geom(int N, int n_det, int n_angles, int NI,
+                                                       int SB = 0) {
+  BandGeom g;
+  g.N = N;
+  g.n_det = n_det;
+  g.n_angles = n_angles;
+  g.NI = NI;
+  g.R = 0;
+  g.SB = SB > 0 ? SB : (NI == 1 ? SKEI_PART_SBL1 : SKEI_PART_SBL4);
+  if (g.SB > N) g.SB = N;
+  if (NI == 1) {
+    g.Prow = (N + 2 * kPad + 3) & ~3;
+    g.Pcol = g.SB == 32   ? ((N + 2 * kPad) | 1)
+             : g.SB == 16 ? ((N + 2 * kPad - 2 + 7) & ~7) + 2
+                          : ((N + 2 * kPad - 4 + 7) & ~7) + 4;
+  } else {
+    g.Pcol = (N + 2 * kPad) | 1;
+    g.Prow = g.Pcol;
+  }
+  g.AB = 0;
+  g.fast = (N % 8 == 0) ? 1 : 0;
+  return g;
+}
+__host__ __device__ __forceinline__ size_t part_smem(const BandGeom &g) {
+  const int Pmax = g.Prow > g.Pcol ? g.Prow : g.Pcol;
+  return (size_t)g.SB * Pmax * g.NI * 4;
+}
+
+struct PartArgs {
+  Jobs jobs;
+  const AngleConst *ang;
+  int *status;
+  BandGeom g1, g4;
+  int gmax;          // image group size of this launch (1 or 4)
+  int AB;            // angles per CTA
+  int nbands;        // ceil(N / SBL); both group sizes use SBL of their own
+  float *part;       // workspace
+  size_t off[kMaxJobs];   // float offset of each job's sums
+};
+
+template <int OP, int NI>
+__device__ __forceinline__ void partial_task(const Job &J, float *part, int b0, int band,
+                                             int a_begin, int AB, int nbands, const BandGeom &g,
+                                             const AngleConst *ang, int *status, float *buf,
+                                             AngleConst *sc, int *sai) {
+  const int tid = threadIdx.x;
+  const int na = min(AB, J.m - a_begin);
+  const int nd = g.n_det, N = g.N;
+  const int s0 = band * g.SB, s1 = min(N, s0 + g.SB);
+  if (na <= 0 || s0 >= N) return;  // uniform over the CTA
+  if (tid < kMaxABP) {
+    int ai = -1;
+    if (tid < na) {
+      ai = J.idx ? J.idx[a_begin + tid] : a_begin + tid;
+      if (ai < 0 || ai >= g.n_angles) {
+        if (band == 0) atomicOr(status, 1);
+        ai = -1;
+      }
+    }
+    sai[tid] = ai;
+    if (ai >= 0) sc[tid] = ang[ai];
+  }
+  __syncthreads();
+  const size_t xo = (size_t)b0 * N * N;
+  const size_t plane = (size_t)nbands * J.m * nd;   // floats per image of sums
+  for (int mode = 1; mode >= 0; --mode) {
+    bool any = false;
+    for (int a = 0; a < na; ++a) any |= (sai[a] >= 0 && sc[a].mode == mode);
+    // angles of the other mode still write their (zero) sums below
+    const int P = mode ? g.Prow : g.Pcol;
+    if (any) {
+      __syncthreads();  // the previous mode's band is no longer read
+      if (NI == 4) stage4(J.in, xo, J.in_bf16, N, mode, s0, s1 - s0, buf, P);
+      else stage1(J.in, xo, J.in_bf16, N, mode, s0, s1 - s0, buf, P, g.fast != 0);
+      __syncthreads();
+    }
+    for (int a = 0; a < na; ++a) {
+      const bool live = sai[a] >= 0;
+      if (live ? sc[a].mode != mode : mode != 0) continue;   // dead angles: written once
+      float *pa = part + ((size_t)b0 * nbands + band) * J.m * nd + (size_t)(a_begin + a) * nd;
+      for (int k = tid; k < nd; k += kThreads) {
+        float acc[NI];
+#pragma unroll
+        for (int i = 0; i < NI; ++i) acc[i] = 0.0f;
+        if (live) {
+          if (OP == OP_JOSEPH) joseph_lines<NI>(sc[a], k, s0, s1, N, buf, P, acc);
+          else bpadj_lines<NI>(sc[a], k, s0, s1, N, buf, P, acc);
+        }
+#pragma unroll
+        for (int i = 0; i < NI; ++i) pa[i * plane + k] = acc[i];
+      }
+    }
+  }
+}
+
+template <int OP>
+__global__ void __launch_bounds__(kThreads) band_partial_kernel(const PartArgs args) {
+  extern __shared__ float4 smem4[];
+  __shared__ AngleConst sc[kMaxABP];
+  __shared__ int sai[kMaxABP];
+  const int z = blockIdx.z;
+  const int g0 = n_groups(args.jobs.j[0].nimg, args.gmax);
+  const int jn = (args.jobs.njobs > 1 && z >= g0) ? 1 : 0;
+  const Job &J = args.jobs.j[jn];
+  int b0, ni;
+  group_at(J.nimg, z - (jn ? g0 : 0), &b0, &ni, args.gmax);
+  float *part = args.part + args.off[jn];
+  float *buf = reinterpret_cast<float *>(smem4);
+  if (ni == 4)
+    partial_task<OP, 4>(J, part, b0, blockIdx.x, blockIdx.y * args.AB, args.AB, args.nbands,
+                        args.g4, args.ang, args.status, buf, sc, sai);
+  else
+    partial_task<OP, 1>(J, part, b0, blockIdx.x, blockIdx.y * args.AB, args.AB, args.nbands,
+                        args.g1, args.ang, args.status, buf, sc, sai);
+}
+
+// out[b][a][k] = epilogue(sum over bands, in order, of the band sums).
+template <int OP>
+__global__ void __launch_bounds__(256)
+    band_reduce_kernel(const Jobs jobs, const AngleConst *ang, int n_angles, int nd, int nbands,
+                       const float *part, size_t off0, size_t off1) {
+  const int y = blockIdx.y;
+  const int jn = (jobs.njobs > 1 && y >= jobs.j[0].nimg) ? 1 : 0;
+  const Job &J = jobs.j[jn];
+  const int b = y - (jn ? jobs.j[0].nimg : 0);
+  const int n = J.m * nd;
+  const float *pb = part + (jn ? off1 : off0) + (size_t)b * nbands * n;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    float s = 0.0f;
+    for (int q = 0; q < nbands; ++q) s += pb[(size_t)q * n + e];
+    const int a = e / nd, k = e - a * nd;
+    int ai = J.idx ? J.idx[a] : a;
+    float v;
+    if (ai < 0 || ai >= n_angles) {
+      v = 0.0f;
+    } else if (OP == OP_JOSEPH) {
+      v = s * ang[ai].W;
+      if (J.aux) v = ld_any(J.aux, ((size_t)b * n_angles + ai) * nd + k, J.aux_bf16) - v;
+      v *= J.alpha;
+    } else {
+      v = s * J.alpha;
+    }
+    st_any(J.out, (size_t)b * n + e, v, J.out_bf16);
+  }
+}
+
+int part_layout(skei_plan p, const Jobs &jobs, int *nbands1, int *nbands4, size_t off[kMaxJobs],
+                size_t *floats, int gm) {
+  const int sb1 = part_geom(p->N, p->n_det, p->n_angles, 1).SB;
+  const int sb4 = part_geom(p->N, p->n_det, p->n_angles, 4).SB;
+  *nbands1 = (p->N + sb1 - 1) / sb1;
+  *nbands4 = (p->N + sb4 - 1) / sb4;
+  // one band count per launch: the finer of the two if both group sizes occur
+  size_t total = 0;
+  for (int q = 0; q < jobs.njobs; ++q) {
+    off[q] = total;
+    total += (size_t)jobs.j[q].nimg * std::max(*nbands1, gm == 4 ? *nbands4 : *nbands1) *
+             jobs.j[q].m * p->n_det;
+  }
+  *floats = total;
+  return SKEI_OK;
+}
+
+template <int OP>
+int launch_band_partial(skei_plan p, const Jobs &jobs, float *work, size_t work_floats,
+                        cudaStream_t st) {
+  int gm = SKEI_PART_GROUP;
+  int nb1 = 0, nb4 = 0;
+  size_t off[kMaxJobs] = {0, 0}, need = 0;
+  part_layout(p, jobs, &nb1, &nb4, off, &need, gm);
+  if (need > work_floats)
+    return set_error(SKEI_EINVAL, "band sums need %zu floats of workspace, %zu given", need,
+                     work_floats);
+  // both group sizes stage bands of their own height; a launch uses one
+  // band count, so single images follow the 4-image band height when both
+  // occur
+  BandGeom g1 = part_geom(p->N, p->n_det, p->n_angles, 1);
+  const BandGeom g4 = part_geom(p->N, p->n_det, p->n_angles, 4);
+  int nbands = nb1;
+  bool any4 = false;
+  for (int q = 0; q < jobs.njobs; ++q) any4 |= gm == 4 && jobs.j[q].nimg >= 4;
+  if (any4) {
+    g1 = part_geom(p->N, p->n_det, p->n_angles, 1, g4.SB);
+    nbands = nb4;
+  }
+  int m_max = 0, ngroups = 0;
+  for (int q = 0; q < jobs.njobs; ++q) {
+    m_max = max(m_max, jobs.j[q].m);
+    ngroups += n_groups(jobs.j[q].nimg, gm);
+  }
+  if (ngroups > 65535) return set_error(SKEI_EINVAL, "too many images in one launch");
+  // angles per CTA: enough CTAs for SKEI_PART_CTAS per SM
+  const long long want = (long long)sm_count() * SKEI_PART_CTAS;
+  long long blocks = (want + (long long)nbands * ngroups - 1) / ((long long)nbands * ngroups);
+  blocks = std::max(1LL, std::min(blocks, (long long)m_max));
+  int AB = (int)((m_max + blocks - 1) / blocks);
+  AB = std::max(1, std::min(AB, kMaxABP));
+  const int nblk = (m_max + AB - 1) / AB;
+  size_t smem = part_smem(g1);
+  if (any4) smem = std::max(smem, part_smem(g4));
+  if (smem > 227 * 1024)
+    return set_error(SKEI_EINVAL, "image of %d pixels needs too much shared memory", p->N);
+  static size_t configured[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (smem > 48 * 1024 && smem > configured[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(band_partial_kernel<OP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_error(e, "band partial kernel: shared memory attribute");
+    configured[dev] = smem;
+  }
+  PartArgs a{jobs, p->d_ang, p->d_status, g1, g4, gm, AB, nbands, work, {off[0], off[1]}};
+  band_partial_kernel<OP><<<dim3(nbands, nblk, ngroups), kThreads, smem, st>>>(a);
+  SKEI_TRY(check_launch("band partial sums launch"));
+  int nimg = 0;
+  for (int q = 0; q < jobs.njobs; ++q) nimg += jobs.j[q].nimg;
+  const int n_max = m_max * p->n_det;
+  const int gx = std::max(1, std::min((n_max + 255) / 256, 4 * sm_count() / std::max(nimg, 1) + 1));
+  band_reduce_kernel<OP><<<dim3(gx, nimg), 256, 0, st>>>(jobs, p->d_ang, p->n_angles, p->n_det,
+                                                           nbands, work, off[0], off[1]);
+  return check_launch("band sums reduction launch");
+}
+
 }  // namespace
 
 int launch_band_jobs(skei_plan p, int op, const Jobs &jobs, cudaStream_t st) {
   if (op == OP_JOSEPH) return launch_band<OP_JOSEPH>(p, jobs, st);
   if (op == OP_BP_ADJ) return launch_band<OP_BP_ADJ>(p, jobs, st);
   return set_error(SKEI_EINVAL, "band launch: unknown operator %d", op);
+}
+
+size_t band_partial_floats(skei_plan p, const Jobs &jobs) {
+  int nb1 = 0, nb4 = 0;
+  size_t off[kMaxJobs] = {0, 0}, need = 0;
+  part_layout(p, jobs, &nb1, &nb4, off, &need, SKEI_PART_GROUP);
+  return need;
+}
+
+int launch_band_partial_jobs(skei_plan p, int op, const Jobs &jobs, float *work,
+                             size_t work_floats, cudaStream_t st) {
+  if (op == OP_JOSEPH) return launch_band_partial<OP_JOSEPH>(p, jobs, work, work_floats, st);
+  if (op == OP_BP_ADJ) return launch_band_partial<OP_BP_ADJ>(p, jobs, work, work_floats, st);
+  return set_error(SKEI_EINVAL, "band partial launch: unknown operator %d", op);
 }
 
 size_t band_batch_smem(int op, int N, int n_det, int n_angles, int AB, int NI) {

@@ -220,6 +220,12 @@ __host__ __device__ __forceinline__ void group_at(int n, int g, int *b0, int *ni
 
 int launch_band_jobs(skei_plan p, int op, const Jobs &jobs, cudaStream_t st);
 int launch_tile_jobs(skei_plan p, int op, const Jobs &jobs, cudaStream_t st);
+// The band operators with a workspace of band sums (two launches: sums per
+// thin band, then their ordered reduction): faster when the caller can give
+// band_partial_floats(p, jobs) floats.
+size_t band_partial_floats(skei_plan p, const Jobs &jobs);
+int launch_band_partial_jobs(skei_plan p, int op, const Jobs &jobs, float *work,
+                             size_t work_floats, cudaStream_t st);
 
 // ------------------------------------------------- batched (persistent) --
 // One instance of a batch - images of one size and angle list, with its own

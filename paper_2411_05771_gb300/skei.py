@@ -19,6 +19,7 @@ from . import build as _build
 __all__ = [
     "F32", "BF16", "Plan", "last_error", "version",
     "proj_fwd", "proj_adj", "proj_fwd_multi", "proj_adj_multi", "Job",
+    "band_sums_workspace_size", "proj_fwd_multi_ws", "backproject_adj_multi_ws",
     "filter", "backproject", "backproject_adj",
     "fbp_workspace_size", "fbp", "fbp_adj", "fbp_noalloc", "rotate", "rotate_adj",
     "ei_workspace_size", "ei_loss_fwd", "ei_loss_finish", "ei_loss_bwd",
@@ -69,6 +70,9 @@ _SIGS = {
     "skei_filter": ([_PLAN, _i, _vp, _i, _f, _vp, _vp], _i),
     "skei_proj_fwd_multi": ([_PLAN, ctypes.POINTER(_Job), _i, _vp], _i),
     "skei_proj_adj_multi": ([_PLAN, ctypes.POINTER(_Job), _i, _vp], _i),
+    "skei_band_sums_workspace_size": ([_PLAN, ctypes.POINTER(_Job), _i], _sz),
+    "skei_proj_fwd_multi_ws": ([_PLAN, ctypes.POINTER(_Job), _i, _vp, _sz, _vp], _i),
+    "skei_backproject_adj_multi_ws": ([_PLAN, ctypes.POINTER(_Job), _i, _vp, _sz, _vp], _i),
     "skei_backproject": ([_PLAN, _i, _vp, _i, _vp, _i, _f, _f, _vp, _vp], _i),
     "skei_backproject_adj": ([_PLAN, _i, _vp, _i, _vp, _i, _f, _vp, _vp], _i),
     "skei_fbp_workspace_size": ([_PLAN, _i, _i, _i], _sz),
@@ -265,6 +269,33 @@ def proj_adj_multi(plan: Plan, jobs) -> None:
     """Several alpha A_S^T in + beta aux applications in one launch."""
     arr = _jobs(plan, jobs, False)
     _check(_lib.skei_proj_adj_multi(plan.handle, arr, len(jobs), _stream()), "skei_proj_adj_multi")
+
+
+def band_sums_workspace_size(plan: Plan, jobs) -> int:
+    """Bytes of workspace the *_multi_ws forms need for these jobs."""
+    arr = _jobs(plan, jobs, True)
+    return int(_lib.skei_band_sums_workspace_size(plan.handle, arr, len(jobs)))
+
+
+def proj_fwd_multi_ws(plan: Plan, jobs, work=None) -> None:
+    """proj_fwd_multi through per-band sums in a workspace (two launches)."""
+    arr = _jobs(plan, jobs, True)
+    nbytes = int(_lib.skei_band_sums_workspace_size(plan.handle, arr, len(jobs)))
+    w = _work(nbytes, jobs[0].inp.device, work)
+    _check(_lib.skei_proj_fwd_multi_ws(plan.handle, arr, len(jobs), _ptr(w),
+                                       w.numel() * w.element_size(), _stream()),
+           "skei_proj_fwd_multi_ws")
+
+
+def backproject_adj_multi_ws(plan: Plan, jobs, work=None) -> None:
+    """Several out = alpha B_S^T in (in [B,N,N], out [B,m,n_det]) through
+    per-band sums in a workspace (two launches)."""
+    arr = _jobs(plan, jobs, True)
+    nbytes = int(_lib.skei_band_sums_workspace_size(plan.handle, arr, len(jobs)))
+    w = _work(nbytes, jobs[0].inp.device, work)
+    _check(_lib.skei_backproject_adj_multi_ws(plan.handle, arr, len(jobs), _ptr(w),
+                                              w.numel() * w.element_size(), _stream()),
+           "skei_backproject_adj_multi_ws")
 
 
 def filter(plan: Plan, p, scale=1.0, out=None) -> torch.Tensor:  # noqa: A001
