@@ -205,8 +205,15 @@ int fbp_adj_impl(skei_plan p, const T *x, int B, const int *idx, int m, T *sino,
 }
 
 // -------------------------------------------------------------- EI loss --
+// Image-angle-lines from which the SkEI step's forward projection uses the
+// band-sums form (build-time knob).
+#ifndef SKEI_STEP_FWD_SUMS_MIN
+#define SKEI_STEP_FWD_SUMS_MIN 200000
+#endif
+constexpr double kStepFwdSumsMin = SKEI_STEP_FWD_SUMS_MIN;
+
 struct EiWork {
-  size_t p_bytes, img_bytes, part_bytes, band_off, band_floats, total;
+  size_t p_bytes, img_bytes, part_bytes, band_off, band_floats, fwd_band_floats, total;
   int cpi, cpr;
 };
 
@@ -221,12 +228,21 @@ EiWork ei_work(skei_plan p, int B, int G, int mc_m, int sk_m) {
   const size_t fwd = 2 * w.p_bytes;
   const size_t bwd = 2 * w.p_bytes + w.img_bytes;
   w.band_off = std::max(std::max(fwd, bwd), w.part_bytes);
-  // band sums of B^T (EI job)
-  Jobs jb{};
+  // band sums of B^T (EI job) and of the fused A launch (MC + EI jobs),
+  // the latter only where the step uses them
+  Jobs jb{}, jf{};
   jb.njobs = 1;
   jb.j[0].nimg = (int)bg;
   jb.j[0].m = sk_m;
+  jf.njobs = 2;
+  jf.j[0].nimg = B;
+  jf.j[0].m = mc_m;
+  jf.j[1].nimg = (int)bg;
+  jf.j[1].m = sk_m;
+  w.fwd_band_floats = band_partial_floats(p, jf);
   w.band_floats = band_partial_floats(p, jb);
+  if (((double)B * mc_m + (double)bg * sk_m) * p->N >= kStepFwdSumsMin)
+    w.band_floats = std::max(w.band_floats, w.fwd_band_floats);
   w.total = w.band_off + align256(w.band_floats * sizeof(float));
   return w;
 }
@@ -247,9 +263,18 @@ int ei_fwd_impl(skei_plan p, const T *x1, const T *y, int B, const int *mc_idx, 
   J.njobs = 2;
   J.j[0] = Job{x1, y, r, mc_idx, mc_m, B, 1.0f, 0.0f, tb, tb, tb};
   J.j[1] = Job{x2, nullptr, pbuf, sk_idx, sk_m, BG, 1.0f, 0.0f, tb, 0, 0};
-  // (the cluster form: for A's 2 taps per line the band-sums form measured
-  // slower at 512^2)
-  if ((rc = launch_band_jobs(p, OP_JOSEPH, J, st))) return rc;
+  // the band-sums form pays on large launches (many image-angles), the
+  // cluster form on small ones (measured on GB300: 8 x 256^2 x 180 angles
+  // 79 vs 147 us; 5 x 512^2 x 30 angles 44 vs 37 us)
+  const double work_units = ((double)B * mc_m + (double)BG * sk_m) * p->N;
+  if (work_units >= kStepFwdSumsMin && w.band_floats >= w.fwd_band_floats) {
+    if ((rc = launch_band_partial_jobs(p, OP_JOSEPH, J,
+                                      reinterpret_cast<float *>(work + w.band_off),
+                                      w.band_floats, st)))
+      return rc;
+  } else if ((rc = launch_band_jobs(p, OP_JOSEPH, J, st))) {
+    return rc;
+  }
   if ((rc = launch_filter<float, float>(p, pbuf, BG * sk_m, (float)(kPi / sk_m), qbuf, st)))
     return rc;
   return launch_backproject<float, T, T>(p, qbuf, BG, sk_idx, sk_m, 1.0f, 0.0f, nullptr, z, st);
