@@ -15,8 +15,11 @@
 // rays, bins and weights are the same for all of them.  A group of 4 images
 // computes them once and reads the 4 images' bins with one 16-byte load
 // (the window holds [bin][image]); jobs whose image count is not a multiple
-// of 4 finish with single-image groups.  Each image sees the same sequence
-// of operations either way.
+// of 4 finish with single-image groups.  When both jobs of a launch use the
+// same angle list and the second has 4 images per image of the first (the
+// MC and EI terms of a step with G = 4), each CTA carries one image of the
+// first job along with a group of the second.  Each image sees the same
+// sequence of operations in every form.
 //
 // A^T: pixel (L, P) (line, position) receives, for each angle, from the two
 // rays whose crossing with line L has integer part P (weight 1-f) and P-1
@@ -32,15 +35,21 @@
 namespace skei {
 namespace {
 
-// Build-time tuning knob: tile height (rows = warps per CTA), 4 or 8.
+// Build-time tuning knobs: tile height (rows), 4 or 8; angle split (1 or
+// 2): with 2, two warps share each tile row, taking alternate angles of
+// every chunk, and their sums are added in a fixed order at the end.
 #ifndef SKEI_TILE_ROWS
 #define SKEI_TILE_ROWS 8
+#endif
+#ifndef SKEI_TILE_SPLIT
+#define SKEI_TILE_SPLIT 1
 #endif
 
 constexpr int kPPT = 4;                  // consecutive pixels per thread
 constexpr int kTW = 32 * kPPT;           // tile width (columns)
-constexpr int kTH = SKEI_TILE_ROWS;      // tile height (rows) = warps per CTA
-constexpr int kThreads = 32 * kTH;
+constexpr int kTH = SKEI_TILE_ROWS;      // tile height (rows)
+constexpr int kSplit = SKEI_TILE_SPLIT;  // warps per tile row
+constexpr int kThreads = 32 * kTH * kSplit;
 constexpr int kWin = 160;                // staged bins per angle (>= kTW + kTH + 6)
 constexpr int kAC = 8;                   // angles per chunk
 
@@ -49,12 +58,14 @@ struct TileArgs {
   int N, n_det, n_angles;
   const AngleConst *ang;
   int *status;
+  int merge;   // job 0's image b rides with job 1's group 4b .. 4b+3 (same angles)
 };
 
 // Shared memory of a tile task: the bins of kAC angles for up to 4 images,
 // [angle][bin][image].
 struct TileSmem {
   alignas(16) float win[kAC * kWin * 4];
+  float winx[kAC * kWin];   // the bins of a riding image of another job
   AngleConst sc[kAC];
   int sai[kAC];
   int kw0[kAC];
@@ -74,24 +85,30 @@ __device__ __forceinline__ void store_run(void *out, size_t o, const float *v, i
   for (int q = 0; q < n_valid; ++q) st_any(out, o + q, v[q], bf16);
 }
 
-// One task: the tile at (i0, j0) of images b0 .. b0 + NI - 1 of job J.
-template <int OP, int NI>
+// One task: the tile at (i0, j0) of images b0 .. b0 + NI - 1 of job J;
+// with XTRA, also image bx of job JX, whose angle list is J's: it shares
+// the pixels' rays and weights and costs only its own taps.
+template <int OP, int NI, bool XTRA = false>
 __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, int N, int nd,
                                           int n_angles, const AngleConst *ang, int *status,
-                                          bool report, TileSmem &sm) {
+                                          bool report, TileSmem &sm, const Job *JX = nullptr,
+                                          int bx = 0) {
   AngleConst *sc = sm.sc;
   int *sai = sm.sai, *kw0 = sm.kw0;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
+  const int half = warp / kTH;             // which angles of each chunk
   const int i_last = min(i0 + kTH, N) - 1, j_last = min(j0 + kTW, N) - 1;
-  const int i = i0 + warp;                 // this thread's row
+  const int i = i0 + warp % kTH;           // this thread's row
   const int jb = j0 + kPPT * lane;         // its first column
 
-  float acc[NI][kPPT];
+  float acc[NI][kPPT], accx[kPPT];
 #pragma unroll
   for (int n = 0; n < NI; ++n)
 #pragma unroll
     for (int q = 0; q < kPPT; ++q) acc[n][q] = 0.0f;
+#pragma unroll
+  for (int q = 0; q < kPPT; ++q) accx[q] = 0.0f;
 
   for (int c0 = 0; c0 < J.m; c0 += kAC) {
     const int nac = min(kAC, J.m - c0);
@@ -125,7 +142,7 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
     for (int e = tid; e < nac * kWin; e += kThreads) {
       const int a = e / kWin, w = e - a * kWin;
       const int ai = sai[a];
-      float v[NI];
+      float v[NI], vx = 0.0f;
 #pragma unroll
       for (int n = 0; n < NI; ++n) v[n] = 0.0f;
       if (ai >= 0) {
@@ -137,17 +154,23 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
             v[n] = ld_any(J.in, ((size_t)(b0 + n) * J.m + c0 + a) * nd + k, J.in_bf16);
             if (OP == OP_JOSEPH_ADJ) v[n] *= W;
           }
+          if (XTRA) {
+            vx = ld_any(JX->in, ((size_t)bx * JX->m + c0 + a) * nd + k, JX->in_bf16);
+            if (OP == OP_JOSEPH_ADJ) vx *= W;
+          }
         }
       }
       if (NI == 4) reinterpret_cast<float4 *>(sm.win)[e] = make_float4(v[0], v[1], v[2], v[3]);
       else sm.win[e] = v[0];
+      if (XTRA) sm.winx[e] = vx;
     }
     __syncthreads();
 
-    for (int a = 0; a < nac; ++a) {
+    for (int a = half; a < nac; a += kSplit) {
       if (sai[a] < 0) continue;
       const AngleConst &C = sc[a];
       const float *wa = sm.win + a * kWin * NI;
+      const float *wx = sm.winx + a * kWin;
       const int base = kw0[a];
       if (OP == OP_JOSEPH_ADJ) {
         const bool row = C.mode != 0;
@@ -187,6 +210,7 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
           } else {
             acc[0][q] = fmaf(w1, wa[s1], fmaf(w2, wa[s2], acc[0][q]));
           }
+          if (XTRA) accx[q] = fmaf(w1, wx[s1], fmaf(w2, wx[s2], accx[q]));
           u += du;
           kc += dkc;
         }
@@ -210,12 +234,37 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
           } else {
             acc[0][q] = fmaf(w, wa[k0 + 1], fmaf(g, wa[k0], acc[0][q]));
           }
+          if (XTRA) accx[q] = fmaf(w, wx[k0 + 1], fmaf(g, wx[k0], accx[q]));
           t += tj;
         }
       }
     }
   }
 
+  if (kSplit > 1) {
+    // the second half's sums through shared memory (the window is free)
+    __syncthreads();
+    float *red = sm.win;
+    const int t0 = tid % (32 * kTH);
+    if (half == 1) {
+#pragma unroll
+      for (int n = 0; n < NI; ++n)
+#pragma unroll
+        for (int q = 0; q < kPPT; ++q) red[(n * kPPT + q) * 32 * kTH + t0] = acc[n][q];
+      if (XTRA)
+#pragma unroll
+        for (int q = 0; q < kPPT; ++q) sm.winx[q * 32 * kTH + t0] = accx[q];
+    }
+    __syncthreads();
+    if (half != 0) return;
+#pragma unroll
+    for (int n = 0; n < NI; ++n)
+#pragma unroll
+      for (int q = 0; q < kPPT; ++q) acc[n][q] += red[(n * kPPT + q) * 32 * kTH + t0];
+    if (XTRA)
+#pragma unroll
+      for (int q = 0; q < kPPT; ++q) accx[q] += sm.winx[q * 32 * kTH + t0];
+  }
   if (i >= N || jb >= N) return;
   const int n_valid = min(kPPT, N - jb);
 #pragma unroll
@@ -230,18 +279,36 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
     }
     store_run(J.out, o, v, n_valid, J.out_bf16);
   }
+  if (XTRA) {
+    const size_t o = ((size_t)bx * N + i) * N + jb;
+    float v[kPPT];
+#pragma unroll
+    for (int q = 0; q < kPPT; ++q) {
+      v[q] = JX->alpha * accx[q];
+      if (JX->beta != 0.0f && JX->aux && q < n_valid)
+        v[q] = fmaf(JX->beta, ld_any(JX->aux, o + q, JX->aux_bf16), v[q]);
+    }
+    store_run(JX->out, o, v, n_valid, JX->out_bf16);
+  }
 }
 
 template <int OP>
 __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs args) {
   __shared__ TileSmem sm;
   const int z = blockIdx.z;
+  const bool report = blockIdx.x == 0 && blockIdx.y == 0;
+  if (args.merge) {
+    // group z of job 1 (images 4z .. 4z+3) with image z of job 0
+    tile_task<OP, 4, true>(args.jobs.j[1], 4 * z, blockIdx.y * kTH, blockIdx.x * kTW, args.N,
+                           args.n_det, args.n_angles, args.ang, args.status, report, sm,
+                           &args.jobs.j[0], z);
+    return;
+  }
   const int g0 = n_groups(args.jobs.j[0].nimg);
   const int jn = (args.jobs.njobs > 1 && z >= g0) ? 1 : 0;
   const Job &J = args.jobs.j[jn];
   int b0, ni;
   group_at(J.nimg, z - (jn ? g0 : 0), &b0, &ni);
-  const bool report = blockIdx.x == 0 && blockIdx.y == 0;
   if (ni == 4)
     tile_task<OP, 4>(J, b0, blockIdx.y * kTH, blockIdx.x * kTW, args.N, args.n_det,
                      args.n_angles, args.ang, args.status, report, sm);
@@ -285,8 +352,13 @@ template <int OP>
 int launch_tile(skei_plan p, const Jobs &jobs, cudaStream_t st) {
   int ngroups = 0;
   for (int q = 0; q < jobs.njobs; ++q) ngroups += n_groups(jobs.j[q].nimg);
+  // two jobs over the same angle list with 4 images of job 1 per image of
+  // job 0 (the MC and EI terms of a step, G = 4): one CTA carries both
+  const int merge = jobs.njobs == 2 && jobs.j[0].idx == jobs.j[1].idx &&
+                    jobs.j[0].m == jobs.j[1].m && jobs.j[1].nimg == 4 * jobs.j[0].nimg;
+  if (merge) ngroups = jobs.j[0].nimg;
   if (ngroups > 65535) return set_error(SKEI_EINVAL, "too many images in one launch");
-  TileArgs a{jobs, p->N, p->n_det, p->n_angles, p->d_ang, p->d_status};
+  TileArgs a{jobs, p->N, p->n_det, p->n_angles, p->d_ang, p->d_status, merge};
   dim3 grid((p->N + kTW - 1) / kTW, (p->N + kTH - 1) / kTH, ngroups);
   tile_kernel<OP><<<grid, kThreads, 0, st>>>(a);
   return check_launch(OP == OP_JOSEPH_ADJ ? "joseph adjoint launch" : "back-projection launch");

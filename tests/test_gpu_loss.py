@@ -54,6 +54,8 @@ def _setup(N, n_ang, B, G, m, sketch_mc, seed=0):
     (256, 180, 8, 4, 45, False),   # the differentiated 256^2 step
     (64, 60, 2, 3, 15, True),      # sketched MC as in Algorithm 2
     (37, 24, 3, 2, 6, True),       # ragged sizes
+    (64, 60, 2, 4, 15, True),      # G = 4, shared sketch: MC images ride with EI groups
+    (100, 30, 1, 4, 10, True),     # the same, one ragged image
 ])
 def test_ei_step_matches_oracle(S, N, n_ang, B, G, m, sketch_mc):
     P = _setup(N, n_ang, B, G, m, sketch_mc)

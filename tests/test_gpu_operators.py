@@ -280,3 +280,29 @@ def test_operators_are_deterministic(S):
     for fn, arg in ((S.proj_fwd, x), (S.proj_adj, p), (S.backproject, p),
                     (S.backproject_adj, x), (S.fbp, p), (S.fbp_adj, x)):
         assert torch.equal(fn(plan, arg), fn(plan, arg))
+
+
+@pytest.mark.parametrize("N,n_ang,B,m", [(64, 60, 2, 15), (100, 30, 1, 30), (37, 24, 3, 8)])
+def test_adjoint_jobs_sharing_the_sketch_match_single_calls(S, N, n_ang, B, m):
+    """Two A^T jobs over the same angle list with 4 images of the second per
+    image of the first run as one launch in which each CTA carries one image
+    of the first job along its group of 4: the results must be bitwise those
+    of separate calls, and match the oracle."""
+    plan = S.Plan(N, n_ang)
+    idx_np = _idx(n_ang, m, 5)
+    idx = None if idx_np is None else torch.tensor(idx_np, dtype=torch.int32, device="cuda")
+    gen = torch.Generator().manual_seed(N)
+    r = torch.randn((B, m, plan.n_det), generator=gen).cuda()
+    v = torch.randn((4 * B, m, plan.n_det), generator=gen).cuda()
+    aux = torch.randn((4 * B, N, N), generator=gen).cuda()
+    o0 = torch.empty((B, N, N), device="cuda")
+    o1 = torch.empty((4 * B, N, N), device="cuda")
+    S.proj_adj_multi(plan, [S.Job(r, o0, idx, alpha=-0.5), S.Job(v, o1, idx, aux=aux, beta=1.0)])
+    ref0 = S.proj_adj(plan, r, idx, alpha=-0.5)
+    ref1 = S.proj_adj(plan, v, idx, alpha=1.0, beta=1.0, out=aux.clone())
+    torch.cuda.synchronize()
+    assert torch.equal(o0, ref0)
+    assert torch.equal(o1, ref1)
+    ang = plan.angles_deg if idx_np is None else O.select(plan.angles_deg, idx_np)
+    assert rel(host(o0), -0.5 * O.proj_adj(host(r), ang, N)) <= FP32_TOL
+    assert rel(host(o1), O.proj_adj(host(v), ang, N) + host(aux)) <= FP32_TOL
