@@ -143,9 +143,15 @@ class Arm:
         self.theta = torch.zeros((N, N), dtype=torch.float32, device=d)
         self.m1 = torch.zeros_like(self.theta)
         self.v1 = torch.zeros_like(self.theta)
-        self.step_no = torch.zeros(1, dtype=torch.int32, device=d)
-        self.idx = torch.zeros(self.m, dtype=torch.int32, device=d)
-        self.g = torch.zeros((B, G), dtype=torch.float64, device=d)
+        # the step's draws live in one device buffer (rotation angles, sketch
+        # rows, step number), so that a step uploads them with one copy
+        self.g_off, self.idx_off = 0, 8 * B * G
+        self.step_off = self.idx_off + 4 * self.m
+        self.param_bytes = (self.step_off + 4 + 15) // 16 * 16
+        self.params = torch.zeros(self.param_bytes, dtype=torch.uint8, device=d)
+        self.g = self.params[self.g_off:self.idx_off].view(torch.float64).view(B, G)
+        self.idx = self.params[self.idx_off:self.step_off].view(torch.int32)
+        self.step_no = self.params[self.step_off:self.step_off + 4].view(torch.int32)
         self.x1 = torch.empty((B, N, N), dtype=self.tdt, device=d)
         self.r = torch.empty((B, self.mc_m, nd), dtype=self.tdt, device=d)
         self.x2 = torch.empty((B, G, N, N), dtype=self.tdt, device=d)
@@ -162,6 +168,19 @@ class Arm:
                                     16), dtype=torch.uint8, device=d)
         idx_all, g_all = step_params(1, wl)
         self.load_params(idx_all[0], g_all[0], 1)
+
+    def pack_params(self, idx_all, g_all, first_step):
+        """Host bytes of the draws of consecutive steps, one row per step, in
+        the layout of self.params."""
+        n = len(idx_all)
+        host = np.zeros((n, self.param_bytes), dtype=np.uint8)
+        host[:, self.g_off:self.idx_off] = np.ascontiguousarray(
+            g_all, dtype=np.float64).reshape(n, -1).view(np.uint8)
+        host[:, self.idx_off:self.step_off] = np.ascontiguousarray(
+            idx_all, dtype=np.int32).reshape(n, -1).view(np.uint8)
+        host[:, self.step_off:self.step_off + 4] = np.arange(
+            first_step, first_step + n, dtype=np.int32).reshape(n, 1).view(np.uint8)
+        return host
 
     def load_params(self, idx, g, step_no):
         import torch
@@ -738,14 +757,10 @@ def main():
                 graph = torch.cuda.CUDAGraph()
                 with torch.cuda.graph(graph, stream=stream):
                     arm.step()
-            host_idx = torch.from_numpy(idx_all).pin_memory()
-            host_g = torch.from_numpy(g_all).pin_memory()
-            host_step = torch.arange(1, W + K + 1, dtype=torch.int32).pin_memory()
+            host_par = torch.from_numpy(arm.pack_params(idx_all, g_all, 1)).pin_memory()
 
             def one(s):
-                arm.idx.copy_(host_idx[s], non_blocking=True)
-                arm.g.copy_(host_g[s], non_blocking=True)
-                arm.step_no.copy_(host_step[s:s + 1], non_blocking=True)
+                arm.params.copy_(host_par[s], non_blocking=True)
                 if graph is not None:
                     graph.replay()
                 else:
@@ -786,9 +801,7 @@ def main():
         host_y = host_y.to(sk.tdt).pin_memory()
     host_loss = torch.empty(1, dtype=torch.float64).pin_memory()
     idx_all, g_all = step_params(K, SKETCHED, first=PSNR_ITERS + 1 + W + K)
-    h_idx = torch.from_numpy(idx_all).pin_memory()
-    h_g = torch.from_numpy(g_all).pin_memory()
-    h_step = torch.arange(1, K + 1, dtype=torch.int32).pin_memory()
+    h_par = torch.from_numpy(sk.pack_params(idx_all, g_all, 1)).pin_memory()
     sk.reset()
     with torch.cuda.stream(stream):
         for s in range(W):
@@ -800,15 +813,13 @@ def main():
         e0.record(stream)
         for s in range(K):
             sk.y.copy_(host_y, non_blocking=True)
-            sk.idx.copy_(h_idx[s], non_blocking=True)
-            sk.g.copy_(h_g[s], non_blocking=True)
-            sk.step_no.copy_(h_step[s:s + 1], non_blocking=True)
+            sk.params.copy_(h_par[s], non_blocking=True)
             sk.step()
             host_loss.copy_(sk.loss, non_blocking=True)
         e1.record(stream)
         stream.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    h2d = host_y.numel() * host_y.element_size() + h_idx[0].numel() * 4 + h_g[0].numel() * 8 + 4
+    h2d = host_y.numel() * host_y.element_size() + sk.param_bytes
     d2h = 8
 
     # per-kernel device times and the roofline of the dominant kernel
