@@ -143,12 +143,39 @@ __device__ __forceinline__ int round_int(float x) {
 __device__ __forceinline__ long long to_fx(double v) { return __double2ll_rn(v * (double)kFxOne); }
 
 // cos and sin in FP64 of an angle in degrees, reduced exactly to
-// [-45, 45] first (exact 0/+-1 at multiples of 90 degrees).
+// [-45, 45] first (exact 0/+-1 at multiples of 90 degrees).  On the reduced
+// angle x (|x| <= pi/4) the Taylor series of sin (through x^15) and cos
+// (through x^16), evaluated in x^2 by Horner's rule, are within 1e-16: a
+// short dependent chain of FP64 FMAs, which matters because a rotation CTA
+// waits for it.
+__device__ __forceinline__ void sincos_taylor(double x, double *s, double *c) {
+  const double x2 = x * x;
+  // sin x = x (1 - x^2/3! + x^4/5! - ... - x^14/15!)
+  double ps = -1.0 / 1307674368000.0;                 // -1/15!
+  ps = fma(ps, x2, 1.0 / 6227020800.0);               //  1/13!
+  ps = fma(ps, x2, -1.0 / 39916800.0);                // -1/11!
+  ps = fma(ps, x2, 1.0 / 362880.0);                   //  1/9!
+  ps = fma(ps, x2, -1.0 / 5040.0);                    // -1/7!
+  ps = fma(ps, x2, 1.0 / 120.0);                      //  1/5!
+  ps = fma(ps, x2, -1.0 / 6.0);                       // -1/3!
+  *s = fma(ps * x2, x, x);
+  // cos x = 1 - x^2/2! + x^4/4! - ... + x^16/16!
+  double pc = 1.0 / 20922789888000.0;                 //  1/16!
+  pc = fma(pc, x2, -1.0 / 87178291200.0);             // -1/14!
+  pc = fma(pc, x2, 1.0 / 479001600.0);                //  1/12!
+  pc = fma(pc, x2, -1.0 / 3628800.0);                 // -1/10!
+  pc = fma(pc, x2, 1.0 / 40320.0);                    //  1/8!
+  pc = fma(pc, x2, -1.0 / 720.0);                     // -1/6!
+  pc = fma(pc, x2, 1.0 / 24.0);                       //  1/4!
+  pc = fma(pc, x2, -0.5);                             // -1/2!
+  *c = fma(pc, x2, 1.0);
+}
+
 __device__ __forceinline__ void trig_deg(double deg, double *c, double *s) {
   double q = floor(deg / 90.0 + 0.5);
   double r = deg - 90.0 * q;
   double sr, cr;
-  sincospi(r / 180.0, &sr, &cr);
+  sincos_taylor(r * (3.14159265358979323846 / 180.0), &sr, &cr);
   long long qi = ((long long)q % 4 + 4) % 4;
   if (qi == 0) { *c = cr;  *s = sr; }
   else if (qi == 1) { *c = -sr; *s = cr; }

@@ -36,13 +36,14 @@ namespace skei {
 namespace {
 
 // Build-time tuning knobs: tile height (rows), 4 or 8; angle split (1 or
-// 2): with 2, two warps share each tile row, taking alternate angles of
-// every chunk, and their sums are added in a fixed order at the end.
+// 2): with 2 (measured faster for B on GB300), two warps share each tile
+// row, taking alternate angles of every chunk, and their sums are added in
+// a fixed order at the end.
 #ifndef SKEI_TILE_ROWS
 #define SKEI_TILE_ROWS 8
 #endif
 #ifndef SKEI_TILE_SPLIT
-#define SKEI_TILE_SPLIT 1
+#define SKEI_TILE_SPLIT 2
 #endif
 
 constexpr int kPPT = 4;                  // consecutive pixels per thread
