@@ -37,8 +37,8 @@ int ensure_ramlak_taps() {
 namespace {
 
 // ------------------------------------------------------------- Ram-Lak --
-// One CTA per sinogram row; the row sits in shared memory between zero
-// margins.  Only odd taps are nonzero besides h(0), so an output k needs
+// One CTA per sinogram row and pass of kFilterOuts outputs; the row sits in
+// shared memory between zero margins.  Only odd taps are nonzero besides h(0), so an output k needs
 // p[k -+ n] for odd n; a thread owns the 4 same-parity outputs
 // k0, k0+2, k0+4, k0+6 and slides one window of 4 left and 4 right inputs
 // from tap n to n+2: two shared loads serve 4 output-taps.  The taps are
@@ -47,17 +47,27 @@ namespace {
 // Shared memory is skewed (one pad word per 8) so the lanes' loads hit
 // distinct banks.
 //   q[k] = scale (h0 p[k] + sum_{n odd} h(n) (p[k-n] + p[k+n]))
+// Build-time tuning knobs: warps per output group (each 128 outputs of a
+// pass) and whether the passes of a row go to separate CTAs (measured on
+// GB300: 3 warps, separate CTAs; 363-bin rows then fill one pass).
+#ifndef SKEI_FILTER_GROUP_WARPS
+#define SKEI_FILTER_GROUP_WARPS 3
+#endif
+#ifndef SKEI_FILTER_PASS_CTAS
+#define SKEI_FILTER_PASS_CTAS 1
+#endif
 constexpr int kSeg = 4;                        // tap segments
-constexpr int kGroupWarps = 6;                 // 6 warps x 128 outputs per pass
+constexpr int kGroupWarps = SKEI_FILTER_GROUP_WARPS;
 constexpr int kFilterThreads = 32 * kGroupWarps * kSeg;
 constexpr int kFilterOuts = 4 * 32 * kGroupWarps;
 
 __host__ __device__ constexpr int skew(int e) { return e + (e >> 3); }
 
-// Filters one row: po[k] = scale (H pr)[k], k < nd.
+// Filters one row: po[k] = scale (H pr)[k], k < nd, for the output passes
+// pass0, pass0 + pstep, ... (kFilterOuts outputs each).
 template <typename Tin, typename Tout>
 __device__ __forceinline__ void ramlak_row(const Tin *pr, Tout *po, int nd, float scale,
-                                           float *smem) {
+                                           float *smem, int pass0 = 0, int pstep = 1) {
   float *red = smem;                                    // [kSeg][kFilterOuts]
   float *pb = red + kSeg * kFilterOuts;
   // zero margins: before the row, the farthest left tap (n <= nd-1, plus the
@@ -75,7 +85,7 @@ __device__ __forceinline__ void ramlak_row(const Tin *pr, Tout *po, int nd, floa
   const int n_odd = nd / 2;                       // number of odd n < nd
   const int groups = (n_odd + 3) / 4;
   const int g0 = (groups * seg) / kSeg, g1 = (groups * (seg + 1)) / kSeg;
-  for (int kb = 0; kb < nd; kb += kFilterOuts) {
+  for (int kb = pass0 * kFilterOuts; kb < nd; kb += pstep * kFilterOuts) {
     __syncthreads();                              // staging done / red reusable
     const int ko = gw * 128 + 8 * (lane >> 1) + (lane & 1);   // offset in the pass
     const int e0 = lp + kb + ko;
@@ -130,7 +140,7 @@ __global__ void __launch_bounds__(kFilterThreads)
   extern __shared__ float4 smem4[];
   const size_t row = blockIdx.x;
   ramlak_row<Tin, Tout>(in + row * nd, out + row * nd, nd, scale,
-                        reinterpret_cast<float *>(smem4));
+                        reinterpret_cast<float *>(smem4), blockIdx.y, gridDim.y);
 }
 
 // Persistent form over the rows of a batch of instances (task = item, row;
@@ -349,7 +359,8 @@ int launch_filter(skei_plan p, const Tin *in, int rows, float scale, Tout *out,
     if (e != cudaSuccess) return cuda_error(e, "ramlak: shared memory attribute");
     configured[dev] = smem;
   }
-  kern<<<rows, kFilterThreads, smem, st>>>(in, out, nd, scale);
+  const int passes = SKEI_FILTER_PASS_CTAS ? (nd + kFilterOuts - 1) / kFilterOuts : 1;
+  kern<<<dim3(rows, passes), kFilterThreads, smem, st>>>(in, out, nd, scale);
   return check_launch("ramlak filter launch");
 }
 
