@@ -26,6 +26,7 @@ __global__ void __launch_bounds__(kRedThreads)
     ei_partials_kernel(const T *x2, const T *x3, const T *r, int64_t n_img, int n_imgseg,
                        int cpi, int64_t r_len, int cpr, float kappa, T *g_x2, T *g_x3,
                        double *partial) {
+  pdl_enter();
   __shared__ double red[kRedThreads / 32];
   const int blk = blockIdx.x;
   // each thread sums its few elements in FP32, the block adds the threads'
@@ -83,6 +84,7 @@ __global__ void __launch_bounds__(kRedThreads)
 __global__ void __launch_bounds__(kRedThreads)
     ei_final_kernel(const double *partial, int B, int G, int cpi, int cpr, double lambda,
                     double mc_scale, double *mc_out, double *ei_out, double *loss_out) {
+  pdl_enter();
   extern __shared__ double seg_sum[];  // [B*G + B]
   const int nseg = B * G + B;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -117,6 +119,7 @@ __global__ void __launch_bounds__(kRedThreads)
 // --------------------------------------------------- stand-in network --
 template <typename T>
 __global__ void residual_add_kernel(const T *u, const float *theta, int n, T *out) {
+  pdl_enter();
   // blockIdx.y selects the image, so no division or modulo per element
   const size_t base = (size_t)blockIdx.y * n;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
@@ -125,6 +128,7 @@ __global__ void residual_add_kernel(const T *u, const float *theta, int n, T *ou
 
 // FP32, n % 4 == 0: four elements per thread and access.
 __global__ void residual_add4_kernel(const float4 *u, const float4 *theta, int n4, float4 *out) {
+  pdl_enter();
   const size_t base = (size_t)blockIdx.y * n4;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n4; e += gridDim.x * blockDim.x) {
     const float4 a = __ldg(u + base + e), t = __ldg(theta + e);
@@ -138,6 +142,7 @@ template <typename T>
 __global__ void adam_kernel(float *theta, int64_t n, const T *g1, int c1, const T *g2, int c2,
                             float *m, float *v, const int *step, float lr, float b1, float b2,
                             float eps, float lnb1, float lnb2) {
+  pdl_enter();
   const float t = (float)max(__ldg(step), 1);
   const float bc1 = -expm1f(t * lnb1), bc2 = -expm1f(t * lnb2);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -157,6 +162,7 @@ __global__ void adam_kernel(float *theta, int64_t n, const T *g1, int c1, const 
 __global__ void adam4_kernel(float4 *theta, int n4, const float4 *g1, int c1, const float4 *g2,
                              int c2, float4 *m, float4 *v, const int *step, float lr, float b1,
                              float b2, float eps, float lnb1, float lnb2) {
+  pdl_enter();
   const float t = (float)max(__ldg(step), 1);
   const float bc1 = -expm1f(t * lnb1), bc2 = -expm1f(t * lnb2);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += gridDim.x * blockDim.x) {
@@ -329,13 +335,13 @@ int ei_finish_impl(const T *x2, const T *x3, const T *r, int B, int G, int N, in
   double *partial = reinterpret_cast<double *>(work);
   const int nblk = B * G * cpi + B * cpr;
   const float kappa = (float)(2.0 * lambda / ((double)B * G));
-  ei_partials_kernel<T><<<nblk, kRedThreads, 0, st>>>(x2, x3, r, n_img, B * G, cpi, r_len, cpr,
-                                                      kappa, g_x2, g_x3, partial);
+  launch_k(ei_partials_kernel<T>, dim3(nblk), dim3(kRedThreads), 0, st, x2, x3, r, n_img, B * G,
+           cpi, r_len, cpr, kappa, g_x2, g_x3, partial);
   if (int rc = check_launch("loss partial sums launch")) return rc;
   const size_t smem = sizeof(double) * (size_t)(B * G + B);
   if (smem > 48 * 1024) return set_error(SKEI_EINVAL, "B*G + B = %d segments is too many", B * G + B);
-  ei_final_kernel<<<1, kRedThreads, smem, st>>>(partial, B, G, cpi, cpr, lambda, mc_scale,
-                                                mc_out, ei_out, loss_out);
+  launch_k(ei_final_kernel, dim3(1), dim3(kRedThreads), smem, st, (const double *)partial, B, G,
+           cpi, cpr, lambda, mc_scale, mc_out, ei_out, loss_out);
   return check_launch("loss final reduction launch");
 }
 
@@ -673,14 +679,14 @@ int skei_residual_add(int dtype, const void *u, const float *theta, int count, i
   const dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 1024), (unsigned)count);
   if (dtype == SKEI_F32 && n % 4 == 0) {
     const dim3 grid4((unsigned)std::min<int64_t>((n / 4 + 255) / 256, 1024), (unsigned)count);
-    residual_add4_kernel<<<grid4, 256, 0, as_stream(stream)>>>(
-        (const float4 *)u, (const float4 *)theta, (int)(n / 4), (float4 *)out);
+    launch_k(residual_add4_kernel, grid4, dim3(256), 0, as_stream(stream), (const float4 *)u,
+             (const float4 *)theta, (int)(n / 4), (float4 *)out);
   } else if (dtype == SKEI_F32)
-    residual_add_kernel<float><<<grid, 256, 0, as_stream(stream)>>>((const float *)u, theta,
-                                                                    (int)n, (float *)out);
+    launch_k(residual_add_kernel<float>, grid, dim3(256), 0, as_stream(stream), (const float *)u,
+             theta, (int)n, (float *)out);
   else
-    residual_add_kernel<bf16><<<grid, 256, 0, as_stream(stream)>>>((const bf16 *)u, theta,
-                                                                   (int)n, (bf16 *)out);
+    launch_k(residual_add_kernel<bf16>, grid, dim3(256), 0, as_stream(stream), (const bf16 *)u,
+             theta, (int)n, (bf16 *)out);
   return check_launch("residual add launch");
 }
 
@@ -702,20 +708,18 @@ int skei_adam_step(float *theta, int64_t n, int dtype, const void *g1, int c1, c
   const bool vec = dtype == SKEI_F32 && n % 4 == 0 && n / 4 < (int64_t)1 << 30 &&
                    ((reinterpret_cast<uintptr_t>(g2) & 15) == 0);
   if (vec)
-    adam4_kernel<<<grid_for(n / 4, 256), 256, 0, as_stream(stream)>>>(
-        (float4 *)theta, (int)(n / 4), (const float4 *)g1, c1, (const float4 *)g2, c2,
-        (float4 *)m, (float4 *)v, step, (float)lr, (float)beta1, (float)beta2, (float)eps, lnb1,
-        lnb2);
+    launch_k(adam4_kernel, dim3(grid_for(n / 4, 256)), dim3(256), 0, as_stream(stream),
+             (float4 *)theta, (int)(n / 4), (const float4 *)g1, c1, (const float4 *)g2, c2,
+             (float4 *)m, (float4 *)v, step, (float)lr, (float)beta1, (float)beta2, (float)eps,
+             lnb1, lnb2);
   else if (dtype == SKEI_F32)
-    adam_kernel<float><<<grid, 256, 0, as_stream(stream)>>>(theta, n, (const float *)g1, c1,
-                                                            (const float *)g2, c2, m, v, step,
-                                                            (float)lr, (float)beta1, (float)beta2,
-                                                            (float)eps, lnb1, lnb2);
+    launch_k(adam_kernel<float>, dim3(grid), dim3(256), 0, as_stream(stream), theta, n,
+             (const float *)g1, c1, (const float *)g2, c2, m, v, step, (float)lr, (float)beta1,
+             (float)beta2, (float)eps, lnb1, lnb2);
   else
-    adam_kernel<bf16><<<grid, 256, 0, as_stream(stream)>>>(theta, n, (const bf16 *)g1, c1,
-                                                           (const bf16 *)g2, c2, m, v, step,
-                                                           (float)lr, (float)beta1, (float)beta2,
-                                                           (float)eps, lnb1, lnb2);
+    launch_k(adam_kernel<bf16>, dim3(grid), dim3(256), 0, as_stream(stream), theta, n,
+             (const bf16 *)g1, c1, (const bf16 *)g2, c2, m, v, step, (float)lr, (float)beta1,
+             (float)beta2, (float)eps, lnb1, lnb2);
   return check_launch("adam launch");
 }
 

@@ -545,6 +545,7 @@ __device__ __forceinline__ void band_task(const Job &J, int b0, int a_begin, con
 template <int OP>
 __global__ void __cluster_dims__(kBands, 1, 1) __launch_bounds__(kThreads)
     band_kernel(const BandArgs args) {
+  pdl_enter();
   extern __shared__ float4 smem4[];
   __shared__ AngleConst sc[kMaxAB];
   __shared__ int sai[kMaxAB];
@@ -736,7 +737,7 @@ int launch_band(skei_plan p, const Jobs &jobs, cudaStream_t st) {
   SKEI_TRY(set_band_smem<OP>(smem));
   const int blocks = (m_max + ab - 1) / ab;
   dim3 grid(kBands, blocks, ngroups);
-  band_kernel<OP><<<grid, kThreads, smem, st>>>(a);
+  launch_k(band_kernel<OP>, grid, dim3(kThreads), smem, st, a);
   return check_launch(OP == OP_JOSEPH ? "joseph forward launch" : "back-projection transpose launch");
 }
 
@@ -891,6 +892,7 @@ __device__ __forceinline__ void partial_task(const Job &J, float *part, int b0, 
 
 template <int OP>
 __global__ void __launch_bounds__(kThreads) band_partial_kernel(const PartArgs args) {
+  pdl_enter();
   extern __shared__ float4 smem4[];
   __shared__ AngleConst sc[kMaxABP];
   __shared__ int sai[kMaxABP];
@@ -915,6 +917,7 @@ template <int OP>
 __global__ void __launch_bounds__(256)
     band_reduce_kernel(const Jobs jobs, const AngleConst *ang, int n_angles, int nd, int nbands,
                        const float *part, size_t off0, size_t off1) {
+  pdl_enter();
   const int y = blockIdx.y;
   const int jn = (jobs.njobs > 1 && y >= jobs.j[0].nimg) ? 1 : 0;
   const Job &J = jobs.j[jn];
@@ -922,8 +925,17 @@ __global__ void __launch_bounds__(256)
   const int n = J.m * nd;
   const float *pb = part + (jn ? off1 : off0) + (size_t)b * nbands * n;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    // the bands in order, 16 loads in flight at a time
     float s = 0.0f;
-    for (int q = 0; q < nbands; ++q) s += pb[(size_t)q * n + e];
+    int q = 0;
+    for (; q + 16 <= nbands; q += 16) {
+      float v[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) v[u] = __ldg(pb + (size_t)(q + u) * n + e);
+#pragma unroll
+      for (int u = 0; u < 16; ++u) s += v[u];
+    }
+    for (; q < nbands; ++q) s += __ldg(pb + (size_t)q * n + e);
     const int a = e / nd, k = e - a * nd;
     int ai = J.idx ? J.idx[a] : a;
     float v;
@@ -1007,14 +1019,15 @@ int launch_band_partial(skei_plan p, const Jobs &jobs, float *work, size_t work_
     configured[dev] = smem;
   }
   PartArgs a{jobs, p->d_ang, p->d_status, g1, g4, gm, AB, nbands, work, {off[0], off[1]}};
-  band_partial_kernel<OP><<<dim3(nbands, nblk, ngroups), kThreads, smem, st>>>(a);
+  launch_k(band_partial_kernel<OP>, dim3(nbands, nblk, ngroups), dim3(kThreads), smem, st, a);
   SKEI_TRY(check_launch("band partial sums launch"));
   int nimg = 0;
   for (int q = 0; q < jobs.njobs; ++q) nimg += jobs.j[q].nimg;
   const int n_max = m_max * p->n_det;
   const int gx = std::max(1, std::min((n_max + 255) / 256, 4 * sm_count() / std::max(nimg, 1) + 1));
-  band_reduce_kernel<OP><<<dim3(gx, nimg), 256, 0, st>>>(jobs, p->d_ang, p->n_angles, p->n_det,
-                                                           nbands, work, off[0], off[1]);
+  launch_k(band_reduce_kernel<OP>, dim3(gx, nimg), dim3(256), 0, st, jobs,
+           (const AngleConst *)p->d_ang, p->n_angles, p->n_det, nbands, (const float *)work,
+           off[0], off[1]);
   return check_launch("band sums reduction launch");
 }
 

@@ -137,6 +137,7 @@ __device__ __forceinline__ void ramlak_row(const Tin *pr, Tout *po, int nd, floa
 template <typename Tin, typename Tout>
 __global__ void __launch_bounds__(kFilterThreads)
     ramlak_kernel(const Tin *in, Tout *out, int nd, float scale) {
+  pdl_enter();
   extern __shared__ float4 smem4[];
   const size_t row = blockIdx.x;
   ramlak_row<Tin, Tout>(in + row * nd, out + row * nd, nd, scale,
@@ -198,6 +199,7 @@ __device__ __forceinline__ RotConst rot_const(double deg, int N) {
 template <typename Tin, typename Tout>
 __global__ void __launch_bounds__(kRotThreads)
     rotate_kernel(const Tin *x, int N, int G, const double *g_deg, Tout *out) {
+  pdl_enter();
   __shared__ RotConst rc;
   const int bg = blockIdx.z, b = bg / G;
   if (threadIdx.x == 0) rc = rot_const(g_deg[bg], N);
@@ -207,24 +209,30 @@ __global__ void __launch_bounds__(kRotThreads)
   const int i_first = blockIdx.y * kRotY * kRotQ + ty;
   if (j >= N) return;
   const Tin *xb = x + (size_t)b * N * N;
+  Tout *ob = out + (size_t)bg * N * N + j;
   long long row = rc.R0 + (long long)j * rc.s + (long long)i_first * rc.c;
   long long col = rc.C0 + (long long)j * rc.c - (long long)i_first * rc.s;
   const long long drow = rc.c * kRotY, dcol = -rc.s * kRotY;
+  // Taps outside the image read as 0 through predicated loads, with no
+  // branch: fma(w, 0, v) = v, so the FMA chain gives what skipping them
+  // would.
 #pragma unroll 2
   for (int q = 0; q < kRotQ; ++q, row += drow, col += dcol) {
     const int i = i_first + kRotY * q;
-    if (i >= N) break;
     const int i0 = ipart(row), j0 = ipart(col);
     const float fr = frac23(row), fc = frac23(col);
     const float gr = 1.0f - fr, gc = 1.0f - fc;
-    const bool r0 = i0 >= 0 && i0 < N, r1 = i0 + 1 >= 0 && i0 + 1 < N;
-    const bool c0 = j0 >= 0 && j0 < N, c1 = j0 + 1 >= 0 && j0 + 1 < N;
-    float v = 0.0f;
-    if (r0 && c0) v = fmaf(gr * gc, ldg_f(xb + (size_t)i0 * N + j0), v);
-    if (r0 && c1) v = fmaf(gr * fc, ldg_f(xb + (size_t)i0 * N + j0 + 1), v);
-    if (r1 && c0) v = fmaf(fr * gc, ldg_f(xb + (size_t)(i0 + 1) * N + j0), v);
-    if (r1 && c1) v = fmaf(fr * fc, ldg_f(xb + (size_t)(i0 + 1) * N + j0 + 1), v);
-    st_f(out + ((size_t)bg * N + i) * N + j, v);
+    const bool r0 = (unsigned)i0 < (unsigned)N, r1 = (unsigned)(i0 + 1) < (unsigned)N;
+    const bool c0 = (unsigned)j0 < (unsigned)N, c1 = (unsigned)(j0 + 1) < (unsigned)N;
+    const Tin *pa = xb + (ptrdiff_t)i0 * N + j0;
+    const float x00 = (r0 & c0) ? ldg_f(pa) : 0.0f, x01 = (r0 & c1) ? ldg_f(pa + 1) : 0.0f;
+    const float x10 = (r1 & c0) ? ldg_f(pa + N) : 0.0f;
+    const float x11 = (r1 & c1) ? ldg_f(pa + N + 1) : 0.0f;
+    float v = fmaf(gr * gc, x00, 0.0f);
+    v = fmaf(gr * fc, x01, v);
+    v = fmaf(fr * gc, x10, v);
+    v = fmaf(fr * fc, x11, v);
+    if (i < N) st_f(ob + (size_t)i * N, v);
   }
 }
 
@@ -232,14 +240,58 @@ __global__ void __launch_bounds__(kRotThreads)
 // sample lands in (a-1, a+1) x (bb-1, bb+1) lie within sqrt 2 of the
 // rotated position of (a, bb), i.e. among 3x3 candidates; each candidate's
 // sample is recomputed exactly in the forward's fixed-point form and
-// weighted with tap_weight, reproducing the forward's weights bitwise.
+// weighted by its exact tap weights, reproducing the forward's bitwise.
 constexpr int kAdjT = 16, kAdjQ = 2;  // CTA tile 16 x 32, 2 pixels/thread
 constexpr int kMaxG = 64;
+
+// Linear-interpolation weight of a sample at fixed-point offset D (|D| < 8,
+// 32-bit) from an integer position q, D = pos - q: 1-f if floor(pos) == q,
+// f if floor(pos) == q-1, with f the 23-bit fraction of pos.  With
+// a = D >> 5 (floor division) both are 1 - |a| 2^-23: for D >= 0, a is f's
+// 23 bits; for D < 0, f's bits are a + 2^23.  Evaluated as the float with
+// bits 0x40000000 - |a| (= 2 - |a| 2^-23, exact) minus 1; the result is
+// <= 0 exactly when the tap gets no weight.
+__device__ __forceinline__ float tap_wf(unsigned D) {
+  return __int_as_float(0x40000000 - abs((int)D >> (kFxBits - 23))) - 1.0f;
+}
+
+template <typename Tin>
+__device__ __forceinline__ float rot_adj_one(const RotConst &r, const Tin *gb, int N, int a,
+                                             int bb, float s) {
+  const float dc = (float)bb - r.C0f, dr = (float)a - r.R0f;
+  const int ri = round_int(fmaf(-r.sf, dc, r.cf * dr));
+  const int rj = round_int(fmaf(r.cf, dc, r.sf * dr));
+  // exact offsets of candidate (ri-1, rj-1)'s sample from (a, bb); an
+  // i step adds (c, -s), a j step (s, c); all within a few pixels, so
+  // exact in 32-bit wrapping arithmetic on the low words
+  const unsigned c32 = (unsigned)r.c, s32 = (unsigned)r.s;
+  const unsigned dr0 = (unsigned)(r.R0 + (long long)(rj - 1) * r.s +
+                                  (long long)(ri - 1) * r.c) - ((unsigned)a << kFxBits);
+  const unsigned dc0 = (unsigned)(r.C0 + (long long)(rj - 1) * r.c -
+                                  (long long)(ri - 1) * r.s) - ((unsigned)bb << kFxBits);
+  bool jv[3];
+#pragma unroll
+  for (int dj = 0; dj < 3; ++dj) jv[dj] = (unsigned)(rj - 1 + dj) < (unsigned)N;
+#pragma unroll
+  for (int di = 0; di < 3; ++di) {
+    const int i = ri - 1 + di;
+    const bool iv = (unsigned)i < (unsigned)N;
+    const Tin *row = gb + (ptrdiff_t)i * N + (rj - 1);
+    const unsigned Dr1 = dr0 + di * c32, Dc1 = dc0 - di * s32;
+#pragma unroll
+    for (int dj = 0; dj < 3; ++dj) {
+      const float wr = tap_wf(Dr1 + dj * s32), wc = tap_wf(Dc1 + dj * c32);
+      if (iv & jv[dj] & (wr > 0.0f) & (wc > 0.0f)) s = fmaf(wr * wc, ldg_f(row + dj), s);
+    }
+  }
+  return s;
+}
 
 template <typename Tin, typename Tout>
 __global__ void __launch_bounds__(kAdjT *kAdjT)
     rotate_adj_kernel(const Tin *gout, int N, int G, const double *g_deg, float alpha,
                       float beta, Tout *gx) {
+  pdl_enter();
   __shared__ RotConst rc[kMaxG];
   const int b = blockIdx.z;
   const int t = threadIdx.y * kAdjT + threadIdx.x;
@@ -253,39 +305,26 @@ __global__ void __launch_bounds__(kAdjT *kAdjT)
     if (t < ng) rc[t] = rot_const(g_deg[(size_t)b * G + g0 + t], N);
     __syncthreads();
     if (bb >= N) continue;
-    for (int g = 0; g < ng; ++g) {
-      const RotConst r = rc[g];
-      const Tin *gb = gout + ((size_t)b * G + g0 + g) * N * N;
+    const Tin *gb = gout + ((size_t)b * G + g0) * N * N;
+    const size_t plane = (size_t)N * N;
+    int g = 0;
+    // two rotations at a time: twice the loads in flight; the sum over g
+    // keeps its order
+    for (; g + 2 <= ng; g += 2) {
+      const RotConst r0 = rc[g], r1 = rc[g + 1];
 #pragma unroll
       for (int q = 0; q < kAdjQ; ++q) {
-        const int a = (blockIdx.y * kAdjQ + q) * kAdjT + threadIdx.y;
-        if (a >= N) continue;
-        const float dc = (float)bb - r.C0f, dr = (float)a - r.R0f;
-        const int ri = round_int(fmaf(-r.sf, dc, r.cf * dr));
-        const int rj = round_int(fmaf(r.cf, dc, r.sf * dr));
-        // exact offsets of candidate (ri-1, rj-1)'s sample from (a, bb); an
-        // i step adds (c, -s), a j step (s, c); all within a few pixels, so
-        // exact in 32-bit wrapping arithmetic on the low words
-        const unsigned c32 = (unsigned)r.c, s32 = (unsigned)r.s;
-        const unsigned dr0 = (unsigned)(r.R0 + (long long)(rj - 1) * r.s +
-                                        (long long)(ri - 1) * r.c) - ((unsigned)a << kFxBits);
-        const unsigned dc0 = (unsigned)(r.C0 + (long long)(rj - 1) * r.c -
-                                        (long long)(ri - 1) * r.s) - ((unsigned)bb << kFxBits);
-        float s = acc[q];
+        const int a = min((blockIdx.y * kAdjQ + q) * kAdjT + threadIdx.y, N - 1);
+        acc[q] = rot_adj_one(r1, gb + (g + 1) * plane, N, a, bb,
+                             rot_adj_one(r0, gb + g * plane, N, a, bb, acc[q]));
+      }
+    }
+    for (; g < ng; ++g) {
+      const RotConst r0 = rc[g];
 #pragma unroll
-        for (int di = 0; di < 3; ++di) {
-          const int i = ri - 1 + di;
-#pragma unroll
-          for (int dj = 0; dj < 3; ++dj) {
-            const int j = rj - 1 + dj;
-            const int Dr = (int)(dr0 + di * c32 + dj * s32);
-            const int Dc = (int)(dc0 - di * s32 + dj * c32);
-            const int wr = tap_w23(Dr), wc = tap_w23(Dc);
-            if ((wr != 0) & (wc != 0) & (i >= 0) & (i < N) & (j >= 0) & (j < N))
-              s = fmaf(w23_to_float(wr) * w23_to_float(wc), ldg_f(gb + (size_t)i * N + j), s);
-          }
-        }
-        acc[q] = s;
+      for (int q = 0; q < kAdjQ; ++q) {
+        const int a = min((blockIdx.y * kAdjQ + q) * kAdjT + threadIdx.y, N - 1);
+        acc[q] = rot_adj_one(r0, gb + g * plane, N, a, bb, acc[q]);
       }
     }
   }
@@ -360,7 +399,7 @@ int launch_filter(skei_plan p, const Tin *in, int rows, float scale, Tout *out,
     configured[dev] = smem;
   }
   const int passes = SKEI_FILTER_PASS_CTAS ? (nd + kFilterOuts - 1) / kFilterOuts : 1;
-  kern<<<dim3(rows, passes), kFilterThreads, smem, st>>>(in, out, nd, scale);
+  launch_k(kern, dim3(rows, passes), dim3(kFilterThreads), smem, st, in, out, nd, scale);
   return check_launch("ramlak filter launch");
 }
 
@@ -368,7 +407,7 @@ template <typename Tin, typename Tout>
 int launch_rotate(const Tin *x, int B, int N, const double *g_deg, int G, Tout *out,
                   cudaStream_t st) {
   dim3 grid((N + kRotX - 1) / kRotX, (N + kRotY * kRotQ - 1) / (kRotY * kRotQ), B * G);
-  rotate_kernel<Tin, Tout><<<grid, kRotThreads, 0, st>>>(x, N, G, g_deg, out);
+  launch_k(rotate_kernel<Tin, Tout>, grid, dim3(kRotThreads), 0, st, x, N, G, g_deg, out);
   return check_launch("rotation launch");
 }
 
@@ -376,8 +415,8 @@ template <typename Tin, typename Tout>
 int launch_rotate_adj(const Tin *gout, int B, int N, const double *g_deg, int G,
                       float alpha, float beta, Tout *gx, cudaStream_t st) {
   dim3 grid((N + kAdjT - 1) / kAdjT, (N + kAdjT * kAdjQ - 1) / (kAdjT * kAdjQ), B);
-  rotate_adj_kernel<Tin, Tout>
-      <<<grid, dim3(kAdjT, kAdjT), 0, st>>>(gout, N, G, g_deg, alpha, beta, gx);
+  launch_k(rotate_adj_kernel<Tin, Tout>, grid, dim3(kAdjT, kAdjT), 0, st, gout, N, G, g_deg,
+           alpha, beta, gx);
   return check_launch("rotation transpose launch");
 }
 

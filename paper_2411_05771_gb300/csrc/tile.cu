@@ -295,6 +295,7 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
 
 template <int OP>
 __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs args) {
+  pdl_enter();
   __shared__ TileSmem sm;
   const int z = blockIdx.z;
   const bool report = blockIdx.x == 0 && blockIdx.y == 0;
@@ -361,7 +362,7 @@ int launch_tile(skei_plan p, const Jobs &jobs, cudaStream_t st) {
   if (ngroups > 65535) return set_error(SKEI_EINVAL, "too many images in one launch");
   TileArgs a{jobs, p->N, p->n_det, p->n_angles, p->d_ang, p->d_status, merge};
   dim3 grid((p->N + kTW - 1) / kTW, (p->N + kTH - 1) / kTH, ngroups);
-  tile_kernel<OP><<<grid, kThreads, 0, st>>>(a);
+  launch_k(tile_kernel<OP>, grid, dim3(kThreads), 0, st, a);
   return check_launch(OP == OP_JOSEPH_ADJ ? "joseph adjoint launch" : "back-projection launch");
 }
 
