@@ -3,8 +3,10 @@
 // and the back-projection B_S of FBP (A_S^dagger = (pi/m) B_S H, Sec. 2.1
 // and 3.1).
 //
-// A CTA owns one tile of a group of images (one warp per tile row, 4
-// consecutive pixels per thread) and walks the angle list in chunks; for
+// A CTA owns one tile of a group of images (one warp per tile row; a thread
+// holds 4 pixels 32 columns apart, so that neighbouring lanes read
+// neighbouring bins, free of shared-memory bank conflicts, and the warp
+// stores 32 consecutive pixels at a time) and walks the angle list in chunks; for
 // each angle it stages in shared memory only the window of detector bins
 // the tile projects onto.  Every thread accumulates its pixels in registers
 // and writes each once: no atomics.  Up to two jobs share a launch (grid.z
@@ -46,7 +48,7 @@ namespace {
 #define SKEI_TILE_SPLIT 2
 #endif
 
-constexpr int kPPT = 4;                  // consecutive pixels per thread
+constexpr int kPPT = 4;                  // pixels per thread, 32 columns apart
 constexpr int kTW = 32 * kPPT;           // tile width (columns)
 constexpr int kTH = SKEI_TILE_ROWS;      // tile height (rows)
 constexpr int kSplit = SKEI_TILE_SPLIT;  // warps per tile row
@@ -72,20 +74,6 @@ struct TileSmem {
   int kw0[kAC];
 };
 
-// Stores kPPT consecutive pixels (n_valid of them inside the image) at
-// element offset o.
-__device__ __forceinline__ void store_run(void *out, size_t o, const float *v, int n_valid,
-                                          int bf16) {
-  if (!bf16) {
-    float *p = static_cast<float *>(out) + o;
-    if (n_valid == kPPT && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
-      *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-      return;
-    }
-  }
-  for (int q = 0; q < n_valid; ++q) st_any(out, o + q, v[q], bf16);
-}
-
 // One task: the tile at (i0, j0) of images b0 .. b0 + NI - 1 of job J;
 // with XTRA, also image bx of job JX, whose angle list is J's: it shares
 // the pixels' rays and weights and costs only its own taps.
@@ -101,7 +89,7 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
   const int half = warp / kTH;             // which angles of each chunk
   const int i_last = min(i0 + kTH, N) - 1, j_last = min(j0 + kTW, N) - 1;
   const int i = i0 + warp % kTH;           // this thread's row
-  const int jb = j0 + kPPT * lane;         // its first column
+  const int jb = j0 + lane;                // its first column; then every 32nd
 
   float acc[NI][kPPT], accx[kPPT];
 #pragma unroll
@@ -181,16 +169,16 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
         const int sA = A < 0 ? -1 : 1;
         const float Tf = C.Tf, Gf = C.Gf, invA = C.invA;
         // u = P - G - L T for the first pixel (low word; exact modulo 2^32);
-        // per step along the row, row mode (P = j) adds 1, column mode
-        // (L = j) subtracts T
+        // per column along the row, row mode (P = j) adds 1, column mode
+        // (L = j) subtracts T; the thread's pixels are 32 columns apart
         const int L0 = row ? i : jb, P0 = row ? jb : i;
         unsigned u = (unsigned)(((long long)P0 << kFxBits) - G - (long long)L0 * T);
-        const unsigned du = row ? (unsigned)kFxOne : (unsigned)(-T);
-        float kc = ((float)P0 - fmaf((float)L0, Tf, Gf)) * invA;
-        const float dkc = row ? invA : -Tf * invA;
+        const unsigned du = 32u * (row ? (unsigned)kFxOne : (unsigned)(-T));
+        const float kc0 = ((float)P0 - fmaf((float)L0, Tf, Gf)) * invA;
+        const float dkc = 32.0f * (row ? invA : -Tf * invA);
 #pragma unroll
         for (int q = 0; q < kPPT; ++q) {
-          const int r = round_int(kc);
+          const int r = round_int(fmaf((float)q, dkc, kc0));
           const int D = (int)((unsigned)r * A32 - u);   // pos(L, r) - P, in (-1, 1)
           const bool right = D >= 0;                     // r is the "1-f" ray
           const int D2 = right ? D - absA32 : D + absA32;
@@ -213,12 +201,11 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
           }
           if (XTRA) accx[q] = fmaf(w1, wx[s1], fmaf(w2, wx[s2], accx[q]));
           u += du;
-          kc += dkc;
         }
       } else {
-        // t(i, j) = t00 + j tj + i ti, stepping along the row by tj
+        // t(i, j) = t00 + j tj + i ti, stepping along the row by 32 tj
         long long t = C.t00 + (long long)jb * C.tj + (long long)i * C.ti;
-        const long long tj = C.tj;
+        const long long tj = 32 * C.tj;
 #pragma unroll
         for (int q = 0; q < kPPT; ++q) {
           int k0 = ipart(t) - base;
@@ -266,30 +253,29 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
 #pragma unroll
       for (int q = 0; q < kPPT; ++q) accx[q] += sm.winx[q * 32 * kTH + t0];
   }
-  if (i >= N || jb >= N) return;
-  const int n_valid = min(kPPT, N - jb);
+  if (i >= N) return;
+  // pixel q of the thread is column jb + 32 q: a warp stores 32 consecutive
+  // pixels per q
 #pragma unroll
   for (int n = 0; n < NI; ++n) {
     const size_t o = ((size_t)(b0 + n) * N + i) * N + jb;
-    float v[kPPT];
 #pragma unroll
     for (int q = 0; q < kPPT; ++q) {
-      v[q] = J.alpha * acc[n][q];
-      if (J.beta != 0.0f && J.aux && q < n_valid)
-        v[q] = fmaf(J.beta, ld_any(J.aux, o + q, J.aux_bf16), v[q]);
+      if (jb + 32 * q >= N) break;
+      float v = J.alpha * acc[n][q];
+      if (J.beta != 0.0f && J.aux) v = fmaf(J.beta, ld_any(J.aux, o + 32 * q, J.aux_bf16), v);
+      st_any(J.out, o + 32 * q, v, J.out_bf16);
     }
-    store_run(J.out, o, v, n_valid, J.out_bf16);
   }
   if (XTRA) {
     const size_t o = ((size_t)bx * N + i) * N + jb;
-    float v[kPPT];
 #pragma unroll
     for (int q = 0; q < kPPT; ++q) {
-      v[q] = JX->alpha * accx[q];
-      if (JX->beta != 0.0f && JX->aux && q < n_valid)
-        v[q] = fmaf(JX->beta, ld_any(JX->aux, o + q, JX->aux_bf16), v[q]);
+      if (jb + 32 * q >= N) break;
+      float v = JX->alpha * accx[q];
+      if (JX->beta != 0.0f && JX->aux) v = fmaf(JX->beta, ld_any(JX->aux, o + 32 * q, JX->aux_bf16), v);
+      st_any(JX->out, o + 32 * q, v, JX->out_bf16);
     }
-    store_run(JX->out, o, v, n_valid, JX->out_bf16);
   }
 }
 
