@@ -780,6 +780,12 @@ int band_batch_clusters(size_t smem, int *clusters) {
 #ifndef SKEI_PART_SBL1
 #define SKEI_PART_SBL1 16
 #endif
+#ifndef SKEI_PART_MINB4
+#define SKEI_PART_MINB4 3     // CTAs per SM the registers of the 4-image partial kernel allow
+#endif
+#ifndef SKEI_PART_MINB1
+#define SKEI_PART_MINB1 1     // the same for single images
+#endif
 #ifndef SKEI_PART_SBL4
 #define SKEI_PART_SBL4 8
 #endif
@@ -890,26 +896,30 @@ __device__ __forceinline__ void partial_task(const Job &J, float *part, int b0, 
   }
 }
 
-template <int OP>
-__global__ void __launch_bounds__(kThreads) band_partial_kernel(const PartArgs args) {
+// Image groups of size 4 per job (none when the launch works on single
+// images); the job's remaining images form single-image groups.
+__device__ __forceinline__ int quads(int nimg, int gmax) { return gmax == 4 ? nimg >> 2 : 0; }
+
+// One CTA: band blockIdx.x, angle block blockIdx.y, image group blockIdx.z
+// among the launch's groups of NI images (job 0's, then job 1's).
+template <int OP, int NI>
+__global__ void __launch_bounds__(kThreads, NI == 4 ? SKEI_PART_MINB4 : SKEI_PART_MINB1)
+    band_partial_kernel(const PartArgs args) {
   pdl_enter();
   extern __shared__ float4 smem4[];
   __shared__ AngleConst sc[kMaxABP];
   __shared__ int sai[kMaxABP];
   const int z = blockIdx.z;
-  const int g0 = n_groups(args.jobs.j[0].nimg, args.gmax);
-  const int jn = (args.jobs.njobs > 1 && z >= g0) ? 1 : 0;
+  const Job &J0 = args.jobs.j[0];
+  const int q0 = quads(J0.nimg, args.gmax);
+  const int c0 = NI == 4 ? q0 : J0.nimg - 4 * q0;
+  const int jn = (args.jobs.njobs > 1 && z >= c0) ? 1 : 0;
   const Job &J = args.jobs.j[jn];
-  int b0, ni;
-  group_at(J.nimg, z - (jn ? g0 : 0), &b0, &ni, args.gmax);
-  float *part = args.part + args.off[jn];
-  float *buf = reinterpret_cast<float *>(smem4);
-  if (ni == 4)
-    partial_task<OP, 4>(J, part, b0, blockIdx.x, blockIdx.y * args.AB, args.AB, args.nbands,
-                        args.g4, args.ang, args.status, buf, sc, sai);
-  else
-    partial_task<OP, 1>(J, part, b0, blockIdx.x, blockIdx.y * args.AB, args.AB, args.nbands,
-                        args.g1, args.ang, args.status, buf, sc, sai);
+  const int zz = z - (jn ? c0 : 0);
+  const int b0 = NI == 4 ? 4 * zz : 4 * quads(J.nimg, args.gmax) + zz;
+  partial_task<OP, NI>(J, args.part + args.off[jn], b0, blockIdx.x, blockIdx.y * args.AB,
+                       args.AB, args.nbands, NI == 4 ? args.g4 : args.g1, args.ang, args.status,
+                       reinterpret_cast<float *>(smem4), sc, sai);
 }
 
 // out[b][a][k] = epilogue(sum over bands, in order, of the band sums).
@@ -969,6 +979,23 @@ int part_layout(skei_plan p, const Jobs &jobs, int *nbands1, int *nbands4, size_
   return SKEI_OK;
 }
 
+template <int OP, int NI>
+int set_partial_smem(size_t smem) {
+  if (smem > 227 * 1024)
+    return set_error(SKEI_EINVAL, "band of %zu bytes needs too much shared memory", smem);
+  static size_t configured[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (smem > 48 * 1024 && smem > configured[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(band_partial_kernel<OP, NI>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_error(e, "band partial kernel: shared memory attribute");
+    configured[dev] = smem;
+  }
+  return SKEI_OK;
+}
+
 template <int OP>
 int launch_band_partial(skei_plan p, const Jobs &jobs, float *work, size_t work_floats,
                         cudaStream_t st) {
@@ -991,10 +1018,13 @@ int launch_band_partial(skei_plan p, const Jobs &jobs, float *work, size_t work_
     g1 = part_geom(p->N, p->n_det, p->n_angles, 1, g4.SB);
     nbands = nb4;
   }
-  int m_max = 0, ngroups = 0;
+  int m_max = 0, ngroups = 0, n4 = 0, n1 = 0;
   for (int q = 0; q < jobs.njobs; ++q) {
     m_max = max(m_max, jobs.j[q].m);
     ngroups += n_groups(jobs.j[q].nimg, gm);
+    const int q4 = gm == 4 ? jobs.j[q].nimg >> 2 : 0;
+    n4 += q4;
+    n1 += jobs.j[q].nimg - 4 * q4;
   }
   if (ngroups > 65535) return set_error(SKEI_EINVAL, "too many images in one launch");
   // angles per CTA: enough CTAs for SKEI_PART_CTAS per SM
@@ -1004,22 +1034,17 @@ int launch_band_partial(skei_plan p, const Jobs &jobs, float *work, size_t work_
   int AB = (int)((m_max + blocks - 1) / blocks);
   AB = std::max(1, std::min(AB, kMaxABP));
   const int nblk = (m_max + AB - 1) / AB;
-  size_t smem = part_smem(g1);
-  if (any4) smem = std::max(smem, part_smem(g4));
-  if (smem > 227 * 1024)
-    return set_error(SKEI_EINVAL, "image of %d pixels needs too much shared memory", p->N);
-  static size_t configured[64] = {0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) dev = 0;
-  if (smem > 48 * 1024 && smem > configured[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(band_partial_kernel<OP>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_error(e, "band partial kernel: shared memory attribute");
-    configured[dev] = smem;
-  }
   PartArgs a{jobs, p->d_ang, p->d_status, g1, g4, gm, AB, nbands, work, {off[0], off[1]}};
-  launch_k(band_partial_kernel<OP>, dim3(nbands, nblk, ngroups), dim3(kThreads), smem, st, a);
+  if (n4 > 0) {
+    SKEI_TRY((set_partial_smem<OP, 4>(part_smem(g4))));
+    launch_k(band_partial_kernel<OP, 4>, dim3(nbands, nblk, n4), dim3(kThreads), part_smem(g4),
+             st, a);
+  }
+  if (n1 > 0) {
+    SKEI_TRY((set_partial_smem<OP, 1>(part_smem(g1))));
+    launch_k(band_partial_kernel<OP, 1>, dim3(nbands, nblk, n1), dim3(kThreads), part_smem(g1),
+             st, a);
+  }
   SKEI_TRY(check_launch("band partial sums launch"));
   int nimg = 0;
   for (int q = 0; q < jobs.njobs; ++q) nimg += jobs.j[q].nimg;
