@@ -72,6 +72,22 @@ struct skei_plan_s {
 
 namespace skei {
 
+// ------------------------------------------------------------ cp.async --
+// 4-byte asynchronous copy global -> shared; with ok false nothing is read
+// and the shared word is zeroed.
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem, bool ok) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem),
+               "r"(ok ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
 // ------------------------------------------------- dependent launches --
 // Build-time knob: SKEI_PDL 1 or 2 launches the operator kernels with
 // programmatic stream serialisation.  Each kernel waits (griddepcontrol.wait)

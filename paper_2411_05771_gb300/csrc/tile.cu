@@ -64,15 +64,89 @@ struct TileArgs {
   int merge;   // job 0's image b rides with job 1's group 4b .. 4b+3 (same angles)
 };
 
-// Shared memory of a tile task: the bins of kAC angles for up to 4 images,
-// [angle][bin][image].
+// Shared memory of a tile task (dynamic: above the 48 KB of static shared
+// memory): two windows, each the bins of kAC angles for up to 4 images,
+// [angle][bin][image], and three slots of chunk constants.  Chunk c is
+// computed from window c % 2 while window c+1 fills by cp.async and the
+// constants of chunk c+2 are set up.
 struct TileSmem {
-  alignas(16) float win[kAC * kWin * 4];
-  float winx[kAC * kWin];   // the bins of a riding image of another job
-  AngleConst sc[kAC];
-  int sai[kAC];
-  int kw0[kAC];
+  alignas(16) float win[2][kAC * kWin * 4];
+  float winx[2][kAC * kWin];   // the bins of a riding image of another job
+  AngleConst sc[3][kAC];
+  int sai[3][kAC];
+  int kw0[3][kAC];
 };
+constexpr size_t kTileSmem = sizeof(TileSmem);
+
+// Constants of chunk c (angles c0 .. c0 + nac - 1 of J's list) into slot
+// `slot`: angle index (or -1 if out of range, reported), its AngleConst and
+// the first bin of the window the tile projects onto.  Threads 0 .. nac-1.
+template <int OP>
+__device__ __forceinline__ void tile_setup(const Job &J, int c0, int nac, int i0, int j0,
+                                           int i_last, int j_last, int n_angles,
+                                           const AngleConst *ang, int *status, bool report,
+                                           TileSmem &sm, int slot) {
+  const int tid = threadIdx.x;
+  if (tid >= nac) return;
+  int ai = J.idx ? J.idx[c0 + tid] : c0 + tid;
+  if (ai < 0 || ai >= n_angles) {
+    if (report) atomicOr(status, 1);
+    ai = -1;
+  }
+  sm.sai[slot][tid] = ai;
+  if (ai < 0) return;
+  const AngleConst C = ang[ai];
+  sm.sc[slot][tid] = C;
+  // bin range of the tile: extremes of an affine function at corners
+  float lo = 3.0e38f;
+  for (int ci = 0; ci < 2; ++ci)
+    for (int cj = 0; cj < 2; ++cj) {
+      const float fi_ = (float)(ci ? i_last : i0), fj_ = (float)(cj ? j_last : j0);
+      const float L = C.mode ? fi_ : fj_, Pp = C.mode ? fj_ : fi_;
+      float v;
+      if (OP == OP_JOSEPH_ADJ) v = (Pp - fmaf(L, C.Tf, C.Gf)) * C.invA;
+      else v = fmaf(fj_, C.tjf, fmaf(fi_, C.tif, C.t00f));
+      lo = fminf(lo, v);
+    }
+  sm.kw0[slot][tid] = (int)floorf(lo) - 3;
+}
+
+// Window of chunk c (constants in `slot`) into window buffer `wb`: one
+// (angle, bin) per thread, the group's images side by side; bins outside
+// the sinogram and dead angles read as 0.  FP32 inputs are copied by
+// cp.async (the caller waits); BF16 inputs are converted and stored.
+template <int NI, bool XTRA>
+__device__ __forceinline__ void tile_window(const Job &J, int b0, int c0, int nac, int nd,
+                                            TileSmem &sm, int slot, int wb, const Job *JX,
+                                            int bx) {
+  const bool async = !J.in_bf16 && (!XTRA || !JX->in_bf16);
+  float *win = sm.win[wb], *winx = sm.winx[wb];
+  for (int e = threadIdx.x; e < nac * kWin; e += kThreads) {
+    const int a = e / kWin, w = e - a * kWin;
+    const int k = sm.kw0[slot][a] + w;
+    const bool ok = sm.sai[slot][a] >= 0 && k >= 0 && k < nd;
+    const int kk = ok ? k : 0;
+    if (async) {
+      const float *src = static_cast<const float *>(J.in);
+#pragma unroll
+      for (int n = 0; n < NI; ++n)
+        cp_async4(win + e * NI + n, src + ((size_t)(b0 + n) * J.m + c0 + a) * nd + kk, ok);
+      if (XTRA)
+        cp_async4(winx + e,
+                  static_cast<const float *>(JX->in) + ((size_t)bx * JX->m + c0 + a) * nd + kk,
+                  ok);
+    } else {
+#pragma unroll
+      for (int n = 0; n < NI; ++n)
+        win[e * NI + n] =
+            ok ? ld_any(J.in, ((size_t)(b0 + n) * J.m + c0 + a) * nd + k, J.in_bf16) : 0.0f;
+      if (XTRA)
+        winx[e] = ok ? ld_any(JX->in, ((size_t)bx * JX->m + c0 + a) * nd + k, JX->in_bf16)
+                     : 0.0f;
+    }
+  }
+  cp_async_commit();
+}
 
 // One task: the tile at (i0, j0) of images b0 .. b0 + NI - 1 of job J;
 // with XTRA, also image bx of job JX, whose angle list is J's: it shares
@@ -82,8 +156,6 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
                                           int n_angles, const AngleConst *ang, int *status,
                                           bool report, TileSmem &sm, const Job *JX = nullptr,
                                           int bx = 0) {
-  AngleConst *sc = sm.sc;
-  int *sai = sm.sai, *kw0 = sm.kw0;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int half = warp / kTH;             // which angles of each chunk
@@ -99,75 +171,39 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
 #pragma unroll
   for (int q = 0; q < kPPT; ++q) accx[q] = 0.0f;
 
-  for (int c0 = 0; c0 < J.m; c0 += kAC) {
-    const int nac = min(kAC, J.m - c0);
-    __syncthreads();  // previous chunk no longer read
-    if (tid < nac) {
-      int ai = J.idx ? J.idx[c0 + tid] : c0 + tid;
-      if (ai < 0 || ai >= n_angles) {
-        if (report) atomicOr(status, 1);
-        ai = -1;
-      }
-      sai[tid] = ai;
-      if (ai >= 0) {
-        const AngleConst C = ang[ai];
-        sc[tid] = C;
-        // bin range of the tile: extremes of an affine function at corners
-        float lo = 3.0e38f;
-        for (int ci = 0; ci < 2; ++ci)
-          for (int cj = 0; cj < 2; ++cj) {
-            const float fi_ = (float)(ci ? i_last : i0), fj_ = (float)(cj ? j_last : j0);
-            const float L = C.mode ? fi_ : fj_, Pp = C.mode ? fj_ : fi_;
-            float v;
-            if (OP == OP_JOSEPH_ADJ) v = (Pp - fmaf(L, C.Tf, C.Gf)) * C.invA;
-            else v = fmaf(fj_, C.tjf, fmaf(fi_, C.tif, C.t00f));
-            lo = fminf(lo, v);
-          }
-        kw0[tid] = (int)floorf(lo) - 3;
-      }
-    }
-    __syncthreads();
-    // window: one (angle, bin) per thread, the group's images side by side
-    for (int e = tid; e < nac * kWin; e += kThreads) {
-      const int a = e / kWin, w = e - a * kWin;
-      const int ai = sai[a];
-      float v[NI], vx = 0.0f;
-#pragma unroll
-      for (int n = 0; n < NI; ++n) v[n] = 0.0f;
-      if (ai >= 0) {
-        const int k = kw0[a] + w;
-        if (k >= 0 && k < nd) {
-          const float W = OP == OP_JOSEPH_ADJ ? sc[a].W : 1.0f;
-#pragma unroll
-          for (int n = 0; n < NI; ++n) {
-            v[n] = ld_any(J.in, ((size_t)(b0 + n) * J.m + c0 + a) * nd + k, J.in_bf16);
-            if (OP == OP_JOSEPH_ADJ) v[n] *= W;
-          }
-          if (XTRA) {
-            vx = ld_any(JX->in, ((size_t)bx * JX->m + c0 + a) * nd + k, JX->in_bf16);
-            if (OP == OP_JOSEPH_ADJ) vx *= W;
-          }
-        }
-      }
-      if (NI == 4) reinterpret_cast<float4 *>(sm.win)[e] = make_float4(v[0], v[1], v[2], v[3]);
-      else sm.win[e] = v[0];
-      if (XTRA) sm.winx[e] = vx;
-    }
-    __syncthreads();
+  const int nch = (J.m + kAC - 1) / kAC;
+  tile_setup<OP>(J, 0, min(kAC, J.m), i0, j0, i_last, j_last, n_angles, ang, status, report,
+                 sm, 0);
+  if (nch > 1)
+    tile_setup<OP>(J, kAC, min(kAC, J.m - kAC), i0, j0, i_last, j_last, n_angles, ang, status,
+                   report, sm, 1);
+  __syncthreads();
+  tile_window<NI, XTRA>(J, b0, 0, min(kAC, J.m), nd, sm, 0, 0, JX, bx);
+
+  for (int c = 0; c < nch; ++c) {
+    const int c0 = c * kAC, nac = min(kAC, J.m - c0), slot = c % 3;
+    cp_async_wait_all();
+    __syncthreads();  // window c and the constants of chunk c+1 are in place
+    if (c + 1 < nch)
+      tile_window<NI, XTRA>(J, b0, c0 + kAC, min(kAC, J.m - c0 - kAC), nd, sm, (c + 1) % 3,
+                            (c + 1) & 1, JX, bx);
+    if (c + 2 < nch)
+      tile_setup<OP>(J, c0 + 2 * kAC, min(kAC, J.m - c0 - 2 * kAC), i0, j0, i_last, j_last,
+                     n_angles, ang, status, report, sm, (c + 2) % 3);
 
     for (int a = half; a < nac; a += kSplit) {
-      if (sai[a] < 0) continue;
-      const AngleConst &C = sc[a];
-      const float *wa = sm.win + a * kWin * NI;
-      const float *wx = sm.winx + a * kWin;
-      const int base = kw0[a];
+      if (sm.sai[slot][a] < 0) continue;
+      const AngleConst &C = sm.sc[slot][a];
+      const float *wa = sm.win[c & 1] + a * kWin * NI;
+      const float *wx = sm.winx[c & 1] + a * kWin;
+      const int base = sm.kw0[slot][a];
       if (OP == OP_JOSEPH_ADJ) {
         const bool row = C.mode != 0;
         const long long A = C.A, T = C.T, G = C.G;
         const unsigned A32 = (unsigned)A;
         const int absA32 = (int)(unsigned)(A < 0 ? -A : A);
         const int sA = A < 0 ? -1 : 1;
-        const float Tf = C.Tf, Gf = C.Gf, invA = C.invA;
+        const float Tf = C.Tf, Gf = C.Gf, invA = C.invA, W = C.W;
         // u = P - G - L T for the first pixel (low word; exact modulo 2^32);
         // per column along the row, row mode (P = j) adds 1, column mode
         // (L = j) subtracts T; the thread's pixels are 32 columns apart
@@ -186,9 +222,10 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
           // construction, the clamp only bounds the read
           const int s1 = min(max(r - base, 1), kWin - 2);
           const int s2 = s1 + (right ? -sA : sA);
-          const float w1 = __int_as_float(0x40000000 - abs(D >> (kFxBits - 23))) - 1.0f;
-          const float w2 = fmaxf(__int_as_float(0x40000000 - abs(D2 >> (kFxBits - 23))) - 1.0f,
-                                 0.0f);
+          // tap weights times the angle's W (the bins are staged unscaled)
+          const float w1 = W * (__int_as_float(0x40000000 - abs(D >> (kFxBits - 23))) - 1.0f);
+          const float w2 =
+              W * fmaxf(__int_as_float(0x40000000 - abs(D2 >> (kFxBits - 23))) - 1.0f, 0.0f);
           if (NI == 4) {
             const float4 v1 = reinterpret_cast<const float4 *>(wa)[s1];
             const float4 v2 = reinterpret_cast<const float4 *>(wa)[s2];
@@ -232,7 +269,7 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
   if (kSplit > 1) {
     // the second half's sums through shared memory (the window is free)
     __syncthreads();
-    float *red = sm.win;
+    float *red = sm.win[0];
     const int t0 = tid % (32 * kTH);
     if (half == 1) {
 #pragma unroll
@@ -241,7 +278,7 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
         for (int q = 0; q < kPPT; ++q) red[(n * kPPT + q) * 32 * kTH + t0] = acc[n][q];
       if (XTRA)
 #pragma unroll
-        for (int q = 0; q < kPPT; ++q) sm.winx[q * 32 * kTH + t0] = accx[q];
+        for (int q = 0; q < kPPT; ++q) sm.winx[0][q * 32 * kTH + t0] = accx[q];
     }
     __syncthreads();
     if (half != 0) return;
@@ -251,7 +288,7 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
       for (int q = 0; q < kPPT; ++q) acc[n][q] += red[(n * kPPT + q) * 32 * kTH + t0];
     if (XTRA)
 #pragma unroll
-      for (int q = 0; q < kPPT; ++q) accx[q] += sm.winx[q * 32 * kTH + t0];
+      for (int q = 0; q < kPPT; ++q) accx[q] += sm.winx[0][q * 32 * kTH + t0];
   }
   if (i >= N) return;
   // pixel q of the thread is column jb + 32 q: a warp stores 32 consecutive
@@ -282,7 +319,8 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
 template <int OP>
 __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs args) {
   pdl_enter();
-  __shared__ TileSmem sm;
+  extern __shared__ float4 tile_smem4[];
+  TileSmem &sm = *reinterpret_cast<TileSmem *>(tile_smem4);
   const int z = blockIdx.z;
   const bool report = blockIdx.x == 0 && blockIdx.y == 0;
   if (args.merge) {
@@ -312,7 +350,8 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs args) {
 template <int OP>
 __global__ void __launch_bounds__(kThreads)
     tile_batch_kernel(const BatchItem *items, const int4 *tasks, int n_tasks, int *queue) {
-  __shared__ TileSmem sm;
+  extern __shared__ float4 tile_smem4[];
+  TileSmem &sm = *reinterpret_cast<TileSmem *>(tile_smem4);
   __shared__ int s_task;
   for (;;) {
     __syncthreads();  // the previous task's reads of s_task and shared memory are done
@@ -336,6 +375,31 @@ __global__ void __launch_bounds__(kThreads)
   if (threadIdx.x == 0) queue_retire(queue, gridDim.x);
 }
 
+// Opts a tile kernel in to its dynamic shared memory, once per device.
+template <typename K>
+int set_tile_smem(K kern, size_t *configured) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (configured[dev] < kTileSmem) {
+    cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
+    if (e != cudaSuccess) return cuda_error(e, "tile kernel: shared memory attribute");
+    configured[dev] = kTileSmem;
+  }
+  return SKEI_OK;
+}
+template <int OP>
+int set_tile_kernel_smem() {
+  static size_t configured[64] = {0};
+  return set_tile_smem(tile_kernel<OP>, configured);
+}
+template <int OP>
+int set_tile_batch_smem() {
+  static size_t configured[64] = {0};
+  return set_tile_smem(tile_batch_kernel<OP>, configured);
+}
+
 template <int OP>
 int launch_tile(skei_plan p, const Jobs &jobs, cudaStream_t st) {
   int ngroups = 0;
@@ -348,7 +412,8 @@ int launch_tile(skei_plan p, const Jobs &jobs, cudaStream_t st) {
   if (ngroups > 65535) return set_error(SKEI_EINVAL, "too many images in one launch");
   TileArgs a{jobs, p->N, p->n_det, p->n_angles, p->d_ang, p->d_status, merge};
   dim3 grid((p->N + kTW - 1) / kTW, (p->N + kTH - 1) / kTH, ngroups);
-  launch_k(tile_kernel<OP>, grid, dim3(kThreads), 0, st, a);
+  SKEI_TRY(set_tile_kernel_smem<OP>());
+  launch_k(tile_kernel<OP>, grid, dim3(kThreads), kTileSmem, st, a);
   return check_launch(OP == OP_JOSEPH_ADJ ? "joseph adjoint launch" : "back-projection launch");
 }
 
@@ -366,10 +431,12 @@ void tile_batch_shape(int *rows, int *cols) {
 }
 
 int tile_batch_occupancy(int op, int *ctas_per_sm) {
+  if (op == OP_JOSEPH_ADJ) SKEI_TRY(set_tile_batch_smem<OP_JOSEPH_ADJ>());
+  else SKEI_TRY(set_tile_batch_smem<OP_BACKPROJECT>());
   int n = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
       &n, op == OP_JOSEPH_ADJ ? tile_batch_kernel<OP_JOSEPH_ADJ> : tile_batch_kernel<OP_BACKPROJECT>,
-      kThreads, 0);
+      kThreads, kTileSmem);
   if (e != cudaSuccess) return cuda_error(e, "tile kernel: occupancy");
   *ctas_per_sm = n > 0 ? n : 1;
   return SKEI_OK;
@@ -377,11 +444,15 @@ int tile_batch_occupancy(int op, int *ctas_per_sm) {
 
 int launch_tile_batch_op(int op, const BatchItem *items, const int4 *tasks, int n_tasks,
                          int ctas, int *queue, cudaStream_t st) {
-  if (op == OP_JOSEPH_ADJ)
-    tile_batch_kernel<OP_JOSEPH_ADJ><<<ctas, kThreads, 0, st>>>(items, tasks, n_tasks, queue);
-  else if (op == OP_BACKPROJECT)
-    tile_batch_kernel<OP_BACKPROJECT><<<ctas, kThreads, 0, st>>>(items, tasks, n_tasks, queue);
-  else
+  if (op == OP_JOSEPH_ADJ) {
+    SKEI_TRY(set_tile_batch_smem<OP_JOSEPH_ADJ>());
+    tile_batch_kernel<OP_JOSEPH_ADJ><<<ctas, kThreads, kTileSmem, st>>>(items, tasks, n_tasks,
+                                                                          queue);
+  } else if (op == OP_BACKPROJECT) {
+    SKEI_TRY(set_tile_batch_smem<OP_BACKPROJECT>());
+    tile_batch_kernel<OP_BACKPROJECT><<<ctas, kThreads, kTileSmem, st>>>(items, tasks, n_tasks,
+                                                                           queue);
+  } else
     return set_error(SKEI_EINVAL, "tile batch: unknown operator %d", op);
   return check_launch(op == OP_JOSEPH_ADJ ? "batched joseph adjoint launch"
                                           : "batched back-projection launch");
