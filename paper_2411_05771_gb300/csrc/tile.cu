@@ -222,10 +222,12 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
           // construction, the clamp only bounds the read
           const int s1 = min(max(r - base, 1), kWin - 2);
           const int s2 = s1 + (right ? -sA : sA);
-          // tap weights times the angle's W (the bins are staged unscaled)
-          const float w1 = W * (__int_as_float(0x40000000 - abs(D >> (kFxBits - 23))) - 1.0f);
+          // tap weights times the angle's W (the bins are staged unscaled):
+          // with x = 2 - |a| 2^-23, the weight x - 1 is exact, so one FMA
+          // W x - W rounds W (x - 1) once, as the product would (W > 0)
+          const float w1 = fmaf(W, __int_as_float(0x40000000 - abs(D >> (kFxBits - 23))), -W);
           const float w2 =
-              W * fmaxf(__int_as_float(0x40000000 - abs(D2 >> (kFxBits - 23))) - 1.0f, 0.0f);
+              fmaxf(fmaf(W, __int_as_float(0x40000000 - abs(D2 >> (kFxBits - 23))), -W), 0.0f);
           if (NI == 4) {
             const float4 v1 = reinterpret_cast<const float4 *>(wa)[s1];
             const float4 v2 = reinterpret_cast<const float4 *>(wa)[s2];
@@ -347,8 +349,13 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs args) {
 // the next task from a global counter (tasks come in decreasing cost order)
 // until none is left.  Task = (item, b0 << 3 | group size, tile row, tile
 // column).
+// CTAs per SM the registers of the persistent tile kernel allow (2: a few
+// bytes of spills, measured faster than 1 CTA of 96 registers)
+#ifndef SKEI_TILE_BATCH_MINB
+#define SKEI_TILE_BATCH_MINB 2
+#endif
 template <int OP>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, SKEI_TILE_BATCH_MINB)
     tile_batch_kernel(const BatchItem *items, const int4 *tasks, int n_tasks, int *queue) {
   extern __shared__ float4 tile_smem4[];
   TileSmem &sm = *reinterpret_cast<TileSmem *>(tile_smem4);
