@@ -587,6 +587,85 @@ def op_line(workload, op, us, samples, peak, **extra):
     print(json.dumps(line), flush=True)
 
 
+def ttt_bn_suite(S, dev, stream, channels=16, layers=4):
+    """BN-only test-time training (Sec. 3.3) on the 512^2 workload: the
+    residual CNN stand-in (frozen seeded 3x3 convolutions, cuDNN, FP32 without
+    TF32; batch-statistics BN + ReLU in libskei) run twice per step around the
+    operators, autograd backward through it, Adam on the BN parameters only;
+    the whole step is one CUDA graph.  Sketched vs plain arm as in the
+    headline (the draws of step 1)."""
+    import torch
+    from paper_2411_05771_gb300 import inputs as I
+    from paper_2411_05771_gb300.autograd import skei_loss
+    from paper_2411_05771_gb300.net import ResCNN
+    saved = (torch.backends.cudnn.allow_tf32, torch.backends.cudnn.benchmark)
+    torch.backends.cudnn.allow_tf32 = False
+    torch.backends.cudnn.benchmark = True
+    prob = make_problem(SKETCHED)
+    plan = S.Plan(N_IMG, N_VIEWS, prob["angs"])
+    f32 = dict(dtype=torch.float32, device=dev)
+    y = torch.tensor(prob["y"], **f32)[None]
+    x0 = S.fbp(plan, y)
+    wts = I.cnn_weights(channels=channels, layers=layers, seed=0)
+    # the BN kernels alone at the network's largest activation: the B G = 4
+    # transformed images x 16 channels of 512^2
+    hbm = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6787.9)) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6787.9
+    v = torch.randn((SKETCHED.B * SKETCHED.G, channels, N_IMG, N_IMG), **f32)
+    gv = torch.randn_like(v)
+    sc, sh = torch.ones(channels, **f32), torch.zeros(channels, **f32)
+    bo = torch.empty_like(v)
+    wbn = torch.empty(S.bn_workspace_size(*v.shape[:2], N_IMG * N_IMG), dtype=torch.uint8,
+                      device=dev)
+    _, mu, rs = S.bn_act_fwd(v, sc, sh, out=bo, work=wbn)
+    nbytes = v.numel() * 4
+    for op, fn, traffic in (("BN+ReLU forward", lambda: S.bn_act_fwd(v, sc, sh, out=bo, work=wbn),
+                             2 * nbytes),
+                            ("BN+ReLU backward",
+                             lambda: S.bn_act_bwd(v, gv, sc, sh, mu, rs, work=wbn), 3 * nbytes)):
+        us = time_graph(fn, stream, reps=10)
+        gbs = traffic / (us * 1e-6) / 1e9
+        print(json.dumps({"suite": "bn-4x16x512x512", "op": op, "us": round(us, 2),
+                          "algorithmic_bytes": traffic, "gb_per_s": round(gbs, 1),
+                          "roofline_frac_hbm": round(gbs / hbm, 3),
+                          "launches": 2}), flush=True)
+    del v, gv, bo, wbn
+
+    res = {}
+    for tag, wl in (("sketched", SKETCHED), ("plain", PLAIN)):
+        idx_all, g_all = step_params(1, wl)
+        idx = None if not wl.sketched else torch.tensor(idx_all[0], dtype=torch.int32,
+                                                         device=dev)
+        mc_idx = idx if wl.mc_sketched else None
+        g = torch.tensor(g_all[0], dtype=torch.float64, device=dev)
+        net = ResCNN(wts, dev)
+        m1, v1 = torch.zeros_like(net.bn), torch.zeros_like(net.bn)
+        step_no = torch.ones((), dtype=torch.int32, device=dev)
+
+        def step(net=net, idx=idx, mc_idx=mc_idx, g=g, m1=m1, v1=v1, wl=wl, step_no=step_no):
+            loss = skei_loss(plan, net(x0), y, net, g, mc_idx, idx, LAM, wl.mc_scale)
+            (gr,) = torch.autograd.grad(loss, [net.bn])
+            with torch.no_grad():
+                S.adam_step(net.bn.data, m1, v1, step_no, gr, lr=LR)
+
+        res[tag] = time_graph(step, stream, reps=5)
+        torch.backends.cudnn.allow_tf32 = True
+        res[tag + "_tf32"] = time_graph(step, stream, reps=5)
+        torch.backends.cudnn.allow_tf32 = False
+    torch.backends.cudnn.allow_tf32, torch.backends.cudnn.benchmark = saved
+    print(json.dumps({"suite": "ttt-bn-512x512-60views-sketch30-G4",
+                      "network": f"residual CNN, {layers} 3x3 conv layers x {channels} "
+                                 "channels, batch-statistics BN + ReLU, FP32 (no TF32)",
+                      "adapted": f"BN scale/shift only ({wts.bn.size} parameters)",
+                      "sketched_steps_per_s": round(1e6 / res["sketched"], 1),
+                      "plain_steps_per_s": round(1e6 / res["plain"], 1),
+                      "speedup": round(res["plain"] / res["sketched"], 3),
+                      "tf32_network": {"sketched_steps_per_s": round(1e6 / res["sketched_tf32"], 1),
+                                       "plain_steps_per_s": round(1e6 / res["plain_tf32"], 1),
+                                       "speedup": round(res["plain_tf32"] / res["sketched_tf32"],
+                                                        3)}}), flush=True)
+
+
 def suite(S, dev, stream):
     """The measurements behind the per-workload table: single operators
     (64^2 with 60 views; 8 x 256^2 with 180 views, full and a 45-angle
@@ -656,6 +735,8 @@ def suite(S, dev, stream):
                       "plain_steps_per_s": round(1e6 / res["plain"], 1),
                       "speedup": round(res["plain"] / res["sketched"], 3),
                       "operator_work_ratio_bound": 3.0}), flush=True)
+
+    ttt_bn_suite(S, dev, stream)
 
     # 16 instances mixing 256^2 / 360 angles and 512^2 / 720 angles
     rng = np.random.default_rng(4)

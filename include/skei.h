@@ -310,6 +310,39 @@ int skei_adam_step(float *theta, int64_t n, int dtype, const void *g1, int c1,
                    double lr, double beta1, double beta2, double eps,
                    void *stream);
 
+/* ------------------------------------------ batch-norm layers (Sec. 3.3) --
+ * The layers that BN-only test-time training adapts: normalisation with the
+ * statistics of the current batch, then the learnable affine map (scale =
+ * theta_1, shift = theta_2 of Sec. 3.3), then an optional ReLU.  For channel
+ * c of v [B][C][HW] (B images of C channels of HW values, contiguous), over
+ * its M = B HW values:
+ *   mean_c = (1/M) sum v,  var_c = (1/M) sum (v - mean_c)^2 (biased),
+ *   rstd_c = 1 / sqrt(var_c + eps),
+ *   out = act(scale_c (v - mean_c) rstd_c + shift_c),  act = ReLU (relu != 0)
+ *         or the identity.
+ * skei_bn_act_fwd writes out (dtype, same layout as v) and the FP32 mean_c,
+ * rstd_c it used (device [C], kept for the backward).
+ * skei_bn_act_bwd takes the forward's v, mean, rstd and the gradient g_out of
+ * out, and writes g_v (dtype, layout of v) and the FP32 per-channel
+ * gradients g_scale = sum g_y (v - mean) rstd and g_shift = sum g_y, where
+ * g_y = g_out where the activation passes (y > 0 for ReLU, y = the affine
+ * map's output) and 0 elsewhere;
+ *   g_v = scale rstd (g_y - g_shift / M - (v - mean) rstd g_scale / M).
+ * Sums are reduced in a fixed order (FP32 within a thread, FP64 beyond), so
+ * results are deterministic.  scale, shift, mean, rstd, g_scale, g_shift are
+ * device float[C].  work: device workspace of at least
+ * skei_bn_workspace_size(B, C, HW) bytes, 16-byte aligned, owned by the
+ * caller.  Errors: SKEI_EINVAL for B, C or HW < 1, C > 65535, eps <= 0, a
+ * NULL or host pointer, or too small a workspace. */
+size_t skei_bn_workspace_size(int B, int C, int64_t HW);
+int skei_bn_act_fwd(int dtype, const void *v, int B, int C, int64_t HW, const float *scale,
+                    const float *shift, int relu, double eps, void *out, float *mean,
+                    float *rstd, void *work, size_t work_bytes, void *stream);
+int skei_bn_act_bwd(int dtype, const void *v, const void *g_out, int B, int C, int64_t HW,
+                    const float *scale, const float *shift, const float *mean,
+                    const float *rstd, int relu, void *g_v, float *g_scale, float *g_shift,
+                    void *work, size_t work_bytes, void *stream);
+
 /* ------------------------------------------------ batched schedule --
  * One operator applied to many instances in one persistent launch per
  * kernel: images of different sizes (each item its own plan), each with its

@@ -15,12 +15,15 @@ Paper map:
   * Algorithm 2   per iteration: draw S_k and T_i, MC + lambda SkEI, Adam step
   * Sec. 4.2.1    CT sketch = one of N interleaved angle subsets
   * Sec. 4.1.3    transforms = rotations; Adam with lr 5e-4
+  * Sec. 3.3      BN-only test-time training: batch-statistics BN layers,
+                  only their affine parameters adapted
 
 Readings where the paper is silent (all recorded in the design notes):
   A_S^dagger is the FBP over the sketch's angles, (pi/m) B_S H; the sketch is
   an unscaled row selection, with the sketched MC term multiplied by
   ``mc_scale``; norms are sums of squares; loss = (1/B) sum_b
-  [mc_b + lambda/G sum_g ei_bg].
+  [mc_b + lambda/G sum_g ei_bg]; a BN layer normalises with the biased batch
+  variance plus eps = 1e-5.
 
 Parity status: every function here is pinned by tests/test_oracle_*.py
 (closed forms, exact symmetries, explicit small matrices, analytic Radon and
@@ -331,6 +334,77 @@ def adam_step(theta, grad, m, v, step: int, lr=5e-4, beta1=0.9, beta2=0.999, eps
     m_hat = m / (1.0 - beta1 ** step)
     v_hat = v / (1.0 - beta2 ** step)
     return theta - lr * m_hat / (np.sqrt(v_hat) + eps), m, v
+
+
+# --------------------------------------------------------------------------
+# BN-only test-time training (Sec. 3.3): batch-statistics BN layers and the
+# residual CNN stand-in built from them
+# --------------------------------------------------------------------------
+
+def _bn_parts(v, scale, shift, eps):
+    axes = (0,) + tuple(range(2, v.ndim))
+    shp = (1, -1) + (1,) * (v.ndim - 2)
+    mu = v.mean(axis=axes, keepdims=True)
+    var = ((v - mu) ** 2).mean(axis=axes, keepdims=True)
+    sigma = np.sqrt(var + eps)
+    xh = (v - mu) / sigma
+    y = _f64(scale).reshape(shp) * xh + _f64(shift).reshape(shp)
+    return axes, shp, sigma, xh, y
+
+
+def bn_act(v, scale, shift, relu=True, eps=1e-5):
+    """Sec. 3.3: BN(v) = theta_1 (v - mu) / sigma + theta_2 per channel of
+    v [B, C, ...], mu and sigma the mean and standard deviation of the current
+    batch (biased variance plus eps: the paper leaves both open), then ReLU."""
+    v = _f64(v)
+    _, _, _, _, y = _bn_parts(v, scale, shift, eps)
+    return np.maximum(y, 0.0) if relu else y
+
+
+def bn_act_bwd(v, g, scale, shift, relu=True, eps=1e-5):
+    """Gradients of bn_act at v for the output gradient g, by the chain rule
+    through the batch statistics: with g_y = g where the ReLU passes,
+    d/dshift = sum g_y, d/dscale = sum g_y x^, and
+    d/dv = (scale / sigma) (g_y - mean(g_y) - x^ mean(g_y x^))."""
+    v, g = _f64(v), _f64(g)
+    axes, shp, sigma, xh, y = _bn_parts(v, scale, shift, eps)
+    gy = g * (y > 0) if relu else g
+    g_shift = gy.sum(axis=axes)
+    g_scale = (gy * xh).sum(axis=axes)
+    M = v.size // v.shape[1]
+    g_v = (_f64(scale).reshape(shp) / sigma) * (
+        gy - g_shift.reshape(shp) / M - xh * g_scale.reshape(shp) / M)
+    return g_v, g_scale, g_shift
+
+
+def rescnn(u, conv, bn, eps=1e-5):
+    """The residual CNN stand-in F(u) = u + h(u): h = 3x3 convolutions (zero
+    padding 1, no bias), each but the last followed by bn_act with ReLU;
+    u [n, N, N] (each image one batch entry, one channel); bn = the flat
+    per-layer (scale, shift) vector.  Convolutions by torch's CPU conv2d in
+    float64 (a library primitive)."""
+    import torch
+    import torch.nn.functional as tf
+    u = _f64(u)
+    h = u[:, None]
+    C = conv[0].shape[0]
+    for l, w in enumerate(conv):
+        h = tf.conv2d(torch.from_numpy(h), torch.from_numpy(_f64(w)), padding=1).numpy()
+        if l < len(conv) - 1:
+            o = 2 * C * l
+            h = bn_act(h, bn[o:o + C], bn[o + C:o + 2 * C], True, eps)
+    return u + h[:, 0]
+
+
+def ttt_bn_loss(bn, conv, x0, y, angles_deg, mc_idx, sk_idx, g_deg, lam, mc_scale, eps=1e-5):
+    """Loss of Eq. (e:skeilossttt) with F = rescnn: x1 = F(x0) (the B
+    measurements' A^dagger y as one batch), x3 = F(z) (the B G transformed
+    reconstructions as one batch), as a function of the BN parameters."""
+    x1 = rescnn(x0, conv, bn, eps)
+    r, x2, z = ei_stage1(x1, y, angles_deg, mc_idx, sk_idx, g_deg)
+    B, G, N = z.shape[0], z.shape[1], z.shape[-1]
+    x3 = rescnn(z.reshape(B * G, N, N), conv, bn, eps).reshape(B, G, N, N)
+    return ei_finish(x2, x3, r, lam, mc_scale)[0]
 
 
 def psnr(x, ref) -> float:

@@ -152,3 +152,38 @@ def rotation_angles(rng: np.random.Generator, B: int, G: int) -> np.ndarray:
 def step_rng(step: int) -> np.random.Generator:
     """Per-iteration randomness (sketch offset, rotations)."""
     return np.random.default_rng(1000 + int(step))
+
+
+# --------------------------------------------------------------------------
+# weights of the residual CNN that stands in for the paper's pre-trained
+# network in BN-only test-time training (Sec. 3.3); the paper's U-Net and
+# its trained weights are not available, so both sides build the same
+# seeded network from these arrays
+# --------------------------------------------------------------------------
+
+@dataclass
+class CnnWeights:
+    conv: list        # float64 [C_out, C_in, 3, 3] per layer: 1 -> C, C -> C ..., C -> 1
+    bn: np.ndarray    # float64 [2 C (L-1)]: per BN layer l, scale[C] then shift[C]
+    channels: int
+    layers: int
+
+
+def cnn_weights(channels: int = 16, layers: int = 4, seed: int = 0) -> CnnWeights:
+    """He-normal 3x3 kernels (std sqrt(2 / (9 C_in))), the last layer scaled
+    by 0.1 so that the residual branch starts small; BN scales drawn around 1
+    and shifts around 0, as after pre-training."""
+    if layers < 2 or channels < 1:
+        raise ValueError("need layers >= 2 and channels >= 1")
+    rng = np.random.default_rng(seed)
+    chans = [1] + [channels] * (layers - 1) + [1]
+    conv = []
+    for l in range(layers):
+        cin, cout = chans[l], chans[l + 1]
+        w = rng.standard_normal((cout, cin, 3, 3)) * math.sqrt(2.0 / (9 * cin))
+        conv.append(w * (0.1 if l == layers - 1 else 1.0))
+    bn = []
+    for _ in range(layers - 1):
+        bn.append(1.0 + 0.1 * rng.standard_normal(channels))
+        bn.append(0.1 * rng.standard_normal(channels))
+    return CnnWeights(conv=conv, bn=np.concatenate(bn), channels=channels, layers=layers)

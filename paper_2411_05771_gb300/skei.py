@@ -24,6 +24,7 @@ __all__ = [
     "fbp_workspace_size", "fbp", "fbp_adj", "fbp_noalloc", "rotate", "rotate_adj",
     "ei_workspace_size", "ei_loss_fwd", "ei_loss_finish", "ei_loss_bwd",
     "residual_add", "adam_step", "library_path",
+    "bn_workspace_size", "bn_act_fwd", "bn_act_bwd",
     "Batch", "BatchItem", "PROJ_FWD", "PROJ_ADJ", "BACKPROJECT", "BACKPROJECT_ADJ", "FILTER",
     "FBP",
 ]
@@ -91,6 +92,11 @@ _SIGS = {
                           _vp, _sz, _vp], _i),
     "skei_residual_add": ([_i, _vp, _vp, _i, _i64, _vp, _vp], _i),
     "skei_adam_step": ([_vp, _i64, _i, _vp, _i, _vp, _i, _vp, _vp, _vp, _d, _d, _d, _d, _vp], _i),
+    "skei_bn_workspace_size": ([_i, _i, _i64], _sz),
+    "skei_bn_act_fwd": ([_i, _vp, _i, _i, _i64, _vp, _vp, _i, _d, _vp, _vp, _vp, _vp, _sz, _vp],
+                        _i),
+    "skei_bn_act_bwd": ([_i, _vp, _vp, _i, _i, _i64, _vp, _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp,
+                         _sz, _vp], _i),
     "skei_batch_create": ([_i, ctypes.POINTER(_BatchItemC), _i, ctypes.POINTER(_BATCH)], _i),
     "skei_batch_run": ([_BATCH, _vp], _i),
     "skei_batch_tune": ([_BATCH, _i, _vp], _i),
@@ -531,6 +537,56 @@ def adam_step(theta, m, v, step_dev, g1, g2=None, lr=5e-4, beta1=0.9, beta2=0.99
     _check(_lib.skei_adam_step(_ptr(theta), n, _dtype_code(g1), _ptr(g1), c1, _ptr(g2), c2,
                                _ptr(m), _ptr(v), _ptr(step_dev), lr, beta1, beta2, eps, _stream()),
            "skei_adam_step")
+
+
+# ------------------------------------------------------ batch-norm layers
+def _bn_shape(v):
+    if v.dim() < 2:
+        raise ValueError("v must be [B, C, ...]")
+    B, C = v.shape[0], v.shape[1]
+    return B, C, v[0, 0].numel()
+
+
+def bn_workspace_size(B: int, C: int, HW: int) -> int:
+    return int(_lib.skei_bn_workspace_size(B, C, HW))
+
+
+def bn_act_fwd(v, scale, shift, relu=True, eps=1e-5, out=None, work=None):
+    """Batch-statistics BN of v [B, C, ...] per channel, then scale/shift
+    (float32 [C]) and ReLU (relu=True): returns (out, mean, rstd)."""
+    _dev(v, "v")
+    B, C, HW = _bn_shape(v)
+    _dev(scale, "scale", torch.float32, (C,))
+    _dev(shift, "shift", torch.float32, (C,))
+    out = torch.empty_like(v) if out is None else out
+    _dev(out, "out", v.dtype, v.shape)
+    mean = torch.empty(C, dtype=torch.float32, device=v.device)
+    rstd = torch.empty_like(mean)
+    nb = bn_workspace_size(B, C, HW)
+    w = _work(nb, v.device, work)
+    _check(_lib.skei_bn_act_fwd(_dtype_code(v), _ptr(v), B, C, HW, _ptr(scale), _ptr(shift),
+                                int(bool(relu)), float(eps), _ptr(out), _ptr(mean), _ptr(rstd),
+                                _ptr(w), nb, _stream()), "skei_bn_act_fwd")
+    return out, mean, rstd
+
+
+def bn_act_bwd(v, g_out, scale, shift, mean, rstd, relu=True, work=None):
+    """Gradients of bn_act_fwd: returns (g_v, g_scale, g_shift)."""
+    _dev(v, "v")
+    B, C, HW = _bn_shape(v)
+    _dev(g_out, "g_out", v.dtype, v.shape)
+    for t, nm in ((scale, "scale"), (shift, "shift"), (mean, "mean"), (rstd, "rstd")):
+        _dev(t, nm, torch.float32, (C,))
+    g_v = torch.empty_like(v)
+    g_scale = torch.empty(C, dtype=torch.float32, device=v.device)
+    g_shift = torch.empty_like(g_scale)
+    nb = bn_workspace_size(B, C, HW)
+    w = _work(nb, v.device, work)
+    _check(_lib.skei_bn_act_bwd(_dtype_code(v), _ptr(v), _ptr(g_out), B, C, HW, _ptr(scale),
+                                _ptr(shift), _ptr(mean), _ptr(rstd), int(bool(relu)), _ptr(g_v),
+                                _ptr(g_scale), _ptr(g_shift), _ptr(w), nb, _stream()),
+           "skei_bn_act_bwd")
+    return g_v, g_scale, g_shift
 
 
 # ------------------------------------------------------- batched schedule
