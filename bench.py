@@ -71,8 +71,10 @@ class Workload:
     sketch or on all views, G rotations per image."""
 
     def __init__(self, N=N_IMG, views=N_VIEWS, m=SKETCH, G=G_ROT, B=BATCH, mc_sketched=True,
-                 noisy=True, draw_m=None):
+                 noisy=True, draw_m=None, per_sample=False):
         self.N, self.views, self.m, self.G, self.B = N, views, m, G, B
+        # per_sample: every measurement draws its own sketch (Algorithm 1)
+        self.per_sample = per_sample and m < views
         self.mc_sketched = mc_sketched and m < views
         self.noisy = noisy
         # sketch size of the per-step offset draw: the plain arm draws as the
@@ -110,15 +112,21 @@ def make_problem(wl=SKETCHED, seed=0):
 
 
 def step_params(n_steps, wl, first=0):
-    """Per-step draws (Algorithm 2): one sketch offset and B x G rotation
-    angles from default_rng(1000 + step)."""
+    """Per-step draws (Algorithm 2): one sketch offset (one per measurement
+    with per_sample, Algorithm 1) and B x G rotation angles from
+    default_rng(1000 + step)."""
     from paper_2411_05771_gb300 import inputs as I
     idx, g = [], []
     for s in range(first, first + n_steps):
         rng = I.step_rng(s)
-        off = I.random_sketch_offset(rng, wl.views, wl.draw_m)
-        idx.append(I.sketch_indices(wl.views, wl.m, off) if wl.sketched
-                   else np.arange(wl.views, dtype=np.int32))
+        if wl.per_sample:
+            idx.append(np.stack([I.sketch_indices(wl.views, wl.m,
+                                                  I.random_sketch_offset(rng, wl.views, wl.draw_m))
+                                 for _ in range(wl.B)]))
+        else:
+            off = I.random_sketch_offset(rng, wl.views, wl.draw_m)
+            idx.append(I.sketch_indices(wl.views, wl.m, off) if wl.sketched
+                       else np.arange(wl.views, dtype=np.int32))
         g.append(I.rotation_angles(rng, wl.B, wl.G))
     return np.stack(idx).astype(np.int32), np.stack(g)
 
@@ -146,11 +154,13 @@ class Arm:
         # the step's draws live in one device buffer (rotation angles, sketch
         # rows, step number), so that a step uploads them with one copy
         self.g_off, self.idx_off = 0, 8 * B * G
-        self.step_off = self.idx_off + 4 * self.m
+        self.step_off = self.idx_off + 4 * self.m * (B if wl.per_sample else 1)
         self.param_bytes = (self.step_off + 4 + 15) // 16 * 16
         self.params = torch.zeros(self.param_bytes, dtype=torch.uint8, device=d)
         self.g = self.params[self.g_off:self.idx_off].view(torch.float64).view(B, G)
         self.idx = self.params[self.idx_off:self.step_off].view(torch.int32)
+        if wl.per_sample:
+            self.idx = self.idx.view(B, self.m)
         self.step_no = self.params[self.step_off:self.step_off + 4].view(torch.int32)
         self.x1 = torch.empty((B, N, N), dtype=self.tdt, device=d)
         self.r = torch.empty((B, self.mc_m, nd), dtype=self.tdt, device=d)
@@ -193,13 +203,15 @@ class Arm:
         mc_idx = self.idx if self.wl.mc_sketched else None
         sk_idx = self.idx if self.sketched else None
         S.residual_add(self.x0, self.theta, out=self.x1)                      # x1 = F(x0)
-        S.ei_loss_fwd(p, self.x1, self.y, self.g, mc_idx, sk_idx, work=self.work,
-                      out=(self.r, self.x2, self.z))
+        fwd = S.ei_loss_fwd_per_sample if self.wl.per_sample else S.ei_loss_fwd
+        bwd = S.ei_loss_bwd_per_sample if self.wl.per_sample else S.ei_loss_bwd
+        fwd(p, self.x1, self.y, self.g, mc_idx, sk_idx, work=self.work,
+            out=(self.r, self.x2, self.z))
         S.residual_add(self.z, self.theta, out=self.x3)                       # x3 = F(z)
         S.ei_loss_finish(self.x2, self.x3, self.r, LAM, self.mc_scale, work=self.work,
                          out=(self.loss, self.mc, self.ei, self.gx2, self.gx3))
-        S.ei_loss_bwd(p, self.r, self.gx2, self.gx3, self.g, self.mc_scale / self.wl.B, mc_idx,
-                      sk_idx, work=self.work, out=self.gx1)
+        bwd(p, self.r, self.gx2, self.gx3, self.g, self.mc_scale / self.wl.B, mc_idx, sk_idx,
+            work=self.work, out=self.gx1)
         # dL/dtheta = dL/dx1 + sum_g dL/dx3 (F's Jacobian is the identity)
         S.adam_step(self.theta, self.m1, self.v1, self.step_no, self.gx1, self.gx3, lr=LR)
 
@@ -723,8 +735,10 @@ def suite(S, dev, stream):
     wp = Workload(N=256, views=180, m=180, G=4, B=8, mc_sketched=False, noisy=False, draw_m=45)
     prob = make_problem(wl)
     plan = S.Plan(256, 180, prob["angs"])
+    ws = Workload(N=256, views=180, m=45, G=4, B=8, mc_sketched=False, noisy=False,
+                  per_sample=True)
     res = {}
-    for tag, w in (("sketched", wl), ("plain", wp)):
+    for tag, w in (("sketched", wl), ("plain", wp), ("per_sample", ws)):
         arm = Arm(S, plan, prob, w, "f32", dev)
         idx_all, g_all = step_params(1, w)
         arm.load_params(idx_all[0], g_all[0], 1)
@@ -735,6 +749,14 @@ def suite(S, dev, stream):
                       "plain_steps_per_s": round(1e6 / res["plain"], 1),
                       "speedup": round(res["plain"] / res["sketched"], 3),
                       "operator_work_ratio_bound": 3.0}), flush=True)
+    # Algorithm 1 over 8 measurements with a sketch each
+    print(json.dumps({"suite": "ei-step-8x4x256x256-180views-sketch45-per-sample", "G": 4,
+                      "B": 8, "mc": "all 180 views", "ei": "45-angle sketch per measurement",
+                      "per_sample_steps_per_s": round(1e6 / res["per_sample"], 1),
+                      "shared_sketch_steps_per_s": round(1e6 / res["sketched"], 1),
+                      "plain_steps_per_s": round(1e6 / res["plain"], 1),
+                      "speedup_vs_plain": round(res["plain"] / res["per_sample"], 3)}),
+          flush=True)
 
     ttt_bn_suite(S, dev, stream)
 

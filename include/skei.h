@@ -291,6 +291,24 @@ int skei_ei_loss_bwd(skei_plan plan, int dtype, const void *r, const void *g_x2,
                      double mc_coef, void *g_x1, void *work, size_t work_bytes,
                      void *stream);
 
+/* The same with an angle list per measurement (Algorithm 1: a sketch S_k
+ * drawn for every sample y_j): mc_idx and sk_idx, where not NULL, are DEVICE
+ * int32 [B][mc_m] and [B][sk_m]; measurement b uses row b for its MC term and
+ * for the EI term of its G transformed images.  The loss is the mean of the
+ * per-measurement losses, so skei_ei_loss_finish is unchanged; workspace,
+ * layouts and errors are those of skei_ei_loss_fwd / skei_ei_loss_bwd.  The
+ * kernels group each measurement's G images as with a shared sketch (groups
+ * of 4 need G % 4 == 0; other G run single images). */
+int skei_ei_loss_fwd_per_sample(skei_plan plan, int dtype, const void *x1, const void *y,
+                                int B, const int *mc_idx, int mc_m, const int *sk_idx,
+                                int sk_m, const double *g_deg, int G, void *r, void *x2,
+                                void *z, void *work, size_t work_bytes, void *stream);
+int skei_ei_loss_bwd_per_sample(skei_plan plan, int dtype, const void *r, const void *g_x2,
+                                const void *g_z, int B, const int *mc_idx, int mc_m,
+                                const int *sk_idx, int sk_m, const double *g_deg, int G,
+                                double mc_coef, void *g_x1, void *work, size_t work_bytes,
+                                void *stream);
+
 /* ------------------------------------------ stand-in network utilities --
  * Not operators of the paper: the residual stand-in network
  * F_theta(u) = u + theta used by the benchmark's test-time-training loop,
@@ -328,7 +346,7 @@ int skei_adam_step(float *theta, int64_t n, int dtype, const void *g1, int c1,
  * g_y = g_out where the activation passes (y > 0 for ReLU, y = the affine
  * map's output) and 0 elsewhere;
  *   g_v = scale rstd (g_y - g_shift / M - (v - mean) rstd g_scale / M).
- * Sums are reduced in a fixed order (FP32 within a thread, FP64 beyond), so
+ * Sums are reduced in a fixed order (FP32 within a warp, FP64 beyond), so
  * results are deterministic.  scale, shift, mean, rstd, g_scale, g_shift are
  * device float[C].  work: device workspace of at least
  * skei_bn_workspace_size(B, C, HW) bytes, 16-byte aligned, owned by the

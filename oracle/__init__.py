@@ -17,6 +17,7 @@ Paper map:
   * Sec. 4.1.3    transforms = rotations; Adam with lr 5e-4
   * Sec. 3.3      BN-only test-time training: batch-statistics BN layers,
                   only their affine parameters adapted
+  * Algorithm 1   several measurements per step, a sketch drawn for each
 
 Readings where the paper is silent (all recorded in the design notes):
   A_S^dagger is the FBP over the sketch's angles, (pi/m) B_S H; the sketch is
@@ -301,6 +302,35 @@ def ei_backward(r, g_x2, g_z, angles_deg, mc_idx, sk_idx, g_deg, mc_scale: float
     return -(2.0 * mc_scale / B) * proj_adj(r, ang_mc, N) + rotate_adj_batch(g_tot, g_deg)
 
 
+def ei_stage1_per_sample(x1, y, angles_deg, mc_rows, sk_rows, g_deg):
+    """Algorithm 1 with a sketch drawn per measurement: measurement b uses row
+    b of mc_rows / sk_rows ([B][m]; None = all angles) for its MC term and for
+    the EI term of its transformed images.  Returns (r, x2, z) stacked over
+    the measurements."""
+    x1, y = _f64(x1), _f64(y)
+    g = np.asarray(g_deg, dtype=np.float64)
+    outs = [ei_stage1(x1[b:b + 1], y[b:b + 1], angles_deg,
+                      None if mc_rows is None else mc_rows[b],
+                      None if sk_rows is None else sk_rows[b], g[b:b + 1])
+            for b in range(x1.shape[0])]
+    return tuple(np.concatenate([o[i] for o in outs]) for i in range(3))
+
+
+def ei_backward_per_sample(r, g_x2, g_z, angles_deg, mc_rows, sk_rows, g_deg,
+                           mc_scale: float):
+    """dL/dx1 for ei_stage1_per_sample.  The loss is the mean over the B
+    measurements, so measurement b's MC term carries mc_scale / B
+    (ei_backward of a single measurement applies 2 mc_scale)."""
+    r, g_x2, g_z = _f64(r), _f64(g_x2), _f64(g_z)
+    g = np.asarray(g_deg, dtype=np.float64)
+    B = r.shape[0]
+    return np.concatenate([
+        ei_backward(r[b:b + 1], g_x2[b:b + 1], g_z[b:b + 1], angles_deg,
+                    None if mc_rows is None else mc_rows[b],
+                    None if sk_rows is None else sk_rows[b], g[b:b + 1], mc_scale / B)
+        for b in range(B)])
+
+
 # --------------------------------------------------------------------------
 # stand-in network F_theta(u) = u + theta and the full test-time objective
 # --------------------------------------------------------------------------
@@ -321,6 +351,24 @@ def ttt_grad(theta, x0, y, angles_deg, mc_idx, sk_idx, g_deg, lam, mc_scale):
     loss, t = ttt_loss(theta, x0, y, angles_deg, mc_idx, sk_idx, g_deg, lam, mc_scale)
     g_x1 = ei_backward(t["r"], t["g_x2"], t["g_x3"], angles_deg, mc_idx, sk_idx,
                        g_deg, mc_scale)
+    return loss, g_x1.sum(axis=0) + t["g_x3"].sum(axis=(0, 1)), t
+
+
+def ttt_loss_per_sample(theta, x0, y, angles_deg, mc_rows, sk_rows, g_deg, lam, mc_scale):
+    """ttt_loss with a sketch per measurement (rows of mc_rows / sk_rows)."""
+    x1 = _f64(x0) + _f64(theta)[None]
+    r, x2, z = ei_stage1_per_sample(x1, y, angles_deg, mc_rows, sk_rows, g_deg)
+    x3 = z + _f64(theta)[None, None]
+    loss, mc, ei, g_x2, g_x3 = ei_finish(x2, x3, r, lam, mc_scale)
+    return loss, dict(r=r, x2=x2, z=z, x3=x3, mc=mc, ei=ei, g_x2=g_x2, g_x3=g_x3)
+
+
+def ttt_grad_per_sample(theta, x0, y, angles_deg, mc_rows, sk_rows, g_deg, lam, mc_scale):
+    """(loss, dL/dtheta) of ttt_loss_per_sample."""
+    loss, t = ttt_loss_per_sample(theta, x0, y, angles_deg, mc_rows, sk_rows, g_deg, lam,
+                                  mc_scale)
+    g_x1 = ei_backward_per_sample(t["r"], t["g_x2"], t["g_x3"], angles_deg, mc_rows, sk_rows,
+                                  g_deg, mc_scale)
     return loss, g_x1.sum(axis=0) + t["g_x3"].sum(axis=(0, 1)), t
 
 

@@ -253,10 +253,13 @@ EiWork ei_work(skei_plan p, int B, int G, int mc_m, int sk_m) {
   return w;
 }
 
+// per_sample: mc_idx and sk_idx hold one angle list per measurement,
+// [B][m] (Algorithm 1 draws a sketch per sample); the G transformed images
+// of measurement b use row b.
 template <typename T>
 int ei_fwd_impl(skei_plan p, const T *x1, const T *y, int B, const int *mc_idx, int mc_m,
                 const int *sk_idx, int sk_m, const double *g_deg, int G, T *r, T *x2, T *z,
-                char *work, cudaStream_t st) {
+                char *work, cudaStream_t st, bool per_sample = false) {
   const EiWork w = ei_work(p, B, G, mc_m, sk_m);
   float *pbuf = reinterpret_cast<float *>(work);
   float *qbuf = reinterpret_cast<float *>(work + w.p_bytes);
@@ -267,8 +270,9 @@ int ei_fwd_impl(skei_plan p, const T *x1, const T *y, int B, const int *mc_idx, 
   // one launch: r = S_mc y - A_mc x1 (MC term) and p = A_S x2 (EI term)
   Jobs J{};
   J.njobs = 2;
-  J.j[0] = Job{x1, y, r, mc_idx, mc_m, B, 1.0f, 0.0f, tb, tb, tb};
-  J.j[1] = Job{x2, nullptr, pbuf, sk_idx, sk_m, BG, 1.0f, 0.0f, tb, 0, 0};
+  const int mc_per = per_sample && mc_idx ? 1 : 0, sk_per = per_sample && sk_idx ? G : 0;
+  J.j[0] = Job{x1, y, r, mc_idx, mc_m, B, 1.0f, 0.0f, tb, tb, tb, mc_per};
+  J.j[1] = Job{x2, nullptr, pbuf, sk_idx, sk_m, BG, 1.0f, 0.0f, tb, 0, 0, sk_per};
   // the band-sums form pays on large launches (many image-angles), the
   // cluster form on small ones (measured on GB300: 8 x 256^2 x 180 angles
   // 79 vs 147 us; 5 x 512^2 x 30 angles 44 vs 37 us)
@@ -283,14 +287,18 @@ int ei_fwd_impl(skei_plan p, const T *x1, const T *y, int B, const int *mc_idx, 
   }
   if ((rc = launch_filter<float, float>(p, pbuf, BG * sk_m, (float)(kPi / sk_m), qbuf, st)))
     return rc;
-  return launch_backproject<float, T, T>(p, qbuf, BG, sk_idx, sk_m, 1.0f, 0.0f, nullptr, z, st);
+  Jobs Jz{};
+  Jz.njobs = 1;
+  Jz.j[0] = Job{qbuf, nullptr, z, sk_idx, sk_m, BG, 1.0f, 0.0f, 0, tb, tb, sk_per};
+  return launch_tile_jobs(p, OP_BACKPROJECT, Jz, st);
 }
 
 template <typename T>
 int ei_bwd_impl(skei_plan p, const T *r, const T *g_x2, const T *g_z, int B, const int *mc_idx,
                 int mc_m, const int *sk_idx, int sk_m, const double *g_deg, int G,
-                double mc_coef, T *g_x1, char *work, cudaStream_t st) {
+                double mc_coef, T *g_x1, char *work, cudaStream_t st, bool per_sample = false) {
   const EiWork w = ei_work(p, B, G, mc_m, sk_m);
+  const int mc_per = per_sample && mc_idx ? 1 : 0, sk_per = per_sample && sk_idx ? G : 0;
   float *ubuf = reinterpret_cast<float *>(work);
   float *vbuf = reinterpret_cast<float *>(work + w.p_bytes);
   float *gtot = reinterpret_cast<float *>(work + 2 * w.p_bytes);
@@ -302,7 +310,7 @@ int ei_bwd_impl(skei_plan p, const T *r, const T *g_x2, const T *g_z, int B, con
     // through z = (pi/m) B_S H A_S x2:  g_x2 + (pi/m) A_S^T H B_S^T g_z
     Jobs Jb{};
     Jb.njobs = 1;
-    Jb.j[0] = Job{g_z, nullptr, ubuf, sk_idx, sk_m, BG, 1.0f, 0.0f, tb, 0, 0};
+    Jb.j[0] = Job{g_z, nullptr, ubuf, sk_idx, sk_m, BG, 1.0f, 0.0f, tb, 0, 0, sk_per};
     if ((rc = launch_band_partial_jobs(p, OP_BP_ADJ, Jb,
                                       reinterpret_cast<float *>(work + w.band_off),
                                       w.band_floats, st)))
@@ -313,14 +321,16 @@ int ei_bwd_impl(skei_plan p, const T *r, const T *g_x2, const T *g_z, int B, con
     // gtot = g_x2 + A_S^T v (EI term)
     Jobs J{};
     J.njobs = 2;
-    J.j[0] = Job{r, nullptr, g_x1, mc_idx, mc_m, B, amc, 0.0f, tb, tb, tb};
-    J.j[1] = Job{vbuf, g_x2, gtot, sk_idx, sk_m, BG, 1.0f, g_x2 ? 1.0f : 0.0f, 0, tb, 0};
+    J.j[0] = Job{r, nullptr, g_x1, mc_idx, mc_m, B, amc, 0.0f, tb, tb, tb, mc_per};
+    J.j[1] = Job{vbuf, g_x2, gtot, sk_idx, sk_m, BG, 1.0f, g_x2 ? 1.0f : 0.0f, 0, tb, 0, sk_per};
     if ((rc = launch_tile_jobs(p, OP_JOSEPH_ADJ, J, st))) return rc;
     return launch_rotate_adj<float, T>(gtot, B, p->N, g_deg, G, 1.0f, 1.0f, g_x1, st);
   }
   // MC term: g_x1 = -2 mc_coef A_mc^T r
-  if ((rc = launch_proj_adj<T, T, T>(p, r, B, mc_idx, mc_m, amc, 0.0f, nullptr, g_x1, st)))
-    return rc;
+  Jobs Jm{};
+  Jm.njobs = 1;
+  Jm.j[0] = Job{r, nullptr, g_x1, mc_idx, mc_m, B, amc, 0.0f, tb, tb, tb, mc_per};
+  if ((rc = launch_tile_jobs(p, OP_JOSEPH_ADJ, Jm, st))) return rc;
   if (g_x2) return launch_rotate_adj<T, T>(g_x2, B, p->N, g_deg, G, 1.0f, 1.0f, g_x1, st);
   return SKEI_OK;
 }
@@ -589,10 +599,10 @@ size_t skei_ei_workspace_size(skei_plan plan, int dtype, int B, int G, int mc_m,
   return ei_work(plan, B, G, mc_m, sk_m).total;
 }
 
-int skei_ei_loss_fwd(skei_plan plan, int dtype, const void *x1, const void *y, int B,
-                     const int *mc_idx, int mc_m, const int *sk_idx, int sk_m,
-                     const double *g_deg, int G, void *r, void *x2, void *z, void *work,
-                     size_t work_bytes, void *stream) {
+static int ei_fwd_entry(skei_plan plan, int dtype, const void *x1, const void *y, int B,
+                        const int *mc_idx, int mc_m, const int *sk_idx, int sk_m,
+                        const double *g_deg, int G, void *r, void *x2, void *z, void *work,
+                        size_t work_bytes, void *stream, bool per_sample) {
   SKEI_TRY(check_common(plan, dtype, B));
   SKEI_TRY(check_rot(dtype, B, plan->N, g_deg, G));
   SKEI_TRY(check_dev_ptr(x1, "x1"));
@@ -606,10 +616,26 @@ int skei_ei_loss_fwd(skei_plan plan, int dtype, const void *x1, const void *y, i
   if (dtype == SKEI_F32)
     return ei_fwd_impl<float>(plan, (const float *)x1, (const float *)y, B, mc_idx, mc_m, sk_idx,
                               sk_m, g_deg, G, (float *)r, (float *)x2, (float *)z, (char *)work,
-                              as_stream(stream));
+                              as_stream(stream), per_sample);
   return ei_fwd_impl<bf16>(plan, (const bf16 *)x1, (const bf16 *)y, B, mc_idx, mc_m, sk_idx, sk_m,
                            g_deg, G, (bf16 *)r, (bf16 *)x2, (bf16 *)z, (char *)work,
-                           as_stream(stream));
+                           as_stream(stream), per_sample);
+}
+
+int skei_ei_loss_fwd(skei_plan plan, int dtype, const void *x1, const void *y, int B,
+                     const int *mc_idx, int mc_m, const int *sk_idx, int sk_m,
+                     const double *g_deg, int G, void *r, void *x2, void *z, void *work,
+                     size_t work_bytes, void *stream) {
+  return ei_fwd_entry(plan, dtype, x1, y, B, mc_idx, mc_m, sk_idx, sk_m, g_deg, G, r, x2, z,
+                      work, work_bytes, stream, false);
+}
+
+int skei_ei_loss_fwd_per_sample(skei_plan plan, int dtype, const void *x1, const void *y, int B,
+                                const int *mc_idx, int mc_m, const int *sk_idx, int sk_m,
+                                const double *g_deg, int G, void *r, void *x2, void *z,
+                                void *work, size_t work_bytes, void *stream) {
+  return ei_fwd_entry(plan, dtype, x1, y, B, mc_idx, mc_m, sk_idx, sk_m, g_deg, G, r, x2, z,
+                      work, work_bytes, stream, true);
 }
 
 size_t skei_ei_finish_workspace_size(int B, int G, int N, int r_len) {
@@ -645,10 +671,10 @@ int skei_ei_loss_finish(int dtype, const void *x2, const void *x3, const void *r
                               (bf16 *)g_x3, (char *)work, as_stream(stream));
 }
 
-int skei_ei_loss_bwd(skei_plan plan, int dtype, const void *r, const void *g_x2, const void *g_z,
-                     int B, const int *mc_idx, int mc_m, const int *sk_idx, int sk_m,
-                     const double *g_deg, int G, double mc_coef, void *g_x1, void *work,
-                     size_t work_bytes, void *stream) {
+static int ei_bwd_entry(skei_plan plan, int dtype, const void *r, const void *g_x2,
+                        const void *g_z, int B, const int *mc_idx, int mc_m, const int *sk_idx,
+                        int sk_m, const double *g_deg, int G, double mc_coef, void *g_x1,
+                        void *work, size_t work_bytes, void *stream, bool per_sample) {
   SKEI_TRY(check_common(plan, dtype, B));
   SKEI_TRY(check_rot(dtype, B, plan->N, g_deg, G));
   SKEI_TRY(check_dev_ptr(r, "r"));
@@ -661,10 +687,27 @@ int skei_ei_loss_bwd(skei_plan plan, int dtype, const void *r, const void *g_x2,
   if (dtype == SKEI_F32)
     return ei_bwd_impl<float>(plan, (const float *)r, (const float *)g_x2, (const float *)g_z, B,
                               mc_idx, mc_m, sk_idx, sk_m, g_deg, G, mc_coef, (float *)g_x1,
-                              (char *)work, as_stream(stream));
+                              (char *)work, as_stream(stream), per_sample);
   return ei_bwd_impl<bf16>(plan, (const bf16 *)r, (const bf16 *)g_x2, (const bf16 *)g_z, B, mc_idx,
                            mc_m, sk_idx, sk_m, g_deg, G, mc_coef, (bf16 *)g_x1, (char *)work,
-                           as_stream(stream));
+                           as_stream(stream), per_sample);
+}
+
+int skei_ei_loss_bwd(skei_plan plan, int dtype, const void *r, const void *g_x2, const void *g_z,
+                     int B, const int *mc_idx, int mc_m, const int *sk_idx, int sk_m,
+                     const double *g_deg, int G, double mc_coef, void *g_x1, void *work,
+                     size_t work_bytes, void *stream) {
+  return ei_bwd_entry(plan, dtype, r, g_x2, g_z, B, mc_idx, mc_m, sk_idx, sk_m, g_deg, G,
+                      mc_coef, g_x1, work, work_bytes, stream, false);
+}
+
+int skei_ei_loss_bwd_per_sample(skei_plan plan, int dtype, const void *r, const void *g_x2,
+                                const void *g_z, int B, const int *mc_idx, int mc_m,
+                                const int *sk_idx, int sk_m, const double *g_deg, int G,
+                                double mc_coef, void *g_x1, void *work, size_t work_bytes,
+                                void *stream) {
+  return ei_bwd_entry(plan, dtype, r, g_x2, g_z, B, mc_idx, mc_m, sk_idx, sk_m, g_deg, G,
+                      mc_coef, g_x1, work, work_bytes, stream, true);
 }
 
 int skei_residual_add(int dtype, const void *u, const float *theta, int count, int64_t n,

@@ -450,8 +450,9 @@ __device__ __forceinline__ void band_task(const Job &J, int b0, int a_begin, con
 
   if (tid < kMaxAB) {
     int ai = -1;
+    const int *idx = job_idx(J, b0);
     if (tid < na) {
-      ai = J.idx ? J.idx[a_begin + tid] : a_begin + tid;
+      ai = idx ? idx[a_begin + tid] : a_begin + tid;
       if (ai < 0 || ai >= g.n_angles) {
         if (band == 0) atomicOr(status, 1);
         ai = -1;
@@ -708,7 +709,7 @@ int launch_band(skei_plan p, const Jobs &jobs, cudaStream_t st) {
   // groups of 4 pay only when, with one angle per cluster, they still leave
   // a cluster task for every concurrent cluster slot: otherwise the launch
   // runs single images
-  int gm = group_max(OP), tasks = 0, slots = 1;
+  int gm = jobs_groupable(jobs) ? group_max(OP) : 1, tasks = 0, slots = 1;
   if (gm == 4) {
     int t1 = 0;
     for (int q = 0; q < jobs.njobs; ++q) t1 += n_groups(jobs.j[q].nimg, 4) * jobs.j[q].m;
@@ -834,7 +835,7 @@ struct PartArgs {
   const AngleConst *ang;
   int *status;
   BandGeom g1, g4;
-  int gmax;          // image group size of this launch (1 or 4)
+  int gmax[kMaxJobs];   // image group size of each job (1 or 4)
   int AB;            // angles per CTA
   int nbands;        // ceil(N / SBL); both group sizes use SBL of their own
   float *part;       // workspace
@@ -853,8 +854,9 @@ __device__ __forceinline__ void partial_task(const Job &J, float *part, int b0, 
   if (na <= 0 || s0 >= N) return;  // uniform over the CTA
   if (tid < kMaxABP) {
     int ai = -1;
+    const int *idx = job_idx(J, b0);
     if (tid < na) {
-      ai = J.idx ? J.idx[a_begin + tid] : a_begin + tid;
+      ai = idx ? idx[a_begin + tid] : a_begin + tid;
       if (ai < 0 || ai >= g.n_angles) {
         if (band == 0) atomicOr(status, 1);
         ai = -1;
@@ -911,12 +913,12 @@ __global__ void __launch_bounds__(kThreads, NI == 4 ? SKEI_PART_MINB4 : SKEI_PAR
   __shared__ int sai[kMaxABP];
   const int z = blockIdx.z;
   const Job &J0 = args.jobs.j[0];
-  const int q0 = quads(J0.nimg, args.gmax);
+  const int q0 = quads(J0.nimg, args.gmax[0]);
   const int c0 = NI == 4 ? q0 : J0.nimg - 4 * q0;
   const int jn = (args.jobs.njobs > 1 && z >= c0) ? 1 : 0;
   const Job &J = args.jobs.j[jn];
   const int zz = z - (jn ? c0 : 0);
-  const int b0 = NI == 4 ? 4 * zz : 4 * quads(J.nimg, args.gmax) + zz;
+  const int b0 = NI == 4 ? 4 * zz : 4 * quads(J.nimg, args.gmax[jn]) + zz;
   partial_task<OP, NI>(J, args.part + args.off[jn], b0, blockIdx.x, blockIdx.y * args.AB,
                        args.AB, args.nbands, NI == 4 ? args.g4 : args.g1, args.ang, args.status,
                        reinterpret_cast<float *>(smem4), sc, sai);
@@ -947,7 +949,8 @@ __global__ void __launch_bounds__(256)
     }
     for (; q < nbands; ++q) s += __ldg(pb + (size_t)q * n + e);
     const int a = e / nd, k = e - a * nd;
-    int ai = J.idx ? J.idx[a] : a;
+    const int *idx = job_idx(J, b);
+    int ai = idx ? idx[a] : a;
     float v;
     if (ai < 0 || ai >= n_angles) {
       v = 0.0f;
@@ -999,10 +1002,14 @@ int set_partial_smem(size_t smem) {
 template <int OP>
 int launch_band_partial(skei_plan p, const Jobs &jobs, float *work, size_t work_floats,
                         cudaStream_t st) {
-  int gm = SKEI_PART_GROUP;
+  // groups of 4 per job, where its images' angle lists allow them; the
+  // workspace layout is the one band_partial_floats sizes
+  int gmj[kMaxJobs] = {1, 1};
+  for (int q = 0; q < jobs.njobs; ++q)
+    gmj[q] = SKEI_PART_GROUP == 4 && job_groupable(jobs.j[q]) ? 4 : 1;
   int nb1 = 0, nb4 = 0;
   size_t off[kMaxJobs] = {0, 0}, need = 0;
-  part_layout(p, jobs, &nb1, &nb4, off, &need, gm);
+  part_layout(p, jobs, &nb1, &nb4, off, &need, SKEI_PART_GROUP);
   if (need > work_floats)
     return set_error(SKEI_EINVAL, "band sums need %zu floats of workspace, %zu given", need,
                      work_floats);
@@ -1013,7 +1020,7 @@ int launch_band_partial(skei_plan p, const Jobs &jobs, float *work, size_t work_
   const BandGeom g4 = part_geom(p->N, p->n_det, p->n_angles, 4);
   int nbands = nb1;
   bool any4 = false;
-  for (int q = 0; q < jobs.njobs; ++q) any4 |= gm == 4 && jobs.j[q].nimg >= 4;
+  for (int q = 0; q < jobs.njobs; ++q) any4 |= gmj[q] == 4 && jobs.j[q].nimg >= 4;
   if (any4) {
     g1 = part_geom(p->N, p->n_det, p->n_angles, 1, g4.SB);
     nbands = nb4;
@@ -1021,8 +1028,8 @@ int launch_band_partial(skei_plan p, const Jobs &jobs, float *work, size_t work_
   int m_max = 0, ngroups = 0, n4 = 0, n1 = 0;
   for (int q = 0; q < jobs.njobs; ++q) {
     m_max = max(m_max, jobs.j[q].m);
-    ngroups += n_groups(jobs.j[q].nimg, gm);
-    const int q4 = gm == 4 ? jobs.j[q].nimg >> 2 : 0;
+    ngroups += n_groups(jobs.j[q].nimg, gmj[q]);
+    const int q4 = gmj[q] == 4 ? jobs.j[q].nimg >> 2 : 0;
     n4 += q4;
     n1 += jobs.j[q].nimg - 4 * q4;
   }
@@ -1034,7 +1041,8 @@ int launch_band_partial(skei_plan p, const Jobs &jobs, float *work, size_t work_
   int AB = (int)((m_max + blocks - 1) / blocks);
   AB = std::max(1, std::min(AB, kMaxABP));
   const int nblk = (m_max + AB - 1) / AB;
-  PartArgs a{jobs, p->d_ang, p->d_status, g1, g4, gm, AB, nbands, work, {off[0], off[1]}};
+  PartArgs a{jobs, p->d_ang, p->d_status, g1, g4, {gmj[0], gmj[1]}, AB, nbands, work,
+             {off[0], off[1]}};
   if (n4 > 0) {
     SKEI_TRY((set_partial_smem<OP, 4>(part_smem(g4))));
     launch_k(band_partial_kernel<OP, 4>, dim3(nbands, nblk, n4), dim3(kThreads), part_smem(g4),

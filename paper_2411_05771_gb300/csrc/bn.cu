@@ -5,8 +5,10 @@
 //   out = act(scale_c (v - mean_c) / sqrt(var_c + eps) + shift_c),
 // act = ReLU or the identity; the backward returns dL/dv, dL/dscale and
 // dL/dshift.  Two launches each way: per-chunk partial sums (FP32 within a
-// thread, FP64 across threads and chunks, fixed order), then the
+// thread and warp, FP64 across warps and chunks, fixed order), then the
 // elementwise pass, whose CTAs each finish their channel's sums.
+#include <type_traits>
+
 #include "common.cuh"
 
 using bf16 = __nv_bfloat16;
@@ -15,7 +17,7 @@ namespace skei {
 namespace {
 
 constexpr int kBnThreads = 256;
-constexpr int kBnChunk = 4096;   // values of one (b, c) plane per CTA
+constexpr int kBnChunk = 16384;  // values of one (b, c) plane per CTA
 constexpr int kBnPer = kBnChunk / kBnThreads;
 
 // Values e0 + 4 t + 4 kBnThreads j (j < kBnPer / 4) of a plane, or the
@@ -25,7 +27,7 @@ __device__ __forceinline__ void chunk_each(const T *pl, long long e0, long long 
                                            Fn f) {
   const int t = threadIdx.x;
   if (vec) {
-#pragma unroll
+#pragma unroll 4
     for (int j = 0; j < kBnPer / 4; ++j) {
       const long long e = e0 + 4LL * (t + j * kBnThreads);
       if (e < e1) {
@@ -45,11 +47,31 @@ __device__ __forceinline__ void chunk_each(const T *pl, long long e0, long long 
   }
 }
 
-// Sum over the CTA of two FP32 per-thread values, in FP64 and a fixed order;
-// the result is valid in thread 0.
+// The FP32 fast path (HW % 4 == 0, 16-byte aligned planes): thread t takes
+// the float4 groups e0 + 4 t + 4 kBnThreads j of the chunk;
+// f(e, v4, g4) for each, with g4 the same group of a second plane (or 0).
+template <typename Fn>
+__device__ __forceinline__ void chunk_each4(const float *pv, const float *pg, long long e0,
+                                            long long e1, Fn f) {
+  const int t = threadIdx.x;
+#pragma unroll 4
+  for (int j = 0; j < kBnPer / 4; ++j) {
+    const long long e = e0 + 4LL * (t + j * kBnThreads);
+    if (e < e1) {
+      const float4 x = __ldg(reinterpret_cast<const float4 *>(pv + e));
+      const float4 g = pg ? __ldg(reinterpret_cast<const float4 *>(pg + e))
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+      f(e, x, g);
+    }
+  }
+}
+
+// Sum over the CTA of two FP32 per-thread values in a fixed order: FP32
+// within a warp (FP64 arithmetic is scarce on this GPU), FP64 across the
+// warps; the result is valid in thread 0.
 __device__ __forceinline__ double2 cta_sum2(float a, float b) {
   __shared__ double2 red[kBnThreads / 32];
-  double x = a, y = b;
+  float x = a, y = b;
   for (int o = 16; o > 0; o >>= 1) {
     x += __shfl_xor_sync(0xffffffffu, x, o);
     y += __shfl_xor_sync(0xffffffffu, y, o);
@@ -141,11 +163,19 @@ __global__ void __launch_bounds__(kBnThreads)
   const size_t o = ((size_t)b * C + c) * HW;
   const long long e0 = (long long)q * kBnChunk, e1 = min(HW, e0 + kBnChunk);
   T *po = out + o;
-  chunk_each(v + o, e0, e1, vec, [&](long long e, float x) {
-    float y = fmaf(x, a, bb);
-    if (relu) y = fmaxf(y, 0.0f);
-    st_f(po + e, y);
-  });
+  auto act = [&](float x) {
+    const float y = fmaf(x, a, bb);
+    return relu ? fmaxf(y, 0.0f) : y;
+  };
+  if constexpr (std::is_same<T, float>::value) {
+    if (vec) {
+      chunk_each4(v + o, nullptr, e0, e1, [&](long long e, float4 x, float4) {
+        *reinterpret_cast<float4 *>(po + e) = make_float4(act(x.x), act(x.y), act(x.z), act(x.w));
+      });
+      return;
+    }
+  }
+  chunk_each(v + o, e0, e1, false, [&](long long e, float x) { st_f(po + e, act(x)); });
 }
 
 // Backward partials: gy = g where the activation passes (y > 0 for ReLU),
@@ -164,12 +194,24 @@ __global__ void __launch_bounds__(kBnThreads)
   affine_of(__ldg(scale + c), __ldg(shift + c), mu, rs, &a, &bb);
   const T *pg = g + o;
   float s = 0.0f, sx = 0.0f;
-  chunk_each(v + o, e0, e1, vec, [&](long long e, float x) {
-    float gy = ldg_f(pg + e);
+  auto acc = [&](float x, float gy) {
     if (relu && !(fmaf(x, a, bb) > 0.0f)) gy = 0.0f;
     s += gy;
     sx = fmaf(gy, (x - mu) * rs, sx);
-  });
+  };
+  bool done = false;
+  if constexpr (std::is_same<T, float>::value) {
+    if (vec) {
+      chunk_each4(v + o, pg, e0, e1, [&](long long, float4 x, float4 gg) {
+        acc(x.x, gg.x);
+        acc(x.y, gg.y);
+        acc(x.z, gg.z);
+        acc(x.w, gg.w);
+      });
+      done = true;
+    }
+  }
+  if (!done) chunk_each(v + o, e0, e1, false, [&](long long e, float x) { acc(x, ldg_f(pg + e)); });
   const double2 r = cta_sum2(s, sx);
   if (threadIdx.x == 0) part[(size_t)c * gridDim.x + blockIdx.x] = r;
 }
@@ -206,11 +248,20 @@ __global__ void __launch_bounds__(kBnThreads)
   const long long e0 = (long long)q * kBnChunk, e1 = min(HW, e0 + kBnChunk);
   const T *pg = g + o;
   T *pv = gv + o;
-  chunk_each(v + o, e0, e1, vec, [&](long long e, float x) {
-    float gy = ldg_f(pg + e);
+  auto grad = [&](float x, float gy) {
     if (relu && !(fmaf(x, a, bb) > 0.0f)) gy = 0.0f;
-    st_f(pv + e, a * (gy - k1 - (x - mu) * rs * k2));
-  });
+    return a * (gy - k1 - (x - mu) * rs * k2);
+  };
+  if constexpr (std::is_same<T, float>::value) {
+    if (vec) {
+      chunk_each4(v + o, pg, e0, e1, [&](long long e, float4 x, float4 gg) {
+        *reinterpret_cast<float4 *>(pv + e) =
+            make_float4(grad(x.x, gg.x), grad(x.y, gg.y), grad(x.z, gg.z), grad(x.w, gg.w));
+      });
+      return;
+    }
+  }
+  chunk_each(v + o, e0, e1, false, [&](long long e, float x) { st_f(pv + e, grad(x, ldg_f(pg + e))); });
 }
 
 struct BnGrid {
@@ -266,7 +317,7 @@ int skei_bn_act_fwd(int dtype, const void *v, int B, int C, int64_t HW, const fl
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   double2 *part = static_cast<double2 *>(work);
   const bool vec = dtype == SKEI_F32 && HW % 4 == 0 &&
-                   (reinterpret_cast<uintptr_t>(v) & 15) == 0;
+                   ((reinterpret_cast<uintptr_t>(v) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
   if (dtype == SKEI_F32) {
     launch_k(bn_stats_kernel<float>, g.grid, dim3(kBnThreads), 0, st, (const float *)v, C,
              (long long)HW, g.nch, vec, part);
@@ -310,7 +361,8 @@ int skei_bn_act_bwd(int dtype, const void *v, const void *g_out, int B, int C, i
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   double2 *part = static_cast<double2 *>(work);
   const bool vec = dtype == SKEI_F32 && HW % 4 == 0 &&
-                   (reinterpret_cast<uintptr_t>(v) & 15) == 0;
+                   ((reinterpret_cast<uintptr_t>(v) | reinterpret_cast<uintptr_t>(g_out) |
+                     reinterpret_cast<uintptr_t>(g_v)) & 15) == 0;
   if (dtype == SKEI_F32) {
     launch_k(bn_bwd_stats_kernel<float>, g.grid, dim3(kBnThreads), 0, st, (const float *)v,
              (const float *)g_out, C, (long long)HW, g.nch, vec, scale, shift, mean, rstd, relu,

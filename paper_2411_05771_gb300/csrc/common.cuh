@@ -245,6 +245,9 @@ struct Job {
   int m, nimg;
   float alpha, beta;
   int in_bf16, aux_bf16, out_bf16;
+  // > 0: idx holds one list per sample, [rows][m], and images
+  // r idx_per .. (r+1) idx_per - 1 use row r (a sketch per sample, Algorithm 1)
+  int idx_per = 0;
 };
 constexpr int kMaxJobs = 2;
 struct Jobs {
@@ -253,6 +256,20 @@ struct Jobs {
 };
 
 enum { OP_JOSEPH = 0, OP_BP_ADJ = 1, OP_JOSEPH_ADJ = 2, OP_BACKPROJECT = 3 };
+
+// The angle list of image b of job J (NULL: all angles).
+__host__ __device__ __forceinline__ const int *job_idx(const Job &J, int b) {
+  return (J.idx && J.idx_per > 0) ? J.idx + (size_t)(b / J.idx_per) * J.m : J.idx;
+}
+// Whether groups of 4 consecutive images of J share one angle list.
+__host__ __device__ __forceinline__ bool job_groupable(const Job &J) {
+  return !J.idx || J.idx_per <= 0 || J.idx_per % 4 == 0;
+}
+inline bool jobs_groupable(const Jobs &J) {
+  for (int q = 0; q < J.njobs; ++q)
+    if (!job_groupable(J.j[q])) return false;
+  return true;
+}
 
 // Image groups.  The images of one job share its angle list, so the
 // operator kernels compute positions and weights once per group of 4 images

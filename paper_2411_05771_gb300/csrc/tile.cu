@@ -62,6 +62,8 @@ struct TileArgs {
   const AngleConst *ang;
   int *status;
   int merge;   // job 0's image b rides with job 1's group 4b .. 4b+3 (same angles)
+  int gmax[kMaxJobs];   // image group size per job (4, or 1 where groups would
+                        // straddle the per-sample angle lists)
 };
 
 // Shared memory of a tile task (dynamic: above the 48 KB of static shared
@@ -82,13 +84,14 @@ constexpr size_t kTileSmem = sizeof(TileSmem);
 // `slot`: angle index (or -1 if out of range, reported), its AngleConst and
 // the first bin of the window the tile projects onto.  Threads 0 .. nac-1.
 template <int OP>
-__device__ __forceinline__ void tile_setup(const Job &J, int c0, int nac, int i0, int j0,
+__device__ __forceinline__ void tile_setup(const Job &J, int b0, int c0, int nac, int i0, int j0,
                                            int i_last, int j_last, int n_angles,
                                            const AngleConst *ang, int *status, bool report,
                                            TileSmem &sm, int slot) {
   const int tid = threadIdx.x;
   if (tid >= nac) return;
-  int ai = J.idx ? J.idx[c0 + tid] : c0 + tid;
+  const int *idx = job_idx(J, b0);
+  int ai = idx ? idx[c0 + tid] : c0 + tid;
   if (ai < 0 || ai >= n_angles) {
     if (report) atomicOr(status, 1);
     ai = -1;
@@ -172,11 +175,11 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
   for (int q = 0; q < kPPT; ++q) accx[q] = 0.0f;
 
   const int nch = (J.m + kAC - 1) / kAC;
-  tile_setup<OP>(J, 0, min(kAC, J.m), i0, j0, i_last, j_last, n_angles, ang, status, report,
+  tile_setup<OP>(J, b0, 0, min(kAC, J.m), i0, j0, i_last, j_last, n_angles, ang, status, report,
                  sm, 0);
   if (nch > 1)
-    tile_setup<OP>(J, kAC, min(kAC, J.m - kAC), i0, j0, i_last, j_last, n_angles, ang, status,
-                   report, sm, 1);
+    tile_setup<OP>(J, b0, kAC, min(kAC, J.m - kAC), i0, j0, i_last, j_last, n_angles, ang,
+                   status, report, sm, 1);
   __syncthreads();
   tile_window<NI, XTRA>(J, b0, 0, min(kAC, J.m), nd, sm, 0, 0, JX, bx);
 
@@ -188,7 +191,7 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
       tile_window<NI, XTRA>(J, b0, c0 + kAC, min(kAC, J.m - c0 - kAC), nd, sm, (c + 1) % 3,
                             (c + 1) & 1, JX, bx);
     if (c + 2 < nch)
-      tile_setup<OP>(J, c0 + 2 * kAC, min(kAC, J.m - c0 - 2 * kAC), i0, j0, i_last, j_last,
+      tile_setup<OP>(J, b0, c0 + 2 * kAC, min(kAC, J.m - c0 - 2 * kAC), i0, j0, i_last, j_last,
                      n_angles, ang, status, report, sm, (c + 2) % 3);
 
     for (int a = half; a < nac; a += kSplit) {
@@ -332,11 +335,11 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs args) {
                            &args.jobs.j[0], z);
     return;
   }
-  const int g0 = n_groups(args.jobs.j[0].nimg);
+  const int g0 = n_groups(args.jobs.j[0].nimg, args.gmax[0]);
   const int jn = (args.jobs.njobs > 1 && z >= g0) ? 1 : 0;
   const Job &J = args.jobs.j[jn];
   int b0, ni;
-  group_at(J.nimg, z - (jn ? g0 : 0), &b0, &ni);
+  group_at(J.nimg, z - (jn ? g0 : 0), &b0, &ni, args.gmax[jn]);
   if (ni == 4)
     tile_task<OP, 4>(J, b0, blockIdx.y * kTH, blockIdx.x * kTW, args.N, args.n_det,
                      args.n_angles, args.ang, args.status, report, sm);
@@ -409,15 +412,25 @@ int set_tile_batch_smem() {
 
 template <int OP>
 int launch_tile(skei_plan p, const Jobs &jobs, cudaStream_t st) {
+  int gmax[kMaxJobs] = {4, 4};
   int ngroups = 0;
-  for (int q = 0; q < jobs.njobs; ++q) ngroups += n_groups(jobs.j[q].nimg);
-  // two jobs over the same angle list with 4 images of job 1 per image of
-  // job 0 (the MC and EI terms of a step, G = 4): one CTA carries both
-  const int merge = jobs.njobs == 2 && jobs.j[0].idx == jobs.j[1].idx &&
-                    jobs.j[0].m == jobs.j[1].m && jobs.j[1].nimg == 4 * jobs.j[0].nimg;
+  for (int q = 0; q < jobs.njobs; ++q) {
+    gmax[q] = job_groupable(jobs.j[q]) ? 4 : 1;
+    ngroups += n_groups(jobs.j[q].nimg, gmax[q]);
+  }
+  // two jobs over the same angle lists with 4 images of job 1 per image of
+  // job 0 (the MC and EI terms of a step, G = 4): one CTA carries both;
+  // with a list per sample, image b of job 0 and images 4b .. 4b+3 of job 1
+  // must read the same row
+  const Job &j0 = jobs.j[0], &j1 = jobs.j[1];
+  const int merge = jobs.njobs == 2 && gmax[1] == 4 && j0.idx == j1.idx && j0.m == j1.m &&
+                    j1.nimg == 4 * j0.nimg &&
+                    ((j0.idx_per <= 0 && j1.idx_per <= 0) ||
+                     (j0.idx_per > 0 && j1.idx_per == 4 * j0.idx_per));
   if (merge) ngroups = jobs.j[0].nimg;
   if (ngroups > 65535) return set_error(SKEI_EINVAL, "too many images in one launch");
-  TileArgs a{jobs, p->N, p->n_det, p->n_angles, p->d_ang, p->d_status, merge};
+  TileArgs a{jobs, p->N, p->n_det, p->n_angles, p->d_ang, p->d_status, merge,
+             {gmax[0], gmax[1]}};
   dim3 grid((p->N + kTW - 1) / kTW, (p->N + kTH - 1) / kTH, ngroups);
   SKEI_TRY(set_tile_kernel_smem<OP>());
   launch_k(tile_kernel<OP>, grid, dim3(kThreads), kTileSmem, st, a);

@@ -23,6 +23,7 @@ __all__ = [
     "filter", "backproject", "backproject_adj",
     "fbp_workspace_size", "fbp", "fbp_adj", "fbp_noalloc", "rotate", "rotate_adj",
     "ei_workspace_size", "ei_loss_fwd", "ei_loss_finish", "ei_loss_bwd",
+    "ei_loss_fwd_per_sample", "ei_loss_bwd_per_sample",
     "residual_add", "adam_step", "library_path",
     "bn_workspace_size", "bn_act_fwd", "bn_act_bwd",
     "Batch", "BatchItem", "PROJ_FWD", "PROJ_ADJ", "BACKPROJECT", "BACKPROJECT_ADJ", "FILTER",
@@ -90,6 +91,10 @@ _SIGS = {
                              _vp, _vp, _sz, _vp], _i),
     "skei_ei_loss_bwd": ([_PLAN, _i, _vp, _vp, _vp, _i, _vp, _i, _vp, _i, _vp, _i, _d, _vp,
                           _vp, _sz, _vp], _i),
+    "skei_ei_loss_fwd_per_sample": ([_PLAN, _i, _vp, _vp, _i, _vp, _i, _vp, _i, _vp, _i, _vp, _vp,
+                                     _vp, _vp, _sz, _vp], _i),
+    "skei_ei_loss_bwd_per_sample": ([_PLAN, _i, _vp, _vp, _vp, _i, _vp, _i, _vp, _i, _vp, _i, _d,
+                                     _vp, _vp, _sz, _vp], _i),
     "skei_residual_add": ([_i, _vp, _vp, _i, _i64, _vp, _vp], _i),
     "skei_adam_step": ([_vp, _i64, _i, _vp, _i, _vp, _i, _vp, _vp, _vp, _d, _d, _d, _d, _vp], _i),
     "skei_bn_workspace_size": ([_i, _i, _i64], _sz),
@@ -435,11 +440,21 @@ def ei_workspace_size(plan: Plan, dtype: int, B: int, G: int, mc_m: int, sk_m: i
     return int(_lib.skei_ei_workspace_size(plan.handle, dtype, B, G, mc_m, sk_m))
 
 
-def ei_loss_fwd(plan: Plan, x1, y, g_deg, mc_idx=None, sk_idx=None, work=None, out=None):
-    """Stage 1 of the (sketched) EI loss.  Returns (r, x2, z)."""
+def _idx_rows(plan: Plan, idx, B: int, per_sample: bool):
+    if not per_sample:
+        return _idx(plan, idx)
+    if idx is None:
+        return None, plan.n_angles
+    _dev(idx, "idx", torch.int32)
+    if idx.dim() != 2 or idx.shape[0] != B:
+        raise ValueError(f"per-sample idx must be [B={B}, m], got {tuple(idx.shape)}")
+    return ctypes.c_void_p(idx.data_ptr()), int(idx.shape[1])
+
+
+def _ei_fwd(plan, x1, y, g_deg, mc_idx, sk_idx, work, out, per_sample):
     B, G = x1.shape[0], g_deg.shape[1]
-    mp, mc_m = _idx(plan, mc_idx)
-    sp, sk_m = _idx(plan, sk_idx)
+    mp, mc_m = _idx_rows(plan, mc_idx, B, per_sample)
+    sp, sk_m = _idx_rows(plan, sk_idx, B, per_sample)
     N, nd = plan.N, plan.n_det
     _dev(x1, "x1", shape=(B, N, N))
     _dev(y, "y", x1.dtype, (B, plan.n_angles, nd))
@@ -455,10 +470,22 @@ def ei_loss_fwd(plan: Plan, x1, y, g_deg, mc_idx=None, sk_idx=None, work=None, o
     code = _dtype_code(x1)
     nb = ei_workspace_size(plan, code, B, G, mc_m, sk_m)
     w = _work(nb, x1.device, work)
-    _check(_lib.skei_ei_loss_fwd(plan.handle, code, _ptr(x1), _ptr(y), B, mp, mc_m, sp, sk_m,
-                                 _ptr(g_deg), G, _ptr(r), _ptr(x2), _ptr(z), _ptr(w), nb,
-                                 _stream()), "skei_ei_loss_fwd")
+    fn = _lib.skei_ei_loss_fwd_per_sample if per_sample else _lib.skei_ei_loss_fwd
+    _check(fn(plan.handle, code, _ptr(x1), _ptr(y), B, mp, mc_m, sp, sk_m, _ptr(g_deg), G,
+              _ptr(r), _ptr(x2), _ptr(z), _ptr(w), nb, _stream()),
+           "skei_ei_loss_fwd_per_sample" if per_sample else "skei_ei_loss_fwd")
     return r, x2, z
+
+
+def ei_loss_fwd(plan: Plan, x1, y, g_deg, mc_idx=None, sk_idx=None, work=None, out=None):
+    """Stage 1 of the (sketched) EI loss.  Returns (r, x2, z)."""
+    return _ei_fwd(plan, x1, y, g_deg, mc_idx, sk_idx, work, out, False)
+
+
+def ei_loss_fwd_per_sample(plan: Plan, x1, y, g_deg, mc_idx=None, sk_idx=None, work=None,
+                           out=None):
+    """Stage 1 with an angle list per measurement: mc_idx, sk_idx int32 [B, m]."""
+    return _ei_fwd(plan, x1, y, g_deg, mc_idx, sk_idx, work, out, True)
 
 
 def ei_loss_finish(x2, x3, r, lam: float, mc_scale: float, want_grads=True, work=None,
@@ -486,12 +513,10 @@ def ei_loss_finish(x2, x3, r, lam: float, mc_scale: float, want_grads=True, work
     return loss, mc, ei, g_x2, g_x3
 
 
-def ei_loss_bwd(plan: Plan, r, g_x2, g_z, g_deg, mc_coef: float, mc_idx=None, sk_idx=None,
-                work=None, out=None):
-    """g_x1 = -2 mc_coef A_mc^T r + sum_g T_g^T [g_x2 + (pi/m) A_S^T H B_S^T g_z]."""
+def _ei_bwd(plan, r, g_x2, g_z, g_deg, mc_coef, mc_idx, sk_idx, work, out, per_sample):
     B, G = g_deg.shape
-    mp, mc_m = _idx(plan, mc_idx)
-    sp, sk_m = _idx(plan, sk_idx)
+    mp, mc_m = _idx_rows(plan, mc_idx, B, per_sample)
+    sp, sk_m = _idx_rows(plan, sk_idx, B, per_sample)
     N, nd = plan.N, plan.n_det
     _dev(r, "r", shape=(B, mc_m, nd))
     _dev(g_x2, "g_x2", r.dtype, (B, G, N, N))
@@ -502,10 +527,23 @@ def ei_loss_bwd(plan: Plan, r, g_x2, g_z, g_deg, mc_coef: float, mc_idx=None, sk
     code = _dtype_code(r)
     nb = ei_workspace_size(plan, code, B, G, mc_m, sk_m)
     w = _work(nb, r.device, work)
-    _check(_lib.skei_ei_loss_bwd(plan.handle, code, _ptr(r), _ptr(g_x2), _ptr(g_z), B, mp, mc_m,
-                                 sp, sk_m, _ptr(g_deg), G, float(mc_coef), _ptr(out), _ptr(w), nb,
-                                 _stream()), "skei_ei_loss_bwd")
+    fn = _lib.skei_ei_loss_bwd_per_sample if per_sample else _lib.skei_ei_loss_bwd
+    _check(fn(plan.handle, code, _ptr(r), _ptr(g_x2), _ptr(g_z), B, mp, mc_m, sp, sk_m,
+              _ptr(g_deg), G, float(mc_coef), _ptr(out), _ptr(w), nb, _stream()),
+           "skei_ei_loss_bwd_per_sample" if per_sample else "skei_ei_loss_bwd")
     return out
+
+
+def ei_loss_bwd(plan: Plan, r, g_x2, g_z, g_deg, mc_coef: float, mc_idx=None, sk_idx=None,
+                work=None, out=None):
+    """g_x1 = -2 mc_coef A_mc^T r + sum_g T_g^T [g_x2 + (pi/m) A_S^T H B_S^T g_z]."""
+    return _ei_bwd(plan, r, g_x2, g_z, g_deg, mc_coef, mc_idx, sk_idx, work, out, False)
+
+
+def ei_loss_bwd_per_sample(plan: Plan, r, g_x2, g_z, g_deg, mc_coef: float, mc_idx=None,
+                           sk_idx=None, work=None, out=None):
+    """The same with an angle list per measurement: mc_idx, sk_idx int32 [B, m]."""
+    return _ei_bwd(plan, r, g_x2, g_z, g_deg, mc_coef, mc_idx, sk_idx, work, out, True)
 
 
 def residual_add(u, theta, out=None) -> torch.Tensor:

@@ -142,3 +142,69 @@ def test_autograd_gradient_vs_oracle_and_finite_differences(S):
     fd = np.array(fd)
     an = g.ravel()[pix]
     assert np.abs(fd - an).max() <= 1e-3 * np.abs(g).max() + 2e-3 * np.abs(an).max()
+
+
+# ------------------------------------------------- a sketch per measurement
+@pytest.mark.parametrize("N,n_ang,B,G,m,sketch_mc", [
+    (256, 180, 8, 4, 45, False),   # Algorithm 1 over 8 measurements, MC on all views
+    (64, 60, 3, 4, 15, True),      # sketched MC: each MC image rides with its EI group
+    (37, 24, 3, 3, 6, True),       # G = 3: groups of 4 would straddle samples
+    (100, 30, 5, 2, 10, False),    # G = 2, ragged
+])
+def test_per_sample_sketches_match_oracle(S, N, n_ang, B, G, m, sketch_mc):
+    P = _setup(N, n_ang, B, G, m, sketch_mc, seed=N + B)
+    rng = np.random.default_rng(N * B)
+    rows = np.stack([I.sketch_indices(n_ang, m, int(rng.integers(0, n_ang // m)))
+                     for _ in range(B)]).astype(np.int32)
+    plan = S.Plan(N, n_ang)
+    lam = 0.7
+    mc_scale = n_ang / m if sketch_mc else 1.0
+    rows_d = dev(rows, torch.int32)
+    mc_d = rows_d if sketch_mc else None
+    mc_rows = rows if sketch_mc else None
+    g_d = dev(P["g"], torch.float64)
+    x1 = dev(P["x1"])
+    theta = 0.01 * np.random.default_rng(2).standard_normal((N, N))
+    r, x2, z = S.ei_loss_fwd_per_sample(plan, x1, dev(P["y"]), g_d, mc_idx=mc_d, sk_idx=rows_d)
+    x3 = S.residual_add(z, dev(theta))
+    loss, mc, ei, g_x2, g_x3 = S.ei_loss_finish(x2, x3, r, lam, mc_scale)
+    g_x1 = S.ei_loss_bwd_per_sample(plan, r, g_x2, g_x3, g_d, mc_scale / B, mc_idx=mc_d,
+                                    sk_idx=rows_d)
+
+    r_o, x2_o, z_o = O.ei_stage1_per_sample(host(x1), P["y"], P["angs"], mc_rows, rows, P["g"])
+    x3_o = z_o + theta[None, None]
+    loss_o, mc_o, ei_o, gx2_o, gx3_o = O.ei_finish(x2_o, x3_o, r_o, lam, mc_scale)
+    gx1_o = O.ei_backward_per_sample(r_o, gx2_o, gx3_o, P["angs"], mc_rows, rows, P["g"],
+                                     mc_scale)
+    y_mc = (P["y"] if mc_rows is None
+            else np.stack([P["y"][b][rows[b]] for b in range(B)]))
+    assert np.linalg.norm(host(r) - r_o) <= FP32_TOL * np.linalg.norm(y_mc)
+    assert rel(host(z), z_o) <= FP32_TOL
+    assert rel(host(g_x1), gx1_o) <= FP32_TOL
+    assert abs(loss.item() - loss_o) <= FP32_TOL * abs(loss_o)
+    assert rel(host(ei), ei_o) <= FP32_TOL
+
+
+@pytest.mark.parametrize("sketch_mc", [False, True])
+def test_per_sample_with_equal_rows_is_the_shared_sketch_bitwise(S, sketch_mc):
+    """The same sketch in every row runs the same kernels in the same order
+    as the shared-sketch entry points: identical bits."""
+    N, n_ang, B, G, m = 64, 60, 3, 4, 15
+    P = _setup(N, n_ang, B, G, m, sketch_mc, seed=9)
+    plan = S.Plan(N, n_ang)
+    idx_d = dev(P["idx"], torch.int32)
+    rows_d = idx_d.repeat(B, 1).contiguous()
+    g_d = dev(P["g"], torch.float64)
+    x1, y = dev(P["x1"]), dev(P["y"])
+    a = S.ei_loss_fwd(plan, x1, y, g_d, mc_idx=idx_d if sketch_mc else None, sk_idx=idx_d)
+    b = S.ei_loss_fwd_per_sample(plan, x1, y, g_d, mc_idx=rows_d if sketch_mc else None,
+                                 sk_idx=rows_d)
+    for u, v in zip(a, b):
+        assert torch.equal(u, v)
+    r, x2, z = a
+    gx = 0.1 * x2
+    ga = S.ei_loss_bwd(plan, r, gx, z, g_d, 0.3, mc_idx=idx_d if sketch_mc else None,
+                       sk_idx=idx_d)
+    gb = S.ei_loss_bwd_per_sample(plan, r, gx, z, g_d, 0.3,
+                                  mc_idx=rows_d if sketch_mc else None, sk_idx=rows_d)
+    assert torch.equal(ga, gb)

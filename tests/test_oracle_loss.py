@@ -104,3 +104,47 @@ def test_psnr_definition():
     ref = np.array([[0.0, 1.0], [2.0, 3.0]])
     x = ref + 0.1
     assert abs(O.psnr(x, ref) - 10 * np.log10(9.0 / 0.01)) < 1e-12
+
+
+def _rows(n_ang, m, B, seed):
+    rng = np.random.default_rng(seed)
+    return np.stack([I.sketch_indices(n_ang, m, int(rng.integers(0, n_ang // m)))
+                     for _ in range(B)])
+
+
+def test_per_sample_sketches_with_equal_rows_are_the_shared_sketch():
+    """Algorithm 1 with the same sketch drawn for every measurement is the
+    shared-sketch loss and gradient."""
+    P = _problem(5, B=3)
+    rows = np.stack([P["idx"]] * 3)
+    args = (P["x0"], P["y"], P["angs"])
+    for mc in (None, "sk"):
+        l1, g1, _ = O.ttt_grad(P["theta"], *args, P["idx"] if mc else None, P["idx"], P["g"],
+                               0.7, 2.0)
+        l2, g2, _ = O.ttt_grad_per_sample(P["theta"], *args, rows if mc else None, rows, P["g"],
+                                          0.7, 2.0)
+        assert abs(l1 - l2) <= 1e-12 * abs(l1)
+        np.testing.assert_allclose(g2, g1, rtol=0, atol=1e-12 * np.abs(g1).max())
+
+
+@pytest.mark.parametrize("mc_rows", [False, True])
+def test_per_sample_gradient_matches_central_differences(mc_rows):
+    """Distinct sketches per measurement: the hand-written gradient (with
+    each measurement's MC coefficient mc_scale / B) against finite
+    differences of the loss (exact: the loss is quadratic in theta)."""
+    P = _problem(6, B=3, G=2)
+    rows = _rows(len(P["angs"]), 4, 3, seed=7)
+    assert len({tuple(r) for r in rows}) > 1
+    args = (P["x0"], P["y"], P["angs"], rows if mc_rows else None, rows, P["g"], 0.7, 3.0)
+    loss, grad, _ = O.ttt_grad_per_sample(P["theta"], *args)
+    rng = np.random.default_rng(8)
+    h = 1e-3
+    v = rng.standard_normal(P["theta"].shape)
+    lp, _ = O.ttt_loss_per_sample(P["theta"] + h * v, *args)
+    lm, _ = O.ttt_loss_per_sample(P["theta"] - h * v, *args)
+    assert abs((lp - lm) / (2 * h) - np.sum(grad * v)) <= 1e-8 * abs(np.sum(grad * v)) + 1e-9
+    # and the loss is the mean of the single-measurement losses
+    parts = [O.ttt_loss(P["theta"], P["x0"][b:b + 1], P["y"][b:b + 1], P["angs"],
+                        rows[b] if mc_rows else None, rows[b], P["g"][b:b + 1], 0.7, 3.0)[0]
+             for b in range(3)]
+    assert abs(loss - np.mean(parts)) <= 1e-12 * abs(loss)
