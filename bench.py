@@ -760,6 +760,18 @@ def suite(S, dev, stream):
 
     ttt_bn_suite(S, dev, stream)
 
+    # Theorem 1 on an explicit 32^2, 100-view A (probe.theorem1)
+    from paper_2411_05771_gb300.probe import theorem1
+    plan32 = S.Plan(32, 100)
+    v = torch.tensor(np.stack([I.rasterize(I.random_ellipses(s), 32) for s in range(8)]),
+                     dtype=torch.float32, device=dev)
+    res = theorem1(plan32, ns_list=(2, 5, 10, 20), v=v)
+    print(json.dumps({"suite": "theorem1-32x32-100views", **{k: res[k] for k in
+                      ("rank", "sigma_1", "sigma_k", "kappa")},
+                      "sketches": [{k: (round(x, 5) if isinstance(x, float) else x)
+                                    for k, x in it.items()} for it in res["sketches"]]}),
+          flush=True)
+
     # 16 instances mixing 256^2 / 360 angles and 512^2 / 720 angles
     rng = np.random.default_rng(4)
     sizes = [(256, 360), (512, 720)] * 8

@@ -18,6 +18,7 @@ Paper map:
   * Sec. 3.3      BN-only test-time training: batch-statistics BN layers,
                   only their affine parameters adapted
   * Algorithm 1   several measurements per step, a sketch drawn for each
+  * Theorem 1     ||U^T (S^T S - I) U|| of the interleaved sketches of A
 
 Readings where the paper is silent (all recorded in the design notes):
   A_S^dagger is the FBP over the sketch's angles, (pi/m) B_S H; the sketch is
@@ -453,6 +454,35 @@ def ttt_bn_loss(bn, conv, x0, y, angles_deg, mc_idx, sk_idx, g_deg, lam, mc_scal
     B, G, N = z.shape[0], z.shape[1], z.shape[-1]
     x3 = rescnn(z.reshape(B * G, N, N), conv, bn, eps).reshape(B, G, N, N)
     return ei_finish(x2, x3, r, lam, mc_scale)[0]
+
+
+# --------------------------------------------------------------------------
+# Theorem 1 (approximation bound of the sketched EI regulariser)
+# --------------------------------------------------------------------------
+
+def explicit_matrix(N: int, angles_deg, n_det: int) -> np.ndarray:
+    """Joseph's A as a dense [len(angles) n_det, N^2] matrix, column j = A e_j."""
+    d = N * N
+    return proj_fwd(np.eye(d).reshape(d, N, N), angles_deg, n_det).reshape(d, -1).T.copy()
+
+
+def sketch_gram_deviation(A, n_angles: int, n_det: int, ns: int, rank_tol: float = 1e-10):
+    """||U^T (S^T S - I) U||_2 for each of the ns interleaved sketches of an
+    n_angles-angle sinogram (offset o selects angles o, o + ns, ...), with
+    S^T S = ns P_o (unbiased over the offsets) and U the left singular
+    vectors of A for its singular values above rank_tol s_1 (the proof of
+    Theorem 1).  Returns (deltas [ns], singular values kept)."""
+    U, s, _ = np.linalg.svd(_f64(A), full_matrices=False)
+    k = int(np.sum(s > rank_tol * s[0]))
+    U = U[:, :k]
+    out = []
+    for o in range(ns):
+        mask = np.zeros(n_angles)
+        mask[o::ns] = 1.0
+        rows = np.repeat(mask, n_det) > 0
+        M = ns * (U[rows].T @ U[rows]) - np.eye(k)
+        out.append(float(np.max(np.abs(np.linalg.eigvalsh(M)))))
+    return np.array(out), s[:k]
 
 
 def psnr(x, ref) -> float:
