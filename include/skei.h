@@ -246,6 +246,16 @@ int skei_rotate_adj(int dtype, const void *gout, int B, int N,
                     const double *g_deg, int G, float alpha, float beta,
                     void *gx, void *stream);
 
+/* The same for images of Ch channels rotated alike (e.g. the real and
+ * imaginary planes of a complex MRI image): x [B][Ch][N][N] ->
+ * out [B][G][Ch][N][N]; gout [B][G][Ch][N][N] -> gx [B][Ch][N][N].
+ * B G Ch <= 65535. */
+int skei_rotate_channels(int dtype, const void *x, int B, int Ch, int N,
+                         const double *g_deg, int G, void *out, void *stream);
+int skei_rotate_adj_channels(int dtype, const void *gout, int B, int Ch, int N,
+                             const double *g_deg, int G, float alpha, float beta,
+                             void *gx, void *stream);
+
 /* ------------------------------------------------- fused EI / SkEI loss --
  * The loss of Eq. (e:skeiloss) / (e:skeilossttt), split around the caller's
  * network F, for B measurements and G rotations each:
@@ -283,6 +293,15 @@ int skei_ei_loss_finish(int dtype, const void *x2, const void *x3,
                         double lambda, double mc_scale, double *mc_out,
                         double *ei_out, double *loss_out, void *g_x2, void *g_x3,
                         void *work, size_t work_bytes, void *stream);
+
+/* The same for transformed images of img_len values each (x2, x3
+ * [B][G][img_len]; e.g. 2 N^2 for a planar complex image). */
+size_t skei_ei_finish_len_workspace_size(int B, int G, int64_t img_len, int r_len);
+int skei_ei_loss_finish_len(int dtype, const void *x2, const void *x3, const void *r, int B,
+                            int G, int64_t img_len, int r_len, double lambda,
+                            double mc_scale, double *mc_out, double *ei_out,
+                            double *loss_out, void *g_x2, void *g_x3, void *work,
+                            size_t work_bytes, void *stream);
 
 /* g_x2 and g_z may be NULL (treated as zero). */
 int skei_ei_loss_bwd(skei_plan plan, int dtype, const void *r, const void *g_x2,
@@ -360,6 +379,45 @@ int skei_bn_act_bwd(int dtype, const void *v, const void *g_out, int B, int C, i
                     const float *scale, const float *shift, const float *mean,
                     const float *rstd, int relu, void *g_v, float *g_scale, float *g_shift,
                     void *work, size_t work_bytes, void *stream);
+
+/* ------------------------------------- multi-coil MRI (Sec. 3.4, Eq. (e:mri)) --
+ * The forward model of the coil-sketched EI: k = M F (C x) for N_c coils,
+ *   k_c[u][v] = M[u][v] (1/N) sum_{p,q} C_c[p][q] x[p][q] e^{-2 pi i (u p + v q) / N}
+ * (unitary 2D DFT, frequency 0 at index 0, no shift; M a 0/1 mask shared by
+ * the coils), its adjoint x = sum_c conj(C_c) F^H (M k_c), and the
+ * coil-combined inverse A^dagger k = dinv * A^H k with dinv = 1 / sum_c |C_c|^2
+ * (0 where that sum is 0).  A coil sketch (PCA virtual coils, then
+ * S_c = [I_R 0; 0 S_low]) is a set of maps with fewer coils: the same calls
+ * with the sketched maps (skei_coil_mix forms them, and the sketched data).
+ *
+ * All complex arrays are FP32 planar: image x [B][2][N][N] (real plane,
+ * imaginary plane), k-space [B][N_c][2][N][N], maps [N_c][2][N][N]; mask and
+ * dinv are real [N][N] (mask NULL = every sample taken).  N is a power of two
+ * in [8, 256]; 1 <= N_c <= 64.  work: a device workspace of at least
+ * skei_mri_workspace_size(N, Nc, B) bytes (16-byte aligned, owned by the
+ * caller).  Errors: SKEI_EINVAL for bad sizes, NULL or host pointers or too
+ * small a workspace.
+ *
+ * skei_mri_fwd: k = alpha (aux - M F (C (w x))) with aux (same layout as k;
+ *   may be k itself), else alpha M F (C (w x)), w a real [N][N] weight on the
+ *   image (xw; NULL = 1): the MC residual y - A x in one call, and A (dinv g)
+ *   for the transpose of A^dagger A.
+ * skei_mri_adj: x = alpha dinv sum_c conj(C_c) F^H (M k_c) + beta x (dinv NULL:
+ *   the adjoint A^H; the per-coil images are summed in coil order).
+ * skei_mri_dinv: dinv from the maps.
+ * skei_coil_mix: out[b][j] = sum_i W[j][i] in[b][i] for complex weights W
+ *   (device float [n_out][n_in][2]) and planar coil data in [B][n_in][2][plane],
+ *   out [B][n_out][2][plane] (no aliasing); n_in, n_out <= 64. */
+size_t skei_mri_workspace_size(int N, int Nc, int B);
+int skei_mri_fwd(int N, int Nc, int B, const float *x, const float *maps, const float *mask,
+                 const float *xw, const float *aux, float alpha, float *k, void *work,
+                 size_t work_bytes, void *stream);
+int skei_mri_adj(int N, int Nc, int B, const float *k, const float *maps, const float *mask,
+                 const float *dinv, float alpha, float beta, float *x, void *work,
+                 size_t work_bytes, void *stream);
+int skei_mri_dinv(int N, int Nc, const float *maps, float *dinv, void *stream);
+int skei_coil_mix(int plane, int B, int n_in, int n_out, const float *W, const float *in,
+                  float *out, void *stream);
 
 /* ------------------------------------------------ batched schedule --
  * One operator applied to many instances in one persistent launch per

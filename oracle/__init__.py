@@ -19,6 +19,8 @@ Paper map:
                   only their affine parameters adapted
   * Algorithm 1   several measurements per step, a sketch drawn for each
   * Theorem 1     ||U^T (S^T S - I) U|| of the interleaved sketches of A
+  * Sec. 3.4, Eq. (e:mri), Algorithm 3   multi-coil MRI A = M F C, PCA coil
+                  compression and the coil sketch S_c = [I_R 0; 0 S_low]
 
 Readings where the paper is silent (all recorded in the design notes):
   A_S^dagger is the FBP over the sketch's angles, (pi/m) B_S H; the sketch is
@@ -483,6 +485,119 @@ def sketch_gram_deviation(A, n_angles: int, n_det: int, ns: int, rank_tol: float
         M = ns * (U[rows].T @ U[rows]) - np.eye(k)
         out.append(float(np.max(np.abs(np.linalg.eigvalsh(M)))))
     return np.array(out), s[:k]
+
+
+# --------------------------------------------------------------------------
+# multi-coil MRI (Sec. 3.4, Eq. (e:mri)) and the coil sketch (Algorithm 3)
+# --------------------------------------------------------------------------
+
+def _cplx(a):
+    a = _f64(a)
+    return a[..., 0, :, :] + 1j * a[..., 1, :, :]
+
+
+def _planar(z):
+    return np.stack([z.real, z.imag], axis=-3)
+
+
+def mri_fwd(x, maps, mask=None):
+    """Eq. (e:mri): k_c = M F (C_c x), F the unitary 2D DFT (frequency 0 at
+    index 0).  x planar [B, 2, N, N], maps [Nc, 2, N, N] -> [B, Nc, 2, N, N].
+    The DFT is numpy's fft2 (a library primitive, norm "ortho")."""
+    k = np.fft.fft2(_cplx(maps)[None] * _cplx(x)[:, None], norm="ortho")
+    if mask is not None:
+        k = k * _f64(mask)
+    return _planar(k)
+
+
+def mri_adj(k, maps, mask=None):
+    """A^H k = sum_c conj(C_c) F^H (M k_c): [B, Nc, 2, N, N] -> [B, 2, N, N]."""
+    kc = _cplx(k)
+    if mask is not None:
+        kc = kc * _f64(mask)
+    return _planar(np.sum(np.conj(_cplx(maps))[None] * np.fft.ifft2(kc, norm="ortho"), axis=1))
+
+
+def mri_dinv(maps):
+    """1 / sum_c |C_c|^2 per pixel, 0 where the sum is 0."""
+    s = np.sum(np.abs(_cplx(maps)) ** 2, axis=0)
+    out = np.zeros_like(s)
+    out[s > 0] = 1.0 / s[s > 0]
+    return out
+
+
+def mri_pinv(k, maps, mask=None):
+    """A^dagger k = dinv A^H k: the coil-combined zero-filled inverse (the
+    least-squares inverse of F C when every sample is taken)."""
+    return mri_adj(k, maps, mask) * mri_dinv(maps)[None, None]
+
+
+def coil_mix(W, x):
+    """out[b, j] = sum_i W[j, i] x[b, i] for complex W [n_out, n_in] and
+    planar coil data x [B, n_in, 2, ...]."""
+    return _planar(np.einsum("ji,bi...->bj...", np.asarray(W, dtype=np.complex128), _cplx(x)))
+
+
+def coil_pca(k, L: int):
+    """Algorithm 3 / Sec. 3.4's PCA coil compression of one measurement's
+    k-space k [Nc, 2, N, N]: centre each coil over its d samples, covariance
+    V_ij = conj(kbar_i) . kbar_j / (d - 1), and the L dominant eigenvectors
+    Q_L [Nc, L] (eigenvalues descending; each eigenvector's phase fixed so
+    that its largest-magnitude entry, the first such, is real positive).
+    Virtual coil l is sum_c Q[c, l] k_c."""
+    K = _cplx(k).reshape(k.shape[0], -1).T                    # [d, Nc]
+    Kb = K - K.mean(axis=0, keepdims=True)
+    V = Kb.conj().T @ Kb / (K.shape[0] - 1)
+    w, Q = np.linalg.eigh(V)
+    order = np.argsort(-w, kind="stable")
+    Q = Q[:, order][:, :L]
+    for l in range(L):
+        i = int(np.argmax(np.abs(Q[:, l])))
+        Q[:, l] *= np.conj(Q[i, l]) / abs(Q[i, l])
+    return Q, w[order]
+
+
+def coil_sketch(L: int, R: int, s_low):
+    """S_c = [[I_R, 0], [0, S_low]] [M_c, L] of Sec. 3.4, S_low the
+    (M_c - R) x (L - R) Rademacher block."""
+    s_low = np.asarray(s_low, dtype=np.float64)
+    Mc = R + s_low.shape[0]
+    S = np.zeros((Mc, L))
+    S[:R, :R] = np.eye(R)
+    S[R:, R:] = s_low
+    return S
+
+
+def mri_ttt_loss(theta, x0, y, maps, mask, g_deg, lam):
+    """Sec. 3.4's coil-sketched EI loss for one measurement with the residual
+    stand-in F(u) = u + theta (theta planar [2, N, N]): MC ||y - A x1||^2 and
+    EI (lambda/G) sum_g ||T_g x1 - F(A^dagger A T_g x1)||^2, A = (maps, mask)
+    (the sketched maps and data for C-SkEI); T_g rotates both planes."""
+    x1 = _f64(x0) + _f64(theta)[None]
+    r = _f64(y) - mri_fwd(x1, maps, mask)
+    G = np.asarray(g_deg).shape[1]
+    x2 = np.stack([np.stack([rotate(x1[0, c], g_deg[0][g]) for c in range(2)])
+                   for g in range(G)])[None]                    # [1, G, 2, N, N]
+    z = mri_pinv(mri_fwd(x2[0], maps, mask), maps, mask)[None]
+    x3 = z + _f64(theta)[None, None]
+    loss, mc, ei, g_x2, g_x3 = ei_finish(x2, x3, r, lam, 1.0)
+    return loss, dict(r=r, x2=x2, z=z, x3=x3, g_x2=g_x2, g_x3=g_x3)
+
+
+def mri_ttt_grad(theta, x0, y, maps, mask, g_deg, lam):
+    """(loss, dL/dtheta) of mri_ttt_loss: the planar real gradient of a
+    complex-linear map P is its adjoint P^H, and (A^dagger A)^H = A^H A dinv,
+    so dL/dx1 = -2 A^H r + sum_g T_g^T [g_x2 + A^H A (dinv g_z)]."""
+    loss, t = mri_ttt_loss(theta, x0, y, maps, mask, g_deg, lam)
+    G = t["x2"].shape[1]
+    dinv = mri_dinv(maps)
+    g_z = t["g_x3"][0]                                          # [G, 2, N, N]
+    g_tot = t["g_x2"][0] + mri_adj(mri_fwd(g_z * dinv[None, None], maps, mask), maps, mask)
+    g_x1 = -2.0 * mri_adj(t["r"], maps, mask)[0]
+    for g in range(G):
+        for c in range(2):
+            g_x1[c] += rotate_adj(g_tot[g, c], g_deg[0][g])
+    return loss, g_x1 + t["g_x3"][0].sum(axis=0), t
 
 
 def psnr(x, ref) -> float:

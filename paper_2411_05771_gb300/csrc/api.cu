@@ -336,10 +336,9 @@ int ei_bwd_impl(skei_plan p, const T *r, const T *g_x2, const T *g_z, int B, con
 }
 
 template <typename T>
-int ei_finish_impl(const T *x2, const T *x3, const T *r, int B, int G, int N, int r_len,
+int ei_finish_impl(const T *x2, const T *x3, const T *r, int B, int G, int64_t n_img, int r_len,
                    double lambda, double mc_scale, double *mc_out, double *ei_out,
                    double *loss_out, T *g_x2, T *g_x3, char *work, cudaStream_t st) {
-  const int64_t n_img = (int64_t)N * N;
   const int cpi = (int)ceil_div((size_t)n_img, kChunk);
   const int cpr = (int)ceil_div((size_t)r_len, kChunk);
   double *partial = reinterpret_cast<double *>(work);
@@ -570,28 +569,43 @@ int skei_fbp_adj(skei_plan plan, int dtype, const void *x, int B, const int *idx
                             as_stream(stream));
 }
 
-int skei_rotate(int dtype, const void *x, int B, int N, const double *g_deg, int G, void *out,
-                void *stream) {
+int skei_rotate_channels(int dtype, const void *x, int B, int Ch, int N, const double *g_deg,
+                         int G, void *out, void *stream) {
   SKEI_TRY(check_rot(dtype, B, N, g_deg, G));
+  if (Ch < 1 || (int64_t)B * G * Ch > 65535)
+    return set_error(SKEI_EINVAL, "rotation: Ch=%d outside [1, 65535 / (B G)]", Ch);
   SKEI_TRY(check_dev_ptr(x, "x"));
   SKEI_TRY(check_dev_ptr(out, "out"));
   if (dtype == SKEI_F32)
     return launch_rotate<float, float>((const float *)x, B, N, g_deg, G, (float *)out,
-                                       as_stream(stream));
+                                       as_stream(stream), Ch);
   return launch_rotate<bf16, bf16>((const bf16 *)x, B, N, g_deg, G, (bf16 *)out,
-                                   as_stream(stream));
+                                   as_stream(stream), Ch);
 }
 
-int skei_rotate_adj(int dtype, const void *gout, int B, int N, const double *g_deg, int G,
-                    float alpha, float beta, void *gx, void *stream) {
+int skei_rotate(int dtype, const void *x, int B, int N, const double *g_deg, int G, void *out,
+                void *stream) {
+  return skei_rotate_channels(dtype, x, B, 1, N, g_deg, G, out, stream);
+}
+
+int skei_rotate_adj_channels(int dtype, const void *gout, int B, int Ch, int N,
+                             const double *g_deg, int G, float alpha, float beta, void *gx,
+                             void *stream) {
   SKEI_TRY(check_rot(dtype, B, N, g_deg, G));
+  if (Ch < 1 || (int64_t)B * Ch > 65535)
+    return set_error(SKEI_EINVAL, "rotation transpose: Ch=%d outside [1, 65535 / B]", Ch);
   SKEI_TRY(check_dev_ptr(gout, "gout"));
   SKEI_TRY(check_dev_ptr(gx, "gx"));
   if (dtype == SKEI_F32)
     return launch_rotate_adj<float, float>((const float *)gout, B, N, g_deg, G, alpha, beta,
-                                           (float *)gx, as_stream(stream));
+                                           (float *)gx, as_stream(stream), Ch);
   return launch_rotate_adj<bf16, bf16>((const bf16 *)gout, B, N, g_deg, G, alpha, beta,
-                                       (bf16 *)gx, as_stream(stream));
+                                       (bf16 *)gx, as_stream(stream), Ch);
+}
+
+int skei_rotate_adj(int dtype, const void *gout, int B, int N, const double *g_deg, int G,
+                    float alpha, float beta, void *gx, void *stream) {
+  return skei_rotate_adj_channels(dtype, gout, B, 1, N, g_deg, G, alpha, beta, gx, stream);
 }
 
 size_t skei_ei_workspace_size(skei_plan plan, int dtype, int B, int G, int mc_m, int sk_m) {
@@ -638,20 +652,26 @@ int skei_ei_loss_fwd_per_sample(skei_plan plan, int dtype, const void *x1, const
                       work, work_bytes, stream, true);
 }
 
-size_t skei_ei_finish_workspace_size(int B, int G, int N, int r_len) {
-  if (B < 1 || G < 1 || N < 1 || r_len < 1) return 0;
-  return align256(((size_t)B * G * ceil_div((size_t)N * N, kChunk) +
+size_t skei_ei_finish_len_workspace_size(int B, int G, int64_t img_len, int r_len) {
+  if (B < 1 || G < 1 || img_len < 1 || r_len < 1) return 0;
+  return align256(((size_t)B * G * ceil_div((size_t)img_len, kChunk) +
                    (size_t)B * ceil_div((size_t)r_len, kChunk)) * sizeof(double));
 }
 
-int skei_ei_loss_finish(int dtype, const void *x2, const void *x3, const void *r, int B, int G,
-                        int N, int r_len, double lambda, double mc_scale, double *mc_out,
-                        double *ei_out, double *loss_out, void *g_x2, void *g_x3, void *work,
-                        size_t work_bytes, void *stream) {
+size_t skei_ei_finish_workspace_size(int B, int G, int N, int r_len) {
+  if (N < 1) return 0;
+  return skei_ei_finish_len_workspace_size(B, G, (int64_t)N * N, r_len);
+}
+
+int skei_ei_loss_finish_len(int dtype, const void *x2, const void *x3, const void *r, int B,
+                            int G, int64_t img_len, int r_len, double lambda, double mc_scale,
+                            double *mc_out, double *ei_out, double *loss_out, void *g_x2,
+                            void *g_x3, void *work, size_t work_bytes, void *stream) {
   SKEI_TRY(check_dtype(dtype));
   SKEI_TRY(check_batch(B));
   if (G < 1 || (int64_t)B * G > 65535) return set_error(SKEI_EINVAL, "bad G=%d", G);
-  if (N < 1 || N > SKEI_MAX_N) return set_error(SKEI_EINVAL, "N=%d outside [1, %d]", N, SKEI_MAX_N);
+  if (img_len < 1 || img_len > ((int64_t)1 << 31))
+    return set_error(SKEI_EINVAL, "img_len=%lld outside [1, 2^31]", (long long)img_len);
   if (r_len < 1) return set_error(SKEI_EINVAL, "r_len=%d must be >= 1", r_len);
   SKEI_TRY(check_dev_ptr(x2, "x2"));
   SKEI_TRY(check_dev_ptr(x3, "x3"));
@@ -661,14 +681,24 @@ int skei_ei_loss_finish(int dtype, const void *x2, const void *x3, const void *r
   if (mc_out && (reinterpret_cast<uintptr_t>(mc_out) % 8)) return set_error(SKEI_EINVAL, "mc_out misaligned");
   if (ei_out && (reinterpret_cast<uintptr_t>(ei_out) % 8)) return set_error(SKEI_EINVAL, "ei_out misaligned");
   if (loss_out && (reinterpret_cast<uintptr_t>(loss_out) % 8)) return set_error(SKEI_EINVAL, "loss_out misaligned");
-  SKEI_TRY(check_work(work, work_bytes, skei_ei_finish_workspace_size(B, G, N, r_len)));
+  SKEI_TRY(check_work(work, work_bytes,
+                      skei_ei_finish_len_workspace_size(B, G, img_len, r_len)));
   if (dtype == SKEI_F32)
-    return ei_finish_impl<float>((const float *)x2, (const float *)x3, (const float *)r, B, G, N,
-                                 r_len, lambda, mc_scale, mc_out, ei_out, loss_out, (float *)g_x2,
-                                 (float *)g_x3, (char *)work, as_stream(stream));
-  return ei_finish_impl<bf16>((const bf16 *)x2, (const bf16 *)x3, (const bf16 *)r, B, G, N, r_len,
-                              lambda, mc_scale, mc_out, ei_out, loss_out, (bf16 *)g_x2,
-                              (bf16 *)g_x3, (char *)work, as_stream(stream));
+    return ei_finish_impl<float>((const float *)x2, (const float *)x3, (const float *)r, B, G,
+                                 img_len, r_len, lambda, mc_scale, mc_out, ei_out, loss_out,
+                                 (float *)g_x2, (float *)g_x3, (char *)work, as_stream(stream));
+  return ei_finish_impl<bf16>((const bf16 *)x2, (const bf16 *)x3, (const bf16 *)r, B, G,
+                              img_len, r_len, lambda, mc_scale, mc_out, ei_out, loss_out,
+                              (bf16 *)g_x2, (bf16 *)g_x3, (char *)work, as_stream(stream));
+}
+
+int skei_ei_loss_finish(int dtype, const void *x2, const void *x3, const void *r, int B, int G,
+                        int N, int r_len, double lambda, double mc_scale, double *mc_out,
+                        double *ei_out, double *loss_out, void *g_x2, void *g_x3, void *work,
+                        size_t work_bytes, void *stream) {
+  if (N < 1 || N > SKEI_MAX_N) return set_error(SKEI_EINVAL, "N=%d outside [1, %d]", N, SKEI_MAX_N);
+  return skei_ei_loss_finish_len(dtype, x2, x3, r, B, G, (int64_t)N * N, r_len, lambda, mc_scale,
+                                 mc_out, ei_out, loss_out, g_x2, g_x3, work, work_bytes, stream);
 }
 
 static int ei_bwd_entry(skei_plan plan, int dtype, const void *r, const void *g_x2,

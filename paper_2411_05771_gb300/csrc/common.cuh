@@ -390,13 +390,13 @@ int launch_backproject_adj(skei_plan p, const Tin *x, int B, const int *idx,
 template <typename Tin, typename Tout>
 int launch_filter(skei_plan p, const Tin *in, int rows, float scale, Tout *out,
                   cudaStream_t st);
-// Rotation: out[b][g] = T_g x[b].
+// Rotation: out[b][g][ch] = T_g x[b][ch] (Ch channels share each angle).
 template <typename Tin, typename Tout>
 int launch_rotate(const Tin *x, int B, int N, const double *g_deg, int G,
-                  Tout *out, cudaStream_t st);
-// Rotation transpose: gx[b] = alpha sum_g T_g^T gout[b][g] + beta gx[b].
+                  Tout *out, cudaStream_t st, int Ch = 1);
+// Rotation transpose: gx[b][ch] = alpha sum_g T_g^T gout[b][g][ch] + beta gx[b][ch].
 template <typename Tin, typename Tout>
 int launch_rotate_adj(const Tin *gout, int B, int N, const double *g_deg, int G,
-                      float alpha, float beta, Tout *gx, cudaStream_t st);
+                      float alpha, float beta, Tout *gx, cudaStream_t st, int Ch = 1);
 
 }  // namespace skei

@@ -198,18 +198,19 @@ __device__ __forceinline__ RotConst rot_const(double deg, int N) {
 
 template <typename Tin, typename Tout>
 __global__ void __launch_bounds__(kRotThreads)
-    rotate_kernel(const Tin *x, int N, int G, const double *g_deg, Tout *out) {
+    rotate_kernel(const Tin *x, int N, int G, int Ch, const double *g_deg, Tout *out) {
   pdl_enter();
   __shared__ RotConst rc;
-  const int bg = blockIdx.z, b = bg / G;
+  // blockIdx.z = (b G + g) Ch + ch: output image; its angle is g_deg[b G + g]
+  const int bgc = blockIdx.z, bg = bgc / Ch, b = bg / G, ch = bgc - bg * Ch;
   if (threadIdx.x == 0) rc = rot_const(g_deg[bg], N);
   __syncthreads();
   const int tx = threadIdx.x % kRotX, ty = threadIdx.x / kRotX;
   const int j = blockIdx.x * kRotX + tx;
   const int i_first = blockIdx.y * kRotY * kRotQ + ty;
   if (j >= N) return;
-  const Tin *xb = x + (size_t)b * N * N;
-  Tout *ob = out + (size_t)bg * N * N + j;
+  const Tin *xb = x + ((size_t)b * Ch + ch) * N * N;
+  Tout *ob = out + (size_t)bgc * N * N + j;
   long long row = rc.R0 + (long long)j * rc.s + (long long)i_first * rc.c;
   long long col = rc.C0 + (long long)j * rc.c - (long long)i_first * rc.s;
   const long long drow = rc.c * kRotY, dcol = -rc.s * kRotY;
@@ -289,11 +290,12 @@ __device__ __forceinline__ float rot_adj_one(const RotConst &r, const Tin *gb, i
 
 template <typename Tin, typename Tout>
 __global__ void __launch_bounds__(kAdjT *kAdjT)
-    rotate_adj_kernel(const Tin *gout, int N, int G, const double *g_deg, float alpha,
+    rotate_adj_kernel(const Tin *gout, int N, int G, int Ch, const double *g_deg, float alpha,
                       float beta, Tout *gx) {
   pdl_enter();
   __shared__ RotConst rc[kMaxG];
-  const int b = blockIdx.z;
+  // blockIdx.z = b Ch + ch: output image
+  const int bc = blockIdx.z, b = bc / Ch, ch = bc - b * Ch;
   const int t = threadIdx.y * kAdjT + threadIdx.x;
   const int bb = blockIdx.x * kAdjT + threadIdx.x;
   float acc[kAdjQ];
@@ -305,8 +307,8 @@ __global__ void __launch_bounds__(kAdjT *kAdjT)
     if (t < ng) rc[t] = rot_const(g_deg[(size_t)b * G + g0 + t], N);
     __syncthreads();
     if (bb >= N) continue;
-    const Tin *gb = gout + ((size_t)b * G + g0) * N * N;
-    const size_t plane = (size_t)N * N;
+    const size_t plane = (size_t)N * N * Ch;   // one rotation's images
+    const Tin *gb = gout + ((size_t)b * G + g0) * plane + (size_t)ch * N * N;
     int g = 0;
     // two rotations at a time: twice the loads in flight; the sum over g
     // keeps its order
@@ -333,7 +335,7 @@ __global__ void __launch_bounds__(kAdjT *kAdjT)
   for (int q = 0; q < kAdjQ; ++q) {
     const int a = (blockIdx.y * kAdjQ + q) * kAdjT + threadIdx.y;
     if (a >= N) continue;
-    const size_t o = ((size_t)b * N + a) * N + bb;
+    const size_t o = ((size_t)bc * N + a) * N + bb;
     float v = alpha * acc[q];
     if (beta != 0.0f) v = fmaf(beta, ldg_f(gx + o), v);
     st_f(gx + o, v);
@@ -405,27 +407,27 @@ int launch_filter(skei_plan p, const Tin *in, int rows, float scale, Tout *out,
 
 template <typename Tin, typename Tout>
 int launch_rotate(const Tin *x, int B, int N, const double *g_deg, int G, Tout *out,
-                  cudaStream_t st) {
-  dim3 grid((N + kRotX - 1) / kRotX, (N + kRotY * kRotQ - 1) / (kRotY * kRotQ), B * G);
-  launch_k(rotate_kernel<Tin, Tout>, grid, dim3(kRotThreads), 0, st, x, N, G, g_deg, out);
+                  cudaStream_t st, int Ch) {
+  dim3 grid((N + kRotX - 1) / kRotX, (N + kRotY * kRotQ - 1) / (kRotY * kRotQ), B * G * Ch);
+  launch_k(rotate_kernel<Tin, Tout>, grid, dim3(kRotThreads), 0, st, x, N, G, Ch, g_deg, out);
   return check_launch("rotation launch");
 }
 
 template <typename Tin, typename Tout>
 int launch_rotate_adj(const Tin *gout, int B, int N, const double *g_deg, int G,
-                      float alpha, float beta, Tout *gx, cudaStream_t st) {
-  dim3 grid((N + kAdjT - 1) / kAdjT, (N + kAdjT * kAdjQ - 1) / (kAdjT * kAdjQ), B);
-  launch_k(rotate_adj_kernel<Tin, Tout>, grid, dim3(kAdjT, kAdjT), 0, st, gout, N, G, g_deg,
-           alpha, beta, gx);
+                      float alpha, float beta, Tout *gx, cudaStream_t st, int Ch) {
+  dim3 grid((N + kAdjT - 1) / kAdjT, (N + kAdjT * kAdjQ - 1) / (kAdjT * kAdjQ), B * Ch);
+  launch_k(rotate_adj_kernel<Tin, Tout>, grid, dim3(kAdjT, kAdjT), 0, st, gout, N, G, Ch,
+           g_deg, alpha, beta, gx);
   return check_launch("rotation transpose launch");
 }
 
 #define SKEI_FR_INST(TI, TO)                                                                  \
   template int launch_filter<TI, TO>(skei_plan, const TI *, int, float, TO *, cudaStream_t);  \
   template int launch_rotate<TI, TO>(const TI *, int, int, const double *, int, TO *,         \
-                                     cudaStream_t);                                          \
+                                     cudaStream_t, int);                                     \
   template int launch_rotate_adj<TI, TO>(const TI *, int, int, const double *, int, float,    \
-                                         float, TO *, cudaStream_t);
+                                         float, TO *, cudaStream_t, int);
 SKEI_FR_INST(float, float)
 SKEI_FR_INST(__nv_bfloat16, __nv_bfloat16)
 SKEI_FR_INST(float, __nv_bfloat16)

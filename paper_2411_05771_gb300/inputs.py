@@ -187,3 +187,58 @@ def cnn_weights(channels: int = 16, layers: int = 4, seed: int = 0) -> CnnWeight
         bn.append(1.0 + 0.1 * rng.standard_normal(channels))
         bn.append(0.1 * rng.standard_normal(channels))
     return CnnWeights(conv=conv, bn=np.concatenate(bn), channels=channels, layers=layers)
+
+
+# --------------------------------------------------------------------------
+# multi-coil MRI stand-ins (Sec. 4.1.2: 15-coil knee k-space at 128 x 128,
+# 4x undersampling; the fastMRI data and ESPIRiT maps are not available)
+# --------------------------------------------------------------------------
+
+def complex_phantom(seed: int, N: int) -> np.ndarray:
+    """Planar complex image [2, N, N]: an ellipse phantom's magnitude times a
+    smooth random phase (low-order polynomial, |phase| < pi/2)."""
+    rng = np.random.default_rng(seed + 5000)
+    mag = rasterize(random_ellipses(seed), N)
+    y, x = np.meshgrid(np.linspace(-1, 1, N), np.linspace(-1, 1, N), indexing="ij")
+    a = rng.uniform(-0.5, 0.5, size=4)
+    ph = a[0] * x + a[1] * y + a[2] * x * y + a[3] * (x * x - y * y)
+    return np.stack([mag * np.cos(ph), mag * np.sin(ph)])
+
+
+def coil_maps(Nc: int, N: int, seed: int = 0) -> np.ndarray:
+    """Planar sensitivity maps [Nc, 2, N, N]: coil c sits on a circle of
+    radius 1.5 (field of view [-1, 1]^2) at angle 2 pi c / Nc; magnitude
+    exp(-|r - r_c|^2 / (2 w^2)) with w = 0.9, phase = the polar angle seen from
+    the coil plus a seeded constant."""
+    rng = np.random.default_rng(seed + 6000)
+    y, x = np.meshgrid(np.linspace(-1, 1, N), np.linspace(-1, 1, N), indexing="ij")
+    maps = np.zeros((Nc, 2, N, N))
+    for c in range(Nc):
+        t = 2 * np.pi * c / Nc
+        cx, cy = 1.5 * np.cos(t), 1.5 * np.sin(t)
+        mag = np.exp(-((x - cx) ** 2 + (y - cy) ** 2) / (2 * 0.9 ** 2))
+        ph = np.arctan2(y - cy, x - cx) + rng.uniform(0, 2 * np.pi)
+        maps[c, 0], maps[c, 1] = mag * np.cos(ph), mag * np.sin(ph)
+    return maps
+
+
+def undersampling_mask(N: int, accel: int = 4, center: float = 0.08, seed: int = 0) -> np.ndarray:
+    """[N, N] 0/1 mask of whole k-space lines along the first axis (frequency
+    0 at index 0, no shift): the ceil(center N) lowest |frequencies| plus
+    random others, N / accel lines in all."""
+    rng = np.random.default_rng(seed + 7000)
+    freq = np.fft.fftfreq(N) * N
+    order = np.argsort(np.abs(freq), kind="stable")
+    n_c = int(np.ceil(center * N))
+    n_all = max(n_c, N // accel)
+    lines = list(order[:n_c])
+    rest = order[n_c:]
+    lines += list(rng.choice(rest, size=n_all - n_c, replace=False))
+    m = np.zeros((N, N))
+    m[np.array(lines, dtype=np.int64)] = 1.0
+    return m
+
+
+def rademacher(rng: np.random.Generator, shape) -> np.ndarray:
+    """i.i.d. +-1 with probability 1/2."""
+    return rng.integers(0, 2, size=shape) * 2.0 - 1.0

@@ -26,6 +26,7 @@ __all__ = [
     "ei_loss_fwd_per_sample", "ei_loss_bwd_per_sample",
     "residual_add", "adam_step", "library_path",
     "bn_workspace_size", "bn_act_fwd", "bn_act_bwd",
+    "mri_workspace_size", "mri_fwd", "mri_adj", "mri_dinv", "coil_mix",
     "Batch", "BatchItem", "PROJ_FWD", "PROJ_ADJ", "BACKPROJECT", "BACKPROJECT_ADJ", "FILTER",
     "FBP",
 ]
@@ -83,6 +84,11 @@ _SIGS = {
     "skei_fbp_noalloc": ([_PLAN, _i, _vp, _i, _vp, _i, _vp, _vp], _i),
     "skei_rotate": ([_i, _vp, _i, _i, _vp, _i, _vp, _vp], _i),
     "skei_rotate_adj": ([_i, _vp, _i, _i, _vp, _i, _f, _f, _vp, _vp], _i),
+    "skei_rotate_channels": ([_i, _vp, _i, _i, _i, _vp, _i, _vp, _vp], _i),
+    "skei_rotate_adj_channels": ([_i, _vp, _i, _i, _i, _vp, _i, _f, _f, _vp, _vp], _i),
+    "skei_ei_finish_len_workspace_size": ([_i, _i, _i64, _i], _sz),
+    "skei_ei_loss_finish_len": ([_i, _vp, _vp, _vp, _i, _i, _i64, _i, _d, _d, _vp, _vp, _vp,
+                                 _vp, _vp, _vp, _sz, _vp], _i),
     "skei_ei_workspace_size": ([_PLAN, _i, _i, _i, _i, _i], _sz),
     "skei_ei_finish_workspace_size": ([_i, _i, _i, _i], _sz),
     "skei_ei_loss_fwd": ([_PLAN, _i, _vp, _vp, _i, _vp, _i, _vp, _i, _vp, _i, _vp, _vp, _vp,
@@ -102,6 +108,11 @@ _SIGS = {
                         _i),
     "skei_bn_act_bwd": ([_i, _vp, _vp, _i, _i, _i64, _vp, _vp, _vp, _vp, _i, _vp, _vp, _vp, _vp,
                          _sz, _vp], _i),
+    "skei_mri_workspace_size": ([_i, _i, _i], _sz),
+    "skei_mri_fwd": ([_i, _i, _i, _vp, _vp, _vp, _vp, _vp, _f, _vp, _vp, _sz, _vp], _i),
+    "skei_mri_adj": ([_i, _i, _i, _vp, _vp, _vp, _vp, _f, _f, _vp, _vp, _sz, _vp], _i),
+    "skei_mri_dinv": ([_i, _i, _vp, _vp, _vp], _i),
+    "skei_coil_mix": ([_i, _i, _i, _i, _vp, _vp, _vp, _vp], _i),
     "skei_batch_create": ([_i, ctypes.POINTER(_BatchItemC), _i, ctypes.POINTER(_BATCH)], _i),
     "skei_batch_run": ([_BATCH, _vp], _i),
     "skei_batch_tune": ([_BATCH, _i, _vp], _i),
@@ -409,30 +420,39 @@ def fbp_noalloc(plan: Plan, sino, idx=None, out=None) -> torch.Tensor:
 
 
 def rotate(x, g_deg, out=None) -> torch.Tensor:
-    """T_g x for every (b, g): x [B, N, N], g_deg float64 [B, G] -> [B, G, N, N]."""
+    """T_g x for every (b, g): x [B, N, N] -> [B, G, N, N], or x [B, Ch, N, N]
+    (channels rotated alike) -> [B, G, Ch, N, N]; g_deg float64 [B, G]."""
     B, N = x.shape[0], x.shape[-1]
     G = g_deg.shape[1]
-    _dev(x, "x", shape=(B, N, N))
+    Ch = x.shape[1] if x.dim() == 4 else 1
+    shp_in = (B, Ch, N, N) if x.dim() == 4 else (B, N, N)
+    shp_out = (B, G, Ch, N, N) if x.dim() == 4 else (B, G, N, N)
+    _dev(x, "x", shape=shp_in)
     _dev(g_deg, "g_deg", torch.float64, (B, G))
-    out = torch.empty((B, G, N, N), device=x.device, dtype=x.dtype) if out is None else out
-    _dev(out, "out", x.dtype, (B, G, N, N))
-    _check(_lib.skei_rotate(_dtype_code(x), _ptr(x), B, N, _ptr(g_deg), G, _ptr(out), _stream()),
-           "skei_rotate")
+    out = torch.empty(shp_out, device=x.device, dtype=x.dtype) if out is None else out
+    _dev(out, "out", x.dtype, shp_out)
+    _check(_lib.skei_rotate_channels(_dtype_code(x), _ptr(x), B, Ch, N, _ptr(g_deg), G,
+                                     _ptr(out), _stream()), "skei_rotate_channels")
     return out
 
 
 def rotate_adj(gout, g_deg, alpha=1.0, beta=0.0, out=None) -> torch.Tensor:
-    """alpha sum_g T_g^T gout[:, g] + beta out; [B, G, N, N] -> [B, N, N]."""
+    """alpha sum_g T_g^T gout[:, g] + beta out: [B, G, N, N] -> [B, N, N], or
+    [B, G, Ch, N, N] -> [B, Ch, N, N]."""
     B, G, N = gout.shape[0], gout.shape[1], gout.shape[-1]
-    _dev(gout, "gout", shape=(B, G, N, N))
+    Ch = gout.shape[2] if gout.dim() == 5 else 1
+    shp_in = (B, G, Ch, N, N) if gout.dim() == 5 else (B, G, N, N)
+    shp_out = (B, Ch, N, N) if gout.dim() == 5 else (B, N, N)
+    _dev(gout, "gout", shape=shp_in)
     _dev(g_deg, "g_deg", torch.float64, (B, G))
     if out is None:
         if beta != 0.0:
             raise ValueError("beta != 0 needs out")
-        out = torch.empty((B, N, N), device=gout.device, dtype=gout.dtype)
-    _dev(out, "out", gout.dtype, (B, N, N))
-    _check(_lib.skei_rotate_adj(_dtype_code(gout), _ptr(gout), B, N, _ptr(g_deg), G, float(alpha),
-                                float(beta), _ptr(out), _stream()), "skei_rotate_adj")
+        out = torch.empty(shp_out, device=gout.device, dtype=gout.dtype)
+    _dev(out, "out", gout.dtype, shp_out)
+    _check(_lib.skei_rotate_adj_channels(_dtype_code(gout), _ptr(gout), B, Ch, N, _ptr(g_deg), G,
+                                         float(alpha), float(beta), _ptr(out), _stream()),
+           "skei_rotate_adj_channels")
     return out
 
 
@@ -490,11 +510,13 @@ def ei_loss_fwd_per_sample(plan: Plan, x1, y, g_deg, mc_idx=None, sk_idx=None, w
 
 def ei_loss_finish(x2, x3, r, lam: float, mc_scale: float, want_grads=True, work=None,
                    out=None):
-    """Returns (loss[1], mc[B], ei[B, G], g_x2, g_x3) with FP64 sums on the device."""
-    B, G, N = x2.shape[0], x2.shape[1], x2.shape[-1]
-    _dev(x2, "x2", shape=(B, G, N, N))
-    _dev(x3, "x3", x2.dtype, (B, G, N, N))
+    """Returns (loss[1], mc[B], ei[B, G], g_x2, g_x3) with FP64 sums on the
+    device; x2, x3 [B, G, ...] (any image shape), r [B, ...]."""
+    B, G = x2.shape[0], x2.shape[1]
+    _dev(x2, "x2")
+    _dev(x3, "x3", x2.dtype, x2.shape)
     _dev(r, "r", x2.dtype)
+    img_len = x2[0, 0].numel()
     r_len = r.numel() // B
     dev = x2.device
     if out is None:
@@ -504,12 +526,12 @@ def ei_loss_finish(x2, x3, r, lam: float, mc_scale: float, want_grads=True, work
                torch.empty_like(x2) if want_grads else None,
                torch.empty_like(x2) if want_grads else None)
     loss, mc, ei, g_x2, g_x3 = out
-    nb = int(_lib.skei_ei_finish_workspace_size(B, G, N, r_len))
+    nb = int(_lib.skei_ei_finish_len_workspace_size(B, G, img_len, r_len))
     w = _work(nb, dev, work)
-    _check(_lib.skei_ei_loss_finish(_dtype_code(x2), _ptr(x2), _ptr(x3), _ptr(r), B, G, N, r_len,
-                                    float(lam), float(mc_scale), _ptr(mc), _ptr(ei), _ptr(loss),
-                                    _ptr(g_x2), _ptr(g_x3), _ptr(w), nb, _stream()),
-           "skei_ei_loss_finish")
+    _check(_lib.skei_ei_loss_finish_len(_dtype_code(x2), _ptr(x2), _ptr(x3), _ptr(r), B, G,
+                                        img_len, r_len, float(lam), float(mc_scale), _ptr(mc),
+                                        _ptr(ei), _ptr(loss), _ptr(g_x2), _ptr(g_x3), _ptr(w), nb,
+                                        _stream()), "skei_ei_loss_finish_len")
     return loss, mc, ei, g_x2, g_x3
 
 
@@ -625,6 +647,85 @@ def bn_act_bwd(v, g_out, scale, shift, mean, rstd, relu=True, work=None):
                                 _ptr(g_scale), _ptr(g_shift), _ptr(w), nb, _stream()),
            "skei_bn_act_bwd")
     return g_v, g_scale, g_shift
+
+
+# --------------------------------------------------------- multi-coil MRI
+def mri_workspace_size(N: int, Nc: int, B: int) -> int:
+    return int(_lib.skei_mri_workspace_size(N, Nc, B))
+
+
+def _mri_dims(maps):
+    _dev(maps, "maps", torch.float32)
+    if maps.dim() != 4 or maps.shape[1] != 2 or maps.shape[2] != maps.shape[3]:
+        raise ValueError("maps must be [Nc, 2, N, N]")
+    return maps.shape[0], maps.shape[-1]
+
+
+def mri_fwd(x, maps, mask=None, aux=None, alpha=1.0, xw=None, out=None, work=None):
+    """k = alpha (aux - M F (C (xw x))) or alpha M F (C (xw x)); x [B, 2, N, N]
+    planar, xw a real [N, N] weight (None = 1)."""
+    Nc, N = _mri_dims(maps)
+    B = x.shape[0]
+    _dev(x, "x", torch.float32, (B, 2, N, N))
+    if mask is not None:
+        _dev(mask, "mask", torch.float32, (N, N))
+    if aux is not None:
+        _dev(aux, "aux", torch.float32, (B, Nc, 2, N, N))
+    if xw is not None:
+        _dev(xw, "xw", torch.float32, (N, N))
+    out = torch.empty((B, Nc, 2, N, N), dtype=torch.float32, device=x.device) \
+        if out is None else out
+    _dev(out, "out", torch.float32, (B, Nc, 2, N, N))
+    nb = mri_workspace_size(N, Nc, B)
+    w = _work(nb, x.device, work)
+    _check(_lib.skei_mri_fwd(N, Nc, B, _ptr(x), _ptr(maps), _ptr(mask), _ptr(xw), _ptr(aux),
+                             float(alpha), _ptr(out), _ptr(w), nb, _stream()), "skei_mri_fwd")
+    return out
+
+
+def mri_adj(k, maps, mask=None, dinv=None, alpha=1.0, beta=0.0, out=None, work=None):
+    """x = alpha dinv sum_c conj(C_c) F^H (M k_c) + beta x; k [B, Nc, 2, N, N]."""
+    Nc, N = _mri_dims(maps)
+    B = k.shape[0]
+    _dev(k, "k", torch.float32, (B, Nc, 2, N, N))
+    if mask is not None:
+        _dev(mask, "mask", torch.float32, (N, N))
+    if dinv is not None:
+        _dev(dinv, "dinv", torch.float32, (N, N))
+    out = torch.empty((B, 2, N, N), dtype=torch.float32, device=k.device) if out is None else out
+    _dev(out, "out", torch.float32, (B, 2, N, N))
+    nb = mri_workspace_size(N, Nc, B)
+    w = _work(nb, k.device, work)
+    _check(_lib.skei_mri_adj(N, Nc, B, _ptr(k), _ptr(maps), _ptr(mask), _ptr(dinv), float(alpha),
+                             float(beta), _ptr(out), _ptr(w), nb, _stream()), "skei_mri_adj")
+    return out
+
+
+def mri_dinv(maps, out=None):
+    Nc, N = _mri_dims(maps)
+    out = torch.empty((N, N), dtype=torch.float32, device=maps.device) if out is None else out
+    _dev(out, "out", torch.float32, (N, N))
+    _check(_lib.skei_mri_dinv(N, Nc, _ptr(maps), _ptr(out), _stream()), "skei_mri_dinv")
+    return out
+
+
+def coil_mix(W, x, out=None):
+    """out[b, j] = sum_i W[j, i] x[b, i] for complex W (complex64 [n_out, n_in]
+    or float32 [n_out, n_in, 2]) and planar coil data x [B, n_in, 2, ...]."""
+    if W.is_complex():
+        W = torch.view_as_real(W.to(torch.complex64)).contiguous()
+    _dev(W, "W", torch.float32)
+    n_out, n_in = W.shape[0], W.shape[1]
+    _dev(x, "x", torch.float32)
+    if x.dim() < 3 or x.shape[1] != n_in or x.shape[2] != 2:
+        raise ValueError("x must be [B, n_in, 2, ...]")
+    B, plane = x.shape[0], x[0, 0, 0].numel()
+    shape = (B, n_out, 2) + tuple(x.shape[3:])
+    out = torch.empty(shape, dtype=torch.float32, device=x.device) if out is None else out
+    _dev(out, "out", torch.float32, shape)
+    _check(_lib.skei_coil_mix(plane, B, n_in, n_out, _ptr(W), _ptr(x), _ptr(out), _stream()),
+           "skei_coil_mix")
+    return out
 
 
 # ------------------------------------------------------- batched schedule
