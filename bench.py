@@ -678,6 +678,66 @@ def ttt_bn_suite(S, dev, stream, channels=16, layers=4):
                                                         3)}}), flush=True)
 
 
+def mri_suite(S, dev, stream, N=128, Nc=15, accel=4, G=1, mc=2):
+    """Multi-coil MRI (Sec. 3.4, Algorithm 3) at 128^2, 15 coils, 4x
+    undersampling: the operators' times, and the EI step (residual stand-in
+    network, one rotation per step) with all 15 coils, with a random subset
+    of `mc` coils per step (SkEI, subsampling sketch) and with the coil
+    sketch of `mc` coils (C-SkEI: 15 PCA virtual coils, R = 1 kept, the rest
+    mixed by a Rademacher block)."""
+    import torch
+    from paper_2411_05771_gb300 import inputs as I
+    from paper_2411_05771_gb300.mri import CoilSketch, CskArm
+    f32 = dict(dtype=torch.float32, device=dev)
+    maps = torch.tensor(I.coil_maps(Nc, N), **f32)
+    mask = torch.tensor(I.undersampling_mask(N, accel), **f32)
+    x_gt = torch.tensor(I.complex_phantom(0, N), **f32)[None]
+    y = S.mri_fwd(x_gt, maps, mask)
+    dinv = S.mri_dinv(maps)
+    x0 = S.mri_adj(y, maps, mask, dinv)
+    k = torch.empty_like(y)
+    xo = torch.empty_like(x0)
+    w = torch.empty(S.mri_workspace_size(N, Nc, 1), dtype=torch.uint8, device=dev)
+    ops = {"A (15 coils)": lambda: S.mri_fwd(x0, maps, mask, out=k, work=w),
+           "A^H (15 coils)": lambda: S.mri_adj(y, maps, mask, out=xo, work=w),
+           "A^dagger (15 coils)": lambda: S.mri_adj(y, maps, mask, dinv, out=xo, work=w)}
+    op_us = {name: round(time_graph(fn, stream), 2) for name, fn in ops.items()}
+    # arms
+    rng = np.random.default_rng(0)
+    g = torch.tensor(rng.uniform(0, 360, (1, G)), dtype=torch.float64, device=dev)
+    res = {}
+    full = CskArm(x0, y, maps, mask, dinv, G)
+    full.g.copy_(g)
+    res["EI (15 coils)"] = time_graph(full.step, stream)
+    # SkEI: a random subset of mc coils, selected inside every step
+    sel = np.zeros((mc, Nc), dtype=np.complex64)
+    sel[np.arange(mc), rng.choice(Nc, mc, replace=False)] = 1.0
+    Wsel = torch.tensor(sel, device=dev)
+    maps_s = S.coil_mix(Wsel, maps[None])[0].contiguous()
+    y_s = S.coil_mix(Wsel, y)
+    dinv_s = S.mri_dinv(maps_s)
+    sub = CskArm(x0, y_s, maps_s, mask, dinv_s, G)
+    sub.g.copy_(g)
+
+    def sk_step():
+        S.coil_mix(Wsel, maps[None], out=maps_s[None])
+        S.coil_mix(Wsel, y, out=y_s)
+        S.mri_dinv(maps_s, out=dinv_s)
+        sub.step()
+    res[f"SkEI ({mc} of {Nc} coils)"] = time_graph(sk_step, stream)
+    cs = CoilSketch(y, maps, Nc, 1, I.rademacher(rng, (mc - 1, Nc - 1)))
+    csk = CskArm(x0, cs.y, cs.maps, mask, cs.dinv, G)
+    csk.g.copy_(g)
+    res[f"C-SkEI ({mc} sketched coils)"] = time_graph(csk.step, stream)
+    base = res["EI (15 coils)"]
+    print(json.dumps({"suite": f"mri-{N}x{N}-{Nc}coils-{accel}x", "op_us": op_us,
+                      "step_us": {k_: round(v, 2) for k_, v in res.items()},
+                      "steps_per_s": {k_: round(1e6 / v, 1) for k_, v in res.items()},
+                      "speedup_vs_EI": {k_: round(base / v, 3) for k_, v in res.items()},
+                      "network": "F(u) = u + theta", "G": G,
+                      "launches_per_step": CskArm.launches_per_step}), flush=True)
+
+
 def suite(S, dev, stream):
     """The measurements behind the per-workload table: single operators
     (64^2 with 60 views; 8 x 256^2 with 180 views, full and a 45-angle
@@ -759,6 +819,7 @@ def suite(S, dev, stream):
           flush=True)
 
     ttt_bn_suite(S, dev, stream)
+    mri_suite(S, dev, stream)
 
     # Theorem 1 on an explicit 32^2, 100-view A (probe.theorem1)
     from paper_2411_05771_gb300.probe import theorem1
