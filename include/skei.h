@@ -180,6 +180,16 @@ int skei_backproject_adj_multi_ws(skei_plan plan, const skei_job *jobs, int njob
 int skei_filter(skei_plan plan, int dtype, const void *p, int rows, float scale,
                 void *q, void *stream);
 
+/* skei_filter_fft: the same linear convolution through the FFT: two rows at a
+ * time packed as one complex row, zero padded to the plan's power of two
+ * L >= 2 n_det - 1, times the exact spectrum of the taps, inverse FFT.  Equal
+ * to skei_filter up to FP32 rounding (not bitwise).  O(L log L) per row pair
+ * instead of O(n_det^2) per row; at 725-bin rows the direct form is still
+ * faster on GB300, so the EI step keeps it.  Plans with n_det < 64 or
+ * L > 4096 run the direct form.  p and q must not alias. */
+int skei_filter_fft(skei_plan plan, int dtype, const void *p, int rows, float scale,
+                    void *q, void *stream);
+
 /* skei_backproject: x = alpha * B_S q + beta * x (unscaled back-projection).
  *   q [B][m][n_det] (dtype);  x [B][N][N] (dtype). */
 int skei_backproject(skei_plan plan, int dtype, const void *q, int B,

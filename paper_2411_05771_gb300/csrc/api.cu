@@ -285,7 +285,7 @@ int ei_fwd_impl(skei_plan p, const T *x1, const T *y, int B, const int *mc_idx, 
   } else if ((rc = launch_band_jobs(p, OP_JOSEPH, J, st))) {
     return rc;
   }
-  if ((rc = launch_filter<float, float>(p, pbuf, BG * sk_m, (float)(kPi / sk_m), qbuf, st)))
+  if ((rc = launch_filter_step<float, float>(p, pbuf, BG * sk_m, (float)(kPi / sk_m), qbuf, st)))
     return rc;
   Jobs Jz{};
   Jz.njobs = 1;
@@ -315,7 +315,8 @@ int ei_bwd_impl(skei_plan p, const T *r, const T *g_x2, const T *g_z, int B, con
                                       reinterpret_cast<float *>(work + w.band_off),
                                       w.band_floats, st)))
       return rc;
-    if ((rc = launch_filter<float, float>(p, ubuf, BG * sk_m, (float)(kPi / sk_m), vbuf, st)))
+    if ((rc = launch_filter_step<float, float>(p, ubuf, BG * sk_m, (float)(kPi / sk_m), vbuf,
+                                               st)))
       return rc;
     // one launch: g_x1 = -2 mc_coef A_mc^T r (MC term) and
     // gtot = g_x2 + A_S^T v (EI term)
@@ -507,6 +508,21 @@ int skei_filter(skei_plan plan, int dtype, const void *p, int rows, float scale,
                                        as_stream(stream));
   return launch_filter<bf16, bf16>(plan, (const bf16 *)p, rows, scale, (bf16 *)q,
                                    as_stream(stream));
+}
+
+int skei_filter_fft(skei_plan plan, int dtype, const void *p, int rows, float scale, void *q,
+                    void *stream) {
+  SKEI_TRY(check_plan(plan));
+  SKEI_TRY(check_dtype(dtype));
+  if (rows < 1) return set_error(SKEI_EINVAL, "rows=%d must be >= 1", rows);
+  SKEI_TRY(check_dev_ptr(p, "p"));
+  SKEI_TRY(check_dev_ptr(q, "q"));
+  if (p == q) return set_error(SKEI_EINVAL, "filter: p and q must not alias");
+  if (dtype == SKEI_F32)
+    return launch_filter_fft<float, float>(plan, (const float *)p, rows, scale, (float *)q,
+                                           as_stream(stream));
+  return launch_filter_fft<bf16, bf16>(plan, (const bf16 *)p, rows, scale, (bf16 *)q,
+                                       as_stream(stream));
 }
 
 int skei_backproject(skei_plan plan, int dtype, const void *q, int B, const int *idx, int m,

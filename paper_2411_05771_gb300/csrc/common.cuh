@@ -68,6 +68,11 @@ struct skei_plan_s {
   std::vector<double> angles_deg;
   skei::AngleConst *d_ang = nullptr;  // [n_angles]
   int *d_status = nullptr;            // bit 0: bad angle index seen
+  // FFT form of the Ram-Lak filter: length fft_len (a power of two
+  // >= 2 n_det - 1; 0 = not available) and the real spectrum of the taps
+  // h(n), |n| < n_det, sampled on it
+  int fft_len = 0;
+  float *d_hspec = nullptr;
 };
 
 namespace skei {
@@ -390,6 +395,17 @@ int launch_backproject_adj(skei_plan p, const Tin *x, int B, const int *idx,
 template <typename Tin, typename Tout>
 int launch_filter(skei_plan p, const Tin *in, int rows, float scale, Tout *out,
                   cudaStream_t st);
+// The same through the plan's FFT form (falls back to the direct form when
+// the plan has none).
+template <typename Tin, typename Tout>
+int launch_filter_fft(skei_plan p, const Tin *in, int rows, float scale, Tout *out,
+                      cudaStream_t st);
+// The form the EI step uses (build-time choice).
+template <typename Tin, typename Tout>
+int launch_filter_step(skei_plan p, const Tin *in, int rows, float scale, Tout *out,
+                       cudaStream_t st);
+// Plan set-up of the FFT form (host: the spectrum in FP64, then upload).
+int make_filter_spectrum(skei_plan p);
 // Rotation: out[b][g][ch] = T_g x[b][ch] (Ch channels share each angle).
 template <typename Tin, typename Tout>
 int launch_rotate(const Tin *x, int B, int N, const double *g_deg, int G,

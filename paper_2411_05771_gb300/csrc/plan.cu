@@ -181,9 +181,11 @@ int skei_plan_create(int N, int n_det, int n_angles, const double *angles_deg,
              (e = cudaMemset(p->d_status, 0, sizeof(int))) != cudaSuccess) {
     rc = cuda_error(e, "skei_plan_create: upload");
   }
+  if (rc == SKEI_OK) rc = make_filter_spectrum(p);
   if (rc != SKEI_OK) {
     cudaFree(p->d_ang);
     cudaFree(p->d_status);
+    cudaFree(p->d_hspec);
     delete p;
     return rc;
   }
@@ -195,6 +197,7 @@ int skei_plan_destroy(skei_plan p) {
   if (!p) return SKEI_OK;
   cudaFree(p->d_ang);
   cudaFree(p->d_status);
+  cudaFree(p->d_hspec);
   p->d_ang = nullptr;
   delete p;
   return SKEI_OK;

@@ -306,3 +306,22 @@ def test_adjoint_jobs_sharing_the_sketch_match_single_calls(S, N, n_ang, B, m):
     ang = plan.angles_deg if idx_np is None else O.select(plan.angles_deg, idx_np)
     assert rel(host(o0), -0.5 * O.proj_adj(host(r), ang, N)) <= FP32_TOL
     assert rel(host(o1), O.proj_adj(host(v), ang, N) + host(aux)) <= FP32_TOL
+
+
+@pytest.mark.parametrize("N,rows", [(20, 7), (64, 60), (100, 31), (256, 180), (512, 120),
+                                    (1000, 5)])
+def test_filter_fft_matches_oracle(S, N, rows):
+    """The FFT form of H: the same linear convolution (zero padding to a power
+    of two >= 2 n_det - 1), odd and even row counts, short rows (direct form)."""
+    plan = S.Plan(N, 4)
+    rng = np.random.default_rng(N + rows)
+    p = rng.standard_normal((rows, plan.n_det))
+    got = S.filter_fft(plan, dev(p), 0.5)
+    assert rel(host(got), 0.5 * O.ramlak(p)) <= FP32_TOL
+    pb = dev(p).to(torch.bfloat16)
+    gb = S.filter_fft(plan, pb, 0.5)
+    assert gb.dtype == torch.bfloat16
+    assert rel(host(gb), 0.5 * O.ramlak(host(pb))) <= 1e-2
+    with pytest.raises(RuntimeError):
+        x = dev(p)
+        S.filter_fft(plan, x, 1.0, out=x)
