@@ -251,7 +251,15 @@ __global__ void __launch_bounds__(kFilterThreads)
 //   row = R0 + j s + i c,   col = C0 + j c - i s,
 // R0 = h(1 - s - c), C0 = h(1 + s - c), h = (N-1)/2; bilinear weights
 // (1-fr)(1-fc), (1-fr)fc, fr(1-fc), fr fc; taps outside the image are 0.
-constexpr int kRotX = 32, kRotY = 8, kRotQ = 8;  // CTA tile 32 x 64, 8 pixels/thread
+// Pixels per thread (knobs; measured on GB300 at 4 x 512^2: 8 for the
+// rotation, 2 for its transpose; 4 / 2 and 1 / 4 were slower).
+#ifndef SKEI_ROT_Q
+#define SKEI_ROT_Q 8
+#endif
+#ifndef SKEI_ROTADJ_Q
+#define SKEI_ROTADJ_Q 2
+#endif
+constexpr int kRotX = 32, kRotY = 8, kRotQ = SKEI_ROT_Q;  // CTA tile 32 x 8 kRotQ
 constexpr int kRotThreads = kRotX * kRotY;
 
 struct RotConst {
@@ -314,7 +322,7 @@ __global__ void __launch_bounds__(kRotThreads)
 // rotated position of (a, bb), i.e. among 3x3 candidates; each candidate's
 // sample is recomputed exactly in the forward's fixed-point form and
 // weighted by its exact tap weights, reproducing the forward's bitwise.
-constexpr int kAdjT = 16, kAdjQ = 2;  // CTA tile 16 x 32, 2 pixels/thread
+constexpr int kAdjT = 16, kAdjQ = SKEI_ROTADJ_Q;  // CTA tile 16 x 16 kAdjQ
 constexpr int kMaxG = 64;
 
 // Linear-interpolation weight of a sample at fixed-point offset D (|D| < 8,

@@ -133,7 +133,7 @@ def test_ttt_bn_loss_and_gradient_vs_oracle(S, B):
     loss = skei_loss(plan, net(x0_d), y_d, net, g_d, None, idx_d, lam, mc_scale)
     (grad,) = torch.autograd.grad(loss, [net.bn])
     ref = O.ttt_bn_loss(wts.bn, wts.conv, x0, y, ang, None, idx, g, lam, mc_scale)
-    assert abs(float(loss) - ref) <= 1e-4 * abs(ref)
+    assert abs(float(loss.detach()) - ref) <= 1e-4 * abs(ref)
     h = 1e-5
     fd = np.zeros_like(wts.bn)
     for i in range(wts.bn.size):
