@@ -433,13 +433,56 @@ __device__ __forceinline__ void bpadj_lines(const AngleConst &C, int k, int s0, 
   }
 }
 
-// One task: the NI images b0.. of job J, angles [a_begin, a_begin + g.AB)
-// of its list, computed by the 8 CTAs of this cluster.  Ends with a cluster
-// barrier, after which the CTA's shared memory may be reused.
+// The list positions spos[0 .. na) of slots a_begin .. a_begin + na - 1 of
+// the mode-partitioned order of an angle list (the row-mode angles in list
+// order, then the others: column mode and bad indices), so that a block of
+// consecutive slots stages its band in one layout; at most one block of a
+// launch holds both.  The list lives on the device (a sketch drawn per
+// step), so every CTA ranks it: a count, then a ballot scan per chunk.
+__device__ __forceinline__ bool row_mode_at(const int *idx, int i, int n_angles,
+                                            const AngleConst *ang) {
+  const int ai = idx ? idx[i] : i;
+  return ai >= 0 && ai < n_angles && ang[ai].mode == 1;
+}
+
+__device__ void partition_block(const int *idx, int m, int n_angles, const AngleConst *ang,
+                                int a_begin, int na, int *spos, int *wsum) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int rows_total = 0;
+  for (int c0 = 0; c0 < m; c0 += kThreads) {
+    const int i = c0 + tid;
+    const unsigned bal = __ballot_sync(0xffffffffu, i < m && row_mode_at(idx, i, n_angles, ang));
+    if (lane == 0) wsum[warp] = __popc(bal);
+    __syncthreads();
+    for (int w = 0; w < kWarps; ++w) rows_total += wsum[w];
+    __syncthreads();
+  }
+  int base = 0;
+  for (int c0 = 0; c0 < m; c0 += kThreads) {
+    const int i = c0 + tid;
+    const bool f = i < m && row_mode_at(idx, i, n_angles, ang);
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) wsum[warp] = __popc(bal);
+    __syncthreads();
+    int before = base;   // row-mode angles before position i
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    before += __popc(bal & ((1u << lane) - 1u));
+    const int slot = f ? before : rows_total + (i - before);
+    if (i < m && slot >= a_begin && slot < a_begin + na) spos[slot - a_begin] = i;
+    for (int w = 0; w < kWarps; ++w) base += wsum[w];
+    __syncthreads();
+  }
+}
+
+// One task: the NI images b0.. of job J, slots [a_begin, a_begin + g.AB)
+// of the mode-partitioned order of its angle list, computed by the 8 CTAs of
+// this cluster.  Ends with a cluster barrier, after which the CTA's shared
+// memory may be reused.
 template <int OP, int NI>
 __device__ __forceinline__ void band_task(const Job &J, int b0, int a_begin, const BandGeom &g,
                                           const AngleConst *ang, int *status, float *smem,
-                                          AngleConst *sc, int *sai, cg::cluster_group &cluster) {
+                                          AngleConst *sc, int *sai, int *spos, int *wsum,
+                                          cg::cluster_group &cluster) {
   const int tid = threadIdx.x;
   const int band = (int)cluster.block_rank();
   if (a_begin >= J.m) return;  // uniform over the cluster: no peer waits for it
@@ -448,11 +491,12 @@ __device__ __forceinline__ void band_task(const Job &J, int b0, int a_begin, con
   float *part = smem;                                       // [AB][n_det][NI]
   float *buf = smem + band_part_floats(g);                  // [SB][P][NI], 16-byte aligned
 
+  const int *idx = job_idx(J, b0);
+  partition_block(idx, J.m, g.n_angles, ang, a_begin, na, spos, wsum);
   if (tid < kMaxAB) {
     int ai = -1;
-    const int *idx = job_idx(J, b0);
     if (tid < na) {
-      ai = idx ? idx[a_begin + tid] : a_begin + tid;
+      ai = idx ? idx[spos[tid]] : spos[tid];
       if (ai < 0 || ai >= g.n_angles) {
         if (band == 0) atomicOr(status, 1);
         ai = -1;
@@ -526,7 +570,7 @@ __device__ __forceinline__ void band_task(const Job &J, int b0, int a_begin, con
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
       const int b = b0 + i;
-      const size_t o = ((size_t)b * J.m + a_begin + a) * nd + k;
+      const size_t o = ((size_t)b * J.m + spos[a]) * nd + k;
       float v;
       if (ai < 0) {
         v = 0.0f;
@@ -549,7 +593,7 @@ __global__ void __cluster_dims__(kBands, 1, 1) __launch_bounds__(kThreads)
   pdl_enter();
   extern __shared__ float4 smem4[];
   __shared__ AngleConst sc[kMaxAB];
-  __shared__ int sai[kMaxAB];
+  __shared__ int sai[kMaxAB], spos[kMaxAB], wsum[kWarps];
   cg::cluster_group cluster = cg::this_cluster();
   // the job and image group of this cluster
   const int z = blockIdx.z;
@@ -561,10 +605,10 @@ __global__ void __cluster_dims__(kBands, 1, 1) __launch_bounds__(kThreads)
   float *smem = reinterpret_cast<float *>(smem4);
   if (ni == 4)
     band_task<OP, 4>(J, b0, blockIdx.y * args.g4.AB, args.g4, args.ang, args.status, smem, sc,
-                     sai, cluster);
+                     sai, spos, wsum, cluster);
   else
     band_task<OP, 1>(J, b0, blockIdx.y * args.g1.AB, args.g1, args.ang, args.status, smem, sc,
-                     sai, cluster);
+                     sai, spos, wsum, cluster);
 }
 
 // Persistent form over the tasks of a batch of instances (plans of their
@@ -578,7 +622,7 @@ __global__ void __cluster_dims__(kBands, 1, 1) __launch_bounds__(kThreads)
                       int *queue) {
   extern __shared__ float4 smem4[];
   __shared__ AngleConst sc[kMaxAB];
-  __shared__ int sai[kMaxAB];
+  __shared__ int sai[kMaxAB], spos[kMaxAB], wsum[kWarps];
   __shared__ int s_task;
   cg::cluster_group cluster = cg::this_cluster();
   const bool leader = cluster.block_rank() == 0 && threadIdx.x == 0;
@@ -596,10 +640,10 @@ __global__ void __cluster_dims__(kBands, 1, 1) __launch_bounds__(kThreads)
     const int b0 = tk.y >> 3, ni = tk.y & 7;
     if (ni == 4) {
       const BandGeom g = band_geom(it.N, it.n_det, it.n_angles, OP, AB, 4);
-      band_task<OP, 4>(J, b0, tk.z, g, it.ang, it.status, smem, sc, sai, cluster);
+      band_task<OP, 4>(J, b0, tk.z, g, it.ang, it.status, smem, sc, sai, spos, wsum, cluster);
     } else {
       const BandGeom g = band_geom(it.N, it.n_det, it.n_angles, OP, AB, 1);
-      band_task<OP, 1>(J, b0, tk.z, g, it.ang, it.status, smem, sc, sai, cluster);
+      band_task<OP, 1>(J, b0, tk.z, g, it.ang, it.status, smem, sc, sai, spos, wsum, cluster);
     }
   }
   if (leader) queue_retire(queue, gridDim.x / kBands);
@@ -781,8 +825,11 @@ int band_batch_clusters(size_t smem, int *clusters) {
 #ifndef SKEI_PART_SBL1
 #define SKEI_PART_SBL1 16
 #endif
+#ifndef SKEI_PART_AB
+#define SKEI_PART_AB 0        // angles per partial CTA (0: from SKEI_PART_CTAS)
+#endif
 #ifndef SKEI_PART_MINB4
-#define SKEI_PART_MINB4 3     // CTAs per SM the registers of the 4-image partial kernel allow
+#define SKEI_PART_MINB4 2     // CTAs per SM the registers of the 4-image partial kernel allow
 #endif
 #ifndef SKEI_PART_MINB1
 #define SKEI_PART_MINB1 1     // the same for single images
@@ -794,7 +841,7 @@ int band_batch_clusters(size_t smem, int *clusters) {
 #define SKEI_PART_GROUP 4
 #endif
 #ifndef SKEI_PART_CTAS
-#define SKEI_PART_CTAS 3      // target CTAs per SM when choosing the angle block
+#define SKEI_PART_CTAS 2      // CTAs per SM of the one wave the angle block aims at
 #endif
 constexpr int kMaxABP = 32;      // angles per partial CTA
 
@@ -846,17 +893,18 @@ template <int OP, int NI>
 __device__ __forceinline__ void partial_task(const Job &J, float *part, int b0, int band,
                                              int a_begin, int AB, int nbands, const BandGeom &g,
                                              const AngleConst *ang, int *status, float *buf,
-                                             AngleConst *sc, int *sai) {
+                                             AngleConst *sc, int *sai, int *spos, int *wsum) {
   const int tid = threadIdx.x;
   const int na = min(AB, J.m - a_begin);
   const int nd = g.n_det, N = g.N;
   const int s0 = band * g.SB, s1 = min(N, s0 + g.SB);
   if (na <= 0 || s0 >= N) return;  // uniform over the CTA
+  const int *idx = job_idx(J, b0);
+  partition_block(idx, J.m, g.n_angles, ang, a_begin, na, spos, wsum);
   if (tid < kMaxABP) {
     int ai = -1;
-    const int *idx = job_idx(J, b0);
     if (tid < na) {
-      ai = idx ? idx[a_begin + tid] : a_begin + tid;
+      ai = idx ? idx[spos[tid]] : spos[tid];
       if (ai < 0 || ai >= g.n_angles) {
         if (band == 0) atomicOr(status, 1);
         ai = -1;
@@ -882,7 +930,7 @@ __device__ __forceinline__ void partial_task(const Job &J, float *part, int b0, 
     for (int a = 0; a < na; ++a) {
       const bool live = sai[a] >= 0;
       if (live ? sc[a].mode != mode : mode != 0) continue;   // dead angles: written once
-      float *pa = part + ((size_t)b0 * nbands + band) * J.m * nd + (size_t)(a_begin + a) * nd;
+      float *pa = part + ((size_t)b0 * nbands + band) * J.m * nd + (size_t)spos[a] * nd;
       for (int k = tid; k < nd; k += kThreads) {
         float acc[NI];
 #pragma unroll
@@ -910,7 +958,7 @@ __global__ void __launch_bounds__(kThreads, NI == 4 ? SKEI_PART_MINB4 : SKEI_PAR
   pdl_enter();
   extern __shared__ float4 smem4[];
   __shared__ AngleConst sc[kMaxABP];
-  __shared__ int sai[kMaxABP];
+  __shared__ int sai[kMaxABP], spos[kMaxABP], wsum[kWarps];
   const int z = blockIdx.z;
   const Job &J0 = args.jobs.j[0];
   const int q0 = quads(J0.nimg, args.gmax[0]);
@@ -921,7 +969,7 @@ __global__ void __launch_bounds__(kThreads, NI == 4 ? SKEI_PART_MINB4 : SKEI_PAR
   const int b0 = NI == 4 ? 4 * zz : 4 * quads(J.nimg, args.gmax[jn]) + zz;
   partial_task<OP, NI>(J, args.part + args.off[jn], b0, blockIdx.x, blockIdx.y * args.AB,
                        args.AB, args.nbands, NI == 4 ? args.g4 : args.g1, args.ang, args.status,
-                       reinterpret_cast<float *>(smem4), sc, sai);
+                       reinterpret_cast<float *>(smem4), sc, sai, spos, wsum);
 }
 
 // out[b][a][k] = epilogue(sum over bands, in order, of the band sums).
@@ -1034,11 +1082,16 @@ int launch_band_partial(skei_plan p, const Jobs &jobs, float *work, size_t work_
     n1 += jobs.j[q].nimg - 4 * q4;
   }
   if (ngroups > 65535) return set_error(SKEI_EINVAL, "too many images in one launch");
-  // angles per CTA: enough CTAs for SKEI_PART_CTAS per SM
-  const long long want = (long long)sm_count() * SKEI_PART_CTAS;
-  long long blocks = (want + (long long)nbands * ngroups - 1) / ((long long)nbands * ngroups);
-  blocks = std::max(1LL, std::min(blocks, (long long)m_max));
-  int AB = (int)((m_max + blocks - 1) / blocks);
+  // angles per CTA: the smallest block whose CTAs fit one wave of
+  // SKEI_PART_CTAS per SM (measured on GB300 at 64 bands x 30 angles: a
+  // CTA costs about one angle of staging plus its angles, and a short
+  // second wave or a lone CTA per SM costs more than larger blocks)
+  const long long slots = (long long)sm_count() * SKEI_PART_CTAS;
+  int AB = 1;
+  while (AB < std::min(m_max, kMaxABP) &&
+         (long long)nbands * ngroups * ((m_max + AB - 1) / AB) > slots)
+    ++AB;
+  if (SKEI_PART_AB > 0) AB = SKEI_PART_AB;
   AB = std::max(1, std::min(AB, kMaxABP));
   const int nblk = (m_max + AB - 1) / AB;
   PartArgs a{jobs, p->d_ang, p->d_status, g1, g4, {gmj[0], gmj[1]}, AB, nbands, work,
