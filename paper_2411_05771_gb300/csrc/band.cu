@@ -56,6 +56,9 @@ namespace {
 #ifndef SKEI_BAND_GROUP_BPADJ
 #define SKEI_BAND_GROUP_BPADJ 4
 #endif
+#ifndef SKEI_BAND_SB1_FWD
+#define SKEI_BAND_SB1_FWD 32   // staged lines per sub-band of the single-image forward (16 or 32)
+#endif
 #ifndef SKEI_BAND_SB4
 #define SKEI_BAND_SB4 8
 #endif
@@ -109,7 +112,7 @@ __host__ __device__ __forceinline__ BandGeom band_geom(int N, int n_det, int n_a
   if (NI == 1) {
     // A: 32 staged lines (fewer per-ray range setups); B^T: 16 (its per-bin
     // work per line is larger, and the smaller band leaves room for more CTAs)
-    const int sb = op == OP_JOSEPH ? 32 : 16;
+    const int sb = op == OP_JOSEPH ? SKEI_BAND_SB1_FWD : 16;
     g.SB = g.R < sb ? g.R : sb;
     // transposed staging writes lines 4q..4q+3 of (32 / (SB/4)) positions
     // per warp: a pitch = 2 mod 8 (16 lines) or odd (32 lines) keeps them in
