@@ -652,19 +652,6 @@ __global__ void __cluster_dims__(kBands, 1, 1) __launch_bounds__(kThreads)
   if (leader) queue_retire(queue, gridDim.x / kBands);
 }
 
-int sm_count() {
-  static int count[64] = {0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) dev = 0;
-  if (!count[dev]) {
-    int c = 0;
-    cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
-    count[dev] = c > 0 ? c : 1;
-  }
-  return count[dev];
-}
-
 template <int OP>
 int set_band_smem(size_t smem) {
   static size_t configured[64] = {0};

@@ -142,6 +142,7 @@ inline int check_launch(const char *where) {
 
 int check_plan(skei_plan p);
 int check_dtype(int dtype);
+int sm_count();   // SMs of the current device
 int check_dev_ptr(const void *p, const char *name);
 int check_idx(skei_plan p, const int *idx, int m);
 int check_batch(int B);

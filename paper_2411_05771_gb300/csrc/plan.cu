@@ -55,6 +55,20 @@ int check_idx(skei_plan p, const int *idx, int m) {
   return SKEI_OK;
 }
 
+// SM count of the current device (cached per device).
+int sm_count() {
+  static int count[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!count[dev]) {
+    int c = 0;
+    cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+    count[dev] = c > 0 ? c : 1;
+  }
+  return count[dev];
+}
+
 int check_batch(int B) {
   if (B < 1 || B > 65535) return set_error(SKEI_EINVAL, "batch B=%d outside [1, 65535]", B);
   return SKEI_OK;

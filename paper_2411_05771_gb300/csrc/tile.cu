@@ -37,10 +37,11 @@
 namespace skei {
 namespace {
 
-// Build-time tuning knobs: tile height (rows), 4 or 8; angle split (1 or
-// 2): with 2 (measured faster for B on GB300), two warps share each tile
-// row, taking alternate angles of every chunk, and their sums are added in
-// a fixed order at the end.
+// Build-time tuning knobs: the largest tile height (rows, <= 8; a launch
+// picks between 4 and this to balance its CTAs over the SMs, the batch
+// kernel uses it as is); angle split (1 or 2): with 2 (measured faster for
+// B on GB300), two warps share each tile row, taking alternate angles of
+// every chunk, and their sums are added in a fixed order at the end.
 #ifndef SKEI_TILE_ROWS
 #define SKEI_TILE_ROWS 8
 #endif
@@ -124,7 +125,7 @@ __device__ __forceinline__ void tile_window(const Job &J, int b0, int c0, int na
                                             int bx) {
   const bool async = !J.in_bf16 && (!XTRA || !JX->in_bf16);
   float *win = sm.win[wb], *winx = sm.winx[wb];
-  for (int e = threadIdx.x; e < nac * kWin; e += kThreads) {
+  for (int e = threadIdx.x; e < nac * kWin; e += blockDim.x) {
     const int a = e / kWin, w = e - a * kWin;
     const int k = sm.kw0[slot][a] + w;
     const bool ok = sm.sai[slot][a] >= 0 && k >= 0 && k < nd;
@@ -161,9 +162,10 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
                                           int bx = 0) {
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  const int half = warp / kTH;             // which angles of each chunk
-  const int i_last = min(i0 + kTH, N) - 1, j_last = min(j0 + kTW, N) - 1;
-  const int i = i0 + warp % kTH;           // this thread's row
+  const int th = blockDim.x / (32 * kSplit);  // tile rows of this launch (<= kTH)
+  const int half = warp / th;              // which angles of each chunk
+  const int i_last = min(i0 + th, N) - 1, j_last = min(j0 + kTW, N) - 1;
+  const int i = i0 + warp % th;            // this thread's row
   const int jb = j0 + lane;                // its first column; then every 32nd
 
   float acc[NI][kPPT], accx[kPPT];
@@ -275,25 +277,25 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
     // the second half's sums through shared memory (the window is free)
     __syncthreads();
     float *red = sm.win[0];
-    const int t0 = tid % (32 * kTH);
+    const int t0 = tid % (32 * th);
     if (half == 1) {
 #pragma unroll
       for (int n = 0; n < NI; ++n)
 #pragma unroll
-        for (int q = 0; q < kPPT; ++q) red[(n * kPPT + q) * 32 * kTH + t0] = acc[n][q];
+        for (int q = 0; q < kPPT; ++q) red[(n * kPPT + q) * 32 * th + t0] = acc[n][q];
       if (XTRA)
 #pragma unroll
-        for (int q = 0; q < kPPT; ++q) sm.winx[0][q * 32 * kTH + t0] = accx[q];
+        for (int q = 0; q < kPPT; ++q) sm.winx[0][q * 32 * th + t0] = accx[q];
     }
     __syncthreads();
     if (half != 0) return;
 #pragma unroll
     for (int n = 0; n < NI; ++n)
 #pragma unroll
-      for (int q = 0; q < kPPT; ++q) acc[n][q] += red[(n * kPPT + q) * 32 * kTH + t0];
+      for (int q = 0; q < kPPT; ++q) acc[n][q] += red[(n * kPPT + q) * 32 * th + t0];
     if (XTRA)
 #pragma unroll
-      for (int q = 0; q < kPPT; ++q) accx[q] += sm.winx[0][q * 32 * kTH + t0];
+      for (int q = 0; q < kPPT; ++q) accx[q] += sm.winx[0][q * 32 * th + t0];
   }
   if (i >= N) return;
   // pixel q of the thread is column jb + 32 q: a warp stores 32 consecutive
@@ -327,10 +329,11 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs args) {
   extern __shared__ float4 tile_smem4[];
   TileSmem &sm = *reinterpret_cast<TileSmem *>(tile_smem4);
   const int z = blockIdx.z;
+  const int th = blockDim.x / (32 * kSplit);   // tile rows chosen by the launch
   const bool report = blockIdx.x == 0 && blockIdx.y == 0;
   if (args.merge) {
     // group z of job 1 (images 4z .. 4z+3) with image z of job 0
-    tile_task<OP, 4, true>(args.jobs.j[1], 4 * z, blockIdx.y * kTH, blockIdx.x * kTW, args.N,
+    tile_task<OP, 4, true>(args.jobs.j[1], 4 * z, blockIdx.y * th, blockIdx.x * kTW, args.N,
                            args.n_det, args.n_angles, args.ang, args.status, report, sm,
                            &args.jobs.j[0], z);
     return;
@@ -341,10 +344,10 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs args) {
   int b0, ni;
   group_at(J.nimg, z - (jn ? g0 : 0), &b0, &ni, args.gmax[jn]);
   if (ni == 4)
-    tile_task<OP, 4>(J, b0, blockIdx.y * kTH, blockIdx.x * kTW, args.N, args.n_det,
+    tile_task<OP, 4>(J, b0, blockIdx.y * th, blockIdx.x * kTW, args.N, args.n_det,
                      args.n_angles, args.ang, args.status, report, sm);
   else
-    tile_task<OP, 1>(J, b0, blockIdx.y * kTH, blockIdx.x * kTW, args.N, args.n_det,
+    tile_task<OP, 1>(J, b0, blockIdx.y * th, blockIdx.x * kTW, args.N, args.n_det,
                      args.n_angles, args.ang, args.status, report, sm);
 }
 
@@ -431,9 +434,23 @@ int launch_tile(skei_plan p, const Jobs &jobs, cudaStream_t st) {
   if (ngroups > 65535) return set_error(SKEI_EINVAL, "too many images in one launch");
   TileArgs a{jobs, p->N, p->n_det, p->n_angles, p->d_ang, p->d_status, merge,
              {gmax[0], gmax[1]}};
-  dim3 grid((p->N + kTW - 1) / kTW, (p->N + kTH - 1) / kTH, ngroups);
+  // tile rows th <= kTH: the fewest CTA rounds per SM times the rows each
+  // CTA covers (measured on GB300: 7 rows at 512^2, i.e. 296 CTAs for 304
+  // slots, beat 8 rows' 256 CTAs by 8 %)
+  const int cols = (p->N + kTW - 1) / kTW;
+  int th = kTH;
+  long long best = -1;
+  for (int t = kTH; t >= 4; --t) {
+    const long long ctas = (long long)cols * ((p->N + t - 1) / t) * ngroups;
+    const long long cost = (ctas + sm_count() - 1) / sm_count() * t;
+    if (best < 0 || cost < best) {
+      best = cost;
+      th = t;
+    }
+  }
+  dim3 grid(cols, (p->N + th - 1) / th, ngroups);
   SKEI_TRY(set_tile_kernel_smem<OP>());
-  launch_k(tile_kernel<OP>, grid, dim3(kThreads), kTileSmem, st, a);
+  launch_k(tile_kernel<OP>, grid, dim3(32 * th * kSplit), kTileSmem, st, a);
   return check_launch(OP == OP_JOSEPH_ADJ ? "joseph adjoint launch" : "back-projection launch");
 }
 
