@@ -818,11 +818,11 @@ int band_batch_clusters(size_t smem, int *clusters) {
 #ifndef SKEI_PART_AB
 #define SKEI_PART_AB 0        // angles per partial CTA (0: from SKEI_PART_CTAS)
 #endif
-#ifndef SKEI_PART_MINB4
-#define SKEI_PART_MINB4 2     // CTAs per SM the registers of the 4-image partial kernel allow
-#endif
+// The 4-image partial kernel comes in two register budgets: 128 registers
+// (2 CTAs per SM) for launches that fit one wave at 2 per SM, 80 (3 per SM)
+// for larger ones.
 #ifndef SKEI_PART_MINB1
-#define SKEI_PART_MINB1 1     // the same for single images
+#define SKEI_PART_MINB1 1     // CTAs per SM the single-image kernel's registers must allow
 #endif
 #ifndef SKEI_PART_SBL4
 #define SKEI_PART_SBL4 8
@@ -942,9 +942,8 @@ __device__ __forceinline__ int quads(int nimg, int gmax) { return gmax == 4 ? ni
 
 // One CTA: band blockIdx.x, angle block blockIdx.y, image group blockIdx.z
 // among the launch's groups of NI images (job 0's, then job 1's).
-template <int OP, int NI>
-__global__ void __launch_bounds__(kThreads, NI == 4 ? SKEI_PART_MINB4 : SKEI_PART_MINB1)
-    band_partial_kernel(const PartArgs args) {
+template <int OP, int NI, int MINB = (NI == 4 ? 2 : SKEI_PART_MINB1)>
+__global__ void __launch_bounds__(kThreads, MINB) band_partial_kernel(const PartArgs args) {
   pdl_enter();
   extern __shared__ float4 smem4[];
   __shared__ AngleConst sc[kMaxABP];
@@ -1020,7 +1019,7 @@ int part_layout(skei_plan p, const Jobs &jobs, int *nbands1, int *nbands4, size_
   return SKEI_OK;
 }
 
-template <int OP, int NI>
+template <int OP, int NI, int MINB>
 int set_partial_smem(size_t smem) {
   if (smem > 227 * 1024)
     return set_error(SKEI_EINVAL, "band of %zu bytes needs too much shared memory", smem);
@@ -1029,7 +1028,7 @@ int set_partial_smem(size_t smem) {
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
   if (smem > 48 * 1024 && smem > configured[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(band_partial_kernel<OP, NI>,
+    cudaError_t e = cudaFuncSetAttribute(band_partial_kernel<OP, NI, MINB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_error(e, "band partial kernel: shared memory attribute");
     configured[dev] = smem;
@@ -1072,29 +1071,43 @@ int launch_band_partial(skei_plan p, const Jobs &jobs, float *work, size_t work_
     n1 += jobs.j[q].nimg - 4 * q4;
   }
   if (ngroups > 65535) return set_error(SKEI_EINVAL, "too many images in one launch");
-  // angles per CTA: the smallest block whose CTAs fit one wave of
-  // SKEI_PART_CTAS per SM (measured on GB300 at 64 bands x 30 angles: a
-  // CTA costs about one angle of staging plus its angles, and a short
-  // second wave or a lone CTA per SM costs more than larger blocks)
+  // angles per CTA (measured on GB300: a CTA costs about one angle of
+  // staging plus its angles; a short second wave or a lone CTA per SM costs
+  // more than larger blocks): the smallest block whose CTAs fit one wave of
+  // SKEI_PART_CTAS (2) per SM with the 128-register kernel; where none does
+  // (many bands or images), about 3 CTAs per SM with the 80-register one
+  const long long units = (long long)nbands * ngroups;
+  const int ab_cap = std::min(m_max, kMaxABP);
   const long long slots = (long long)sm_count() * SKEI_PART_CTAS;
-  int AB = 1;
-  while (AB < std::min(m_max, kMaxABP) &&
-         (long long)nbands * ngroups * ((m_max + AB - 1) / AB) > slots)
-    ++AB;
+  int AB = 0;
+  for (int ab = 1; ab <= ab_cap && !AB; ++ab)
+    if (units * ((m_max + ab - 1) / ab) <= slots) AB = ab;
+  const bool one_wave = AB > 0;
+  if (!one_wave) {
+    long long blocks = (3LL * sm_count() + units - 1) / units;
+    blocks = std::max(1LL, std::min(blocks, (long long)m_max));
+    AB = (int)((m_max + blocks - 1) / blocks);
+  }
   if (SKEI_PART_AB > 0) AB = SKEI_PART_AB;
   AB = std::max(1, std::min(AB, kMaxABP));
   const int nblk = (m_max + AB - 1) / AB;
+  AB = (m_max + nblk - 1) / nblk;   // balanced blocks
   PartArgs a{jobs, p->d_ang, p->d_status, g1, g4, {gmj[0], gmj[1]}, AB, nbands, work,
              {off[0], off[1]}};
-  if (n4 > 0) {
-    SKEI_TRY((set_partial_smem<OP, 4>(part_smem(g4))));
-    launch_k(band_partial_kernel<OP, 4>, dim3(nbands, nblk, n4), dim3(kThreads), part_smem(g4),
-             st, a);
+  if (n4 > 0 && one_wave) {
+    SKEI_TRY((set_partial_smem<OP, 4, 2>(part_smem(g4))));
+    launch_k(band_partial_kernel<OP, 4, 2>, dim3(nbands, nblk, n4), dim3(kThreads),
+             part_smem(g4), st, a);
+  } else if (n4 > 0) {
+    SKEI_TRY((set_partial_smem<OP, 4, 3>(part_smem(g4))));
+    launch_k(band_partial_kernel<OP, 4, 3>, dim3(nbands, nblk, n4), dim3(kThreads),
+             part_smem(g4), st, a);
   }
   if (n1 > 0) {
-    SKEI_TRY((set_partial_smem<OP, 1>(part_smem(g1))));
-    launch_k(band_partial_kernel<OP, 1>, dim3(nbands, nblk, n1), dim3(kThreads), part_smem(g1),
-             st, a);
+    constexpr int m1 = SKEI_PART_MINB1;
+    SKEI_TRY((set_partial_smem<OP, 1, m1>(part_smem(g1))));
+    launch_k(band_partial_kernel<OP, 1, m1>, dim3(nbands, nblk, n1), dim3(kThreads),
+             part_smem(g1), st, a);
   }
   SKEI_TRY(check_launch("band partial sums launch"));
   int nimg = 0;
