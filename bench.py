@@ -98,6 +98,14 @@ SKETCHED = Workload()                                   # the headline arm
 PLAIN = Workload(m=N_VIEWS, mc_sketched=False, draw_m=SKETCH)   # full operators
 
 
+def workload_config():
+    """The workload keys both arms of the bench report."""
+    n_det = int(np.ceil(N_IMG * np.sqrt(2.0))) | 1
+    return {"workload": f"ttt-{N_IMG}x{N_IMG}-{N_VIEWS}views-{n_det}bins-sketch{SKETCH}-G{G_ROT}",
+            "N": N_IMG, "views": N_VIEWS, "n_det": n_det, "sketch": SKETCH, "G": G_ROT,
+            "B": BATCH, "lambda": LAM, "network": "F(u)=u+theta", "optimizer": "adam lr 5e-4"}
+
+
 def make_problem(wl=SKETCHED, seed=0):
     from paper_2411_05771_gb300 import inputs as I
     angs = I.uniform_angles(wl.views)
@@ -535,7 +543,7 @@ def reference_arm(args):
         "n_gpus": args.gpus, "steps": n, "warmup": min(args.warmup, 1),
         "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "ttt-512x512-60views-725bins-sketch30-G4", "arm": "sketched"},
+        "config": dict(workload_config(), arm="sketched"),
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{n} sketched TTT steps at 512^2 (FP64 C oracle, 1 thread)"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -1030,11 +1038,8 @@ def main():
             "vs_baseline": None,
             "dtype": args.dtype,
             "data": "synthetic",
-            "config": {"workload": "ttt-512x512-60views-725bins-sketch30-G4",
-                       "N": N_IMG, "views": N_VIEWS, "n_det": plan.n_det, "sketch": SKETCH,
-                       "G": G_ROT, "B": BATCH, "lambda": LAM, "network": "F(u)=u+theta",
-                       "optimizer": "adam lr 5e-4", "graph": True,
-                       "l2": "flushed between timed steps (256 MiB write, untimed)"},
+            "config": dict(workload_config(), graph=True,
+                           l2="flushed between timed steps (256 MiB write, untimed)"),
             "plain": {"value": K / (pl_ms * 1e-3), "ms_per_step": pl_ms / K, "dtype": "f32"},
             "speedup_vs_plain": pl_ms / sk_ms,
             "psnr": psnr_block(curve_sk, curve_pl, sk_ms / K, pl_ms / K),
