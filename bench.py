@@ -186,6 +186,11 @@ class Arm:
                                     16), dtype=torch.uint8, device=d)
         idx_all, g_all = step_params(1, wl)
         self.load_params(idx_all[0], g_all[0], 1)
+        # kernels per step: residual 1 + forward 4 (5 where its A launch
+        # sums bands) + residual 1 + loss 2 + backward 5 + Adam 1
+        mc_idx = self.idx if wl.mc_sketched else None
+        sk_idx = self.idx if self.sketched else None
+        self.launches_per_step = 14 + S.ei_fwd_form(plan, B, G, mc_idx, sk_idx, wl.per_sample)
 
     def pack_params(self, idx_all, g_all, first_step):
         """Host bytes of the draws of consecutive steps, one row per step, in
@@ -222,8 +227,6 @@ class Arm:
             work=self.work, out=self.gx1)
         # dL/dtheta = dL/dx1 + sum_g dL/dx3 (F's Jacobian is the identity)
         S.adam_step(self.theta, self.m1, self.v1, self.step_no, self.gx1, self.gx3, lr=LR)
-
-    launches_per_step = 14  # 1 + 4 + 1 + 2 + 5 + 1 kernels, see step()
 
     def reset(self):
         self.theta.zero_()
@@ -348,12 +351,13 @@ class Clocks:
 def kernel_breakdown(S, arm, stream, reps=20):
     """Device time of every operator of one step, each re-issued with the
     step's own arguments through the public entry point that runs the same
-    kernels (B^T: its workspace form, two launches): `reps`
+    kernels (B^T, and A where the step sums bands: the workspace form, two
+    launches): `reps`
     copies are captured in a CUDA graph and the replay is timed with CUDA
     events on the launching stream."""
     import torch
     p = arm.plan
-    mc_idx = arm.idx if arm.sketched else None
+    mc_idx = arm.idx if arm.wl.mc_sketched else None
     sk_idx = arm.idx if arm.sketched else None
     wl = arm.wl
     N, BG, m = wl.N, wl.B * wl.G, arm.m
@@ -372,13 +376,18 @@ def kernel_breakdown(S, arm, stream, reps=20):
     gx2 = arm.gx2.reshape(BG, N, N)
     z = arm.z.reshape(BG, N, N)
     fwd_jobs = [S.Job(arm.x1, arm.r, mc_idx, aux=arm.y), S.Job(x2, pbuf, sk_idx)]
+    # the form the step's own A launch takes (band sums: two launches)
+    fwd_sums = S.ei_fwd_form(p, wl.B, wl.G, mc_idx, sk_idx, arm.wl.per_sample) == 1
+    wfwd = torch.empty(max(S.band_sums_workspace_size(p, fwd_jobs), 16), dtype=torch.uint8,
+                       device="cuda")
     bpa_jobs = [S.Job(gx3, p_t, sk_idx)]
     wsum = torch.empty(max(S.band_sums_workspace_size(p, bpa_jobs), 16), dtype=torch.uint8,
                        device="cuda")
     ops = {
         "residual_add(x1)": lambda: S.residual_add(arm.x0, arm.theta, out=arm.x1),
         "rotate": lambda: S.rotate(arm.x1, arm.g, out=arm.x2),
-        "joseph_fwd(MC+EI)": lambda: S.proj_fwd_multi(p, fwd_jobs),
+        "joseph_fwd(MC+EI)": ((lambda: S.proj_fwd_multi_ws(p, fwd_jobs, work=wfwd)) if fwd_sums
+                              else (lambda: S.proj_fwd_multi(p, fwd_jobs))),
         "ramlak(fwd)": lambda: S.filter(p, pbuf, np.pi / m, out=qbuf),
         "backproject": lambda: S.backproject(p, q_t, sk_idx, out=z),
         "residual_add(x3)": lambda: S.residual_add(arm.z, arm.theta, out=arm.x3),
@@ -805,8 +814,13 @@ def suite(S, dev, stream):
     plan = S.Plan(256, 180, prob["angs"])
     ws = Workload(N=256, views=180, m=45, G=4, B=8, mc_sketched=False, noisy=False,
                   per_sample=True)
+    # the MC term on the sketch too (Algorithm 2's form), shared or per measurement
+    wm = Workload(N=256, views=180, m=45, G=4, B=8, mc_sketched=True, noisy=False)
+    wmp = Workload(N=256, views=180, m=45, G=4, B=8, mc_sketched=True, noisy=False,
+                   per_sample=True)
     res = {}
-    for tag, w in (("sketched", wl), ("plain", wp), ("per_sample", ws)):
+    for tag, w in (("sketched", wl), ("plain", wp), ("per_sample", ws), ("mc_sketched", wm),
+                   ("mc_sketched_per_sample", wmp)):
         arm = Arm(S, plan, prob, w, "f32", dev)
         idx_all, g_all = step_params(1, w)
         arm.load_params(idx_all[0], g_all[0], 1)
@@ -824,6 +838,13 @@ def suite(S, dev, stream):
                       "shared_sketch_steps_per_s": round(1e6 / res["sketched"], 1),
                       "plain_steps_per_s": round(1e6 / res["plain"], 1),
                       "speedup_vs_plain": round(res["plain"] / res["per_sample"], 3)}),
+          flush=True)
+    print(json.dumps({"suite": "ei-step-8x4x256x256-180views-sketch45-mc-sketched", "G": 4,
+                      "B": 8, "mc": "the 45-angle sketch", "ei": "the same sketch",
+                      "shared_sketch_steps_per_s": round(1e6 / res["mc_sketched"], 1),
+                      "per_sample_steps_per_s": round(1e6 / res["mc_sketched_per_sample"], 1),
+                      "plain_steps_per_s": round(1e6 / res["plain"], 1),
+                      "speedup_vs_plain": round(res["plain"] / res["mc_sketched"], 3)}),
           flush=True)
 
     ttt_bn_suite(S, dev, stream)
@@ -916,7 +937,7 @@ def main():
         arm.step()
         arm.step()
         torch.cuda.synchronize()
-        print(json.dumps({"profile_run": "ok", "launches": 2 + 2 * Arm.launches_per_step}))
+        print(json.dumps({"profile_run": "ok", "launches": 2 + 2 * arm.launches_per_step}))
         return
     sk = Arm(S, plan, prob, SKETCHED, args.dtype, dev)
     pl = Arm(S, plan, prob, PLAIN, "f32", dev)
@@ -1045,7 +1066,7 @@ def main():
             "psnr": psnr_block(curve_sk, curve_pl, sk_ms / K, pl_ms / K),
             "e2e": {"value": K / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": Arm.launches_per_step * K,
+            "gpu_launches": sk.launches_per_step * K,
             "roofline": roof,
             "kernels": kernels,
             "clocks": clk,

@@ -289,6 +289,19 @@ int skei_rotate_adj_channels(int dtype, const void *gout, int B, int Ch, int N,
 size_t skei_ei_workspace_size(skei_plan plan, int dtype, int B, int G, int mc_m,
                               int sk_m);
 
+/* Host-only query: the form skei_ei_loss_fwd (per_sample = 0) or
+ * skei_ei_loss_fwd_per_sample (per_sample = 1) gives its fused A launch for
+ * these arguments (the angle-list pointers are compared, not read):
+ * 1 = per-band sums in the workspace, then their ordered reduction (two
+ * launches, the kernels of skei_proj_fwd_multi_ws on the same two jobs);
+ * 0 = the cluster form (one launch, those of skei_proj_fwd_multi).  The
+ * band-sums form is taken for launches of many image-angles, and where the
+ * MC and EI terms share one angle list with G = 4 (the MC image then rides
+ * in the CTAs of the EI group's four images).  Returns SKEI_EINVAL on bad
+ * arguments. */
+int skei_ei_fwd_form(skei_plan plan, int B, int G, const int *mc_idx, int mc_m,
+                     const int *sk_idx, int sk_m, int per_sample);
+
 int skei_ei_loss_fwd(skei_plan plan, int dtype, const void *x1, const void *y,
                      int B, const int *mc_idx, int mc_m, const int *sk_idx,
                      int sk_m, const double *g_deg, int G, void *r, void *x2,

@@ -247,10 +247,37 @@ EiWork ei_work(skei_plan p, int B, int G, int mc_m, int sk_m) {
   jf.j[1].m = sk_m;
   w.fwd_band_floats = band_partial_floats(p, jf);
   w.band_floats = band_partial_floats(p, jb);
-  if (((double)B * mc_m + (double)bg * sk_m) * p->N >= kStepFwdSumsMin)
+  // (G = 4 with equal list lengths: the MC image may ride, if the lists
+  // are one)
+  if (((double)B * mc_m + (double)bg * sk_m) * p->N >= kStepFwdSumsMin ||
+      (G == 4 && mc_m == sk_m))
     w.band_floats = std::max(w.band_floats, w.fwd_band_floats);
   w.total = w.band_off + align256(w.band_floats * sizeof(float));
   return w;
+}
+
+// The two jobs of the step's fused A launch (MC term, EI term).
+Jobs ei_fwd_jobs(const void *x1, const void *y, void *r, int B, const int *mc_idx, int mc_m,
+                 const void *x2, void *pbuf, const int *sk_idx, int sk_m, int G, int tb,
+                 bool per_sample) {
+  Jobs J{};
+  J.njobs = 2;
+  const int mc_per = per_sample && mc_idx ? 1 : 0, sk_per = per_sample && sk_idx ? G : 0;
+  J.j[0] = Job{x1, y, r, mc_idx, mc_m, B, 1.0f, 0.0f, tb, tb, tb, mc_per};
+  J.j[1] = Job{x2, nullptr, pbuf, sk_idx, sk_m, B * G, 1.0f, 0.0f, tb, 0, 0, sk_per};
+  return J;
+}
+
+// Whether the fused A launch takes the band-sums form: it pays on large
+// launches (many image-angles) and where the MC image rides in the EI
+// group's CTAs; the cluster form on small launches otherwise (measured on
+// GB300: 8 x 256^2 x 180 angles 79 vs 147 us; 5 x 512^2 x 30 angles 44 vs
+// 37 us apart, 32 vs 36 us riding).
+bool ei_fwd_sums(skei_plan p, const EiWork &w, const Jobs &J) {
+  const double work_units = ((double)J.j[0].nimg * J.j[0].m + (double)J.j[1].nimg * J.j[1].m) *
+                            p->N;
+  return (work_units >= kStepFwdSumsMin || band_sums_merge(J)) &&
+         w.band_floats >= w.fwd_band_floats;
 }
 
 // per_sample: mc_idx and sk_idx hold one angle list per measurement,
@@ -268,16 +295,9 @@ int ei_fwd_impl(skei_plan p, const T *x1, const T *y, int B, const int *mc_idx, 
   int rc;
   if ((rc = launch_rotate<T, T>(x1, B, p->N, g_deg, G, x2, st))) return rc;
   // one launch: r = S_mc y - A_mc x1 (MC term) and p = A_S x2 (EI term)
-  Jobs J{};
-  J.njobs = 2;
-  const int mc_per = per_sample && mc_idx ? 1 : 0, sk_per = per_sample && sk_idx ? G : 0;
-  J.j[0] = Job{x1, y, r, mc_idx, mc_m, B, 1.0f, 0.0f, tb, tb, tb, mc_per};
-  J.j[1] = Job{x2, nullptr, pbuf, sk_idx, sk_m, BG, 1.0f, 0.0f, tb, 0, 0, sk_per};
-  // the band-sums form pays on large launches (many image-angles), the
-  // cluster form on small ones (measured on GB300: 8 x 256^2 x 180 angles
-  // 79 vs 147 us; 5 x 512^2 x 30 angles 44 vs 37 us)
-  const double work_units = ((double)B * mc_m + (double)BG * sk_m) * p->N;
-  if (work_units >= kStepFwdSumsMin && w.band_floats >= w.fwd_band_floats) {
+  const Jobs J = ei_fwd_jobs(x1, y, r, B, mc_idx, mc_m, x2, pbuf, sk_idx, sk_m, G, tb, per_sample);
+  const int sk_per = per_sample && sk_idx ? G : 0;
+  if (ei_fwd_sums(p, w, J)) {
     if ((rc = launch_band_partial_jobs(p, OP_JOSEPH, J,
                                       reinterpret_cast<float *>(work + w.band_off),
                                       w.band_floats, st)))
@@ -627,6 +647,16 @@ int skei_rotate_adj(int dtype, const void *gout, int B, int N, const double *g_d
 size_t skei_ei_workspace_size(skei_plan plan, int dtype, int B, int G, int mc_m, int sk_m) {
   if (check_plan(plan) || check_dtype(dtype) || B < 1 || G < 1 || mc_m < 1 || sk_m < 1) return 0;
   return ei_work(plan, B, G, mc_m, sk_m).total;
+}
+
+int skei_ei_fwd_form(skei_plan plan, int B, int G, const int *mc_idx, int mc_m,
+                     const int *sk_idx, int sk_m, int per_sample) {
+  if (check_plan(plan) || B < 1 || G < 1 || mc_m < 1 || sk_m < 1 || mc_m > plan->n_angles ||
+      sk_m > plan->n_angles)
+    return set_error(SKEI_EINVAL, "skei_ei_fwd_form: bad arguments");
+  const Jobs J = ei_fwd_jobs(nullptr, nullptr, nullptr, B, mc_idx, mc_m, nullptr, nullptr, sk_idx,
+                             sk_m, G, 0, per_sample != 0);
+  return ei_fwd_sums(plan, ei_work(plan, B, G, mc_m, sk_m), J) ? 1 : 0;
 }
 
 static int ei_fwd_entry(skei_plan plan, int dtype, const void *x1, const void *y, int B,

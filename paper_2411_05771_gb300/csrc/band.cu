@@ -343,10 +343,14 @@ __device__ __forceinline__ void line_range(float lam0, float lam1, float inv1, f
 
 // Joseph: adds to acc[i] the linear interpolations of image i of the group
 // at the fixed-point crossings pos(L, k) = G + k A + L T of lines [s0, s1)
-// of the staged band, line by line in order.
-template <int NI>
+// of the staged band, line by line in order; with XTRA also those of a
+// riding single image staged at bufx (pitch Px) into *accx, from the same
+// positions and weights.
+template <int NI, bool XTRA = false>
 __device__ __forceinline__ void joseph_lines(const AngleConst &C, int k, int s0, int s1, int N,
-                                             const float *buf, int P, float (&acc)[NI]) {
+                                             const float *buf, int P, float (&acc)[NI],
+                                             const float *bufx = nullptr, int Px = 0,
+                                             float *accx = nullptr) {
   int lo, hi;
   // taps are nonzero only for pos in (-1, N); the relaxed window keeps every
   // such line and never reads beyond the kPad zero positions
@@ -355,6 +359,8 @@ __device__ __forceinline__ void joseph_lines(const AngleConst &C, int k, int s0,
   const long long T = C.T;
   long long pos = C.G + (long long)k * C.A + (long long)lo * T;
   const float *row = buf + ((lo - s0) * P + kPad) * NI;
+  const float *rowx = XTRA ? bufx + (lo - s0) * Px + kPad : nullptr;
+  float ax = XTRA ? *accx : 0.0f;
 #pragma unroll 4
   for (int l = lo; l < hi; ++l) {
     const int j0 = ipart(pos);
@@ -370,9 +376,14 @@ __device__ __forceinline__ void joseph_lines(const AngleConst &C, int k, int s0,
     } else {
       acc[0] = fmaf(g, row[j0], fmaf(f, row[j0 + 1], acc[0]));
     }
+    if (XTRA) {
+      ax = fmaf(g, rowx[j0], fmaf(f, rowx[j0 + 1], ax));
+      rowx += Px;
+    }
     row += P * NI;
     pos += T;
   }
+  if (XTRA) *accx = ax;
 }
 
 // A tap weight max(1 - |e|, 0) of an offset e = E 2^-28 whose sign is known
@@ -821,6 +832,9 @@ int band_batch_clusters(size_t smem, int *clusters) {
 // The 4-image partial kernel comes in two register budgets: 128 registers
 // (2 CTAs per SM) for launches that fit one wave at 2 per SM, 80 (3 per SM)
 // for larger ones.
+#ifndef SKEI_PART_MERGE
+#define SKEI_PART_MERGE 1
+#endif
 #ifndef SKEI_PART_MINB1
 #define SKEI_PART_MINB1 1     // CTAs per SM the single-image kernel's registers must allow
 #endif
@@ -877,13 +891,20 @@ struct PartArgs {
   int nbands;        // ceil(N / SBL); both group sizes use SBL of their own
   float *part;       // workspace
   size_t off[kMaxJobs];   // float offset of each job's sums
+  int merge;         // A: job 0's image z rides with job 1's group 4z .. 4z+3 (same angles)
 };
 
-template <int OP, int NI>
+// With XTRA (Joseph only), image bx of job JX, whose angle list is J's,
+// rides along: staged after the group's band (geometry gx, same lines), it
+// shares every crossing's position and weights and costs only its taps;
+// its sums go to partx.
+template <int OP, int NI, bool XTRA = false>
 __device__ __forceinline__ void partial_task(const Job &J, float *part, int b0, int band,
                                              int a_begin, int AB, int nbands, const BandGeom &g,
                                              const AngleConst *ang, int *status, float *buf,
-                                             AngleConst *sc, int *sai, int *spos, int *wsum) {
+                                             AngleConst *sc, int *sai, int *spos, int *wsum,
+                                             const Job *JX = nullptr, float *partx = nullptr,
+                                             int bx = 0, const BandGeom *gx = nullptr) {
   const int tid = threadIdx.x;
   const int na = min(AB, J.m - a_begin);
   const int nd = g.n_det, N = g.N;
@@ -906,31 +927,40 @@ __device__ __forceinline__ void partial_task(const Job &J, float *part, int b0, 
   __syncthreads();
   const size_t xo = (size_t)b0 * N * N;
   const size_t plane = (size_t)nbands * J.m * nd;   // floats per image of sums
+  float *bufx = nullptr;
+  if (XTRA) bufx = buf + (size_t)g.SB * (g.Prow > g.Pcol ? g.Prow : g.Pcol) * NI;
   for (int mode = 1; mode >= 0; --mode) {
     bool any = false;
     for (int a = 0; a < na; ++a) any |= (sai[a] >= 0 && sc[a].mode == mode);
     // angles of the other mode still write their (zero) sums below
     const int P = mode ? g.Prow : g.Pcol;
+    const int Px = XTRA ? (mode ? gx->Prow : gx->Pcol) : 0;
     if (any) {
       __syncthreads();  // the previous mode's band is no longer read
       if (NI == 4) stage4(J.in, xo, J.in_bf16, N, mode, s0, s1 - s0, buf, P);
       else stage1(J.in, xo, J.in_bf16, N, mode, s0, s1 - s0, buf, P, g.fast != 0);
+      if (XTRA)
+        stage1(JX->in, (size_t)bx * N * N, JX->in_bf16, N, mode, s0, s1 - s0, bufx, Px,
+               gx->fast != 0);
       __syncthreads();
     }
     for (int a = 0; a < na; ++a) {
       const bool live = sai[a] >= 0;
       if (live ? sc[a].mode != mode : mode != 0) continue;   // dead angles: written once
       float *pa = part + ((size_t)b0 * nbands + band) * J.m * nd + (size_t)spos[a] * nd;
+      float *pax = XTRA ? partx + ((size_t)bx * nbands + band) * JX->m * nd + (size_t)spos[a] * nd
+                        : nullptr;
       for (int k = tid; k < nd; k += kThreads) {
-        float acc[NI];
+        float acc[NI], ax = 0.0f;
 #pragma unroll
         for (int i = 0; i < NI; ++i) acc[i] = 0.0f;
         if (live) {
-          if (OP == OP_JOSEPH) joseph_lines<NI>(sc[a], k, s0, s1, N, buf, P, acc);
+          if (OP == OP_JOSEPH) joseph_lines<NI, XTRA>(sc[a], k, s0, s1, N, buf, P, acc, bufx, Px, &ax);
           else bpadj_lines<NI>(sc[a], k, s0, s1, N, buf, P, acc);
         }
 #pragma unroll
         for (int i = 0; i < NI; ++i) pa[i * plane + k] = acc[i];
+        if (XTRA) pax[k] = ax;
       }
     }
   }
@@ -950,6 +980,16 @@ __global__ void __launch_bounds__(kThreads, MINB) band_partial_kernel(const Part
   __shared__ int sai[kMaxABP], spos[kMaxABP], wsum[kWarps];
   const int z = blockIdx.z;
   const Job &J0 = args.jobs.j[0];
+  if constexpr (OP == OP_JOSEPH && NI == 4) {
+    if (args.merge) {
+      // group z of job 1 (images 4z .. 4z+3) with image z of job 0
+      partial_task<OP, 4, true>(args.jobs.j[1], args.part + args.off[1], 4 * z, blockIdx.x,
+                                blockIdx.y * args.AB, args.AB, args.nbands, args.g4, args.ang,
+                                args.status, reinterpret_cast<float *>(smem4), sc, sai, spos,
+                                wsum, &J0, args.part + args.off[0], z, &args.g1);
+      return;
+    }
+  }
   const int q0 = quads(J0.nimg, args.gmax[0]);
   const int c0 = NI == 4 ? q0 : J0.nimg - 4 * q0;
   const int jn = (args.jobs.njobs > 1 && z >= c0) ? 1 : 0;
@@ -1036,6 +1076,22 @@ int set_partial_smem(size_t smem) {
   return SKEI_OK;
 }
 
+}  // namespace
+
+// Joseph over two jobs on the same angle lists, 4 images of job 1 per image
+// of job 0 (the MC and EI terms of a step, G = 4): job 0's image z rides
+// with job 1's group z; with a list per sample, image z and images
+// 4z .. 4z+3 must read the same row.
+bool band_sums_merge(const Jobs &jobs) {
+  const Job &j0 = jobs.j[0], &j1 = jobs.j[1];
+  return SKEI_PART_MERGE && SKEI_PART_GROUP == 4 && jobs.njobs == 2 && job_groupable(j1) &&
+         j0.idx == j1.idx && j0.m == j1.m && j1.nimg == 4 * j0.nimg &&
+         ((j0.idx_per <= 0 && j1.idx_per <= 0) ||
+          (j0.idx_per > 0 && j1.idx_per == 4 * j0.idx_per));
+}
+
+namespace {
+
 template <int OP>
 int launch_band_partial(skei_plan p, const Jobs &jobs, float *work, size_t work_floats,
                         cudaStream_t st) {
@@ -1070,6 +1126,11 @@ int launch_band_partial(skei_plan p, const Jobs &jobs, float *work, size_t work_
     n4 += q4;
     n1 += jobs.j[q].nimg - 4 * q4;
   }
+  const int merge = OP == OP_JOSEPH && band_sums_merge(jobs);
+  if (merge) {
+    ngroups = n4 = jobs.j[0].nimg;
+    n1 = 0;
+  }
   if (ngroups > 65535) return set_error(SKEI_EINVAL, "too many images in one launch");
   // angles per CTA (measured on GB300: a CTA costs about one angle of
   // staging plus its angles; a short second wave or a lone CTA per SM costs
@@ -1093,15 +1154,16 @@ int launch_band_partial(skei_plan p, const Jobs &jobs, float *work, size_t work_
   const int nblk = (m_max + AB - 1) / AB;
   AB = (m_max + nblk - 1) / nblk;   // balanced blocks
   PartArgs a{jobs, p->d_ang, p->d_status, g1, g4, {gmj[0], gmj[1]}, AB, nbands, work,
-             {off[0], off[1]}};
+             {off[0], off[1]}, merge};
+  const size_t smem4 = part_smem(g4) + (merge ? part_smem(g1) : 0);
   if (n4 > 0 && one_wave) {
-    SKEI_TRY((set_partial_smem<OP, 4, 2>(part_smem(g4))));
-    launch_k(band_partial_kernel<OP, 4, 2>, dim3(nbands, nblk, n4), dim3(kThreads),
-             part_smem(g4), st, a);
+    SKEI_TRY((set_partial_smem<OP, 4, 2>(smem4)));
+    launch_k(band_partial_kernel<OP, 4, 2>, dim3(nbands, nblk, n4), dim3(kThreads), smem4, st,
+             a);
   } else if (n4 > 0) {
-    SKEI_TRY((set_partial_smem<OP, 4, 3>(part_smem(g4))));
-    launch_k(band_partial_kernel<OP, 4, 3>, dim3(nbands, nblk, n4), dim3(kThreads),
-             part_smem(g4), st, a);
+    SKEI_TRY((set_partial_smem<OP, 4, 3>(smem4)));
+    launch_k(band_partial_kernel<OP, 4, 3>, dim3(nbands, nblk, n4), dim3(kThreads), smem4, st,
+             a);
   }
   if (n1 > 0) {
     constexpr int m1 = SKEI_PART_MINB1;

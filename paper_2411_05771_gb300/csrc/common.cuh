@@ -304,6 +304,10 @@ int launch_tile_jobs(skei_plan p, int op, const Jobs &jobs, cudaStream_t st);
 size_t band_partial_floats(skei_plan p, const Jobs &jobs);
 int launch_band_partial_jobs(skei_plan p, int op, const Jobs &jobs, float *work,
                              size_t work_floats, cudaStream_t st);
+// Whether Joseph's band sums over these two jobs carry job 0's images in the
+// CTAs of job 1's groups of 4 (same angle lists, 4 images of job 1 per image
+// of job 0).
+bool band_sums_merge(const Jobs &jobs);
 
 // ------------------------------------------------- batched (persistent) --
 // One instance of a batch - images of one size and angle list, with its own

@@ -22,7 +22,7 @@ __all__ = [
     "band_sums_workspace_size", "proj_fwd_multi_ws", "backproject_adj_multi_ws",
     "filter", "filter_fft", "backproject", "backproject_adj",
     "fbp_workspace_size", "fbp", "fbp_adj", "fbp_noalloc", "rotate", "rotate_adj",
-    "ei_workspace_size", "ei_loss_fwd", "ei_loss_finish", "ei_loss_bwd",
+    "ei_workspace_size", "ei_fwd_form", "ei_loss_fwd", "ei_loss_finish", "ei_loss_bwd",
     "ei_loss_fwd_per_sample", "ei_loss_bwd_per_sample",
     "residual_add", "adam_step", "library_path",
     "bn_workspace_size", "bn_act_fwd", "bn_act_bwd",
@@ -91,6 +91,7 @@ _SIGS = {
     "skei_ei_loss_finish_len": ([_i, _vp, _vp, _vp, _i, _i, _i64, _i, _d, _d, _vp, _vp, _vp,
                                  _vp, _vp, _vp, _sz, _vp], _i),
     "skei_ei_workspace_size": ([_PLAN, _i, _i, _i, _i, _i], _sz),
+    "skei_ei_fwd_form": ([_PLAN, _i, _i, _vp, _i, _vp, _i, _i], _i),
     "skei_ei_finish_workspace_size": ([_i, _i, _i, _i], _sz),
     "skei_ei_loss_fwd": ([_PLAN, _i, _vp, _vp, _i, _vp, _i, _vp, _i, _vp, _i, _vp, _vp, _vp,
                           _vp, _sz, _vp], _i),
@@ -483,6 +484,17 @@ def _idx_rows(plan: Plan, idx, B: int, per_sample: bool):
     if idx.dim() != 2 or idx.shape[0] != B:
         raise ValueError(f"per-sample idx must be [B={B}, m], got {tuple(idx.shape)}")
     return ctypes.c_void_p(idx.data_ptr()), int(idx.shape[1])
+
+
+def ei_fwd_form(plan: Plan, B: int, G: int, mc_idx=None, sk_idx=None,
+                per_sample: bool = False) -> int:
+    """1 if ei_loss_fwd's fused A launch takes the band-sums form (the
+    kernels of proj_fwd_multi_ws), 0 for the cluster form (proj_fwd_multi)."""
+    mp, mc_m = _idx_rows(plan, mc_idx, B, per_sample)
+    sp, sk_m = _idx_rows(plan, sk_idx, B, per_sample)
+    rc = int(_lib.skei_ei_fwd_form(plan.handle, B, G, mp, mc_m, sp, sk_m, int(per_sample)))
+    _check(rc if rc < 0 else 0, "skei_ei_fwd_form")
+    return rc
 
 
 def _ei_fwd(plan, x1, y, g_deg, mc_idx, sk_idx, work, out, per_sample):

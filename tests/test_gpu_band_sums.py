@@ -76,6 +76,39 @@ def test_forward_with_band_sums(S, N, n_ang, j0, j1):
         assert rel(host(o), host(jb.out)) <= 1e-6, f"job {q} vs cluster form"
 
 
+@pytest.mark.parametrize("N,n_ang,B,m", [(37, 24, 1, 8), (64, 60, 3, 15), (256, 180, 2, 45),
+                                         (512, 60, 1, 60)])
+def test_forward_band_sums_single_image_rides_with_its_group(S, N, n_ang, B, m):
+    """Two jobs on one angle list with 4 images of job 1 per image of job 0
+    (the MC and EI terms of a step with G = 4): image b of job 0 is summed in
+    the CTAs of job 1's images 4b .. 4b+3.  Its sums are those of the same
+    launch with the list given twice (no riding), bit for bit."""
+    plan = S.Plan(N, n_ang)
+    gen = torch.Generator().manual_seed(3 * N + m)
+    idx_np = _sk(n_ang, m, 5)
+    idx = None if idx_np is None else torch.tensor(idx_np, dtype=torch.int32, device="cuda")
+    x0 = torch.randn((B, N, N), generator=gen).cuda()
+    x1 = torch.randn((4 * B, N, N), generator=gen).cuda()
+    y = torch.randn((B, n_ang, plan.n_det), generator=gen).cuda()
+    nan = dict(fill_value=float("nan"), device="cuda")
+    jobs = [S.Job(x0, torch.full((B, m, plan.n_det), **nan), idx, aux=y),
+            S.Job(x1, torch.full((4 * B, m, plan.n_det), **nan), idx)]
+    S.proj_fwd_multi_ws(plan, jobs)
+    idx2 = None if idx is None else idx.clone()
+    if idx2 is None:   # a full list given explicitly: same angles, another pointer
+        idx2 = torch.arange(n_ang, dtype=torch.int32, device="cuda")
+    apart = [S.Job(x0, torch.full((B, m, plan.n_det), **nan), idx2, aux=y),
+             S.Job(x1, torch.full((4 * B, m, plan.n_det), **nan), idx)]
+    S.proj_fwd_multi_ws(plan, apart)
+    torch.cuda.synchronize()
+    ang = plan.angles_deg if idx_np is None else O.select(plan.angles_deg, idx_np)
+    yS = host(y) if idx_np is None else host(y)[:, idx_np]
+    assert rel(host(jobs[0].out), yS - O.proj_fwd(host(x0), ang, plan.n_det)) <= FP32_TOL
+    assert rel(host(jobs[1].out), O.proj_fwd(host(x1), ang, plan.n_det)) <= FP32_TOL
+    assert torch.equal(jobs[0].out, apart[0].out)
+    assert torch.equal(jobs[1].out, apart[1].out)
+
+
 @pytest.mark.parametrize("N,n_ang,j0,j1", CASES)
 def test_backproject_transpose_with_band_sums(S, N, n_ang, j0, j1):
     plan = S.Plan(N, n_ang)

@@ -208,3 +208,19 @@ def test_per_sample_with_equal_rows_is_the_shared_sketch_bitwise(S, sketch_mc):
     gb = S.ei_loss_bwd_per_sample(plan, r, gx, z, g_d, 0.3,
                                   mc_idx=rows_d if sketch_mc else None, sk_idx=rows_d)
     assert torch.equal(ga, gb)
+
+
+def test_forward_form_query(S):
+    """skei_ei_fwd_form: the riding band-sums form where the MC and EI terms
+    share one list with G = 4; the cluster form for a small launch
+    otherwise; bad sizes are refused."""
+    plan = S.Plan(64, 60)
+    idx = dev(I.sketch_indices(60, 15, 1), torch.int32)
+    other = idx.clone()
+    assert S.ei_fwd_form(plan, 2, 4, idx, idx) == 1
+    assert S.ei_fwd_form(plan, 2, 4, other, idx) == 0
+    assert S.ei_fwd_form(plan, 2, 3, idx, idx) == 0
+    rows = idx.repeat(2, 1).contiguous()
+    assert S.ei_fwd_form(plan, 2, 4, rows, rows, per_sample=True) == 1
+    with pytest.raises(RuntimeError):
+        S.ei_fwd_form(plan, 0, 4, idx, idx)
