@@ -361,6 +361,19 @@ int skei_ei_loss_bwd_per_sample(skei_plan plan, int dtype, const void *r, const 
 int skei_residual_add(int dtype, const void *u, const float *theta, int count,
                       int64_t n, void *out, void *stream);
 
+/* skei_step_draws: the draws of one iteration from a resident table.
+ * Algorithm 2 draws a sketch and G rotation angles every iteration; with
+ * the draws of K iterations resident as rows of `table` [n_rows][row_bytes]
+ * (DEVICE), this copies row *counter to dst (DEVICE, row_bytes) and
+ * advances *counter (DEVICE int) by one, in stream order, so that a captured
+ * step graph replays K iterations, each with its own draws, without a host
+ * copy.  A counter outside [0, n_rows) copies nothing and is set to -1
+ * (sticky: the caller reads it back after the run).  One CTA; 16-byte words
+ * where row_bytes and both pointers allow.  Returns SKEI_EINVAL for NULL or
+ * misaligned pointers, n_rows < 1 or row_bytes < 1. */
+int skei_step_draws(const void *table, int n_rows, int64_t row_bytes, int *counter,
+                    void *dst, void *stream);
+
 /* skei_adam_step: g[i] = sum_{c<c1} g1[c][i] + sum_{c<c2} g2[c][i] (g1, g2 in
  * dtype; g2 may be NULL with c2 = 0), then one Adam update of theta, m, v
  * (float, n entries) with bias correction for the step number *step (DEVICE

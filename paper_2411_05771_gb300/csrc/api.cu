@@ -141,7 +141,7 @@ __global__ void residual_add4_kernel(const float4 *u, const float4 *theta, int n
 template <typename T>
 __global__ void adam_kernel(float *theta, int64_t n, const T *g1, int c1, const T *g2, int c2,
                             float *m, float *v, const int *step, float lr, float b1, float b2,
-                            float eps, float lnb1, float lnb2) {
+                            float omb1, float omb2, float eps, float lnb1, float lnb2) {
   pdl_enter();
   const float t = (float)max(__ldg(step), 1);
   const float bc1 = -expm1f(t * lnb1), bc2 = -expm1f(t * lnb2);
@@ -150,8 +150,8 @@ __global__ void adam_kernel(float *theta, int64_t n, const T *g1, int c1, const 
     float g = 0.0f;
     for (int c = 0; c < c1; ++c) g += ldg_f(g1 + (int64_t)c * n + i);
     for (int c = 0; c < c2; ++c) g += ldg_f(g2 + (int64_t)c * n + i);
-    const float mi = fmaf(b1, m[i], (1.0f - b1) * g);
-    const float vi = fmaf(b2, v[i], (1.0f - b2) * g * g);
+    const float mi = fmaf(b1, m[i], omb1 * g);
+    const float vi = fmaf(b2, v[i], omb2 * g * g);
     m[i] = mi;
     v[i] = vi;
     theta[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
@@ -161,7 +161,8 @@ __global__ void adam_kernel(float *theta, int64_t n, const T *g1, int c1, const 
 // FP32 gradients, n % 4 == 0: four elements per thread and access.
 __global__ void adam4_kernel(float4 *theta, int n4, const float4 *g1, int c1, const float4 *g2,
                              int c2, float4 *m, float4 *v, const int *step, float lr, float b1,
-                             float b2, float eps, float lnb1, float lnb2) {
+                             float b2, float omb1, float omb2, float eps, float lnb1,
+                             float lnb2) {
   pdl_enter();
   const float t = (float)max(__ldg(step), 1);
   const float bc1 = -expm1f(t * lnb1), bc2 = -expm1f(t * lnb2);
@@ -180,14 +181,36 @@ __global__ void adam4_kernel(float4 *theta, int n4, const float4 *g1, int c1, co
     const float *pg = &g.x;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      pm[q] = fmaf(b1, pm[q], (1.0f - b1) * pg[q]);
-      pv[q] = fmaf(b2, pv[q], (1.0f - b2) * pg[q] * pg[q]);
+      pm[q] = fmaf(b1, pm[q], omb1 * pg[q]);
+      pv[q] = fmaf(b2, pv[q], omb2 * pg[q] * pg[q]);
       pt[q] -= lr * (pm[q] / bc1) / (sqrtf(pv[q] / bc2) + eps);
     }
     m[i] = mi;
     v[i] = vi;
     theta[i] = th;
   }
+}
+
+// Row *counter of a resident table of per-iteration draws into dst, then
+// *counter + 1 (Algorithm 2 draws a sketch and G rotations every
+// iteration); a counter outside [0, n_rows) copies nothing and becomes -1.
+// V: uint4 where the row is a whole number of aligned 16-byte words, else
+// unsigned char.
+template <typename V>
+__global__ void step_draws_kernel(const V *table, int n_rows, int64_t row_words, int *counter,
+                                  V *dst) {
+  pdl_enter();
+  __shared__ int s_row;
+  if (threadIdx.x == 0) s_row = *counter;
+  __syncthreads();
+  const int r = s_row;
+  if (r < 0 || r >= n_rows) {
+    if (threadIdx.x == 0) *counter = -1;
+    return;
+  }
+  const V *src = table + (size_t)r * row_words;
+  for (int64_t i = threadIdx.x; i < row_words; i += blockDim.x) dst[i] = src[i];
+  if (threadIdx.x == 0) *counter = r + 1;
 }
 
 int grid_for(int64_t n, int threads) {
@@ -809,6 +832,26 @@ int skei_residual_add(int dtype, const void *u, const float *theta, int count, i
   return check_launch("residual add launch");
 }
 
+int skei_step_draws(const void *table, int n_rows, int64_t row_bytes, int *counter, void *dst,
+                    void *stream) {
+  if (n_rows < 1 || row_bytes < 1)
+    return set_error(SKEI_EINVAL, "step draws: n_rows=%d, row_bytes=%lld must be >= 1", n_rows,
+                     (long long)row_bytes);
+  SKEI_TRY(check_dev_ptr(table, "table"));
+  SKEI_TRY(check_dev_ptr(dst, "dst"));
+  if (!counter || reinterpret_cast<uintptr_t>(counter) % 4)
+    return set_error(SKEI_EINVAL, "counter is NULL or misaligned");
+  const bool vec = row_bytes % 16 == 0 && reinterpret_cast<uintptr_t>(table) % 16 == 0 &&
+                   reinterpret_cast<uintptr_t>(dst) % 16 == 0;
+  if (vec)
+    launch_k(step_draws_kernel<uint4>, dim3(1), dim3(256), 0, as_stream(stream),
+             (const uint4 *)table, n_rows, row_bytes / 16, counter, (uint4 *)dst);
+  else
+    launch_k(step_draws_kernel<unsigned char>, dim3(1), dim3(256), 0, as_stream(stream),
+             (const unsigned char *)table, n_rows, row_bytes, counter, (unsigned char *)dst);
+  return check_launch("step draws launch");
+}
+
 int skei_adam_step(float *theta, int64_t n, int dtype, const void *g1, int c1, const void *g2,
                    int c2, float *m, float *v, const int *step, double lr, double beta1,
                    double beta2, double eps, void *stream) {
@@ -824,21 +867,23 @@ int skei_adam_step(float *theta, int64_t n, int dtype, const void *g1, int c1, c
     return set_error(SKEI_EINVAL, "Adam betas must lie in (0, 1)");
   const int grid = grid_for(n, 256);
   const float lnb1 = (float)std::log(beta1), lnb2 = (float)std::log(beta2);
+  // 1 - beta from FP64: 1 - (float)0.999 would be 1.3e-5 off 0.001
+  const float omb1 = (float)(1.0 - beta1), omb2 = (float)(1.0 - beta2);
   const bool vec = dtype == SKEI_F32 && n % 4 == 0 && n / 4 < (int64_t)1 << 30 &&
                    ((reinterpret_cast<uintptr_t>(g2) & 15) == 0);
   if (vec)
     launch_k(adam4_kernel, dim3(grid_for(n / 4, 256)), dim3(256), 0, as_stream(stream),
              (float4 *)theta, (int)(n / 4), (const float4 *)g1, c1, (const float4 *)g2, c2,
-             (float4 *)m, (float4 *)v, step, (float)lr, (float)beta1, (float)beta2, (float)eps,
-             lnb1, lnb2);
+             (float4 *)m, (float4 *)v, step, (float)lr, (float)beta1, (float)beta2, omb1, omb2,
+             (float)eps, lnb1, lnb2);
   else if (dtype == SKEI_F32)
     launch_k(adam_kernel<float>, dim3(grid), dim3(256), 0, as_stream(stream), theta, n,
              (const float *)g1, c1, (const float *)g2, c2, m, v, step, (float)lr, (float)beta1,
-             (float)beta2, (float)eps, lnb1, lnb2);
+             (float)beta2, omb1, omb2, (float)eps, lnb1, lnb2);
   else
     launch_k(adam_kernel<bf16>, dim3(grid), dim3(256), 0, as_stream(stream), theta, n,
              (const bf16 *)g1, c1, (const bf16 *)g2, c2, m, v, step, (float)lr, (float)beta1,
-             (float)beta2, (float)eps, lnb1, lnb2);
+             (float)beta2, omb1, omb2, (float)eps, lnb1, lnb2);
   return check_launch("adam launch");
 }
 

@@ -206,8 +206,10 @@ __device__ __forceinline__ void sincos_taylor(double x, double *s, double *c) {
 }
 
 __device__ __forceinline__ void trig_deg(double deg, double *c, double *s) {
-  double q = floor(deg / 90.0 + 0.5);
-  double r = deg - 90.0 * q;
+  // quadrant by a multiply, not a division (a shorter dependent chain; at a
+  // tie, deg = 45 + 90 k, either neighbour gives a valid reduced angle)
+  double q = floor(fma(deg, 1.0 / 90.0, 0.5));
+  double r = fma(-90.0, q, deg);
   double sr, cr;
   sincos_taylor(r * (3.14159265358979323846 / 180.0), &sr, &cr);
   long long qi = ((long long)q % 4 + 4) % 4;

@@ -24,7 +24,7 @@ __all__ = [
     "fbp_workspace_size", "fbp", "fbp_adj", "fbp_noalloc", "rotate", "rotate_adj",
     "ei_workspace_size", "ei_fwd_form", "ei_loss_fwd", "ei_loss_finish", "ei_loss_bwd",
     "ei_loss_fwd_per_sample", "ei_loss_bwd_per_sample",
-    "residual_add", "adam_step", "library_path",
+    "residual_add", "adam_step", "step_draws", "library_path",
     "bn_workspace_size", "bn_act_fwd", "bn_act_bwd",
     "mri_workspace_size", "mri_fwd", "mri_adj", "mri_dinv", "coil_mix",
     "Batch", "BatchItem", "PROJ_FWD", "PROJ_ADJ", "BACKPROJECT", "BACKPROJECT_ADJ", "FILTER",
@@ -105,6 +105,7 @@ _SIGS = {
                                      _vp, _vp, _sz, _vp], _i),
     "skei_residual_add": ([_i, _vp, _vp, _i, _i64, _vp, _vp], _i),
     "skei_adam_step": ([_vp, _i64, _i, _vp, _i, _vp, _i, _vp, _vp, _vp, _d, _d, _d, _d, _vp], _i),
+    "skei_step_draws": ([_vp, _i, _i64, _vp, _vp, _vp], _i),
     "skei_bn_workspace_size": ([_i, _i, _i64], _sz),
     "skei_bn_act_fwd": ([_i, _vp, _i, _i, _i64, _vp, _vp, _i, _d, _vp, _vp, _vp, _vp, _sz, _vp],
                         _i),
@@ -623,6 +624,22 @@ def adam_step(theta, m, v, step_dev, g1, g2=None, lr=5e-4, beta1=0.9, beta2=0.99
     _check(_lib.skei_adam_step(_ptr(theta), n, _dtype_code(g1), _ptr(g1), c1, _ptr(g2), c2,
                                _ptr(m), _ptr(v), _ptr(step_dev), lr, beta1, beta2, eps, _stream()),
            "skei_adam_step")
+
+
+def step_draws(table, counter, out):
+    """On the device: out = row counter of table [n_rows, ...] (bytes of one
+    row), then counter += 1; a counter outside [0, n_rows) copies nothing and
+    becomes -1.  counter is a CUDA int32 tensor of one element."""
+    _dev(table, "table")
+    _dev(counter, "counter", torch.int32, (1,))
+    _dev(out, "out")
+    if table.dim() < 2:
+        raise ValueError("table must be [n_rows, ...]")
+    row_bytes = table[0].numel() * table.element_size()
+    if out.numel() * out.element_size() != row_bytes:
+        raise ValueError(f"out holds {out.numel() * out.element_size()} bytes, a row {row_bytes}")
+    _check(_lib.skei_step_draws(_ptr(table), table.shape[0], row_bytes, _ptr(counter), _ptr(out),
+                                _stream()), "skei_step_draws")
 
 
 # ------------------------------------------------------ batch-norm layers
