@@ -568,6 +568,21 @@ int skei_filter_fft(skei_plan plan, int dtype, const void *p, int rows, float sc
                                        as_stream(stream));
 }
 
+int skei_filter_tc(skei_plan plan, int dtype, const void *p, int rows, float scale, void *q,
+                   void *stream) {
+  SKEI_TRY(check_plan(plan));
+  SKEI_TRY(check_dtype(dtype));
+  if (rows < 1) return set_error(SKEI_EINVAL, "rows=%d must be >= 1", rows);
+  SKEI_TRY(check_dev_ptr(p, "p"));
+  SKEI_TRY(check_dev_ptr(q, "q"));
+  if (p == q) return set_error(SKEI_EINVAL, "filter: p and q must not alias");
+  if (dtype == SKEI_F32)
+    return launch_filter_tc<float, float>(plan, (const float *)p, rows, scale, (float *)q,
+                                          as_stream(stream));
+  return launch_filter_tc<bf16, bf16>(plan, (const bf16 *)p, rows, scale, (bf16 *)q,
+                                      as_stream(stream));
+}
+
 int skei_backproject(skei_plan plan, int dtype, const void *q, int B, const int *idx, int m,
                      float alpha, float beta, void *x, void *stream) {
   SKEI_TRY(check_common(plan, dtype, B));

@@ -407,6 +407,11 @@ int launch_filter(skei_plan p, const Tin *in, int rows, float scale, Tout *out,
 template <typename Tin, typename Tout>
 int launch_filter_fft(skei_plan p, const Tin *in, int rows, float scale, Tout *out,
                       cudaStream_t st);
+// The same as tensor-core matrix products (3 TF32 products per FP32 product;
+// the direct form beyond 2048 bins).
+template <typename Tin, typename Tout>
+int launch_filter_tc(skei_plan p, const Tin *in, int rows, float scale, Tout *out,
+                     cudaStream_t st);
 // The form the EI step uses (build-time choice).
 template <typename Tin, typename Tout>
 int launch_filter_step(skei_plan p, const Tin *in, int rows, float scale, Tout *out,

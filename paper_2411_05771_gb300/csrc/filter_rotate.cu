@@ -3,6 +3,7 @@
 // transform group (Sec. 4.1.3) with their exact gathered transposes.
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 
 #include "fft.cuh"
 
@@ -246,6 +247,143 @@ __global__ void __launch_bounds__(kFilterThreads)
   if (threadIdx.x == 0) queue_retire(queue, gridDim.x);
 }
 
+// ----------------------------------------- Ram-Lak, tensor-core form --
+// The filter of a tile of 16 rows and 32 outputs as the matrix product
+// Q = P H^T with H[k][j] = h(|k - j|) (Toeplitz in the taps): warp-level TF32
+// tensor-core MMAs (m16n8k8).  Each FP32 operand is split into a TF32 head
+// and a TF32 tail, x = hi + lo, and the three products hi.hi + hi.lo + lo.hi
+// (the lo.lo term is below FP32 rounding) of each step of 8 bins go to a
+// fresh accumulator that one IEEE addition adds to the running sum: with
+// the tensor cores' own accumulation over the whole row, smooth sinograms
+// (whose filtered rows are 160-310 times smaller than the rows) lost 4x the
+// direct form's accuracy; with fresh steps, 2x.  The 8 warps of a CTA split the row length
+// and add their partial tiles in a fixed order.  Rows of up to kTcMaxNd
+// bins (the staged tile must fit shared memory); longer rows take the
+// direct form.
+// (Measured on GB300 at 120 rows of 725 bins: 9.4 us against the direct
+// form's 7.9; 16, 64 and 128 outputs per CTA or 4 warps were slower still.)
+constexpr int kTcRows = 16, kTcOuts = 32, kTcWarps = 8, kTcThreads = 32 * kTcWarps;
+constexpr int kTcMaxNd = 2048;
+constexpr int kTcTapPad = kTcOuts + 16;   // zero taps beyond n_det that an index may reach
+
+__host__ __device__ __forceinline__ int tc_pitch(int nd) {
+  // a multiple of 32 plus 4 words: the A-fragment loads (rows g, columns t)
+  // of a warp hit 32 distinct banks
+  return ((((nd + 7) & ~7) + 31) & ~31) + 4;
+}
+static size_t tc_smem(int nd) {
+  return sizeof(float) * ((size_t)kTcRows * tc_pitch(nd) + 2 * (size_t)(nd + kTcTapPad) +
+                          (size_t)kTcWarps * kTcRows * kTcOuts);
+}
+
+__device__ __forceinline__ unsigned to_tf32(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// c += a b for one 16 x 8 x 8 TF32 product: a row-major 16 x 8 (lane
+// g = lane / 4, t = lane % 4 holds (g, t), (g+8, t), (g, t+4), (g+8, t+4)),
+// b 8 x 8 by columns ((t, g), (t+4, g)), c 16 x 8 ((g, 2t), (g, 2t+1),
+// (g+8, 2t), (g+8, 2t+1)).
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const unsigned (&a)[4], unsigned b0,
+                                         unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 "
+      "{%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <typename Tin, typename Tout>
+__global__ void __launch_bounds__(kTcThreads)
+    ramlak_tc_kernel(const Tin *in, Tout *out, int rows, int nd, float scale,
+                     const float *taps) {
+  extern __shared__ float4 smem4[];
+  const int pitch = tc_pitch(nd), Kp = (nd + 7) & ~7, ntap = nd + kTcTapPad;
+  float *Ps = reinterpret_cast<float *>(smem4);          // [16][pitch] rows of P
+  float *th = Ps + kTcRows * pitch, *tl = th + ntap;     // tap heads and tails
+  float *red = tl + ntap;                                // [warps][16][32]
+  const int r0 = blockIdx.y * kTcRows, k0 = blockIdx.x * kTcOuts;
+  // the taps do not depend on the preceding kernel: split them first (read
+  // through a global pointer: the lanes' distinct addresses would serialise
+  // in the constant cache)
+  for (int d = threadIdx.x; d < ntap; d += kTcThreads) {
+    const float h = d < nd ? __ldg(taps + d) : 0.0f;
+    const float hi = __uint_as_float(to_tf32(h));
+    th[d] = hi;
+    tl[d] = __uint_as_float(to_tf32(h - hi));
+  }
+  pdl_enter();
+  // the 16 rows, zero beyond the rows and bins: every load in flight at once
+  // (FP32: asynchronous copies, zero-filled where out of range)
+  for (int r = 0; r < kTcRows; ++r) {
+    const bool live = r0 + r < rows;
+    const Tin *pr = in + (size_t)(live ? r0 + r : 0) * nd;
+    for (int j = threadIdx.x; j < Kp; j += kTcThreads) {
+      const bool ok = live && j < nd;
+      if constexpr (std::is_same<Tin, float>::value)
+        cp_async4(&Ps[r * pitch + j], ok ? pr + j : in, ok);
+      else
+        Ps[r * pitch + j] = ok ? ldg_f(pr + j) : 0.0f;
+    }
+  }
+  if constexpr (std::is_same<Tin, float>::value) {
+    cp_async_commit();
+    cp_async_wait_all();
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int steps = Kp / 8;
+  const int s0 = warp * steps / kTcWarps, s1 = (warp + 1) * steps / kTcWarps;
+  float acc[kTcOuts / 8][4];
+#pragma unroll
+  for (int nb = 0; nb < kTcOuts / 8; ++nb)
+    acc[nb][0] = acc[nb][1] = acc[nb][2] = acc[nb][3] = 0.0f;
+  for (int s = s0; s < s1; ++s) {
+    const int j = 8 * s + t;
+    const float x[4] = {Ps[g * pitch + j], Ps[(g + 8) * pitch + j], Ps[g * pitch + j + 4],
+                        Ps[(g + 8) * pitch + j + 4]};
+    unsigned ah[4], al[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      ah[i] = to_tf32(x[i]);
+      al[i] = to_tf32(x[i] - __uint_as_float(ah[i]));
+    }
+#pragma unroll
+    for (int nb = 0; nb < kTcOuts / 8; ++nb) {
+      // B[j][k] = h(|k - j|) at (j, k0 + 8 nb + g) and (j + 4, ...)
+      const int d = k0 + 8 * nb + g - j;
+      const int i0 = abs(d), i1 = abs(d - 4);
+      const unsigned bh0 = __float_as_uint(th[i0]), bh1 = __float_as_uint(th[i1]);
+      const unsigned bl0 = __float_as_uint(tl[i0]), bl1 = __float_as_uint(tl[i1]);
+      float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      mma_tf32(c, al, bh0, bh1);
+      mma_tf32(c, ah, bl0, bl1);
+      mma_tf32(c, ah, bh0, bh1);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[nb][i] += c[i];
+    }
+  }
+  float *rw = red + warp * (kTcRows * kTcOuts);
+#pragma unroll
+  for (int nb = 0; nb < kTcOuts / 8; ++nb) {
+    const int c = 8 * nb + 2 * t;
+    rw[g * kTcOuts + c] = acc[nb][0];
+    rw[g * kTcOuts + c + 1] = acc[nb][1];
+    rw[(g + 8) * kTcOuts + c] = acc[nb][2];
+    rw[(g + 8) * kTcOuts + c + 1] = acc[nb][3];
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < kTcRows * kTcOuts; o += kTcThreads) {
+    float v = red[o];
+#pragma unroll
+    for (int w = 1; w < kTcWarps; ++w) v += red[w * (kTcRows * kTcOuts) + o];
+    const int row = r0 + o / kTcOuts, k = k0 + o % kTcOuts;
+    if (row < rows && k < nd) st_f(out + (size_t)row * nd + k, scale * v);
+  }
+}
+
 // ------------------------------------------------------------ rotation --
 // Output pixel (i, j) samples the input at R(-g)(x_j, y_i), in fixed point
 //   row = R0 + j s + i c,   col = C0 + j c - i s,
@@ -485,12 +623,41 @@ int launch_filter(skei_plan p, const Tin *in, int rows, float scale, Tout *out,
   return check_launch("ramlak filter launch");
 }
 
-// Whether the EI step filters through the FFT form (knob): at 120 rows of
-// 725 bins it measured 14.7 us against the direct form's 7.9 on GB300 (60
-// CTAs of 22 barrier-separated radix-2 stages are latency-bound), so the
-// step keeps the direct form; skei_filter_fft always takes the FFT form.
-#ifndef SKEI_FILTER_FFT
-#define SKEI_FILTER_FFT 0
+template <typename Tin, typename Tout>
+int launch_filter_tc(skei_plan p, const Tin *in, int rows, float scale, Tout *out,
+                     cudaStream_t st) {
+  const int nd = p->n_det;
+  if (nd > kTcMaxNd || rows > 65535 * kTcRows) return launch_filter(p, in, rows, scale, out, st);
+  const size_t smem = tc_smem(nd);
+  auto kern = ramlak_tc_kernel<Tin, Tout>;
+  static size_t configured[64] = {0};
+  static const float *taps[64] = {nullptr};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!taps[dev]) {
+    void *a = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&a, c_ramlak);
+    if (e != cudaSuccess) return cuda_error(e, "ramlak taps: symbol address");
+    taps[dev] = static_cast<const float *>(a);
+  }
+  if (smem > 48 * 1024 && smem > configured[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return cuda_error(e, "ramlak tensor-core form: shared memory attribute");
+    configured[dev] = smem;
+  }
+  launch_k(kern, dim3((nd + kTcOuts - 1) / kTcOuts, (rows + kTcRows - 1) / kTcRows),
+           dim3(kTcThreads), smem, st, in, out, rows, nd, scale, taps[dev]);
+  return check_launch("ramlak tensor-core launch");
+}
+
+// The EI step's filter form (knob: 0 direct, 1 FFT, 2 tensor-core).  At 120
+// rows of 725 bins on GB300: direct 7.9 us, tensor-core 9.4 us, FFT 14.7 us
+// (60 CTAs of 22 barrier-separated radix-2 stages are latency-bound), so the
+// step keeps the direct form.
+#ifndef SKEI_STEP_FILTER
+#define SKEI_STEP_FILTER 0
 #endif
 template <typename Tin, typename Tout>
 int launch_filter_fft(skei_plan p, const Tin *in, int rows, float scale, Tout *out,
@@ -499,8 +666,9 @@ int launch_filter_fft(skei_plan p, const Tin *in, int rows, float scale, Tout *o
 template <typename Tin, typename Tout>
 int launch_filter_step(skei_plan p, const Tin *in, int rows, float scale, Tout *out,
                        cudaStream_t st) {
-  return SKEI_FILTER_FFT ? launch_filter_fft(p, in, rows, scale, out, st)
-                         : launch_filter(p, in, rows, scale, out, st);
+  if (SKEI_STEP_FILTER == 1) return launch_filter_fft(p, in, rows, scale, out, st);
+  if (SKEI_STEP_FILTER == 2) return launch_filter_tc(p, in, rows, scale, out, st);
+  return launch_filter(p, in, rows, scale, out, st);
 }
 
 template <typename Tin, typename Tout>
@@ -548,6 +716,8 @@ int launch_rotate_adj(const Tin *gout, int B, int N, const double *g_deg, int G,
                                          cudaStream_t);                                      \
   template int launch_filter_step<TI, TO>(skei_plan, const TI *, int, float, TO *,            \
                                           cudaStream_t);                                     \
+  template int launch_filter_tc<TI, TO>(skei_plan, const TI *, int, float, TO *,              \
+                                        cudaStream_t);                                       \
   template int launch_rotate<TI, TO>(const TI *, int, int, const double *, int, TO *,         \
                                      cudaStream_t, int);                                     \
   template int launch_rotate_adj<TI, TO>(const TI *, int, int, const double *, int, float,    \

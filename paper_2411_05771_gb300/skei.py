@@ -20,7 +20,7 @@ __all__ = [
     "F32", "BF16", "Plan", "last_error", "version",
     "proj_fwd", "proj_adj", "proj_fwd_multi", "proj_adj_multi", "Job",
     "band_sums_workspace_size", "proj_fwd_multi_ws", "backproject_adj_multi_ws",
-    "filter", "filter_fft", "backproject", "backproject_adj",
+    "filter", "filter_fft", "filter_tc", "backproject", "backproject_adj",
     "fbp_workspace_size", "fbp", "fbp_adj", "fbp_noalloc", "rotate", "rotate_adj",
     "ei_workspace_size", "ei_fwd_form", "ei_loss_fwd", "ei_loss_finish", "ei_loss_bwd",
     "ei_loss_fwd_per_sample", "ei_loss_bwd_per_sample",
@@ -72,6 +72,7 @@ _SIGS = {
     "skei_proj_adj": ([_PLAN, _i, _vp, _i, _vp, _i, _f, _f, _vp, _vp], _i),
     "skei_filter": ([_PLAN, _i, _vp, _i, _f, _vp, _vp], _i),
     "skei_filter_fft": ([_PLAN, _i, _vp, _i, _f, _vp, _vp], _i),
+    "skei_filter_tc": ([_PLAN, _i, _vp, _i, _f, _vp, _vp], _i),
     "skei_proj_fwd_multi": ([_PLAN, ctypes.POINTER(_Job), _i, _vp], _i),
     "skei_proj_adj_multi": ([_PLAN, ctypes.POINTER(_Job), _i, _vp], _i),
     "skei_band_sums_workspace_size": ([_PLAN, ctypes.POINTER(_Job), _i], _sz),
@@ -346,6 +347,20 @@ def filter_fft(plan: Plan, p, scale=1.0, out=None) -> torch.Tensor:
     rows = p.numel() // plan.n_det
     _check(_lib.skei_filter_fft(plan.handle, _dtype_code(p), _ptr(p), rows, float(scale),
                                 _ptr(out), _stream()), "skei_filter_fft")
+    return out
+
+
+def filter_tc(plan: Plan, p, scale=1.0, out=None) -> torch.Tensor:
+    """filter() as tensor-core matrix products (equal up to FP32 rounding);
+    out must not alias p."""
+    if p.shape[-1] != plan.n_det:
+        raise ValueError("last axis must hold n_det bins")
+    _dev(p, "p")
+    out = torch.empty_like(p) if out is None else out
+    _dev(out, "out", p.dtype, p.shape)
+    rows = p.numel() // plan.n_det
+    _check(_lib.skei_filter_tc(plan.handle, _dtype_code(p), _ptr(p), rows, float(scale),
+                               _ptr(out), _stream()), "skei_filter_tc")
     return out
 
 

@@ -325,3 +325,28 @@ def test_filter_fft_matches_oracle(S, N, rows):
     with pytest.raises(RuntimeError):
         x = dev(p)
         S.filter_fft(plan, x, 1.0, out=x)
+
+
+@pytest.mark.parametrize("N,rows", [(5, 3), (20, 7), (64, 60), (100, 31), (256, 180), (512, 120),
+                                    (1024, 17), (1500, 5)])
+def test_filter_tc_matches_oracle(S, N, rows):
+    """The tensor-core form of H (TF32 head + tail products): ragged row and
+    bin counts around the 16 x 32 tiles, the step's 120 x 725 rows, and rows
+    beyond 2048 bins (direct form)."""
+    plan = S.Plan(N, 4)
+    rng = np.random.default_rng(3 * N + rows)
+    p = rng.standard_normal((rows, plan.n_det))
+    got = S.filter_tc(plan, dev(p), 0.5)
+    ref = 0.5 * O.ramlak(p)
+    assert rel(host(got), ref) <= FP32_TOL
+    # near the direct form: both are FP32 evaluations of the same sums
+    assert rel(host(got), host(S.filter(plan, dev(p), 0.5))) <= 2e-6
+    pb = dev(p).to(torch.bfloat16)
+    gb = S.filter_tc(plan, pb, 0.5)
+    assert gb.dtype == torch.bfloat16
+    assert rel(host(gb), 0.5 * O.ramlak(host(pb))) <= 1e-2
+    again = S.filter_tc(plan, dev(p), 0.5)
+    assert torch.equal(again, got)
+    with pytest.raises(RuntimeError):
+        x = dev(p)
+        S.filter_tc(plan, x, 1.0, out=x)
