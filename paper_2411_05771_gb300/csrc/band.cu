@@ -737,7 +737,9 @@ int choose_ab(skei_plan p, const Jobs &jobs, int gm, int *tasks, int *slots_out)
     int per_sm = (int)((228 * 1024) / (bytes + 2304));
     per_sm = max(1, min(per_sm, 8));
     const int slots = max(1, sm_count() * per_sm / kBands);
-    const double cost = band_estimate(jobs, p->n_det, ab, slots, gm, 1.0, 0.4);
+    // a single image's staging costs about 0.4 angles per 16 staged lines
+    const int sb1 = band_geom(p->N, p->n_det, p->n_angles, OP, ab, 1).SB;
+    const double cost = band_estimate(jobs, p->n_det, ab, slots, gm, 1.0, 0.4 * sb1 / 16.0);
     if (cost <= best_cost) { best_cost = cost; best_ab = ab; best_slots = slots; }
   }
   if (SKEI_BAND_AB > 0) best_ab = min(SKEI_BAND_AB, ab_max);
