@@ -42,6 +42,8 @@ LAM, LR = 1.0, 5e-4
 PSNR_ITERS = 1000          # iterations of each arm's PSNR trajectory
 PSNR_REF_ITERS = 200       # the TTT run length of the equal-PSNR comparison
 L2_FLUSH_BYTES = 256 << 20
+MIN_TIMED_S = 1.0          # device time the timed region lasts at the least
+MAX_TIMED_STEPS = 20000
 
 
 def parse():
@@ -234,60 +236,60 @@ class Arm:
         self.v1.zero_()
 
 
-def psnr_curve(arm, x_gt, iters, every=25):
+def psnr_curve(arm, x_gt, iters):
     """Algorithm 2 for `iters` iterations from theta = 0; PSNR of F(x0) =
-    x0 + theta against the phantom every `every` iterations (untimed)."""
+    x0 + theta against the phantom after every iteration (untimed; the
+    squared errors are summed on the device and read back once)."""
     import torch
     arm.reset()
     idx_all, g_all = step_params(iters, arm.wl)
-    rngv = float(x_gt.max() - x_gt.min())
-    curve = {}
+    gt = torch.tensor(x_gt, dtype=torch.float64, device=arm.theta.device)
+    sse = torch.empty(iters + 1, dtype=torch.float64, device=gt.device)
     for s in range(iters + 1):
-        if s % every == 0:
-            torch.cuda.synchronize()
-            rec = (arm.x0.double() + arm.theta.double()).cpu().numpy()[0]
-            curve[s] = 10 * np.log10(rngv * rngv / float(np.mean((rec - x_gt) ** 2)))
+        sse[s] = ((arm.x0[0].double() + arm.theta.double() - gt) ** 2).sum()
         if s == iters:
             break
         arm.load_params(idx_all[s], g_all[s], s + 1)
         arm.step()
-    return curve
+    rngv = float(x_gt.max() - x_gt.min())
+    mse = sse.cpu().numpy() / x_gt.size
+    return {s: float(10 * np.log10(rngv * rngv / mse[s])) for s in range(iters + 1)}
 
 
 def psnr_block(c_sk, c_pl, ms_sk, ms_pl):
-    """Equal-PSNR comparison: the sketched arm's time to reach the plain
-    arm's PSNR after PSNR_REF_ITERS iterations, and to reach the plain arm's
-    best PSNR over the whole trajectory."""
+    """Equal-PSNR comparison on trajectories observed after every iteration:
+    the first sketched iteration within 0.1 dB of (and the first at or
+    above) the plain arm's PSNR after PSNR_REF_ITERS iterations, and of its
+    best PSNR over the run; each with the time ratio plain / sketched."""
     ref = c_pl[PSNR_REF_ITERS]
     best_it = max(c_pl, key=c_pl.get)
     best = c_pl[best_it]
-    out = {"iters_run": PSNR_ITERS, "fbp_x0": c_pl[0],
+    out = {"iters_run": PSNR_ITERS, "sampled": "every iteration", "fbp_x0": c_pl[0],
            "at_ref_iters": {"iters": PSNR_REF_ITERS, "plain": ref, "sketched": c_sk[PSNR_REF_ITERS],
                             "delta_db": c_sk[PSNR_REF_ITERS] - ref},
            "plain_best": {"psnr": best, "iters": best_it},
-           "sketched_final": c_sk[max(c_sk)]}
+           "sketched_best": {"psnr": max(c_sk.values()), "iters": max(c_sk, key=c_sk.get)}}
     for key, target, it_pl in (("to_plain_ref", ref, PSNR_REF_ITERS), ("to_plain_best", best, best_it)):
-        it_sk = iters_to_reach(c_sk, target)
-        if it_sk is None:
-            out[key] = {"target_db": target, "sketched_iters": None}
-            continue
-        t_pl, t_sk = it_pl * ms_pl, it_sk * ms_sk
-        out[key] = {"target_db": target, "plain_iters": it_pl, "sketched_iters": it_sk,
-                    "plain_ms": t_pl, "sketched_ms": t_sk, "speedup": t_pl / t_sk}
+        blk = {"target_db": target, "plain_iters": it_pl, "plain_ms": it_pl * ms_pl}
+        for tag, thr in (("within_0.1db", target - 0.1), ("reached", target)):
+            it_sk = first_at(c_sk, thr)
+            if it_sk is None:
+                blk[tag] = None
+                continue
+            blk[tag] = {"sketched_iters": it_sk, "sketched_psnr": c_sk[it_sk],
+                        "delta_db": c_sk[it_sk] - target, "sketched_ms": it_sk * ms_sk,
+                        "speedup": (it_pl * ms_pl) / max(it_sk * ms_sk, 1e-30)}
+        out[key] = blk
     out["curve_every_100"] = {"plain": {k: round(v, 3) for k, v in c_pl.items() if k % 100 == 0},
                               "sketched": {k: round(v, 3) for k, v in c_sk.items() if k % 100 == 0}}
     return out
 
 
-def iters_to_reach(curve, target):
-    """First iteration (linearly interpolated between samples) at which the
-    curve reaches `target`, or None."""
-    its = sorted(curve)
-    for a, b in zip(its, its[1:]):
-        if curve[a] >= target:
-            return float(a)
-        if curve[b] >= target:
-            return a + (b - a) * (target - curve[a]) / (curve[b] - curve[a])
+def first_at(curve, target):
+    """First observed iteration at which the curve is >= target, or None."""
+    for it in sorted(curve):
+        if curve[it] >= target:
+            return it
     return None
 
 
@@ -537,24 +539,73 @@ def cpu_oracle_steps(prob, n_steps, sketched):
     return n_steps / (time.perf_counter() - t0)
 
 
+def _oracle_worker(n_steps, barrier, queue):
+    """One replica of the oracle's TTT run (a spawned process): set-up, then
+    `n_steps` timed steps once every replica is ready."""
+    prob = make_problem()
+    barrier.wait()
+    queue.put(n_steps / cpu_oracle_steps(prob, n_steps, True))
+
+
+def cpu_replicas(n_steps, procs=None):
+    """The FP64 oracle on every host core: `procs` (default: all cores)
+    independent replicas of the sketched TTT step in spawned processes, one
+    thread each, started together.  Returns (steps/s over all replicas =
+    total steps / the slowest replica's time, processes)."""
+    import multiprocessing as mp
+    import oracle as O
+    O.build()   # once, before the replicas load it
+    procs = procs or os.cpu_count() or 1
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                            "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        barrier, queue = ctx.Barrier(procs), ctx.Queue()
+        ps = [ctx.Process(target=_oracle_worker, args=(n_steps, barrier, queue))
+              for _ in range(procs)]
+        for p_ in ps:
+            p_.start()
+        secs = []
+        while len(secs) < procs:
+            try:
+                secs.append(queue.get(timeout=5))
+            except Exception:   # queue.Empty: check that no replica died
+                dead = [p_.exitcode for p_ in ps if p_.exitcode not in (None, 0)]
+                if dead:
+                    for p_ in ps:
+                        p_.kill()
+                    raise RuntimeError(f"oracle replica failed (exit codes {dead})")
+        for p_ in ps:
+            p_.join()
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return procs * n_steps / max(secs), procs
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    prob = make_problem()
     n = args.steps if args.steps > 0 else 3
     n = max(1, min(n, 5))
-    for _ in range(min(args.warmup, 1)):
-        cpu_oracle_steps(prob, 1, True)
-    v = cpu_oracle_steps(prob, n, True)
+    if args.warmup > 0:
+        cpu_replicas(1)
+    v, procs = cpu_replicas(n)
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
         "n_gpus": args.gpus, "steps": n, "warmup": min(args.warmup, 1),
         "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": dict(workload_config(), arm="sketched"),
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{n} sketched TTT steps at 512^2 (FP64 C oracle, 1 thread)"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": procs, "kind": "oracle",
+                         "sample": f"{procs} replicas (one per host core, one thread each) x "
+                                   f"{n} sketched TTT steps at 512^2 (FP64 C oracle)"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -941,14 +992,31 @@ def main():
         return
     sk = Arm(S, plan, prob, SKETCHED, args.dtype, dev)
     pl = Arm(S, plan, prob, PLAIN, "f32", dev)
+    other = "bf16" if args.dtype == "f32" else "f32"
+    sk2 = Arm(S, plan, prob, SKETCHED, other, dev)
 
     # reconstruction quality: both arms, same start, same draws
     curve_sk = psnr_curve(sk, prob["x_gt"], PSNR_ITERS)
     curve_pl = psnr_curve(pl, prob["x_gt"], PSNR_ITERS)
+    curve_sk2 = psnr_curve(sk2, prob["x_gt"], PSNR_ITERS)
 
-    K, W = args.steps, max(args.warmup, 3)
+    K_req, W = args.steps, max(args.warmup, 3)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
+
+    def estimate_ms(arm):
+        """Device time of one graph-replayed step (a short untimed probe),
+        used to size the timed region to at least MIN_TIMED_S."""
+        arm.reset()
+        us = time_graph(arm.step, stream, reps=20)
+        arm.reset()
+        return 1e-3 * us
+
+    # the timed region lasts at least MIN_TIMED_S of device time, so that
+    # the clock record has samples whatever --steps is; `steps` reports the
+    # steps actually timed
+    K = max(K_req, min(MAX_TIMED_STEPS, int(np.ceil(1e3 * MIN_TIMED_S / estimate_ms(pl)))),
+            min(MAX_TIMED_STEPS, int(np.ceil(1e3 * MIN_TIMED_S / estimate_ms(sk)))))
 
     def timed(arm):
         """Device time of K graph-replayed steps.  The draws of all W + K
@@ -1001,7 +1069,8 @@ def main():
         return dev_ms, t_wall, clk
 
     sk_ms, sk_wall, clk = timed(sk)
-    pl_ms, _, _ = timed(pl)
+    pl_ms, pl_wall, clk_pl = timed(pl)
+    sk2_ms, _, clk2 = timed(sk2)
 
     # end to end through the public API (eager calls from Python), with the
     # measurement copied host->device and the loss read back every step
@@ -1046,10 +1115,11 @@ def main():
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline:
-            n_cpu = args.cpu_steps or 6
-            v = cpu_oracle_steps(prob, n_cpu, True)
-            cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"{n_cpu} sketched TTT steps at 512^2 (FP64 C oracle, 1 thread)"}
+            n_cpu = args.cpu_steps or 2
+            v, procs = cpu_replicas(n_cpu)
+            cpu = {"value": v, "unit": UNIT, "cores": procs, "kind": "oracle",
+                   "sample": f"{procs} replicas (one per host core, one thread each) x {n_cpu} "
+                             "sketched TTT steps at 512^2 (FP64 C oracle)"}
         line = {
             "metric": METRIC,
             "value": value,
@@ -1066,9 +1136,19 @@ def main():
             "config": dict(workload_config(), graph=True,
                            l2="flushed between timed steps (256 MiB write, untimed)",
                            draws="all steps' draws resident; each step's graph loads its row"),
-            "plain": {"value": K / (pl_ms * 1e-3), "ms_per_step": pl_ms / K, "dtype": "f32"},
+            "steps_requested": K_req,
+            "plain": {"value": K / (pl_ms * 1e-3), "ms_per_step": pl_ms / K, "dtype": "f32",
+                      "clocks": clk_pl},
             "speedup_vs_plain": pl_ms / sk_ms,
             "psnr": psnr_block(curve_sk, curve_pl, sk_ms / K, pl_ms / K),
+            f"sketched_{other}": {
+                "value": K / (sk2_ms * 1e-3), "ms_per_step": sk2_ms / K, "dtype": other,
+                "storage": "images and sinograms in BF16, FP32 arithmetic" if other == "bf16"
+                else "FP32", "speedup_vs_plain": pl_ms / sk2_ms, "clocks": clk2,
+                "psnr": {k: v for k, v in psnr_block(curve_sk2, curve_pl, sk2_ms / K,
+                                                     pl_ms / K).items()
+                         if k in ("at_ref_iters", "to_plain_ref", "to_plain_best",
+                                  "sketched_best")}},
             "e2e": {"value": K / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": (sk.launches_per_step + 1) * K,   # + the draws kernel

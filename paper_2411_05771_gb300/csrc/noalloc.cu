@@ -1,13 +1,12 @@
 // skei_fbp_noalloc: the FBP of skei_fbp for callers that cannot allocate
 // device memory.  Its only scratch - the filtered sinogram - lives in a
 // static device array of this library instead of a caller workspace.
-#include <mutex>
-
 #include "common.cuh"
 
 // One array per GPU that loads the library, held until the process exits.
 // Host code must not use the symbol as an address: it is a host-side
-// stand-in; skei_fbp_noalloc looks the real device address up per device.
+// stand-in; skei_fbp_noalloc looks the real device address up on the
+// current device.
 static __device__ __align__(256) float g_fbp_scratch[SKEI_FBP_NOALLOC_MAX_FLOATS];
 
 namespace skei {
@@ -15,23 +14,16 @@ namespace {
 
 constexpr double kPiNoAlloc = 3.14159265358979323846;
 
-// Device address of g_fbp_scratch on the current device, looked up once per
-// device with that device current.
+// Device address of g_fbp_scratch on the current device, with that device
+// current.  It is looked up on every call: the lookup allocates nothing and
+// is cheap once the module is loaded, and a cached address would go stale if
+// the caller reset the device (cudaDeviceReset) and the array moved.  The
+// first call on a device also loads the library's module there.
 int scratch_address(float **out) {
-  static std::mutex mu;
-  static float *addr[64] = {nullptr};
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_error(e, "skei_fbp_noalloc: cudaGetDevice");
-  if (dev < 0 || dev >= 64) return set_error(SKEI_EINVAL, "device %d out of range", dev);
-  std::lock_guard<std::mutex> lock(mu);
-  if (!addr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_fbp_scratch);
-    if (e != cudaSuccess) return cuda_error(e, "skei_fbp_noalloc: cudaGetSymbolAddress");
-    addr[dev] = static_cast<float *>(p);
-  }
-  *out = addr[dev];
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_fbp_scratch);
+  if (e != cudaSuccess) return cuda_error(e, "skei_fbp_noalloc: cudaGetSymbolAddress");
+  *out = static_cast<float *>(p);
   return SKEI_OK;
 }
 

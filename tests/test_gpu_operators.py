@@ -160,7 +160,8 @@ def test_filter_backproject_fbp(S, N, n_ang, B, m):
     assert rel(host(S.fbp_adj(plan, dev(x), idx_d)), O.fbp_adj(x, angs, plan.n_det)) <= FP32_TOL
 
 
-@pytest.mark.parametrize("N,B,G", [(64, 1, 4), (256, 2, 4), (37, 3, 2), (8, 1, 5)])
+@pytest.mark.parametrize("N,B,G", [(64, 1, 4), (256, 2, 4), (37, 3, 2), (8, 1, 5),
+                                   (512, 1, 4)])   # the 512^2 step's rotations
 def test_rotate_and_transpose(S, N, B, G):
     rng = np.random.default_rng(N)
     x = rng.standard_normal((B, N, N))

@@ -59,6 +59,8 @@ def test_noalloc_fbp_rejects_sizes_beyond_its_scratch(S):
         S.fbp_noalloc(plan, sino, out=out)
     torch.cuda.synchronize()
     assert bool((out == 7.0).all())   # nothing was launched
-    # the largest size that fits still works
-    ok = torch.randn(1, n_ang, plan.n_det, device="cuda")
+    # the largest batch that fits still works (B m n_det <= the maximum:
+    # the size check is pinned from both sides)
+    B_max = S.FBP_NOALLOC_MAX_FLOATS // (n_ang * plan.n_det)
+    ok = torch.randn(B_max, n_ang, plan.n_det, device="cuda")
     assert _rel(S.fbp_noalloc(plan, ok), S.fbp(plan, ok)) <= FP32_TOL
