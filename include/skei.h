@@ -241,9 +241,10 @@ int skei_fbp_adj(skei_plan plan, int dtype, const void *x, int B,
  * held by every GPU that loads the library until the process exits.
  *   - B * m * n_det must not exceed SKEI_FBP_NOALLOC_MAX_FLOATS; a larger
  *     call returns SKEI_EINVAL and launches nothing.
- *   - The first call on a device looks the array's device address up once,
- *     with that device current; make that first call before any stream
- *     capture.
+ *   - Every call looks the array's device address up on the current
+ *     device (so a device reset between calls is safe); the first call on a
+ *     device also loads the library's module there, so make that first call
+ *     before any stream capture.
  *   - Nothing is allocated: no cudaMalloc, cudaFree or allocating library
  *     routine runs in this call.
  *   - All calls share the one array and it keeps the last call's contents;
@@ -254,6 +255,27 @@ int skei_fbp_adj(skei_plan plan, int dtype, const void *x, int B,
 #define SKEI_FBP_NOALLOC_MAX_FLOATS 1048576
 int skei_fbp_noalloc(skei_plan plan, int dtype, const void *sino, int B,
                      const int *idx, int m, void *x, void *stream);
+
+/* ---------------------------------------------------------------- roofs --
+ * skei_measure_roofs: measurement, no counterpart in the paper.  Times four
+ * microbenchmarks on `stream` and returns the measured peaks that bound the
+ * operator kernels (the projectors are bound by FP32 arithmetic and by
+ * shared-memory taps, not by HBM or tensor cores):
+ *   fp32_flops       FP32 FMA rate, flop/s (one FMA counts 2);
+ *   smem_bytes       shared-memory load bandwidth (16-byte loads), bytes/s;
+ *   l2_bytes         L2 read bandwidth (a 32 MiB buffer swept 16 times);
+ *   dram_read_bytes  DRAM read bandwidth (the rest of `work`, swept once).
+ * work: DEVICE scratch of at least SKEI_ROOFS_WORK_BYTES bytes (caller-owned;
+ * its contents are read, never trusted).  Synchronises the stream (it waits
+ * for its own CUDA events).  Errors: SKEI_EINVAL (NULL out, small or
+ * non-device work), SKEI_ECUDA. */
+typedef struct {
+  double fp32_flops, smem_bytes, l2_bytes, dram_read_bytes;
+  int sms;
+} skei_roofs;
+#define SKEI_ROOFS_L2_BYTES (32u << 20)
+#define SKEI_ROOFS_WORK_BYTES (1u << 30)
+int skei_measure_roofs(void *work, size_t work_bytes, skei_roofs *out, void *stream);
 
 /* ------------------------------------------------------------ rotations --
  * skei_rotate: out[b][g] = T_{g_deg[b][g]} x[b] (Sec. 4.1.3: the transform

@@ -155,7 +155,8 @@ __device__ __forceinline__ float4 load4(const void *x, size_t i, int bf16) {
 
 // Stages lines [s0, s0 + nl) of one image (element offset xo in x) into buf
 // (pitch P positions): mode 1 copies rows, mode 0 copies columns
-// transposed.  kPad zero positions on each side.
+// transposed.  PAD zero positions on each side.
+template <int PAD = kPad>
 __device__ __forceinline__ void stage1(const void *x, size_t xo, int bf16, int N, int mode,
                                        int s0, int nl, float *buf, int P, bool fast) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -164,7 +165,7 @@ __device__ __forceinline__ void stage1(const void *x, size_t xo, int bf16, int N
       // 4 loads in flight per thread before their stores
       for (int r = warp; r < nl; r += kWarps) {
         const size_t src = xo + (size_t)(s0 + r) * N;
-        float *dst = buf + r * P + kPad;
+        float *dst = buf + r * P + PAD;
         int c = 4 * lane;
         for (; c + 384 < N; c += 512) {
           const float4 a = load4(x, src + c, bf16), b = load4(x, src + c + 128, bf16);
@@ -180,7 +181,7 @@ __device__ __forceinline__ void stage1(const void *x, size_t xo, int bf16, int N
     } else {
       for (int r = warp; r < nl; r += kWarps) {
         const size_t src = xo + (size_t)(s0 + r) * N;
-        float *dst = buf + r * P + kPad;
+        float *dst = buf + r * P + PAD;
         for (int c = lane; c < N; c += 32) dst[c] = ld_any(x, src + c, bf16);
       }
     }
@@ -193,7 +194,7 @@ __device__ __forceinline__ void stage1(const void *x, size_t xo, int bf16, int N
       const int per_warp = 32 / qn;
       const int step = kWarps * per_warp;
       auto put = [&](int p, const float4 &v) {
-        float *dst = buf + (4 * q) * P + kPad + p;
+        float *dst = buf + (4 * q) * P + PAD + p;
         dst[0] = v.x;
         dst[P] = v.y;
         dst[2 * P] = v.z;
@@ -215,16 +216,16 @@ __device__ __forceinline__ void stage1(const void *x, size_t xo, int bf16, int N
     } else {
       for (int p = warp; p < N; p += kWarps)
         for (int l = lane; l < nl; l += 32)
-          buf[l * P + kPad + p] = ld_any(x, xo + (size_t)p * N + s0 + l, bf16);
+          buf[l * P + PAD + p] = ld_any(x, xo + (size_t)p * N + s0 + l, bf16);
     }
   }
   const int npad = P - N;
   for (int r = warp; r < nl; r += kWarps)
-    for (int c = lane; c < npad; c += 32) buf[r * P + (c < kPad ? c : N + c)] = 0.0f;
+    for (int c = lane; c < npad; c += 32) buf[r * P + (c < PAD ? c : N + c)] = 0.0f;
 }
 
 // The same for 4 images (element offset xo + i N^2), interleaved: position
-// p of line l holds the 4 images' values at buf[4 (l P + kPad + p) + i].
+// p of line l holds the 4 images' values at buf[4 (l P + PAD + p) + i].
 // Needs nl <= 8 and an odd pitch P.
 //
 // FP32 fast path (N, s0, nl multiples of 4): every thread loads 4
@@ -241,6 +242,7 @@ __device__ __forceinline__ void store_block(float4 *dst, int step, const float4 
   dst[3 * step] = make_float4(v[0].w, v[1].w, v[2].w, v[3].w);
 }
 
+template <int PAD = kPad>
 __device__ __forceinline__ void stage4(const void *x, size_t xo, int bf16, int N, int mode,
                                        int s0, int nl, float *buf, int P) {
   const size_t plane = (size_t)N * N;
@@ -254,7 +256,7 @@ __device__ __forceinline__ void stage4(const void *x, size_t xo, int bf16, int N
     const int ngroups = N >> 2, step_g = kThreads >> 3;
     if (r < nl) {
       const size_t row4 = ((size_t)(s0 + r) * N) >> 2;
-      float4 *dst = b4 + r * P + kPad;
+      float4 *dst = b4 + r * P + PAD;
       int g = pg;
       for (; g + step_g < ngroups; g += 2 * step_g) {
         float4 va[4], vb[4];
@@ -276,7 +278,7 @@ __device__ __forceinline__ void stage4(const void *x, size_t xo, int bf16, int N
   } else if (fast) {
     const int lgs = nl >> 2;                          // 4-line groups (1 or 2)
     const int lg = tid % lgs, p0 = tid / lgs, step_p = kThreads / lgs;
-    float4 *dst = b4 + (4 * lg) * P + kPad;
+    float4 *dst = b4 + (4 * lg) * P + PAD;
     int p = p0;
     for (; p + step_p < N; p += 2 * step_p) {
       float4 va[4], vb[4];
@@ -298,7 +300,7 @@ __device__ __forceinline__ void stage4(const void *x, size_t xo, int bf16, int N
     // one position per thread: 4 coalesced loads, one 16-byte store
     for (int r = 0; r < nl; ++r) {
       const size_t src = xo + (size_t)(s0 + r) * N;
-      float4 *dst = b4 + r * P + kPad;
+      float4 *dst = b4 + r * P + PAD;
       for (int c = tid; c < N; c += kThreads)
         dst[c] = make_float4(ld_any(x, src + c, bf16), ld_any(x, src + plane + c, bf16),
                              ld_any(x, src + 2 * plane + c, bf16),
@@ -311,7 +313,7 @@ __device__ __forceinline__ void stage4(const void *x, size_t xo, int bf16, int N
     if (l < nl) {
       for (int p = tid >> 3; p < N; p += kThreads / 8) {
         const size_t src = xo + (size_t)p * N + s0 + l;
-        b4[l * P + kPad + p] = make_float4(ld_any(x, src, bf16), ld_any(x, src + plane, bf16),
+        b4[l * P + PAD + p] = make_float4(ld_any(x, src, bf16), ld_any(x, src + plane, bf16),
                                            ld_any(x, src + 2 * plane, bf16),
                                            ld_any(x, src + 3 * plane, bf16));
       }
@@ -320,7 +322,7 @@ __device__ __forceinline__ void stage4(const void *x, size_t xo, int bf16, int N
   const int npad = P - N;
   for (int e = tid; e < nl * npad; e += kThreads) {
     const int r = e / npad, c = e - r * npad;
-    b4[r * P + (c < kPad ? c : N + c)] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    b4[r * P + (c < PAD ? c : N + c)] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   }
 }
 
@@ -852,9 +854,13 @@ int band_batch_clusters(size_t smem, int *clusters) {
 constexpr int kMaxABP = 32;      // angles per partial CTA
 
 // Staging geometry of one band of SB lines (0: the group size's default).
-// Transposed single-image staging writes 4-line groups of (32 / (SB/4))
-// positions per warp: a column pitch = 4 mod 8 (8 lines), 2 mod 8 (16) or
-// odd (32) keeps them in distinct banks.
+// A staged line carries kPartPad(SB) zero positions on each side: wide
+// enough that every tap of a ray (A) or bin (B^T) that meets the band at all
+// falls inside the padded line, so the band's lines are summed without
+// per-line range tests.  Transposed single-image staging writes 4-line
+// groups of (32 / (SB/4)) positions per warp: a column pitch = 4 mod 8
+// (8 lines), 2 mod 8 (16) or odd (32) keeps them in distinct banks.
+__host__ __device__ constexpr int kPartPad(int SB) { return SB + 8; }
 __host__ __device__ __forceinline__ BandGeom part_geom(int N, int n_det, int n_angles, int NI,
                                                        int SB = 0) {
   BandGeom g;
@@ -864,14 +870,14 @@ __host__ __device__ __forceinline__ BandGeom part_geom(int N, int n_det, int n_a
   g.NI = NI;
   g.R = 0;
   g.SB = SB > 0 ? SB : (NI == 1 ? SKEI_PART_SBL1 : SKEI_PART_SBL4);
-  if (g.SB > N) g.SB = N;
+  const int pad = kPartPad(g.SB);
   if (NI == 1) {
-    g.Prow = (N + 2 * kPad + 3) & ~3;
-    g.Pcol = g.SB == 32   ? ((N + 2 * kPad) | 1)
-             : g.SB == 16 ? ((N + 2 * kPad - 2 + 7) & ~7) + 2
-                          : ((N + 2 * kPad - 4 + 7) & ~7) + 4;
+    g.Prow = (N + 2 * pad + 3) & ~3;
+    g.Pcol = g.SB == 32   ? ((N + 2 * pad) | 1)
+             : g.SB == 16 ? ((N + 2 * pad - 2 + 7) & ~7) + 2
+                          : ((N + 2 * pad - 4 + 7) & ~7) + 4;
   } else {
-    g.Pcol = (N + 2 * kPad) | 1;
+    g.Pcol = (N + 2 * pad) | 1;
     g.Prow = g.Pcol;
   }
   g.AB = 0;
@@ -896,21 +902,161 @@ struct PartArgs {
   int merge;         // A: job 0's image z rides with job 1's group 4z .. 4z+3 (same angles)
 };
 
+// Joseph over the SB staged lines of a band for ray k: adds to acc[i] the
+// linear interpolations of image i of the group at the crossings
+// pos(s0 + l, k) = G0 + k A + l T, l = 0 .. SB-1 (G0 = G + s0 T), line by
+// line in order; with XTRA also those of a riding single image staged at
+// bufx (pitch Px) into ax, from the same positions and weights.
+//
+// The positions are exact: every 8 lines the 64-bit crossing is split into
+// its nearest integer J0 and a 32-bit offset r (|r| <= 1/2 px), and r + l T
+// (|T| <= 1 px, l < 8, so |r| < 8 px: no overflow of the 28 fractional
+// bits) gives each line's integer part J0 + (r >> 28) and the 23-bit
+// fraction of its low bits, bitwise those of the 64-bit position.  A ray
+// with no crossing inside (-1, N) on any line of the band adds nothing and
+// is skipped; for the others every tap lies within SB + 1 positions of the
+// image, inside the kPartPad(SB) zero positions of each staged line, so
+// crossings outside the image read zeros and add exact zeros: no per-line
+// range test.
+template <int SB, int NI, bool XTRA>
+__device__ __forceinline__ void joseph_band(const AngleConst &C, long long G0, int k, int N,
+                                            const float *buf, int P, float (&acc)[NI],
+                                            const float *bufx, int Px, float &ax) {
+  static_assert(SB % 8 == 0, "bands of whole 8-line blocks");
+  constexpr int PAD = kPartPad(SB);
+  const long long T = C.T;
+  const long long p0 = G0 + (long long)k * C.A;
+  const long long pl = p0 + (long long)(SB - 1) * T;
+  const long long lo = p0 < pl ? p0 : pl, hi = p0 < pl ? pl : p0;
+  if (hi <= -kFxOne || lo >= ((long long)N << kFxBits)) return;
+  const int T32 = (int)T;
+#pragma unroll
+  for (int h = 0; h < SB; h += 8) {
+    const long long ph = p0 + (long long)h * T;
+    const int J0 = (int)((ph + (kFxOne >> 1)) >> kFxBits);
+    int r = (int)(ph - ((long long)J0 << kFxBits));
+    const float *row = buf + (h * P + J0 + PAD) * NI;
+    const float *rowx = XTRA ? bufx + h * Px + J0 + PAD : nullptr;
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+      const int j = r >> kFxBits;
+      const float f =
+          __uint_as_float(0x3F800000u | (((unsigned)r >> (kFxBits - 23)) & 0x7FFFFFu)) - 1.0f;
+      const float g = 1.0f - f;
+      const float *q = row + (l * P + j) * NI;
+      if (NI == 4) {
+        const float4 v0 = *reinterpret_cast<const float4 *>(q);
+        const float4 v1 = *reinterpret_cast<const float4 *>(q + 4);
+        acc[0] = fmaf(g, v0.x, fmaf(f, v1.x, acc[0]));
+        acc[1] = fmaf(g, v0.y, fmaf(f, v1.y, acc[1]));
+        acc[2] = fmaf(g, v0.z, fmaf(f, v1.z, acc[2]));
+        acc[3] = fmaf(g, v0.w, fmaf(f, v1.w, acc[3]));
+      } else {
+        acc[0] = fmaf(g, q[0], fmaf(f, q[1], acc[0]));
+      }
+      if (XTRA) {
+        const float *qx = rowx + l * Px + j;
+        ax = fmaf(g, qx[0], fmaf(f, qx[1], ax));
+      }
+      r += T32;
+    }
+  }
+}
+
+// The weight max(1 - |E|, 0) of an exact offset E = e 2^-28 of known sign
+// (NEG: E < 0), as the back-projector weights it: the fraction truncated to
+// 23 bits, clamped by a saturating add.
+template <bool NEG>
+__device__ __forceinline__ float side_weight_sat(int E) {
+  const int a = E >> (kFxBits - 23);
+  return __saturatef(__int_as_float(NEG ? 0x40000000 + a : 0x40000000 - a) - 1.0f);
+}
+
+// One line of B^T for bin k: the nearest pixel r (exact offset D = t(L, r)
+// - k, |D| <= |bstep|/2 after one re-centring step) and its neighbours r-1,
+// r+1, weighted as the back-projector weights them, added in the order
+// r-1, r, r+1.  UP: D can only leave [-half, half] upwards (bline >= 0) or,
+// with !UP, downwards; FIRST checks both sides (the first line's r comes
+// from an FP32 estimate).
+template <int NI, bool FIRST, bool UP>
+__device__ __forceinline__ void bpadj_line(int &r, int &D, int half, int abs_bs, int sgn,
+                                           const float *row, float (&acc)[NI]) {
+  if (FIRST ? D > half : (UP && D > half)) { r -= sgn; D -= abs_bs; }
+  else if (FIRST ? D < -half : (!UP && D < -half)) { r += sgn; D += abs_bs; }
+  const float w_m = side_weight_sat<true>(D - abs_bs);     // pixel r - sgn
+  const float w_mid = __int_as_float(0x40000000 - abs(D >> (kFxBits - 23))) - 1.0f;
+  const float w_p = side_weight_sat<false>(D + abs_bs);    // pixel r + sgn
+  const float wl = sgn > 0 ? w_m : w_p, wr = sgn > 0 ? w_p : w_m;
+  const float *q = row + r * NI;
+  if (NI == 4) {
+    const float4 a = *reinterpret_cast<const float4 *>(q - 4);
+    const float4 b = *reinterpret_cast<const float4 *>(q);
+    const float4 c = *reinterpret_cast<const float4 *>(q + 4);
+    acc[0] = fmaf(wr, c.x, fmaf(w_mid, b.x, fmaf(wl, a.x, acc[0])));
+    acc[1] = fmaf(wr, c.y, fmaf(w_mid, b.y, fmaf(wl, a.y, acc[1])));
+    acc[2] = fmaf(wr, c.z, fmaf(w_mid, b.z, fmaf(wl, a.z, acc[2])));
+    acc[3] = fmaf(wr, c.w, fmaf(w_mid, b.w, fmaf(wl, a.w, acc[3])));
+  } else {
+    acc[0] = fmaf(wr, q[1], fmaf(w_mid, q[0], fmaf(wl, q[-1], acc[0])));
+  }
+}
+
+// B^T over the SB staged lines of a band for bin k: on each line
+// L = s0 + l the pixels whose bin coordinate t(L, P) = T0 + l bline +
+// P bstep (T0 = t00 + s0 bline) lies within one bin of k.  r and D are
+// carried from line to line (D grows by bline, |bline| <= |bstep|, so one
+// re-centring step per line keeps |D| <= |bstep|/2).  A bin whose nearest
+// pixels stay more than 2 positions outside the image on every line of the
+// band adds nothing and is skipped; for the others every tap lies within
+// SB + 4 positions of the image, inside the zero padding.
+template <int SB, int NI>
+__device__ __forceinline__ void bpadj_band(const AngleConst &C, long long T0, float T0f, int k,
+                                           int N, const float *buf, int P, float (&acc)[NI]) {
+  constexpr int PAD = kPartPad(SB);
+  const float inv = C.inv_bstep;
+  const float c0 = ((float)k - T0f) * inv;                       // nearest pixel, first line
+  const float cl = fmaf(-(float)(SB - 1) * C.blinef, inv, c0);   // and last line
+  if (fmaxf(c0, cl) < -3.0f || fminf(c0, cl) > (float)N + 2.0f) return;
+  int r = round_int(c0);
+  const int bs = (int)(unsigned)C.bstep, bl = (int)(unsigned)C.bline;
+  const int abs_bs = abs(bs), half = abs_bs >> 1, sgn = bs < 0 ? -1 : 1;
+  // D = t(s0, r) - k on the low words (exact: |D| < 2^31)
+  int D = (int)((unsigned)T0 + (unsigned)r * (unsigned)bs - ((unsigned)k << kFxBits));
+  const float *row = buf + PAD * NI;
+  bpadj_line<NI, true, true>(r, D, half, abs_bs, sgn, row, acc);
+  if (bl >= 0) {
+#pragma unroll
+    for (int l = 1; l < SB; ++l) {
+      D += bl;
+      bpadj_line<NI, false, true>(r, D, half, abs_bs, sgn, row + l * P * NI, acc);
+    }
+  } else {
+#pragma unroll
+    for (int l = 1; l < SB; ++l) {
+      D += bl;
+      bpadj_line<NI, false, false>(r, D, half, abs_bs, sgn, row + l * P * NI, acc);
+    }
+  }
+}
+
 // With XTRA (Joseph only), image bx of job JX, whose angle list is J's,
 // rides along: staged after the group's band (geometry gx, same lines), it
 // shares every crossing's position and weights and costs only its taps;
-// its sums go to partx.
-template <int OP, int NI, bool XTRA = false>
+// its sums go to partx.  Bands are SB lines; a band past the last image
+// line stages zero lines.
+template <int OP, int NI, int SB, bool XTRA = false>
 __device__ __forceinline__ void partial_task(const Job &J, float *part, int b0, int band,
                                              int a_begin, int AB, int nbands, const BandGeom &g,
                                              const AngleConst *ang, int *status, float *buf,
                                              AngleConst *sc, int *sai, int *spos, int *wsum,
+                                             long long *s0c, float *s0f,
                                              const Job *JX = nullptr, float *partx = nullptr,
                                              int bx = 0, const BandGeom *gx = nullptr) {
+  constexpr int PAD = kPartPad(SB);
   const int tid = threadIdx.x;
   const int na = min(AB, J.m - a_begin);
   const int nd = g.n_det, N = g.N;
-  const int s0 = band * g.SB, s1 = min(N, s0 + g.SB);
+  const int s0 = band * SB, s1 = min(N, s0 + SB), nl = s1 - s0;
   if (na <= 0 || s0 >= N) return;  // uniform over the CTA
   const int *idx = job_idx(J, b0);
   partition_block(idx, J.m, g.n_angles, ang, a_begin, na, spos, wsum);
@@ -924,13 +1070,21 @@ __device__ __forceinline__ void partial_task(const Job &J, float *part, int b0, 
       }
     }
     sai[tid] = ai;
-    if (ai >= 0) sc[tid] = ang[ai];
+    if (ai >= 0) {
+      const AngleConst C = ang[ai];
+      sc[tid] = C;
+      // the band's first line: A's crossing constant G + s0 T, B^T's bin
+      // coordinate t00 + s0 bline (exact) and its FP32 estimate
+      s0c[tid] = OP == OP_JOSEPH ? C.G + (long long)s0 * C.T : C.t00 + (long long)s0 * C.bline;
+      s0f[tid] = fmaf((float)s0, C.blinef, C.t00f);
+    }
   }
   __syncthreads();
   const size_t xo = (size_t)b0 * N * N;
   const size_t plane = (size_t)nbands * J.m * nd;   // floats per image of sums
+  const int Pm = g.Prow > g.Pcol ? g.Prow : g.Pcol;
   float *bufx = nullptr;
-  if (XTRA) bufx = buf + (size_t)g.SB * (g.Prow > g.Pcol ? g.Prow : g.Pcol) * NI;
+  if (XTRA) bufx = buf + (size_t)SB * Pm * NI;
   for (int mode = 1; mode >= 0; --mode) {
     bool any = false;
     for (int a = 0; a < na; ++a) any |= (sai[a] >= 0 && sc[a].mode == mode);
@@ -939,11 +1093,15 @@ __device__ __forceinline__ void partial_task(const Job &J, float *part, int b0, 
     const int Px = XTRA ? (mode ? gx->Prow : gx->Pcol) : 0;
     if (any) {
       __syncthreads();  // the previous mode's band is no longer read
-      if (NI == 4) stage4(J.in, xo, J.in_bf16, N, mode, s0, s1 - s0, buf, P);
-      else stage1(J.in, xo, J.in_bf16, N, mode, s0, s1 - s0, buf, P, g.fast != 0);
+      if (NI == 4) stage4<PAD>(J.in, xo, J.in_bf16, N, mode, s0, nl, buf, P);
+      else stage1<PAD>(J.in, xo, J.in_bf16, N, mode, s0, nl, buf, P, g.fast != 0);
       if (XTRA)
-        stage1(JX->in, (size_t)bx * N * N, JX->in_bf16, N, mode, s0, s1 - s0, bufx, Px,
-               gx->fast != 0);
+        stage1<PAD>(JX->in, (size_t)bx * N * N, JX->in_bf16, N, mode, s0, nl, bufx, Px,
+                    gx->fast != 0);
+      // lines past the image (last band) read as zeros
+      for (int e = tid; e < (SB - nl) * P * NI; e += kThreads) buf[nl * P * NI + e] = 0.0f;
+      if (XTRA)
+        for (int e = tid; e < (SB - nl) * Px; e += kThreads) bufx[nl * Px + e] = 0.0f;
       __syncthreads();
     }
     for (int a = 0; a < na; ++a) {
@@ -957,8 +1115,10 @@ __device__ __forceinline__ void partial_task(const Job &J, float *part, int b0, 
 #pragma unroll
         for (int i = 0; i < NI; ++i) acc[i] = 0.0f;
         if (live) {
-          if (OP == OP_JOSEPH) joseph_lines<NI, XTRA>(sc[a], k, s0, s1, N, buf, P, acc, bufx, Px, &ax);
-          else bpadj_lines<NI>(sc[a], k, s0, s1, N, buf, P, acc);
+          if (OP == OP_JOSEPH)
+            joseph_band<SB, NI, XTRA>(sc[a], s0c[a], k, N, buf, P, acc, bufx, Px, ax);
+          else
+            bpadj_band<SB, NI>(sc[a], s0c[a], s0f[a], k, N, buf, P, acc);
         }
 #pragma unroll
         for (int i = 0; i < NI; ++i) pa[i * plane + k] = acc[i];
@@ -972,23 +1132,26 @@ __device__ __forceinline__ void partial_task(const Job &J, float *part, int b0, 
 // images); the job's remaining images form single-image groups.
 __device__ __forceinline__ int quads(int nimg, int gmax) { return gmax == 4 ? nimg >> 2 : 0; }
 
-// One CTA: band blockIdx.x, angle block blockIdx.y, image group blockIdx.z
-// among the launch's groups of NI images (job 0's, then job 1's).
-template <int OP, int NI, int MINB = (NI == 4 ? 2 : SKEI_PART_MINB1)>
+// One CTA: band blockIdx.x (SB lines), angle block blockIdx.y, image group
+// blockIdx.z among the launch's groups of NI images (job 0's, then job 1's).
+template <int OP, int NI, int MINB, int SB>
 __global__ void __launch_bounds__(kThreads, MINB) band_partial_kernel(const PartArgs args) {
   pdl_enter();
   extern __shared__ float4 smem4[];
   __shared__ AngleConst sc[kMaxABP];
+  __shared__ long long s0c[kMaxABP];
+  __shared__ float s0f[kMaxABP];
   __shared__ int sai[kMaxABP], spos[kMaxABP], wsum[kWarps];
   const int z = blockIdx.z;
   const Job &J0 = args.jobs.j[0];
   if constexpr (OP == OP_JOSEPH && NI == 4) {
     if (args.merge) {
       // group z of job 1 (images 4z .. 4z+3) with image z of job 0
-      partial_task<OP, 4, true>(args.jobs.j[1], args.part + args.off[1], 4 * z, blockIdx.x,
-                                blockIdx.y * args.AB, args.AB, args.nbands, args.g4, args.ang,
-                                args.status, reinterpret_cast<float *>(smem4), sc, sai, spos,
-                                wsum, &J0, args.part + args.off[0], z, &args.g1);
+      partial_task<OP, 4, SB, true>(args.jobs.j[1], args.part + args.off[1], 4 * z, blockIdx.x,
+                                    blockIdx.y * args.AB, args.AB, args.nbands, args.g4,
+                                    args.ang, args.status, reinterpret_cast<float *>(smem4), sc,
+                                    sai, spos, wsum, s0c, s0f, &J0, args.part + args.off[0], z,
+                                    &args.g1);
       return;
     }
   }
@@ -998,9 +1161,10 @@ __global__ void __launch_bounds__(kThreads, MINB) band_partial_kernel(const Part
   const Job &J = args.jobs.j[jn];
   const int zz = z - (jn ? c0 : 0);
   const int b0 = NI == 4 ? 4 * zz : 4 * quads(J.nimg, args.gmax[jn]) + zz;
-  partial_task<OP, NI>(J, args.part + args.off[jn], b0, blockIdx.x, blockIdx.y * args.AB,
-                       args.AB, args.nbands, NI == 4 ? args.g4 : args.g1, args.ang, args.status,
-                       reinterpret_cast<float *>(smem4), sc, sai, spos, wsum);
+  partial_task<OP, NI, SB>(J, args.part + args.off[jn], b0, blockIdx.x, blockIdx.y * args.AB,
+                           args.AB, args.nbands, NI == 4 ? args.g4 : args.g1, args.ang,
+                           args.status, reinterpret_cast<float *>(smem4), sc, sai, spos, wsum,
+                           s0c, s0f);
 }
 
 // out[b][a][k] = epilogue(sum over bands, in order, of the band sums).
@@ -1061,7 +1225,7 @@ int part_layout(skei_plan p, const Jobs &jobs, int *nbands1, int *nbands4, size_
   return SKEI_OK;
 }
 
-template <int OP, int NI, int MINB>
+template <int OP, int NI, int MINB, int SB>
 int set_partial_smem(size_t smem) {
   if (smem > 227 * 1024)
     return set_error(SKEI_EINVAL, "band of %zu bytes needs too much shared memory", smem);
@@ -1070,7 +1234,7 @@ int set_partial_smem(size_t smem) {
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
   if (smem > 48 * 1024 && smem > configured[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(band_partial_kernel<OP, NI, MINB>,
+    cudaError_t e = cudaFuncSetAttribute(band_partial_kernel<OP, NI, MINB, SB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_error(e, "band partial kernel: shared memory attribute");
     configured[dev] = smem;
@@ -1158,20 +1322,28 @@ int launch_band_partial(skei_plan p, const Jobs &jobs, float *work, size_t work_
   PartArgs a{jobs, p->d_ang, p->d_status, g1, g4, {gmj[0], gmj[1]}, AB, nbands, work,
              {off[0], off[1]}, merge};
   const size_t smem4 = part_smem(g4) + (merge ? part_smem(g1) : 0);
+  constexpr int sb4 = SKEI_PART_SBL4, sb1 = SKEI_PART_SBL1;
   if (n4 > 0 && one_wave) {
-    SKEI_TRY((set_partial_smem<OP, 4, 2>(smem4)));
-    launch_k(band_partial_kernel<OP, 4, 2>, dim3(nbands, nblk, n4), dim3(kThreads), smem4, st,
-             a);
+    SKEI_TRY((set_partial_smem<OP, 4, 2, sb4>(smem4)));
+    launch_k(band_partial_kernel<OP, 4, 2, sb4>, dim3(nbands, nblk, n4), dim3(kThreads), smem4,
+             st, a);
   } else if (n4 > 0) {
-    SKEI_TRY((set_partial_smem<OP, 4, 3>(smem4)));
-    launch_k(band_partial_kernel<OP, 4, 3>, dim3(nbands, nblk, n4), dim3(kThreads), smem4, st,
-             a);
+    SKEI_TRY((set_partial_smem<OP, 4, 3, sb4>(smem4)));
+    launch_k(band_partial_kernel<OP, 4, 3, sb4>, dim3(nbands, nblk, n4), dim3(kThreads), smem4,
+             st, a);
   }
   if (n1 > 0) {
+    // single images take the 4-image band height when both occur
     constexpr int m1 = SKEI_PART_MINB1;
-    SKEI_TRY((set_partial_smem<OP, 1, m1>(part_smem(g1))));
-    launch_k(band_partial_kernel<OP, 1, m1>, dim3(nbands, nblk, n1), dim3(kThreads),
-             part_smem(g1), st, a);
+    if (g1.SB == sb4) {
+      SKEI_TRY((set_partial_smem<OP, 1, m1, sb4>(part_smem(g1))));
+      launch_k(band_partial_kernel<OP, 1, m1, sb4>, dim3(nbands, nblk, n1), dim3(kThreads),
+               part_smem(g1), st, a);
+    } else {
+      SKEI_TRY((set_partial_smem<OP, 1, m1, sb1>(part_smem(g1))));
+      launch_k(band_partial_kernel<OP, 1, m1, sb1>, dim3(nbands, nblk, n1), dim3(kThreads),
+               part_smem(g1), st, a);
+    }
   }
   SKEI_TRY(check_launch("band partial sums launch"));
   int nimg = 0;

@@ -28,10 +28,11 @@ __all__ = [
     "bn_workspace_size", "bn_act_fwd", "bn_act_bwd",
     "mri_workspace_size", "mri_fwd", "mri_adj", "mri_dinv", "coil_mix",
     "Batch", "BatchItem", "PROJ_FWD", "PROJ_ADJ", "BACKPROJECT", "BACKPROJECT_ADJ", "FILTER",
-    "FBP",
+    "FBP", "measure_roofs", "ROOFS_WORK_BYTES",
 ]
 
 F32, BF16 = 0, 1
+ROOFS_WORK_BYTES = 1 << 30
 
 library_path = _build.LIB
 if not os.path.exists(library_path):
@@ -50,6 +51,12 @@ class _Job(ctypes.Structure):
                 ("dtype_out", ctypes.c_int), ("in_", ctypes.c_void_p), ("aux", ctypes.c_void_p),
                 ("out", ctypes.c_void_p), ("idx", ctypes.c_void_p), ("m", ctypes.c_int),
                 ("B", ctypes.c_int), ("alpha", ctypes.c_float), ("beta", ctypes.c_float)]
+
+
+class _Roofs(ctypes.Structure):
+    _fields_ = [("fp32_flops", ctypes.c_double), ("smem_bytes", ctypes.c_double),
+                ("l2_bytes", ctypes.c_double), ("dram_read_bytes", ctypes.c_double),
+                ("sms", ctypes.c_int)]
 
 
 class _BatchItemC(ctypes.Structure):
@@ -123,6 +130,7 @@ _SIGS = {
     "skei_batch_info": ([_BATCH, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
                          ctypes.POINTER(_i)], _i),
     "skei_batch_destroy": ([_BATCH], _i),
+    "skei_measure_roofs": ([_vp, _sz, ctypes.POINTER(_Roofs), _vp], _i),
 }
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -856,3 +864,16 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def measure_roofs(work=None) -> dict:
+    """skei_measure_roofs: measured FP32 FMA rate (flop/s), shared-memory load
+    bandwidth, L2 and DRAM read bandwidths (bytes/s) on the current device and
+    stream.  `work` is a CUDA byte tensor of >= ROOFS_WORK_BYTES (allocated
+    here when omitted).  Synchronises the stream."""
+    work = _work(ROOFS_WORK_BYTES, torch.device("cuda", torch.cuda.current_device()), work)
+    out = _Roofs()
+    _check(_lib.skei_measure_roofs(_ptr(work), work.numel(), ctypes.byref(out), _stream()),
+           "skei_measure_roofs")
+    return {"fp32_flops": out.fp32_flops, "smem_bytes": out.smem_bytes,
+            "l2_bytes": out.l2_bytes, "dram_read_bytes": out.dram_read_bytes, "sms": out.sms}
