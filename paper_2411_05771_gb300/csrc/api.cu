@@ -321,15 +321,18 @@ int ei_fwd_impl(skei_plan p, const T *x1, const T *y, int B, const int *mc_idx, 
   const Jobs J = ei_fwd_jobs(x1, y, r, B, mc_idx, mc_m, x2, pbuf, sk_idx, sk_m, G, tb, per_sample);
   const int sk_per = per_sample && sk_idx ? G : 0;
   if (ei_fwd_sums(p, w, J)) {
+    // band sums; their reduction also filters the EI rows: q = (pi/m) H A_S x2
+    const FilterReq fr{1, (float)(kPi / sk_m), qbuf};
     if ((rc = launch_band_partial_jobs(p, OP_JOSEPH, J,
                                       reinterpret_cast<float *>(work + w.band_off),
-                                      w.band_floats, st)))
+                                      w.band_floats, st, &fr)))
       return rc;
-  } else if ((rc = launch_band_jobs(p, OP_JOSEPH, J, st))) {
-    return rc;
+  } else {
+    if ((rc = launch_band_jobs(p, OP_JOSEPH, J, st))) return rc;
+    if ((rc = launch_filter_step<float, float>(p, pbuf, BG * sk_m, (float)(kPi / sk_m), qbuf,
+                                               st)))
+      return rc;
   }
-  if ((rc = launch_filter_step<float, float>(p, pbuf, BG * sk_m, (float)(kPi / sk_m), qbuf, st)))
-    return rc;
   Jobs Jz{};
   Jz.njobs = 1;
   Jz.j[0] = Job{qbuf, nullptr, z, sk_idx, sk_m, BG, 1.0f, 0.0f, 0, tb, tb, sk_per};
@@ -354,12 +357,11 @@ int ei_bwd_impl(skei_plan p, const T *r, const T *g_x2, const T *g_z, int B, con
     Jobs Jb{};
     Jb.njobs = 1;
     Jb.j[0] = Job{g_z, nullptr, ubuf, sk_idx, sk_m, BG, 1.0f, 0.0f, tb, 0, 0, sk_per};
+    // band sums of B_S^T g_z; their reduction also filters: v = (pi/m) H B_S^T g_z
+    const FilterReq fr{0, (float)(kPi / sk_m), vbuf};
     if ((rc = launch_band_partial_jobs(p, OP_BP_ADJ, Jb,
                                       reinterpret_cast<float *>(work + w.band_off),
-                                      w.band_floats, st)))
-      return rc;
-    if ((rc = launch_filter_step<float, float>(p, ubuf, BG * sk_m, (float)(kPi / sk_m), vbuf,
-                                               st)))
+                                      w.band_floats, st, &fr)))
       return rc;
     // one launch: g_x1 = -2 mc_coef A_mc^T r (MC term) and
     // gtot = g_x2 + A_S^T v (EI term)

@@ -1260,7 +1260,7 @@ namespace {
 
 template <int OP>
 int launch_band_partial(skei_plan p, const Jobs &jobs, float *work, size_t work_floats,
-                        cudaStream_t st) {
+                        cudaStream_t st, const FilterReq *fr) {
   // groups of 4 per job, where its images' angle lists allow them; the
   // workspace layout is the one band_partial_floats sizes
   int gmj[kMaxJobs] = {1, 1};
@@ -1346,6 +1346,8 @@ int launch_band_partial(skei_plan p, const Jobs &jobs, float *work, size_t work_
     }
   }
   SKEI_TRY(check_launch("band partial sums launch"));
+  if (fr)
+    return launch_band_sum_filter(p, OP, jobs, nbands, nbands, work, off[0], off[1], *fr, st);
   int nimg = 0;
   for (int q = 0; q < jobs.njobs; ++q) nimg += jobs.j[q].nimg;
   const int n_max = m_max * p->n_det;
@@ -1372,9 +1374,9 @@ size_t band_partial_floats(skei_plan p, const Jobs &jobs) {
 }
 
 int launch_band_partial_jobs(skei_plan p, int op, const Jobs &jobs, float *work,
-                             size_t work_floats, cudaStream_t st) {
-  if (op == OP_JOSEPH) return launch_band_partial<OP_JOSEPH>(p, jobs, work, work_floats, st);
-  if (op == OP_BP_ADJ) return launch_band_partial<OP_BP_ADJ>(p, jobs, work, work_floats, st);
+                             size_t work_floats, cudaStream_t st, const FilterReq *fr) {
+  if (op == OP_JOSEPH) return launch_band_partial<OP_JOSEPH>(p, jobs, work, work_floats, st, fr);
+  if (op == OP_BP_ADJ) return launch_band_partial<OP_BP_ADJ>(p, jobs, work, work_floats, st, fr);
   return set_error(SKEI_EINVAL, "band partial launch: unknown operator %d", op);
 }
 

@@ -304,8 +304,23 @@ int launch_tile_jobs(skei_plan p, int op, const Jobs &jobs, cudaStream_t st);
 // thin band, then their ordered reduction): faster when the caller can give
 // band_partial_floats(p, jobs) floats.
 size_t band_partial_floats(skei_plan p, const Jobs &jobs);
+// With a filter request, the second launch also filters the rows of one
+// job: fout = scale H (the job's rows), FP32, written instead of the job's
+// own output (the step's filtered sinograms); the other job's rows are
+// written as usual.
+struct FilterReq {
+  int job;        // 0 or 1
+  float scale;
+  float *out;     // [rows of the job][n_det]
+};
 int launch_band_partial_jobs(skei_plan p, int op, const Jobs &jobs, float *work,
-                             size_t work_floats, cudaStream_t st);
+                             size_t work_floats, cudaStream_t st,
+                             const FilterReq *fr = nullptr);
+// The second pass of the band sums fused with the filter (in the filter's
+// translation unit, next to its taps).
+int launch_band_sum_filter(skei_plan p, int op, const Jobs &jobs, int nb0, int nb1,
+                           const float *part, size_t off0, size_t off1, const FilterReq &fr,
+                           cudaStream_t st);
 // Whether Joseph's band sums over these two jobs carry job 0's images in the
 // CTAs of job 1's groups of 4 (same angle lists, 4 images of job 1 per image
 // of job 0).

@@ -14,6 +14,10 @@ namespace skei {
 // so one copy lives in constant memory, where a warp-uniform read is a
 // broadcast that costs no shared-memory bandwidth.
 __constant__ float c_ramlak[SKEI_MAX_NDET];
+// The odd taps as pairs (h(n), h(n)), n = 2i + 1 (the even taps beyond h(0)
+// are zero): one 8-byte constant load feeds a packed FP32 pair.
+__constant__ float2 c_ramlak_odd[SKEI_MAX_NDET / 2 + 4];
+__constant__ float2 c_ramlak_pair0[1];   // (h(0), h(0))
 
 // Uploads the taps once per device (called by skei_plan_create, so never
 // inside a stream capture).
@@ -30,6 +34,13 @@ int ensure_ramlak_taps() {
     taps[n] = n == 0 ? 0.25f
                      : (n % 2 == 0 ? 0.0f : (float)(-1.0 / (M_PI * M_PI * (double)n * (double)n)));
   cudaError_t e = cudaMemcpyToSymbol(c_ramlak, taps.data(), sizeof(float) * SKEI_MAX_NDET);
+  if (e != cudaSuccess) return cuda_error(e, "ramlak taps upload");
+  std::vector<float2> odd(SKEI_MAX_NDET / 2 + 4, make_float2(0.0f, 0.0f));
+  for (int i = 0; 2 * i + 1 < SKEI_MAX_NDET; ++i) odd[i] = make_float2(taps[2 * i + 1], taps[2 * i + 1]);
+  e = cudaMemcpyToSymbol(c_ramlak_odd, odd.data(), sizeof(float2) * odd.size());
+  if (e != cudaSuccess) return cuda_error(e, "ramlak odd taps upload");
+  const float2 h0 = make_float2(taps[0], taps[0]);
+  e = cudaMemcpyToSymbol(c_ramlak_pair0, &h0, sizeof(float2));
   if (e != cudaSuccess) return cuda_error(e, "ramlak taps upload");
   done[dev] = true;
   return SKEI_OK;
@@ -110,115 +121,175 @@ __global__ void __launch_bounds__(kFftThreads)
 }
 
 // ------------------------------------------------------------- Ram-Lak --
-// One CTA per sinogram row and pass of kFilterOuts outputs; the row sits in
-// shared memory between zero margins.  Only odd taps are nonzero besides h(0), so an output k needs
-// p[k -+ n] for odd n; a thread owns the 4 same-parity outputs
-// k0, k0+2, k0+4, k0+6 and slides one window of 4 left and 4 right inputs
-// from tap n to n+2: two shared loads serve 4 output-taps.  The taps are
-// split into kSeg segments handled by different warps (short dependency
-// chains, 4x the warps), whose partial sums are added in a fixed order.
-// Shared memory is skewed (one pad word per 8) so the lanes' loads hit
-// distinct banks.
 //   q[k] = scale (h0 p[k] + sum_{n odd} h(n) (p[k-n] + p[k+n]))
-// Build-time tuning knobs: warps per output group (each 128 outputs of a
-// pass) and whether the passes of a row go to separate CTAs (measured on
-// GB300: 3 warps, separate CTAs; 363-bin rows then fill one pass).
-#ifndef SKEI_FILTER_GROUP_WARPS
-#define SKEI_FILTER_GROUP_WARPS 3
+// (the even taps beyond h(0) are zero).  A thread owns 8 consecutive
+// outputs as 4 pairs; for an odd tap n it needs the pairs
+// (p[k-n], p[k-n+1]) and (p[k+n], p[k+n+1]) of each output pair, which
+// start at odd offsets from the even outputs, so the row is staged a second
+// time shifted by one element (`po`), where they are 8-byte aligned.  From
+// tap n to n+2 the left window slides by one pair and the right one the
+// other way: two 8-byte loads per tap serve 8 output-taps, and the packed
+// FP32 pair instructions (add.f32x2, fma.rn.f32x2) do two IEEE operations
+// each.  The odd taps are split into kFSeg segments handled by different
+// warps (short dependency chains, more warps), whose partial sums are added
+// in a fixed order.  Lanes are 8 outputs (32 bytes) apart, so the staged
+// rows are skewed by two words per 32 to keep their 8-byte loads free of
+// bank conflicts.  Build-time knob: kFSeg.
+#ifndef SKEI_FILTER_SEGMENTS
+#define SKEI_FILTER_SEGMENTS 8
 #endif
-#ifndef SKEI_FILTER_PASS_CTAS
-#define SKEI_FILTER_PASS_CTAS 1
-#endif
-constexpr int kSeg = 4;                        // tap segments
-constexpr int kGroupWarps = SKEI_FILTER_GROUP_WARPS;
-constexpr int kFilterThreads = 32 * kGroupWarps * kSeg;
-constexpr int kFilterOuts = 4 * 32 * kGroupWarps;
+constexpr int kFSeg = SKEI_FILTER_SEGMENTS;
+// Skewed shared-memory index of row element e: two pad words per 32, the
+// boundaries placed so that the 4 pairs that one tap group loads from a
+// window never straddle one (left window: boundary after e = 5 mod 32;
+// right window: after 7 mod 32), so a group needs one address computation.
+__host__ __device__ constexpr int skewL(int e) { return e + 2 * ((e + 26) >> 5); }
+__host__ __device__ constexpr int skewR(int e) { return e + 2 * ((e + 24) >> 5); }
+__host__ __device__ constexpr int f_outs(int GW) { return 256 * GW; }   // outputs per pass
+__host__ __device__ inline int f_lp(int nd) { return (nd + 10 + 7) & ~7; }  // left margin
+__host__ __device__ inline int f_len(int nd, int outs) {
+  const int passes = (nd + outs - 1) / outs;
+  return (f_lp(nd) + passes * outs + nd + 24 + 31) & ~31;
+}
+__host__ __device__ inline int f_words(int len) { return len + 2 * (len / 32 + 2); }
+// Group warps (each 256 outputs of a pass) of the launch for rows of nd bins.
+inline int f_group_warps(int nd) { return nd > 512 ? 3 : (nd > 256 ? 2 : 1); }
+// Shared memory: the segments' partial sums, then three skewed copies of the
+// row (even-aligned; shifted by one for each window).
+inline size_t f_smem(int nd, int GW) {
+  const int outs = f_outs(GW);
+  return sizeof(float) * ((size_t)kFSeg * outs + 3 * (size_t)f_words(f_len(nd, outs)));
+}
 
-__host__ __device__ constexpr int skew(int e) { return e + (e >> 3); }
+// A pair of FP32 values held in one 64-bit register pair (low word first),
+// the operand of the packed instructions: loads, stores and arithmetic move
+// it whole, so no packing or unpacking moves are needed.
+typedef unsigned long long f2x;
+__device__ __forceinline__ f2x f2_add(f2x a, f2x b) {
+  f2x d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x f2_mul(f2x a, f2x b) {
+  f2x d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x f2_fma(f2x a, f2x b, f2x c) {
+  f2x d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
 
-// Filters one row: po[k] = scale (H pr)[k], k < nd, for the output passes
-// pass0, pass0 + pstep, ... (kFilterOuts outputs each).
-template <typename Tin, typename Tout>
-__device__ __forceinline__ void ramlak_row(const Tin *pr, Tout *po, int nd, float scale,
-                                           float *smem, int pass0 = 0, int pstep = 1) {
-  float *red = smem;                                    // [kSeg][kFilterOuts]
-  float *pb = red + kSeg * kFilterOuts;
-  // zero margins: before the row, the farthest left tap (n <= nd-1, plus the
-  // window's 2 extra); after it, the last pass's outputs (rounded up to
-  // kFilterOuts) plus the farthest right tap
-  const int lp = nd + 8;
-  const int len = lp + ((nd + kFilterOuts - 1) / kFilterOuts) * kFilterOuts + nd + 16;
-  for (int e = threadIdx.x; e < len; e += kFilterThreads) {
+// Stages one row, p[k] = load(k) for k < nd, into pe (pe[e] = p[e - lp],
+// skewL) and the shifted copies pl, pr (p[e + 1 - lp], skewL and skewR),
+// zero outside the row; all threads, then a barrier.
+template <typename F>
+__device__ __forceinline__ void f_stage(F load, int nd, int len, float *pe, float *pl, float *pr) {
+  const int lp = f_lp(nd);
+  for (int e = threadIdx.x; e < len; e += blockDim.x) {
     const int k = e - lp;
-    pb[skew(e)] = (k >= 0 && k < nd) ? ldg_f(pr + k) : 0.0f;
+    const float v = (k >= 0 && k < nd) ? load(k) : 0.0f;
+    pe[skewL(e)] = v;
+    if (e > 0) {
+      pl[skewL(e - 1)] = v;
+      pr[skewR(e - 1)] = v;
+    }
   }
+  if (threadIdx.x == 0) {
+    pl[skewL(len - 1)] = 0.0f;
+    pr[skewR(len - 1)] = 0.0f;
+  }
+  __syncthreads();
+}
+
+// Filters the staged row: out[k] = scale (H p)[k], k < nd, for the passes
+// pass0, pass0 + pstep, ... of f_outs(GW) outputs.  32 GW kFSeg threads.
+template <int GW, typename Tout>
+__device__ __forceinline__ void f_compute(int nd, float scale, float *red, const float *pe,
+                                          const float *pl, const float *pr, Tout *out, int pass0,
+                                          int pstep) {
+  constexpr int outs = f_outs(GW);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int gw = warp % kGroupWarps, seg = warp / kGroupWarps;
-  // odd taps 1, 3, ..., n_last, split into kSeg runs of whole 4-tap groups
-  const int n_odd = nd / 2;                       // number of odd n < nd
-  const int groups = (n_odd + 3) / 4;
-  const int g0 = (groups * seg) / kSeg, g1 = (groups * (seg + 1)) / kSeg;
-  for (int kb = pass0 * kFilterOuts; kb < nd; kb += pstep * kFilterOuts) {
-    __syncthreads();                              // staging done / red reusable
-    const int ko = gw * 128 + 8 * (lane >> 1) + (lane & 1);   // offset in the pass
-    const int e0 = lp + kb + ko;
-    float acc[4], L[4], R[4];
-    const int nfirst = 1 + 8 * g0;
+  const int gw = warp % GW, seg = warp / GW;
+  const int lp = f_lp(nd);
+  // odd taps 1, 3, ..., split into kFSeg runs of whole 4-tap groups
+  const int groups = (nd / 2 + 3) / 4;
+  const int g0 = (groups * seg) / kFSeg, g1 = (groups * (seg + 1)) / kFSeg;
+  const f2x h0 = reinterpret_cast<const f2x *>(c_ramlak_pair0)[0];
+  const f2x *hodd = reinterpret_cast<const f2x *>(c_ramlak_odd);
+  // the pair (p[k], p[k+1]) for k + lp odd (shifted copies) and even (pe)
+  auto ldl = [&](int k) { return *reinterpret_cast<const f2x *>(pl + skewL(k + lp - 1)); };
+  auto ldr = [&](int k) { return *reinterpret_cast<const f2x *>(pr + skewR(k + lp - 1)); };
+  auto lde = [&](int k) { return *reinterpret_cast<const f2x *>(pe + skewL(k + lp)); };
+  for (int kb = pass0 * outs; kb < nd; kb += pstep * outs) {
+    const int ko = 8 * (lane + 32 * gw);
+    const int k0 = kb + ko;
+    f2x acc[4], L[4], R[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[j] = seg == 0 ? f2_mul(h0, lde(k0 + 2 * j)) : 0ull;
+    const int n1 = 1 + 8 * g0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      acc[j] = (seg == 0) ? c_ramlak[0] * pb[skew(e0 + 2 * j)] : 0.0f;
-      L[j] = pb[skew(e0 + 2 * j - nfirst)];
-      R[j] = pb[skew(e0 + 2 * j + nfirst)];
-    }
-    // skewed addresses of the next left / right loads, per tap t = 0..3 of a
-    // group; a group moves them by -8 / +8 elements, i.e. -9 / +9 words
-    int aL[4], aR[4];
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      aL[t] = skew(e0 - (nfirst + 2 * t) - 2);
-      aR[t] = skew(e0 + 6 + (nfirst + 2 * t) + 2);
+      L[j] = ldl(k0 + 2 * j - n1);
+      R[j] = ldr(k0 + 2 * j + n1);
     }
     for (int gi = g0; gi < g1; ++gi) {
-      const int n0 = 1 + 8 * gi;
+      // the group's new left pairs start at element index bL - 2t (bL = 4
+      // mod 8), the right ones at bR + 2t (bR = 0 mod 8): one skewed base
+      // each, no boundary inside
+      const f2x *ql = reinterpret_cast<const f2x *>(pl + skewL(k0 + lp - 4 - 8 * gi));
+      const f2x *qr = reinterpret_cast<const f2x *>(pr + skewR(k0 + lp + 8 + 8 * gi));
+      const f2x *hg = hodd + 4 * gi;
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        const int n = n0 + 2 * t;
-        const float h = n < nd ? c_ramlak[n] : 0.0f;
+        const f2x hh = hg[t];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[j] = fmaf(h, L[j] + R[j], acc[j]);
-        const float l_new = pb[aL[t]], r_new = pb[aR[t]];
-        aL[t] -= 9;
-        aR[t] += 9;
-        L[3] = L[2]; L[2] = L[1]; L[1] = L[0]; L[0] = l_new;
-        R[0] = R[1]; R[1] = R[2]; R[2] = R[3]; R[3] = r_new;
+        for (int j = 0; j < 4; ++j) acc[j] = f2_fma(hh, f2_add(L[j], R[j]), acc[j]);
+        L[3] = L[2]; L[2] = L[1]; L[1] = L[0]; L[0] = ql[-t];
+        R[0] = R[1]; R[1] = R[2]; R[2] = R[3]; R[3] = qr[t];
       }
     }
+    __syncthreads();   // red of the previous pass is no longer read
 #pragma unroll
-    for (int j = 0; j < 4; ++j) red[seg * kFilterOuts + ko + 2 * j] = acc[j];
+    for (int j = 0; j < 4; ++j) *reinterpret_cast<f2x *>(red + seg * outs + ko + 2 * j) = acc[j];
     __syncthreads();
-    for (int o = threadIdx.x; o < kFilterOuts; o += kFilterThreads) {
+    for (int o = threadIdx.x; o < outs; o += blockDim.x) {
       const int k = kb + o;
       if (k >= nd) continue;
       float v = red[o];
 #pragma unroll
-      for (int sg = 1; sg < kSeg; ++sg) v += red[sg * kFilterOuts + o];
-      st_f(po + k, scale * v);
+      for (int sg = 1; sg < kFSeg; ++sg) v += red[sg * outs + o];
+      st_f(out + k, scale * v);
     }
   }
 }
 
-template <typename Tin, typename Tout>
-__global__ void __launch_bounds__(kFilterThreads)
+// Filters one row from global memory (a CTA of 32 GW kFSeg threads).
+template <int GW, typename Tin, typename Tout>
+__device__ __forceinline__ void ramlak_row(const Tin *pr, Tout *po_out, int nd, float scale,
+                                           float *smem, int pass0, int pstep) {
+  constexpr int outs = f_outs(GW);
+  const int len = f_len(nd, outs), words = f_words(len);
+  float *red = smem, *pe = red + kFSeg * outs, *pl = pe + words, *prr = pl + words;
+  f_stage([&](int k) { return ldg_f(pr + k); }, nd, len, pe, pl, prr);
+  f_compute<GW>(nd, scale, red, pe, pl, prr, po_out, pass0, pstep);
+}
+
+template <int GW, typename Tin, typename Tout>
+__global__ void __launch_bounds__(32 * GW * kFSeg)
     ramlak_kernel(const Tin *in, Tout *out, int nd, float scale) {
   pdl_enter();
   extern __shared__ float4 smem4[];
   const size_t row = blockIdx.x;
-  ramlak_row<Tin, Tout>(in + row * nd, out + row * nd, nd, scale,
-                        reinterpret_cast<float *>(smem4), blockIdx.y, gridDim.y);
+  ramlak_row<GW, Tin, Tout>(in + row * nd, out + row * nd, nd, scale,
+                            reinterpret_cast<float *>(smem4), blockIdx.y, gridDim.y);
 }
 
 // Persistent form over the rows of a batch of instances (task = item, row;
-// rows come in decreasing n_det order).
+// rows come in decreasing n_det order); every row in passes of 768 outputs.
+constexpr int kFBatchGW = 3;
+constexpr int kFilterThreads = 32 * kFBatchGW * kFSeg;
 __global__ void __launch_bounds__(kFilterThreads)
     ramlak_batch_kernel(const BatchItem *items, const int4 *tasks, int n_tasks, int *queue) {
   extern __shared__ float4 smem4[];
@@ -234,17 +305,85 @@ __global__ void __launch_bounds__(kFilterThreads)
     const BatchItem &it = items[tk.x];
     const int nd = it.n_det;
     const size_t o = (size_t)tk.y * nd;
+    constexpr int G = kFBatchGW;
     if (it.in_bf16) {
       const __nv_bfloat16 *pi = static_cast<const __nv_bfloat16 *>(it.in) + o;
-      if (it.out_bf16) ramlak_row(pi, static_cast<__nv_bfloat16 *>(it.out) + o, nd, it.alpha, smem);
-      else ramlak_row(pi, static_cast<float *>(it.out) + o, nd, it.alpha, smem);
+      if (it.out_bf16)
+        ramlak_row<G>(pi, static_cast<__nv_bfloat16 *>(it.out) + o, nd, it.alpha, smem, 0, 1);
+      else ramlak_row<G>(pi, static_cast<float *>(it.out) + o, nd, it.alpha, smem, 0, 1);
     } else {
       const float *pi = static_cast<const float *>(it.in) + o;
-      if (it.out_bf16) ramlak_row(pi, static_cast<__nv_bfloat16 *>(it.out) + o, nd, it.alpha, smem);
-      else ramlak_row(pi, static_cast<float *>(it.out) + o, nd, it.alpha, smem);
+      if (it.out_bf16)
+        ramlak_row<G>(pi, static_cast<__nv_bfloat16 *>(it.out) + o, nd, it.alpha, smem, 0, 1);
+      else ramlak_row<G>(pi, static_cast<float *>(it.out) + o, nd, it.alpha, smem, 0, 1);
     }
   }
   if (threadIdx.x == 0) queue_retire(queue, gridDim.x);
+}
+
+// ------------------------------------------ band sums, then the filter --
+// The second pass of the workspace form of A or B^T (the per-band sums of
+// the band kernels, [image][band][angle][bin]) fused with the Ram-Lak
+// filter of the step: one CTA per sinogram row adds the row's bands in
+// order (as the separate reduction does) and applies the operator's
+// epilogue; rows of job `fjob` are then filtered in the same CTA and only
+// their filtered values are written (to fout, FP32, fscale H), the other
+// job's rows are written as they are (A's MC residual y - A x).
+template <int OP, int GW>
+__global__ void __launch_bounds__(32 * GW * kFSeg)
+    band_sum_filter_kernel(const Jobs jobs, const AngleConst *ang, int n_angles, int nd, int nb0,
+                           int nb1, const float *part, size_t off0, size_t off1, int fjob,
+                           float fscale, float *fout) {
+  pdl_enter();
+  extern __shared__ float4 smem4[];
+  constexpr int outs = f_outs(GW);
+  const int row = blockIdx.x;
+  const int rows0 = jobs.j[0].nimg * jobs.j[0].m;
+  const int jn = row >= rows0 ? 1 : 0;
+  const Job &J = jobs.j[jn];
+  const int r = row - (jn ? rows0 : 0);
+  const int b = r / J.m, a = r - b * J.m;
+  const int nb = jn ? nb1 : nb0;
+  const size_t n = (size_t)J.m * nd;
+  const float *pb = part + (jn ? off1 : off0) + (size_t)b * nb * n + (size_t)a * nd;
+  const int *idx = job_idx(J, b);
+  const int ai = idx ? idx[a] : a;
+  const bool dead = ai < 0 || ai >= n_angles;
+  const float W = (OP == 0 && !dead) ? ang[ai].W : 1.0f;
+  // the row's value at bin k: its bands in order, 32 loads in flight
+  auto value = [&](int k) {
+    float s = 0.0f;
+    int q = 0;
+    for (; q + 32 <= nb; q += 32) {
+      float v[32];
+#pragma unroll
+      for (int u = 0; u < 32; ++u) v[u] = __ldg(pb + (size_t)(q + u) * n + k);
+#pragma unroll
+      for (int u = 0; u < 32; ++u) s += v[u];
+    }
+    for (; q < nb; ++q) s += __ldg(pb + (size_t)q * n + k);
+    float v;
+    if (dead) {
+      v = 0.0f;
+    } else if (OP == 0) {
+      v = s * W;
+      if (J.aux) v = ld_any(J.aux, ((size_t)b * n_angles + ai) * nd + k, J.aux_bf16) - v;
+      v *= J.alpha;
+    } else {
+      v = s * J.alpha;
+    }
+    return v;
+  };
+  if (jn != fjob) {
+    for (int k = threadIdx.x; k < nd; k += blockDim.x)
+      st_any(J.out, (size_t)b * n + (size_t)a * nd + k, value(k), J.out_bf16);
+    return;
+  }
+  const int len = f_len(nd, outs), words = f_words(len);
+  float *red = reinterpret_cast<float *>(smem4), *pe = red + kFSeg * outs, *pl = pe + words,
+        *prr = pl + words;
+  f_stage(value, nd, len, pe, pl, prr);
+  f_compute<GW>(nd, fscale, red, pe, pl, prr, fout + (size_t)r * nd, 0, 1);
 }
 
 // ----------------------------------------- Ram-Lak, tensor-core form --
@@ -562,12 +701,8 @@ __global__ void __launch_bounds__(kAdjT *kAdjT)
 
 }  // namespace
 
-// Dynamic shared memory of a filter CTA for rows of nd bins: the segment
-// partials, then the skewed row between its zero margins.
-static size_t filter_smem(int nd) {
-  const int len = (nd + 8) + ((nd + kFilterOuts - 1) / kFilterOuts) * kFilterOuts + nd + 16;
-  return (size_t)(kSeg * kFilterOuts + skew(len + 16) + 1) * sizeof(float);
-}
+// Dynamic shared memory of a batched filter CTA for rows of nd bins.
+static size_t filter_smem(int nd) { return f_smem(nd, kFBatchGW); }
 
 static int set_filter_batch_smem(size_t smem) {
   static size_t configured[64] = {0};
@@ -602,12 +737,12 @@ int launch_filter_batch(const BatchItem *items, const int4 *tasks, int n_tasks, 
   return check_launch("batched ramlak filter launch");
 }
 
-template <typename Tin, typename Tout>
-int launch_filter(skei_plan p, const Tin *in, int rows, float scale, Tout *out,
-                  cudaStream_t st) {
+template <int GW, typename Tin, typename Tout>
+int launch_filter_gw(skei_plan p, const Tin *in, int rows, float scale, Tout *out,
+                     cudaStream_t st) {
   const int nd = p->n_det;
-  const size_t smem = filter_smem(nd);
-  auto kern = ramlak_kernel<Tin, Tout>;
+  const size_t smem = f_smem(nd, GW);
+  auto kern = ramlak_kernel<GW, Tin, Tout>;
   static size_t configured[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -618,9 +753,58 @@ int launch_filter(skei_plan p, const Tin *in, int rows, float scale, Tout *out,
     if (e != cudaSuccess) return cuda_error(e, "ramlak: shared memory attribute");
     configured[dev] = smem;
   }
-  const int passes = SKEI_FILTER_PASS_CTAS ? (nd + kFilterOuts - 1) / kFilterOuts : 1;
-  launch_k(kern, dim3(rows, passes), dim3(kFilterThreads), smem, st, in, out, nd, scale);
+  const int passes = (nd + f_outs(GW) - 1) / f_outs(GW);
+  launch_k(kern, dim3(rows, passes), dim3(32 * GW * kFSeg), smem, st, in, out, nd, scale);
   return check_launch("ramlak filter launch");
+}
+
+template <typename Tin, typename Tout>
+int launch_filter(skei_plan p, const Tin *in, int rows, float scale, Tout *out,
+                  cudaStream_t st) {
+  switch (f_group_warps(p->n_det)) {
+    case 1: return launch_filter_gw<1>(p, in, rows, scale, out, st);
+    case 2: return launch_filter_gw<2>(p, in, rows, scale, out, st);
+    default: return launch_filter_gw<3>(p, in, rows, scale, out, st);
+  }
+}
+
+template <int OP, int GW>
+int launch_band_sum_filter_gw(skei_plan p, const Jobs &jobs, int nb0, int nb1, const float *part,
+                              size_t off0, size_t off1, const FilterReq &fr, cudaStream_t st) {
+  const int nd = p->n_det;
+  const size_t smem = f_smem(nd, GW);
+  auto kern = band_sum_filter_kernel<OP, GW>;
+  static size_t configured[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (smem > 48 * 1024 && smem > configured[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return cuda_error(e, "band sums + filter: shared memory attribute");
+    configured[dev] = smem;
+  }
+  long long rows = 0;
+  for (int q = 0; q < jobs.njobs; ++q) rows += (long long)jobs.j[q].nimg * jobs.j[q].m;
+  if (rows > 0x7fffffff) return set_error(SKEI_EINVAL, "band sums + filter: too many rows");
+  launch_k(kern, dim3((unsigned)rows), dim3(32 * GW * kFSeg), smem, st, jobs,
+           (const AngleConst *)p->d_ang, p->n_angles, nd, nb0, nb1, part, off0, off1, fr.job,
+           fr.scale, fr.out);
+  return check_launch("band sums + filter launch");
+}
+
+int launch_band_sum_filter(skei_plan p, int op, const Jobs &jobs, int nb0, int nb1,
+                           const float *part, size_t off0, size_t off1, const FilterReq &fr,
+                           cudaStream_t st) {
+  const int gw = f_group_warps(p->n_det);
+  if (op == OP_JOSEPH) {
+    if (gw == 1) return launch_band_sum_filter_gw<OP_JOSEPH, 1>(p, jobs, nb0, nb1, part, off0, off1, fr, st);
+    if (gw == 2) return launch_band_sum_filter_gw<OP_JOSEPH, 2>(p, jobs, nb0, nb1, part, off0, off1, fr, st);
+    return launch_band_sum_filter_gw<OP_JOSEPH, 3>(p, jobs, nb0, nb1, part, off0, off1, fr, st);
+  }
+  if (gw == 1) return launch_band_sum_filter_gw<OP_BP_ADJ, 1>(p, jobs, nb0, nb1, part, off0, off1, fr, st);
+  if (gw == 2) return launch_band_sum_filter_gw<OP_BP_ADJ, 2>(p, jobs, nb0, nb1, part, off0, off1, fr, st);
+  return launch_band_sum_filter_gw<OP_BP_ADJ, 3>(p, jobs, nb0, nb1, part, off0, off1, fr, st);
 }
 
 template <typename Tin, typename Tout>
