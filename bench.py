@@ -184,15 +184,18 @@ class Arm:
         self.mc = torch.empty(B, dtype=torch.float64, device=d)
         self.ei = torch.empty((B, G), dtype=torch.float64, device=d)
         code = S.F32 if dtype == "f32" else S.BF16
-        self.work = torch.empty(max(S.ei_workspace_size(plan, code, B, G, self.mc_m, self.m),
+        self.work = torch.empty(max(S.ttt_residual_workspace_size(plan, code, B, G, self.mc_m,
+                                                                  self.m),
+                                    S.ei_workspace_size(plan, code, B, G, self.mc_m, self.m),
                                     16), dtype=torch.uint8, device=d)
         idx_all, g_all = step_params(1, wl)
         self.load_params(idx_all[0], g_all[0], 1)
-        # kernels per step: residual 1 + forward 4 (5 where its A launch
-        # sums bands) + residual 1 + loss 2 + backward 5 + Adam 1
-        mc_idx = self.idx if wl.mc_sketched else None
-        sk_idx = self.idx if self.sketched else None
-        self.launches_per_step = 14 + S.ei_fwd_form(plan, B, G, mc_idx, sk_idx, wl.per_sample)
+        # kernels per step (skei_ttt_residual_step): rotation (+ x1) 1, A 2
+        # (band sums or clusters, then their reduction with the filter), B
+        # (+ x3) 1, loss partials 1, B^T 2, A^T 1, rotation transpose (+ Adam
+        # + the loss's final pass) 1; with several measurements the Adam
+        # update and the final pass take a launch each
+        self.launches_per_step = (9 if B == 1 else 11) if not wl.per_sample else 13
 
     def pack_params(self, idx_all, g_all, first_step):
         """Host bytes of the draws of consecutive steps, one row per step, in
@@ -214,20 +217,29 @@ class Arm:
         self.step_no.fill_(step_no)
 
     def step(self):
+        """Algorithm 2's iteration: x1 = F(x0), the loss forward, its
+        backward and Adam on theta (dL/dtheta = dL/dx1 + sum_g dL/dx3, F's
+        Jacobian being the identity), in one library call; with a sketch
+        per measurement, the separate calls."""
         S, p = self.S, self.plan
         mc_idx = self.idx if self.wl.mc_sketched else None
         sk_idx = self.idx if self.sketched else None
+        if not self.wl.per_sample:
+            S.ttt_residual_step(p, self.x0, self.theta, self.m1, self.v1, self.step_no, self.y,
+                                self.g, mc_idx, sk_idx, LAM, self.mc_scale, LR,
+                                out=(self.x1, self.r, self.x2, self.z, self.x3, self.gx2,
+                                     self.gx3, self.gx1, self.loss, self.mc, self.ei),
+                                work=self.work)
+            return
         S.residual_add(self.x0, self.theta, out=self.x1)                      # x1 = F(x0)
-        fwd = S.ei_loss_fwd_per_sample if self.wl.per_sample else S.ei_loss_fwd
-        bwd = S.ei_loss_bwd_per_sample if self.wl.per_sample else S.ei_loss_bwd
-        fwd(p, self.x1, self.y, self.g, mc_idx, sk_idx, work=self.work,
-            out=(self.r, self.x2, self.z))
+        S.ei_loss_fwd_per_sample(p, self.x1, self.y, self.g, mc_idx, sk_idx, work=self.work,
+                                 out=(self.r, self.x2, self.z))
         S.residual_add(self.z, self.theta, out=self.x3)                       # x3 = F(z)
         S.ei_loss_finish(self.x2, self.x3, self.r, LAM, self.mc_scale, work=self.work,
                          out=(self.loss, self.mc, self.ei, self.gx2, self.gx3))
-        bwd(p, self.r, self.gx2, self.gx3, self.g, self.mc_scale / self.wl.B, mc_idx, sk_idx,
-            work=self.work, out=self.gx1)
-        # dL/dtheta = dL/dx1 + sum_g dL/dx3 (F's Jacobian is the identity)
+        S.ei_loss_bwd_per_sample(p, self.r, self.gx2, self.gx3, self.g,
+                                 self.mc_scale / self.wl.B, mc_idx, sk_idx, work=self.work,
+                                 out=self.gx1)
         S.adam_step(self.theta, self.m1, self.v1, self.step_no, self.gx1, self.gx3, lr=LR)
 
     def reset(self):
@@ -352,11 +364,12 @@ class Clocks:
 
 def kernel_breakdown(S, arm, stream, reps=20):
     """Device time of every operator of one step, each re-issued with the
-    step's own arguments through the public entry point that runs the same
-    kernels (B^T, and A where the step sums bands: the workspace form, two
-    launches): `reps`
-    copies are captured in a CUDA graph and the replay is timed with CUDA
-    events on the launching stream."""
+    step's own arguments through its public entry point (A and B^T in the
+    band-sums form: sums, then their reduction, two launches; the step
+    itself fuses that reduction with the filter, and the network and Adam
+    into the rotations and the back-projection): `reps` copies are captured
+    in a CUDA graph and the replay is timed with CUDA events on the
+    launching stream."""
     import torch
     p = arm.plan
     mc_idx = arm.idx if arm.wl.mc_sketched else None
@@ -386,24 +399,17 @@ def kernel_breakdown(S, arm, stream, reps=20):
     wsum = torch.empty(max(S.band_sums_workspace_size(p, bpa_jobs), 16), dtype=torch.uint8,
                        device="cuda")
     ops = {
-        "residual_add(x1)": lambda: S.residual_add(arm.x0, arm.theta, out=arm.x1),
         "rotate": lambda: S.rotate(arm.x1, arm.g, out=arm.x2),
         "joseph_fwd(MC+EI)": ((lambda: S.proj_fwd_multi_ws(p, fwd_jobs, work=wfwd)) if fwd_sums
                               else (lambda: S.proj_fwd_multi(p, fwd_jobs))),
         "ramlak(fwd)": lambda: S.filter(p, pbuf, np.pi / m, out=qbuf),
         "backproject": lambda: S.backproject(p, q_t, sk_idx, out=z),
-        "residual_add(x3)": lambda: S.residual_add(arm.z, arm.theta, out=arm.x3),
-        "loss_finish": lambda: S.ei_loss_finish(
-            arm.x2, arm.x3, arm.r, LAM, arm.mc_scale, work=arm.work,
-            out=(arm.loss, arm.mc, arm.ei, arm.gx2, arm.gx3)),
         "backproject_adj": lambda: S.backproject_adj_multi_ws(p, bpa_jobs, work=wsum),
         "ramlak(bwd)": lambda: S.filter(p, pbuf, np.pi / m, out=qbuf),
         "joseph_adj(MC+EI)": lambda: S.proj_adj_multi(
             p, [S.Job(arm.r, arm.gx1, mc_idx, alpha=-2.0 * arm.mc_scale / wl.B),
                 S.Job(qbuf, gtot.reshape(BG, N, N), sk_idx, aux=gx2, beta=1.0)]),
         "rotate_adj": lambda: S.rotate_adj(gtot_t, arm.g, beta=1.0, out=arm.gx1),
-        "adam": lambda: S.adam_step(arm.theta, arm.m1, arm.v1, arm.step_no, arm.gx1, arm.gx3,
-                                    lr=LR),
     }
     times = {}
     with torch.cuda.stream(stream):
@@ -499,25 +505,60 @@ def measured_traffic(kernel):
     return None
 
 
-def roofline_entry(plan, arm, bd, dom, dev):
-    import torch
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    work = algorithmic_flops(plan, arm, dom)
-    if not work:
-        return {"bound": "hbm", "kernel": dom, "achieved": None, "peak": peaks.get("hbm_gbs"),
-                "unit": "GB/s", "frac": None, "traffic": measured_traffic(dom)}
-    peak = sm_count * 128 * 2 * max_mhz * 1e6 / 1e12
-    achieved = work / (bd[dom] * 1e-6) / 1e12
-    return {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": measured_traffic(dom),
-            "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 flop x {max_mhz:.0f} MHz",
-            "work": f"{FLOPS_PER_SAMPLE} flop per interpolation sample", "launch_us": bd[dom]}
+SMEM_BYTES_PER_SAMPLE = 8   # two 4-byte taps per interpolation sample
+
+
+def algorithmic_bytes(plan, arm, name):
+    """Compulsory DRAM bytes of an operator kernel of the step: its input
+    images or sinograms once, its outputs once (4-byte storage)."""
+    wl = arm.wl
+    N, nd, BG, B = plan.N, plan.n_det, wl.B * wl.G, wl.B
+    m, mc_m = arm.m, arm.mc_m
+    img, sino = 4 * N * N, 4 * nd
+    if name.startswith("joseph_fwd"):      # x1, x2 in; r (+ y rows) and p out
+        return (B + BG) * img + B * mc_m * sino * 2 + BG * m * sino
+    if name.startswith("joseph_adj"):      # r, v in; g_x2 in, g_x1, g_tot out
+        return (B * mc_m + BG * m) * sino + (BG + B + BG) * img
+    if name.startswith("backproject_adj"):  # g_z in, sinogram out
+        return BG * img + BG * m * sino
+    if name.startswith("backproject"):      # filtered sinogram in, z out
+        return BG * m * sino + BG * img
+    if name.startswith("ramlak"):
+        return 2 * BG * m * sino
+    return None
+
+
+def roofline_entry(plan, arm, bd, dom, roofs, peaks):
+    """The roofline of kernel `dom`: t_roof = max(FP32 work / FMA rate,
+    shared-memory tap bytes / shared-memory bandwidth, compulsory DRAM bytes
+    / DRAM bandwidth), every rate measured on this GPU (skei_measure_roofs;
+    DRAM: MEASURED_PEAKS.json's copy bandwidth where present); frac =
+    t_roof / measured time, reported against the binding roof."""
+    t = bd[dom] * 1e-6
+    flops = algorithmic_flops(plan, arm, dom)
+    samples = flops / FLOPS_PER_SAMPLE if flops and not dom.startswith("ramlak") else 0
+    smem = SMEM_BYTES_PER_SAMPLE * samples
+    dram = algorithmic_bytes(plan, arm, dom) or 0
+    hbm = float(peaks.get("hbm_gbs", 0.0)) * 1e9 or roofs["dram_read_bytes"]
+    times = {"fp32": (flops or 0) / roofs["fp32_flops"], "smem": smem / roofs["smem_bytes"],
+             "hbm": dram / hbm}
+    bound = max(times, key=times.get)
+    unit_peak = {"fp32": (roofs["fp32_flops"] / 1e12, "TFLOP/s", (flops or 0) / t / 1e12),
+                 "smem": (roofs["smem_bytes"] / 1e9, "GB/s", smem / t / 1e9),
+                 "hbm": (hbm / 1e9, "GB/s", dram / t / 1e9)}
+    peak, unit, achieved = unit_peak[bound]
+    return {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": times[bound] / t, "traffic": measured_traffic(dom),
+            "peak_source": "measured on this GPU: skei_measure_roofs (FP32 FMA chains, 16-byte "
+                           "shared loads)" + ("; HBM: MEASURED_PEAKS.json copy bandwidth"
+                                              if peaks.get("hbm_gbs") else
+                                              "; DRAM: skei_measure_roofs streaming read"),
+            "work": f"{FLOPS_PER_SAMPLE} flop and {SMEM_BYTES_PER_SAMPLE} shared-memory bytes "
+                    "(two 4-byte taps) per interpolation sample; compulsory DRAM bytes: inputs "
+                    "and outputs once",
+            "launch_us": bd[dom],
+            "roof_us": {k: round(v * 1e6, 3) for k, v in times.items()},
+            "frac_by_roof": {k: round(v / t, 4) for k, v in times.items()}}
 
 
 def cpu_oracle_steps(prob, n_steps, sketched):
@@ -1100,15 +1141,25 @@ def main():
     h2d = host_y.numel() * host_y.element_size() + sk.param_bytes
     d2h = 8
 
-    # per-kernel device times and the roofline of the dominant kernel
+    # per-kernel device times and the roofline of the dominant kernel, on
+    # roofs measured on this GPU
     bd = kernel_breakdown(S, sk, stream)
     dom = max(bd, key=bd.get)
-    roof = roofline_entry(plan, sk, bd, dom, dev)
-    kernels = {k: {"us": round(v, 2)} for k, v in bd.items()}
-    for k in kernels:
-        w = algorithmic_flops(plan, sk, k)
-        if w:
-            kernels[k]["tflops"] = round(w / (bd[k] * 1e-6) / 1e12, 3)
+    with torch.cuda.stream(stream):
+        roofs = S.measure_roofs()
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    roof = roofline_entry(plan, sk, bd, dom, roofs, peaks)
+    kernels = {}
+    for k, v in bd.items():
+        kernels[k] = {"us": round(v, 2)}
+        if algorithmic_flops(plan, sk, k):
+            e = roofline_entry(plan, sk, bd, k, roofs, peaks)
+            kernels[k].update(bound=e["bound"], frac=round(e["frac"], 4),
+                              tflops=round(algorithmic_flops(plan, sk, k) / (v * 1e-6) / 1e12, 3))
 
     sk_ms_max, value = whole_job(sk_ms, K, world, dev)
 
@@ -1153,6 +1204,10 @@ def main():
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": (sk.launches_per_step + 1) * K,   # + the draws kernel
             "roofline": roof,
+            "roofs_measured": {"fp32_tflops": roofs["fp32_flops"] / 1e12,
+                               "smem_gbs": roofs["smem_bytes"] / 1e9,
+                               "l2_gbs": roofs["l2_bytes"] / 1e9,
+                               "dram_read_gbs": roofs["dram_read_bytes"] / 1e9, "sms": roofs["sms"]},
             "kernels": kernels,
             "clocks": clk,
             "cpu_baseline": cpu,

@@ -256,6 +256,43 @@ int skei_fbp_adj(skei_plan plan, int dtype, const void *x, int B,
 int skei_fbp_noalloc(skei_plan plan, int dtype, const void *sino, int B,
                      const int *idx, int m, void *x, void *stream);
 
+/* ----------------------------------------------- residual-network step --
+ * skei_ttt_residual_step: one iteration of Algorithm 2 (test-time training
+ * with the sketched EI loss, Eq. (e:skeilossttt); Eq. (e:skeiloss) over B
+ * measurements) for the network F_theta(u) = u + theta, a learnable image
+ * residual: the operator launches of skei_ei_loss_fwd, skei_ei_loss_finish
+ * and skei_ei_loss_bwd, and Adam (Kingma and Ba; Algorithm 2's optimiser)
+ * on theta, with the network folded into them:
+ *   x1 = x0 + theta                 (written by the rotation launch)
+ *   r, x2, z                        as skei_ei_loss_fwd (mc_idx, sk_idx)
+ *   x3 = z + theta                  (the back-projection's second output)
+ *   mc, ei, loss, g_x2, g_x3        as skei_ei_loss_finish (lambda, mc_scale)
+ *   g_x1 = dL/dx1                   as skei_ei_loss_bwd (g_z = g_x3,
+ *                                   mc_coef = mc_scale / B)
+ *   theta, m, v                     one Adam step with dL/dtheta =
+ *                                   sum_b g_x1[b] + sum_{b,g} g_x3[b][g]
+ *                                   (lr, beta1, beta2, eps; *step >= 1, on
+ *                                   the device, as skei_adam_step)
+ * Every result is bitwise the one of that sequence of calls (with
+ * skei_residual_add for F); one measurement (B = 1) takes 9 launches, more
+ * measurements 11 (their gradients sum over the images).
+ *   x0 [B][N][N], y [B][n_angles][n_det], x1 [B][N][N], r [B][mc_m][n_det],
+ *   x2, z, x3, g_x2, g_x3 [B][G][N][N], g_x1 [B][N][N]: dtype; theta, m, v
+ *   [N][N] FP32, updated in place; mc_out [B], ei_out [B][G], loss_out [1]
+ *   device doubles (each may be NULL); g_deg DEVICE double [B][G];
+ *   mc_idx / sk_idx DEVICE int angle lists (NULL: all angles).
+ * work: DEVICE, skei_ttt_residual_workspace_size bytes.  Errors as
+ * skei_ei_loss_fwd and skei_adam_step. */
+size_t skei_ttt_residual_workspace_size(skei_plan plan, int dtype, int B, int G, int mc_m,
+                                        int sk_m);
+int skei_ttt_residual_step(skei_plan plan, int dtype, const void *x0, float *theta, float *m,
+                           float *v, const int *step, const void *y, int B, const int *mc_idx,
+                           int mc_m, const int *sk_idx, int sk_m, const double *g_deg, int G,
+                           double lambda, double mc_scale, double lr, double beta1, double beta2,
+                           double eps, void *x1, void *r, void *x2, void *z, void *x3, void *g_x2,
+                           void *g_x3, void *g_x1, double *mc_out, double *ei_out,
+                           double *loss_out, void *work, size_t work_bytes, void *stream);
+
 /* ---------------------------------------------------------------- roofs --
  * skei_measure_roofs: measurement, no counterpart in the paper.  Times four
  * microbenchmarks on `stream` and returns the measured peaks that bound the

@@ -3,6 +3,7 @@
 // operator kernels, plus the FP64 loss reductions and the stand-in network's
 // helpers (residual add, Adam).
 #include <cmath>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -86,34 +87,7 @@ __global__ void __launch_bounds__(kRedThreads)
                     double mc_scale, double *mc_out, double *ei_out, double *loss_out) {
   pdl_enter();
   extern __shared__ double seg_sum[];  // [B*G + B]
-  const int nseg = B * G + B;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int sgi = warp; sgi < nseg; sgi += kRedThreads / 32) {
-    const bool img = sgi < B * G;
-    const int nch = img ? cpi : cpr;
-    const double *src = img ? partial + (size_t)sgi * cpi
-                            : partial + (size_t)B * G * cpi + (size_t)(sgi - B * G) * cpr;
-    double s = 0.0;
-    for (int c = lane; c < nch; c += 32) s += src[c];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) seg_sum[sgi] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double loss = 0.0;
-    for (int b = 0; b < B; ++b) {
-      const double mc = mc_scale * seg_sum[B * G + b];
-      double ei = 0.0;
-      for (int g = 0; g < G; ++g) {
-        const double e = seg_sum[b * G + g];
-        if (ei_out) ei_out[b * G + g] = e;
-        ei += e;
-      }
-      if (mc_out) mc_out[b] = mc;
-      loss += mc + lambda / G * ei;
-    }
-    if (loss_out) *loss_out = loss / B;
-  }
+  ei_final_block(partial, B, G, cpi, cpr, lambda, mc_scale, mc_out, ei_out, loss_out, seg_sum);
 }
 
 // --------------------------------------------------- stand-in network --
@@ -306,17 +280,34 @@ bool ei_fwd_sums(skei_plan p, const EiWork &w, const Jobs &J) {
 // per_sample: mc_idx and sk_idx hold one angle list per measurement,
 // [B][m] (Algorithm 1 draws a sketch per sample); the G transformed images
 // of measurement b use row b.
+// The residual network F(u) = u + theta folded into the step (all NULL
+// otherwise): x1 = x0 + theta is computed by the rotation launch (x1 is
+// then an output), and x3 = z + theta by the back-projection's epilogue.
+template <typename T>
+struct Residual {
+  const T *x0 = nullptr;
+  const float *theta = nullptr;
+  T *x3 = nullptr;
+};
+
 template <typename T>
 int ei_fwd_impl(skei_plan p, const T *x1, const T *y, int B, const int *mc_idx, int mc_m,
                 const int *sk_idx, int sk_m, const double *g_deg, int G, T *r, T *x2, T *z,
-                char *work, cudaStream_t st, bool per_sample = false) {
+                char *work, cudaStream_t st, bool per_sample = false,
+                const Residual<T> &res = Residual<T>()) {
   const EiWork w = ei_work(p, B, G, mc_m, sk_m);
   float *pbuf = reinterpret_cast<float *>(work);
   float *qbuf = reinterpret_cast<float *>(work + w.p_bytes);
   const int BG = B * G;
   const int tb = is_bf16<T>();
   int rc;
-  if ((rc = launch_rotate<T, T>(x1, B, p->N, g_deg, G, x2, st))) return rc;
+  if (res.x0) {
+    if ((rc = launch_rotate_residual<T>(res.x0, res.theta, B, p->N, g_deg, G,
+                                        const_cast<T *>(x1), x2, st)))
+      return rc;
+  } else if ((rc = launch_rotate<T, T>(x1, B, p->N, g_deg, G, x2, st))) {
+    return rc;
+  }
   // one launch: r = S_mc y - A_mc x1 (MC term) and p = A_S x2 (EI term)
   const Jobs J = ei_fwd_jobs(x1, y, r, B, mc_idx, mc_m, x2, pbuf, sk_idx, sk_m, G, tb, per_sample);
   const int sk_per = per_sample && sk_idx ? G : 0;
@@ -336,13 +327,23 @@ int ei_fwd_impl(skei_plan p, const T *x1, const T *y, int B, const int *mc_idx, 
   Jobs Jz{};
   Jz.njobs = 1;
   Jz.j[0] = Job{qbuf, nullptr, z, sk_idx, sk_m, BG, 1.0f, 0.0f, 0, tb, tb, sk_per};
+  if (res.x3) {
+    Jz.j[0].out2 = res.x3;
+    Jz.j[0].add2 = res.theta;
+    Jz.j[0].out2_bf16 = tb;
+  }
   return launch_tile_jobs(p, OP_BACKPROJECT, Jz, st);
 }
 
+// With last_rotation false (and g_z given) the final rotation transpose is
+// left to the caller: g_x1 then holds the MC term only, and the EI term's
+// unrotated gradients g_x2 + A_S^T v are in the workspace (FP32,
+// [B][G][N][N] at 2 p_bytes).
 template <typename T>
 int ei_bwd_impl(skei_plan p, const T *r, const T *g_x2, const T *g_z, int B, const int *mc_idx,
                 int mc_m, const int *sk_idx, int sk_m, const double *g_deg, int G,
-                double mc_coef, T *g_x1, char *work, cudaStream_t st, bool per_sample = false) {
+                double mc_coef, T *g_x1, char *work, cudaStream_t st, bool per_sample = false,
+                bool last_rotation = true) {
   const EiWork w = ei_work(p, B, G, mc_m, sk_m);
   const int mc_per = per_sample && mc_idx ? 1 : 0, sk_per = per_sample && sk_idx ? G : 0;
   float *ubuf = reinterpret_cast<float *>(work);
@@ -370,6 +371,7 @@ int ei_bwd_impl(skei_plan p, const T *r, const T *g_x2, const T *g_z, int B, con
     J.j[0] = Job{r, nullptr, g_x1, mc_idx, mc_m, B, amc, 0.0f, tb, tb, tb, mc_per};
     J.j[1] = Job{vbuf, g_x2, gtot, sk_idx, sk_m, BG, 1.0f, g_x2 ? 1.0f : 0.0f, 0, tb, 0, sk_per};
     if ((rc = launch_tile_jobs(p, OP_JOSEPH_ADJ, J, st))) return rc;
+    if (!last_rotation) return SKEI_OK;
     return launch_rotate_adj<float, T>(gtot, B, p->N, g_deg, G, 1.0f, 1.0f, g_x1, st);
   }
   // MC term: g_x1 = -2 mc_coef A_mc^T r
@@ -398,6 +400,83 @@ int ei_finish_impl(const T *x2, const T *x3, const T *r, int B, int G, int64_t n
   launch_k(ei_final_kernel, dim3(1), dim3(kRedThreads), smem, st, (const double *)partial, B, G,
            cpi, cpr, lambda, mc_scale, mc_out, ei_out, loss_out);
   return check_launch("loss final reduction launch");
+}
+
+// ------------------------------------------------ residual-network step --
+// Algorithm 2's iteration for the network F_theta(u) = u + theta, the
+// operator launches of skei_ei_loss_fwd / finish / bwd and Adam with the
+// network folded in (see skei_ttt_residual_step).
+size_t ttt_loss_off(skei_plan p, int B, int G, int mc_m, int sk_m) {
+  return align256(ei_work(p, B, G, mc_m, sk_m).total);
+}
+
+void adam_consts(double lr, double beta1, double beta2, double eps, AdamArgs *a) {
+  a->lr = (float)lr;
+  a->b1 = (float)beta1;
+  a->b2 = (float)beta2;
+  // 1 - beta from FP64: 1 - (float)0.999 would be 1.3e-5 off 0.001
+  a->omb1 = (float)(1.0 - beta1);
+  a->omb2 = (float)(1.0 - beta2);
+  a->eps = (float)eps;
+  a->lnb1 = (float)std::log(beta1);
+  a->lnb2 = (float)std::log(beta2);
+}
+
+template <typename T>
+int ttt_step_impl(skei_plan p, const T *x0, float *theta, float *m, float *v, const int *step,
+                  const T *y, int B, const int *mc_idx, int mc_m, const int *sk_idx, int sk_m,
+                  const double *g_deg, int G, double lambda, double mc_scale, const AdamArgs &ad,
+                  T *x1, T *r, T *x2, T *z, T *x3, T *g_x2, T *g_x3, T *g_x1, double *mc_out,
+                  double *ei_out, double *loss_out, char *work, cudaStream_t st) {
+  const int N = p->N;
+  Residual<T> res;
+  res.x0 = x0;
+  res.theta = theta;
+  res.x3 = x3;
+  SKEI_TRY(ei_fwd_impl<T>(p, x1, y, B, mc_idx, mc_m, sk_idx, sk_m, g_deg, G, r, x2, z, work, st,
+                          false, res));
+  // loss partials (and the backward seeds g_x2, g_x3) into their own
+  // workspace region: the final pass runs in the last launch
+  const int64_t n_img = (int64_t)N * N;
+  const int r_len = mc_m * p->n_det;
+  const int cpi = (int)ceil_div((size_t)n_img, kChunk), cpr = (int)ceil_div((size_t)r_len, kChunk);
+  double *partial = reinterpret_cast<double *>(work + ttt_loss_off(p, B, G, mc_m, sk_m));
+  const float kappa = (float)(2.0 * lambda / ((double)B * G));
+  launch_k(ei_partials_kernel<T>, dim3(B * G * cpi + B * cpr), dim3(kRedThreads), 0, st,
+           (const T *)x2, (const T *)x3, (const T *)r, n_img, B * G, cpi, (int64_t)r_len, cpr,
+           kappa, g_x2, g_x3, partial);
+  SKEI_TRY(check_launch("loss partial sums launch"));
+  const LossFinal lf{partial, B, G, cpi, cpr, lambda, mc_scale, mc_out, ei_out, loss_out};
+  // F's Jacobian is the identity: dL/dz = dL/dx3
+  const double mc_coef = mc_scale / B;
+  if (B == 1) {
+    SKEI_TRY(ei_bwd_impl<T>(p, r, g_x2, g_x3, B, mc_idx, mc_m, sk_idx, sk_m, g_deg, G, mc_coef,
+                            g_x1, work, st, false, false));
+    const EiWork w = ei_work(p, B, G, mc_m, sk_m);
+    const float *gtot = reinterpret_cast<const float *>(work + 2 * w.p_bytes);
+    return launch_rotate_adj_adam<T>(gtot, N, g_deg, G, g_x1, g_x3, ad, lf, st);
+  }
+  // several measurements share theta: the gradient sums over them, so the
+  // update is a launch of its own
+  SKEI_TRY(ei_bwd_impl<T>(p, r, g_x2, g_x3, B, mc_idx, mc_m, sk_idx, sk_m, g_deg, G, mc_coef,
+                          g_x1, work, st));
+  const size_t smem = sizeof(double) * (size_t)(B * G + B);
+  launch_k(ei_final_kernel, dim3(1), dim3(kRedThreads), smem, st, (const double *)partial, B, G,
+           cpi, cpr, lambda, mc_scale, mc_out, ei_out, loss_out);
+  SKEI_TRY(check_launch("loss final reduction launch"));
+  const int n = N * N;
+  if (std::is_same<T, float>::value && n % 4 == 0) {
+    launch_k(adam4_kernel, dim3(grid_for(n / 4, 256)), dim3(256), 0, st,
+             reinterpret_cast<float4 *>(theta), n / 4, reinterpret_cast<const float4 *>(g_x1), B,
+             reinterpret_cast<const float4 *>(g_x3), B * G, reinterpret_cast<float4 *>(m),
+             reinterpret_cast<float4 *>(v), step, ad.lr, ad.b1, ad.b2, ad.omb1, ad.omb2, ad.eps,
+             ad.lnb1, ad.lnb2);
+  } else {
+    launch_k(adam_kernel<T>, dim3(grid_for(n, 256)), dim3(256), 0, st, theta, (int64_t)n,
+             (const T *)g_x1, B, (const T *)g_x3, B * G, m, v, step, ad.lr, ad.b1, ad.b2,
+             ad.omb1, ad.omb2, ad.eps, ad.lnb1, ad.lnb2);
+  }
+  return check_launch("adam launch");
 }
 
 // --------------------------------------------------------- validation --
@@ -824,6 +903,54 @@ int skei_ei_loss_bwd_per_sample(skei_plan plan, int dtype, const void *r, const 
                                 void *stream) {
   return ei_bwd_entry(plan, dtype, r, g_x2, g_z, B, mc_idx, mc_m, sk_idx, sk_m, g_deg, G,
                       mc_coef, g_x1, work, work_bytes, stream, true);
+}
+
+size_t skei_ttt_residual_workspace_size(skei_plan plan, int dtype, int B, int G, int mc_m,
+                                        int sk_m) {
+  if (check_plan(plan) || check_dtype(dtype) || B < 1 || G < 1 || mc_m < 1 || sk_m < 1) return 0;
+  return ttt_loss_off(plan, B, G, mc_m, sk_m) +
+         skei_ei_finish_len_workspace_size(B, G, (int64_t)plan->N * plan->N, mc_m * plan->n_det);
+}
+
+int skei_ttt_residual_step(skei_plan plan, int dtype, const void *x0, float *theta, float *m,
+                           float *v, const int *step, const void *y, int B, const int *mc_idx,
+                           int mc_m, const int *sk_idx, int sk_m, const double *g_deg, int G,
+                           double lambda, double mc_scale, double lr, double beta1, double beta2,
+                           double eps, void *x1, void *r, void *x2, void *z, void *x3, void *g_x2,
+                           void *g_x3, void *g_x1, double *mc_out, double *ei_out,
+                           double *loss_out, void *work, size_t work_bytes, void *stream) {
+  SKEI_TRY(check_common(plan, dtype, B));
+  SKEI_TRY(check_rot(dtype, B, plan->N, g_deg, G));
+  const void *ptrs[] = {x0, theta, m, v, y, x1, r, x2, z, x3, g_x2, g_x3, g_x1};
+  const char *names[] = {"x0", "theta", "m", "v", "y", "x1", "r", "x2", "z", "x3", "g_x2",
+                         "g_x3", "g_x1"};
+  for (int i = 0; i < 13; ++i) SKEI_TRY(check_dev_ptr(ptrs[i], names[i]));
+  if (!step || reinterpret_cast<uintptr_t>(step) % 4)
+    return set_error(SKEI_EINVAL, "step is NULL or misaligned");
+  for (const double *q : {mc_out, ei_out, loss_out})
+    if (q && reinterpret_cast<uintptr_t>(q) % 8) return set_error(SKEI_EINVAL, "a loss output is misaligned");
+  if (!(beta1 > 0.0 && beta1 < 1.0 && beta2 > 0.0 && beta2 < 1.0))
+    return set_error(SKEI_EINVAL, "Adam betas must lie in (0, 1)");
+  if (!mc_idx) mc_m = plan->n_angles;
+  if (!sk_idx) sk_m = plan->n_angles;
+  SKEI_TRY(check_idx(plan, mc_idx, mc_m));
+  SKEI_TRY(check_idx(plan, sk_idx, sk_m));
+  SKEI_TRY(check_work(work, work_bytes,
+                      skei_ttt_residual_workspace_size(plan, dtype, B, G, mc_m, sk_m)));
+  AdamArgs ad{theta, m, v, step};
+  adam_consts(lr, beta1, beta2, eps, &ad);
+  cudaStream_t st = as_stream(stream);
+  if (dtype == SKEI_F32)
+    return ttt_step_impl<float>(plan, (const float *)x0, theta, m, v, step, (const float *)y, B,
+                                mc_idx, mc_m, sk_idx, sk_m, g_deg, G, lambda, mc_scale, ad,
+                                (float *)x1, (float *)r, (float *)x2, (float *)z, (float *)x3,
+                                (float *)g_x2, (float *)g_x3, (float *)g_x1, mc_out, ei_out,
+                                loss_out, (char *)work, st);
+  return ttt_step_impl<bf16>(plan, (const bf16 *)x0, theta, m, v, step, (const bf16 *)y, B, mc_idx,
+                             mc_m, sk_idx, sk_m, g_deg, G, lambda, mc_scale, ad, (bf16 *)x1,
+                             (bf16 *)r, (bf16 *)x2, (bf16 *)z, (bf16 *)x3, (bf16 *)g_x2,
+                             (bf16 *)g_x3, (bf16 *)g_x1, mc_out, ei_out, loss_out, (char *)work,
+                             st);
 }
 
 int skei_residual_add(int dtype, const void *u, const float *theta, int count, int64_t n,

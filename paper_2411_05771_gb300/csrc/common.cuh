@@ -236,6 +236,70 @@ __device__ __forceinline__ void st_any(void *p, size_t i, float v, int bf16) {
 template <typename T> __host__ __device__ constexpr int is_bf16() { return 0; }
 template <> __host__ __device__ constexpr int is_bf16<__nv_bfloat16>() { return 1; }
 
+// Rounds an FP32 value to storage type T and back (what storing then
+// loading it gives).
+template <typename T>
+__device__ __forceinline__ float rnd_store(float v) {
+  if constexpr (is_bf16<T>()) return __bfloat162float(__float2bfloat16_rn(v));
+  else return v;
+}
+
+// The final pass of the loss reductions, by one CTA of any shape whose
+// thread count is a whole number (>= 1) of warps (seg_sum: B G + B doubles
+// of shared memory): the segment sums of the per-chunk partials in a fixed
+// order, then
+// loss = (1/B) sum_b [mc_scale ||r_b||^2 + (lambda/G) sum_g ||x2 - x3||^2].
+__device__ __forceinline__ void ei_final_block(const double *partial, int B, int G, int cpi,
+                                               int cpr, double lambda, double mc_scale,
+                                               double *mc_out, double *ei_out, double *loss_out,
+                                               double *seg_sum) {
+  const int nseg = B * G + B;
+  // linear thread index: the CTA may be 2D or 3D
+  const int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+  const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nthreads >> 5;
+  for (int sgi = warp; sgi < nseg; sgi += nwarps) {
+    const bool img = sgi < B * G;
+    const int nch = img ? cpi : cpr;
+    const double *src = img ? partial + (size_t)sgi * cpi
+                            : partial + (size_t)B * G * cpi + (size_t)(sgi - B * G) * cpr;
+    double s = 0.0;
+    for (int c = lane; c < nch; c += 32) s += src[c];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) seg_sum[sgi] = s;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double loss = 0.0;
+    for (int b = 0; b < B; ++b) {
+      const double mc = mc_scale * seg_sum[B * G + b];
+      double ei = 0.0;
+      for (int g = 0; g < G; ++g) {
+        const double e = seg_sum[b * G + g];
+        if (ei_out) ei_out[b * G + g] = e;
+        ei += e;
+      }
+      if (mc_out) mc_out[b] = mc;
+      loss += mc + lambda / G * ei;
+    }
+    if (loss_out) *loss_out = loss / B;
+  }
+}
+
+// Adam's constants (Kingma and Ba 2015) as the kernels take them.
+struct AdamArgs {
+  float *theta, *m, *v;
+  const int *step;
+  float lr, b1, b2, omb1, omb2, eps, lnb1, lnb2;
+};
+// The loss's final pass, done by one CTA of a later launch.
+struct LossFinal {
+  const double *partial;
+  int B, G, cpi, cpr;
+  double lambda, mc_scale;
+  double *mc_out, *ei_out, *loss_out;
+};
+
 // One operator application over a batch of images, as the band and tile
 // kernels see it.  Up to kMaxJobs jobs share a launch (grid.z spans the
 // images of all of them): the fused EI step projects x1 (MC term) and x2
@@ -256,6 +320,12 @@ struct Job {
   // > 0: idx holds one list per sample, [rows][m], and images
   // r idx_per .. (r+1) idx_per - 1 use row r (a sketch per sample, Algorithm 1)
   int idx_per = 0;
+  // tile operators only: a second output out2 = (out as stored) + add2, add2
+  // one FP32 image [N][N] for every image of the job (the residual network
+  // F(u) = u + theta applied to the output)
+  void *out2 = nullptr;
+  const float *add2 = nullptr;
+  int out2_bf16 = 0;
 };
 constexpr int kMaxJobs = 2;
 struct Jobs {
@@ -441,5 +511,18 @@ int launch_rotate(const Tin *x, int B, int N, const double *g_deg, int G,
 template <typename Tin, typename Tout>
 int launch_rotate_adj(const Tin *gout, int B, int N, const double *g_deg, int G,
                       float alpha, float beta, Tout *gx, cudaStream_t st, int Ch = 1);
+// The rotation of the residual network's output: x1 = x0 + theta (stored as
+// T) and out[b][g] = T_g x1[b], in one launch.
+template <typename T>
+int launch_rotate_residual(const T *x0, const float *theta, int B, int N, const double *g_deg,
+                           int G, T *x1, T *out, cudaStream_t st);
+// The last launch of the residual network's step (one measurement):
+// gx = sum_g T_g^T gout[g] + gx (stored as T), then Adam on theta with the
+// gradient gx + sum_g g_x3[g] (F(u) = u + theta is applied to x1 and to the
+// G reconstructions); the loss's final pass rides in the first CTA.
+template <typename T>
+int launch_rotate_adj_adam(const float *gout, int N, const double *g_deg, int G, T *gx,
+                           const T *g_x3, const AdamArgs &adam, const LossFinal &lf,
+                           cudaStream_t st);
 
 }  // namespace skei

@@ -699,6 +699,127 @@ __global__ void __launch_bounds__(kAdjT *kAdjT)
   }
 }
 
+// The rotation of x1 = x0 + theta (the residual network's output): every
+// tap is x1 as stored (the FP32 sum rounded to T), so the result is bitwise
+// the rotation of a stored x1; the CTAs of rotation g = 0 also store x1 at
+// their own pixels.
+template <typename T>
+__global__ void __launch_bounds__(kRotThreads)
+    rotate_residual_kernel(const T *x0, const float *theta, int N, int G, const double *g_deg,
+                           T *x1, T *out) {
+  pdl_enter();
+  __shared__ RotConst rc;
+  const int bg = blockIdx.z, b = bg / G, g = bg - b * G;
+  if (threadIdx.x == 0) rc = rot_const(g_deg[bg], N);
+  __syncthreads();
+  const int tx = threadIdx.x % kRotX, ty = threadIdx.x / kRotX;
+  const int j = blockIdx.x * kRotX + tx;
+  const int i_first = blockIdx.y * kRotY * kRotQ + ty;
+  if (j >= N) return;
+  const T *xb = x0 + (size_t)b * N * N;
+  T *ob = out + (size_t)bg * N * N + j;
+  long long row = rc.R0 + (long long)j * rc.s + (long long)i_first * rc.c;
+  long long col = rc.C0 + (long long)j * rc.c - (long long)i_first * rc.s;
+  const long long drow = rc.c * kRotY, dcol = -rc.s * kRotY;
+  auto x1v = [&](ptrdiff_t e) { return rnd_store<T>(ldg_f(xb + e) + __ldg(theta + e)); };
+#pragma unroll 2
+  for (int q = 0; q < kRotQ; ++q, row += drow, col += dcol) {
+    const int i = i_first + kRotY * q;
+    const int i0 = ipart(row), j0 = ipart(col);
+    const float fr = frac23(row), fc = frac23(col);
+    const float gr = 1.0f - fr, gc = 1.0f - fc;
+    const bool r0 = (unsigned)i0 < (unsigned)N, r1 = (unsigned)(i0 + 1) < (unsigned)N;
+    const bool c0 = (unsigned)j0 < (unsigned)N, c1 = (unsigned)(j0 + 1) < (unsigned)N;
+    const ptrdiff_t e = (ptrdiff_t)i0 * N + j0;
+    const float x00 = (r0 & c0) ? x1v(e) : 0.0f, x01 = (r0 & c1) ? x1v(e + 1) : 0.0f;
+    const float x10 = (r1 & c0) ? x1v(e + N) : 0.0f;
+    const float x11 = (r1 & c1) ? x1v(e + N + 1) : 0.0f;
+    float v = fmaf(gr * gc, x00, 0.0f);
+    v = fmaf(gr * fc, x01, v);
+    v = fmaf(fr * gc, x10, v);
+    v = fmaf(fr * fc, x11, v);
+    if (i < N) {
+      st_f(ob + (size_t)i * N, v);
+      if (g == 0) {
+        const size_t o = (size_t)i * N + j;
+        st_f(x1 + (size_t)b * N * N + o, ldg_f(xb + o) + __ldg(theta + o));
+      }
+    }
+  }
+}
+
+// The last launch of the residual network's step, one measurement: the
+// rotation transpose gx = sum_g T_g^T gout[g] + gx (gx holds the MC term's
+// A^T part; stored as T), then, per pixel, Adam on theta with the gradient
+// d loss / d theta = gx + sum_g g_x3[g] (as stored), summed in that order;
+// CTA 0 also does the loss's final pass (its partials are complete: the
+// launches in between did not touch them).
+template <typename T>
+__global__ void __launch_bounds__(kAdjT *kAdjT)
+    rotate_adj_adam_kernel(const float *gout, int N, int G, const double *g_deg, T *gx,
+                           const T *g_x3, const AdamArgs adam, const LossFinal lf) {
+  pdl_enter();
+  __shared__ RotConst rc[kMaxG];
+  extern __shared__ double seg_sum[];
+  const int t = threadIdx.y * kAdjT + threadIdx.x;
+  const int bb = blockIdx.x * kAdjT + threadIdx.x;
+  float acc[kAdjQ];
+#pragma unroll
+  for (int q = 0; q < kAdjQ; ++q) acc[q] = 0.0f;
+  const size_t plane = (size_t)N * N;
+  for (int g0 = 0; g0 < G; g0 += kMaxG) {
+    const int ng = min(kMaxG, G - g0);
+    __syncthreads();
+    if (t < ng) rc[t] = rot_const(g_deg[g0 + t], N);
+    __syncthreads();
+    if (bb >= N) continue;
+    const float *gb = gout + (size_t)g0 * plane;
+    int g = 0;
+    for (; g + 2 <= ng; g += 2) {
+      const RotConst r0 = rc[g], r1 = rc[g + 1];
+#pragma unroll
+      for (int q = 0; q < kAdjQ; ++q) {
+        const int a = min((blockIdx.y * kAdjQ + q) * kAdjT + threadIdx.y, N - 1);
+        acc[q] = rot_adj_one(r1, gb + (g + 1) * plane, N, a, bb,
+                             rot_adj_one(r0, gb + g * plane, N, a, bb, acc[q]));
+      }
+    }
+    for (; g < ng; ++g) {
+      const RotConst r0 = rc[g];
+#pragma unroll
+      for (int q = 0; q < kAdjQ; ++q) {
+        const int a = min((blockIdx.y * kAdjQ + q) * kAdjT + threadIdx.y, N - 1);
+        acc[q] = rot_adj_one(r0, gb + g * plane, N, a, bb, acc[q]);
+      }
+    }
+  }
+  if (bb < N) {
+    const float tstep = (float)max(__ldg(adam.step), 1);
+    const float bc1 = -expm1f(tstep * adam.lnb1), bc2 = -expm1f(tstep * adam.lnb2);
+#pragma unroll
+    for (int q = 0; q < kAdjQ; ++q) {
+      const int a = (blockIdx.y * kAdjQ + q) * kAdjT + threadIdx.y;
+      if (a >= N) continue;
+      const size_t o = (size_t)a * N + bb;
+      const float v = fmaf(1.0f, ldg_f(gx + o), acc[q]);
+      st_f(gx + o, v);
+      float gr = 0.0f;
+      gr += rnd_store<T>(v);
+      for (int c = 0; c < G; ++c) gr += ldg_f(g_x3 + (size_t)c * plane + o);
+      const float mi = fmaf(adam.b1, adam.m[o], adam.omb1 * gr);
+      const float vi = fmaf(adam.b2, adam.v[o], adam.omb2 * gr * gr);
+      adam.m[o] = mi;
+      adam.v[o] = vi;
+      adam.theta[o] -= adam.lr * (mi / bc1) / (sqrtf(vi / bc2) + adam.eps);
+    }
+  }
+  if (blockIdx.x == 0 && blockIdx.y == 0) {
+    __syncthreads();
+    ei_final_block(lf.partial, lf.B, lf.G, lf.cpi, lf.cpr, lf.lambda, lf.mc_scale, lf.mc_out,
+                   lf.ei_out, lf.loss_out, seg_sum);
+  }
+}
+
 }  // namespace
 
 // Dynamic shared memory of a batched filter CTA for rows of nd bins.
@@ -893,6 +1014,39 @@ int launch_rotate_adj(const Tin *gout, int B, int N, const double *g_deg, int G,
            g_deg, alpha, beta, gx);
   return check_launch("rotation transpose launch");
 }
+
+template <typename T>
+int launch_rotate_residual(const T *x0, const float *theta, int B, int N, const double *g_deg,
+                           int G, T *x1, T *out, cudaStream_t st) {
+  dim3 grid((N + kRotX - 1) / kRotX, (N + kRotY * kRotQ - 1) / (kRotY * kRotQ), B * G);
+  launch_k(rotate_residual_kernel<T>, grid, dim3(kRotThreads), 0, st, x0, theta, N, G, g_deg, x1,
+           out);
+  return check_launch("residual rotation launch");
+}
+
+template <typename T>
+int launch_rotate_adj_adam(const float *gout, int N, const double *g_deg, int G, T *gx,
+                           const T *g_x3, const AdamArgs &adam, const LossFinal &lf,
+                           cudaStream_t st) {
+  dim3 grid((N + kAdjT - 1) / kAdjT, (N + kAdjT * kAdjQ - 1) / (kAdjT * kAdjQ), 1);
+  const size_t smem = sizeof(double) * (size_t)(lf.B * lf.G + lf.B);
+  if (smem > 48 * 1024) return set_error(SKEI_EINVAL, "B*G + B = %d segments is too many", lf.B * lf.G + lf.B);
+  launch_k(rotate_adj_adam_kernel<T>, grid, dim3(kAdjT, kAdjT), smem, st, gout, N, G, g_deg, gx,
+           g_x3, adam, lf);
+  return check_launch("rotation transpose + Adam launch");
+}
+template int launch_rotate_residual<float>(const float *, const float *, int, int,
+                                           const double *, int, float *, float *, cudaStream_t);
+template int launch_rotate_residual<__nv_bfloat16>(const __nv_bfloat16 *, const float *, int,
+                                                   int, const double *, int, __nv_bfloat16 *,
+                                                   __nv_bfloat16 *, cudaStream_t);
+template int launch_rotate_adj_adam<float>(const float *, int, const double *, int, float *,
+                                           const float *, const AdamArgs &, const LossFinal &,
+                                           cudaStream_t);
+template int launch_rotate_adj_adam<__nv_bfloat16>(const float *, int, const double *, int,
+                                                   __nv_bfloat16 *, const __nv_bfloat16 *,
+                                                   const AdamArgs &, const LossFinal &,
+                                                   cudaStream_t);
 
 #define SKEI_FR_INST(TI, TO)                                                                  \
   template int launch_filter<TI, TO>(skei_plan, const TI *, int, float, TO *, cudaStream_t);  \

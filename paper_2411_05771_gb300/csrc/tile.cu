@@ -309,6 +309,13 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
       float v = J.alpha * acc[n][q];
       if (J.beta != 0.0f && J.aux) v = fmaf(J.beta, ld_any(J.aux, o + 32 * q, J.aux_bf16), v);
       st_any(J.out, o + 32 * q, v, J.out_bf16);
+      if (J.out2) {
+        // the value as stored, then the residual: what a separate
+        // out + add2 pass would read and write
+        const float vs = J.out_bf16 ? __bfloat162float(__float2bfloat16_rn(v)) : v;
+        st_any(J.out2, o + 32 * q, vs + __ldg(J.add2 + (size_t)i * N + jb + 32 * q),
+               J.out2_bf16);
+      }
     }
   }
   if (XTRA) {

@@ -28,7 +28,8 @@ __all__ = [
     "bn_workspace_size", "bn_act_fwd", "bn_act_bwd",
     "mri_workspace_size", "mri_fwd", "mri_adj", "mri_dinv", "coil_mix",
     "Batch", "BatchItem", "PROJ_FWD", "PROJ_ADJ", "BACKPROJECT", "BACKPROJECT_ADJ", "FILTER",
-    "FBP", "measure_roofs", "ROOFS_WORK_BYTES",
+    "FBP", "measure_roofs", "ROOFS_WORK_BYTES", "ttt_residual_workspace_size",
+    "ttt_residual_step",
 ]
 
 F32, BF16 = 0, 1
@@ -131,6 +132,10 @@ _SIGS = {
                          ctypes.POINTER(_i)], _i),
     "skei_batch_destroy": ([_BATCH], _i),
     "skei_measure_roofs": ([_vp, _sz, ctypes.POINTER(_Roofs), _vp], _i),
+    "skei_ttt_residual_workspace_size": ([_PLAN, _i, _i, _i, _i, _i], _sz),
+    "skei_ttt_residual_step": ([_PLAN, _i, _vp, _vp, _vp, _vp, _vp, _vp, _i, _vp, _i, _vp, _i,
+                                _vp, _i, _d, _d, _d, _d, _d, _d] + [_vp] * 11 + [_vp, _sz, _vp],
+                               _i),
 }
 for _name, (_args, _res) in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -647,6 +652,53 @@ def adam_step(theta, m, v, step_dev, g1, g2=None, lr=5e-4, beta1=0.9, beta2=0.99
     _check(_lib.skei_adam_step(_ptr(theta), n, _dtype_code(g1), _ptr(g1), c1, _ptr(g2), c2,
                                _ptr(m), _ptr(v), _ptr(step_dev), lr, beta1, beta2, eps, _stream()),
            "skei_adam_step")
+
+
+def ttt_residual_workspace_size(plan: Plan, dtype: int, B: int, G: int, mc_m: int,
+                                sk_m: int) -> int:
+    return int(_lib.skei_ttt_residual_workspace_size(plan.handle, dtype, B, G, mc_m, sk_m))
+
+
+def ttt_residual_step(plan: Plan, x0, theta, m, v, step_dev, y, g_deg, mc_idx=None, sk_idx=None,
+                      lam=1.0, mc_scale=1.0, lr=5e-4, beta1=0.9, beta2=0.999, eps=1e-8,
+                      out=None, work=None):
+    """skei_ttt_residual_step: Algorithm 2's iteration for F(u) = u + theta
+    (theta, m, v updated in place).  out = (x1, r, x2, z, x3, g_x2, g_x3, g_x1,
+    loss, mc, ei), allocated when None; returns it."""
+    B, G = x0.shape[0], g_deg.shape[1]
+    mp, mc_m = _idx_rows(plan, mc_idx, B, False)
+    sp, sk_m = _idx_rows(plan, sk_idx, B, False)
+    N, nd = plan.N, plan.n_det
+    _dev(x0, "x0", shape=(B, N, N))
+    _dev(y, "y", x0.dtype, (B, plan.n_angles, nd))
+    _dev(g_deg, "g_deg", torch.float64, (B, G))
+    for t, nm in ((theta, "theta"), (m, "m"), (v, "v")):
+        _dev(t, nm, torch.float32, (N, N))
+    _dev(step_dev, "step", torch.int32)
+    dev, dt = x0.device, x0.dtype
+    if out is None:
+        img = lambda *sh: torch.empty(sh, device=dev, dtype=dt)  # noqa: E731
+        out = (img(B, N, N), img(B, mc_m, nd), img(B, G, N, N), img(B, G, N, N),
+               img(B, G, N, N), img(B, G, N, N), img(B, G, N, N), img(B, N, N),
+               torch.empty(1, device=dev, dtype=torch.float64),
+               torch.empty(B, device=dev, dtype=torch.float64),
+               torch.empty((B, G), device=dev, dtype=torch.float64))
+    x1, r, x2, z, x3, gx2, gx3, gx1, loss, mc, ei = out
+    for t, nm, sh in ((x1, "x1", (B, N, N)), (r, "r", (B, mc_m, nd)), (x2, "x2", (B, G, N, N)),
+                      (z, "z", (B, G, N, N)), (x3, "x3", (B, G, N, N)),
+                      (gx2, "g_x2", (B, G, N, N)), (gx3, "g_x3", (B, G, N, N)),
+                      (gx1, "g_x1", (B, N, N))):
+        _dev(t, nm, dt, sh)
+    code = _dtype_code(x0)
+    nb = ttt_residual_workspace_size(plan, code, B, G, mc_m, sk_m)
+    w = _work(nb, dev, work)
+    _check(_lib.skei_ttt_residual_step(
+        plan.handle, code, _ptr(x0), _ptr(theta), _ptr(m), _ptr(v), _ptr(step_dev), _ptr(y), B,
+        mp, mc_m, sp, sk_m, _ptr(g_deg), G, float(lam), float(mc_scale), float(lr), float(beta1),
+        float(beta2), float(eps), _ptr(x1), _ptr(r), _ptr(x2), _ptr(z), _ptr(x3), _ptr(gx2),
+        _ptr(gx3), _ptr(gx1), _ptr(mc), _ptr(ei), _ptr(loss), _ptr(w), nb, _stream()),
+        "skei_ttt_residual_step")
+    return out
 
 
 def step_draws(table, counter, out):
