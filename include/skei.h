@@ -66,7 +66,6 @@ extern "C" {
 #define SKEI_EINVAL   (-1)  /* bad shape, pointer, alignment, dtype or size   */
 #define SKEI_ENOMEM   (-2)  /* plan allocation failed                          */
 #define SKEI_ECUDA    (-3)  /* a CUDA runtime call or kernel launch failed     */
-#define SKEI_ETIMEOUT (-4)  /* a bounded device wait gave up                   */
 
 #define SKEI_F32  0
 #define SKEI_BF16 1
@@ -80,6 +79,19 @@ typedef struct skei_plan_s *skei_plan;
 
 /* Library version (major*10000 + minor*100 + patch). */
 int skei_version(void);
+
+/* Bounds-check build (no counterpart in the paper: a debugging aid in place
+ * of a memory checker).  libskei_check.so is built with SKEI_CHECK = 1: the
+ * operator kernels (band, tile and filter kernels) range-check their shared
+ * and global indices; an index outside its buffer sets a bit of a device
+ * check word and the access is skipped (a load reads 0), nothing traps.
+ * skei_check_build returns 1 in that build, 0 otherwise.  skei_check_status
+ * synchronises the device and returns the bits seen since the last reset
+ * (band kernels: bits 0-7, tile kernels 8-15, filter 16-23; always 0 in the
+ * normal build); reset != 0 clears them.  Errors: SKEI_EINVAL (NULL bits),
+ * SKEI_ECUDA. */
+int skei_check_build(void);
+int skei_check_status(unsigned *bits, int reset);
 
 /* Message describing the last failing call on this thread ("" if none).
  * The string stays valid until the next call on this thread. */

@@ -13,6 +13,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libskei.so")
+# the bounds-check build (SKEI_CHECK = 1), objects of its own
+CHECK_DIR = os.path.join(PKG, "_build_check")
+CHECK_LIB = os.path.join(CHECK_DIR, "libskei_check.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -31,29 +34,32 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def _stale(extra_flags) -> bool:
-    if not os.path.exists(LIB):
+def _stale(extra_flags, lib=LIB, out_dir=OUT_DIR) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     deps += [os.path.join(INCLUDE, "skei.h"), os.path.abspath(__file__)]
-    stamp = os.path.join(OUT_DIR, "flags.txt")
+    stamp = os.path.join(out_dir, "flags.txt")
     flags = " ".join(ARCH + NVCC_FLAGS + list(extra_flags))
     if not os.path.exists(stamp) or open(stamp).read() != flags:
         return True
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile every csrc/*.cu for sm_103a and link libskei.so.  Returns its path."""
-    if not force and not _stale(extra_flags):
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), check: bool = False) -> str:
+    """Compile every csrc/*.cu for sm_103a and link libskei.so (check: the
+    bounds-check build libskei_check.so, SKEI_CHECK = 1).  Returns its path."""
+    lib, out_dir = (CHECK_LIB, CHECK_DIR) if check else (LIB, OUT_DIR)
+    extra_flags = list(extra_flags) + (["-DSKEI_CHECK=1"] if check else [])
+    if not force and not _stale(extra_flags, lib, out_dir):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [cc, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
@@ -66,15 +72,15 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
-        raise RuntimeError(f"link of libskei.so failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    with open(os.path.join(OUT_DIR, "flags.txt"), "w") as f:
+        raise RuntimeError(f"link of {os.path.basename(lib)} failed:\n{r.stderr}")
+    os.replace(tmp, lib)
+    with open(os.path.join(out_dir, "flags.txt"), "w") as f:
         f.write(" ".join(ARCH + NVCC_FLAGS + list(extra_flags)))
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

@@ -153,6 +153,14 @@ __device__ __forceinline__ float4 load4(const void *x, size_t i, int bf16) {
   return __ldg(reinterpret_cast<const float4 *>(static_cast<const float *>(x) + i));
 }
 
+// A shared-memory store of the band staging, range-checked in the check
+// build.
+template <typename V>
+__device__ __forceinline__ void sts(V *p, const V &v) {
+  if (SKEI_CHECK && !ck_smem(p, sizeof(V), CK_BAND_STAGE)) return;
+  *p = v;
+}
+
 // Stages lines [s0, s0 + nl) of one image (element offset xo in x) into buf
 // (pitch P positions): mode 1 copies rows, mode 0 copies columns
 // transposed.  PAD zero positions on each side.
@@ -170,19 +178,19 @@ __device__ __forceinline__ void stage1(const void *x, size_t xo, int bf16, int N
         for (; c + 384 < N; c += 512) {
           const float4 a = load4(x, src + c, bf16), b = load4(x, src + c + 128, bf16);
           const float4 d = load4(x, src + c + 256, bf16), e = load4(x, src + c + 384, bf16);
-          *reinterpret_cast<float4 *>(dst + c) = a;
-          *reinterpret_cast<float4 *>(dst + c + 128) = b;
-          *reinterpret_cast<float4 *>(dst + c + 256) = d;
-          *reinterpret_cast<float4 *>(dst + c + 384) = e;
+          sts(reinterpret_cast<float4 *>(dst + c), a);
+          sts(reinterpret_cast<float4 *>(dst + c + 128), b);
+          sts(reinterpret_cast<float4 *>(dst + c + 256), d);
+          sts(reinterpret_cast<float4 *>(dst + c + 384), e);
         }
         for (; c < N; c += 128)
-          *reinterpret_cast<float4 *>(dst + c) = load4(x, src + c, bf16);
+          sts(reinterpret_cast<float4 *>(dst + c), load4(x, src + c, bf16));
       }
     } else {
       for (int r = warp; r < nl; r += kWarps) {
         const size_t src = xo + (size_t)(s0 + r) * N;
         float *dst = buf + r * P + PAD;
-        for (int c = lane; c < N; c += 32) dst[c] = ld_any(x, src + c, bf16);
+        for (int c = lane; c < N; c += 32) sts(dst + c, ld_any(x, src + c, bf16));
       }
     }
   } else {
@@ -195,10 +203,10 @@ __device__ __forceinline__ void stage1(const void *x, size_t xo, int bf16, int N
       const int step = kWarps * per_warp;
       auto put = [&](int p, const float4 &v) {
         float *dst = buf + (4 * q) * P + PAD + p;
-        dst[0] = v.x;
-        dst[P] = v.y;
-        dst[2 * P] = v.z;
-        dst[3 * P] = v.w;
+        sts(dst, v.x);
+        sts(dst + P, v.y);
+        sts(dst + 2 * P, v.z);
+        sts(dst + 3 * P, v.w);
       };
       int p = warp * per_warp + (lane >> qs);
       // 4 loads in flight per thread before their stores
@@ -216,12 +224,12 @@ __device__ __forceinline__ void stage1(const void *x, size_t xo, int bf16, int N
     } else {
       for (int p = warp; p < N; p += kWarps)
         for (int l = lane; l < nl; l += 32)
-          buf[l * P + PAD + p] = ld_any(x, xo + (size_t)p * N + s0 + l, bf16);
+          sts(buf + l * P + PAD + p, ld_any(x, xo + (size_t)p * N + s0 + l, bf16));
     }
   }
   const int npad = P - N;
   for (int r = warp; r < nl; r += kWarps)
-    for (int c = lane; c < npad; c += 32) buf[r * P + (c < PAD ? c : N + c)] = 0.0f;
+    for (int c = lane; c < npad; c += 32) sts(buf + r * P + (c < PAD ? c : N + c), 0.0f);
 }
 
 // The same for 4 images (element offset xo + i N^2), interleaved: position
@@ -236,10 +244,10 @@ __device__ __forceinline__ void stage1(const void *x, size_t xo, int bf16, int N
 // 1): 8 lines x 4 position groups per warp; columns (mode 0): pairs of
 // 4-line groups x consecutive positions.
 __device__ __forceinline__ void store_block(float4 *dst, int step, const float4 (&v)[4]) {
-  dst[0] = make_float4(v[0].x, v[1].x, v[2].x, v[3].x);
-  dst[step] = make_float4(v[0].y, v[1].y, v[2].y, v[3].y);
-  dst[2 * step] = make_float4(v[0].z, v[1].z, v[2].z, v[3].z);
-  dst[3 * step] = make_float4(v[0].w, v[1].w, v[2].w, v[3].w);
+  sts(dst, make_float4(v[0].x, v[1].x, v[2].x, v[3].x));
+  sts(dst + step, make_float4(v[0].y, v[1].y, v[2].y, v[3].y));
+  sts(dst + 2 * step, make_float4(v[0].z, v[1].z, v[2].z, v[3].z));
+  sts(dst + 3 * step, make_float4(v[0].w, v[1].w, v[2].w, v[3].w));
 }
 
 template <int PAD = kPad>
@@ -302,9 +310,9 @@ __device__ __forceinline__ void stage4(const void *x, size_t xo, int bf16, int N
       const size_t src = xo + (size_t)(s0 + r) * N;
       float4 *dst = b4 + r * P + PAD;
       for (int c = tid; c < N; c += kThreads)
-        dst[c] = make_float4(ld_any(x, src + c, bf16), ld_any(x, src + plane + c, bf16),
-                             ld_any(x, src + 2 * plane + c, bf16),
-                             ld_any(x, src + 3 * plane + c, bf16));
+        sts(dst + c, make_float4(ld_any(x, src + c, bf16), ld_any(x, src + plane + c, bf16),
+                                 ld_any(x, src + 2 * plane + c, bf16),
+                                 ld_any(x, src + 3 * plane + c, bf16)));
     }
   } else {
     // 8 consecutive threads take the 8 lines of one position: with an odd
@@ -313,16 +321,16 @@ __device__ __forceinline__ void stage4(const void *x, size_t xo, int bf16, int N
     if (l < nl) {
       for (int p = tid >> 3; p < N; p += kThreads / 8) {
         const size_t src = xo + (size_t)p * N + s0 + l;
-        b4[l * P + PAD + p] = make_float4(ld_any(x, src, bf16), ld_any(x, src + plane, bf16),
-                                           ld_any(x, src + 2 * plane, bf16),
-                                           ld_any(x, src + 3 * plane, bf16));
+        sts(b4 + l * P + PAD + p,
+            make_float4(ld_any(x, src, bf16), ld_any(x, src + plane, bf16),
+                        ld_any(x, src + 2 * plane, bf16), ld_any(x, src + 3 * plane, bf16)));
       }
     }
   }
   const int npad = P - N;
   for (int e = tid; e < nl * npad; e += kThreads) {
     const int r = e / npad, c = e - r * npad;
-    b4[r * P + (c < PAD ? c : N + c)] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    sts(b4 + r * P + (c < PAD ? c : N + c), make_float4(0.0f, 0.0f, 0.0f, 0.0f));
   }
 }
 
@@ -900,6 +908,7 @@ struct PartArgs {
   float *part;       // workspace
   size_t off[kMaxJobs];   // float offset of each job's sums
   int merge;         // A: job 0's image z rides with job 1's group 4z .. 4z+3 (same angles)
+  size_t work_floats;   // workspace extent (range checks of the check build)
 };
 
 // Joseph over the SB staged lines of a band for ray k: adds to acc[i] the
@@ -945,18 +954,18 @@ __device__ __forceinline__ void joseph_band(const AngleConst &C, long long G0, i
       const float g = 1.0f - f;
       const float *q = row + (l * P + j) * NI;
       if (NI == 4) {
-        const float4 v0 = *reinterpret_cast<const float4 *>(q);
-        const float4 v1 = *reinterpret_cast<const float4 *>(q + 4);
+        const float4 v0 = lds_ck(reinterpret_cast<const float4 *>(q), CK_BAND_TAP);
+        const float4 v1 = lds_ck(reinterpret_cast<const float4 *>(q + 4), CK_BAND_TAP);
         acc[0] = fmaf(g, v0.x, fmaf(f, v1.x, acc[0]));
         acc[1] = fmaf(g, v0.y, fmaf(f, v1.y, acc[1]));
         acc[2] = fmaf(g, v0.z, fmaf(f, v1.z, acc[2]));
         acc[3] = fmaf(g, v0.w, fmaf(f, v1.w, acc[3]));
       } else {
-        acc[0] = fmaf(g, q[0], fmaf(f, q[1], acc[0]));
+        acc[0] = fmaf(g, lds_ck(q, CK_BAND_TAP), fmaf(f, lds_ck(q + 1, CK_BAND_TAP), acc[0]));
       }
       if (XTRA) {
         const float *qx = rowx + l * Px + j;
-        ax = fmaf(g, qx[0], fmaf(f, qx[1], ax));
+        ax = fmaf(g, lds_ck(qx, CK_BAND_TAP), fmaf(f, lds_ck(qx + 1, CK_BAND_TAP), ax));
       }
       r += T32;
     }
@@ -989,15 +998,16 @@ __device__ __forceinline__ void bpadj_line(int &r, int &D, int half, int abs_bs,
   const float wl = sgn > 0 ? w_m : w_p, wr = sgn > 0 ? w_p : w_m;
   const float *q = row + r * NI;
   if (NI == 4) {
-    const float4 a = *reinterpret_cast<const float4 *>(q - 4);
-    const float4 b = *reinterpret_cast<const float4 *>(q);
-    const float4 c = *reinterpret_cast<const float4 *>(q + 4);
+    const float4 a = lds_ck(reinterpret_cast<const float4 *>(q - 4), CK_BAND_TAP);
+    const float4 b = lds_ck(reinterpret_cast<const float4 *>(q), CK_BAND_TAP);
+    const float4 c = lds_ck(reinterpret_cast<const float4 *>(q + 4), CK_BAND_TAP);
     acc[0] = fmaf(wr, c.x, fmaf(w_mid, b.x, fmaf(wl, a.x, acc[0])));
     acc[1] = fmaf(wr, c.y, fmaf(w_mid, b.y, fmaf(wl, a.y, acc[1])));
     acc[2] = fmaf(wr, c.z, fmaf(w_mid, b.z, fmaf(wl, a.z, acc[2])));
     acc[3] = fmaf(wr, c.w, fmaf(w_mid, b.w, fmaf(wl, a.w, acc[3])));
   } else {
-    acc[0] = fmaf(wr, q[1], fmaf(w_mid, q[0], fmaf(wl, q[-1], acc[0])));
+    acc[0] = fmaf(wr, lds_ck(q + 1, CK_BAND_TAP),
+                  fmaf(w_mid, lds_ck(q, CK_BAND_TAP), fmaf(wl, lds_ck(q - 1, CK_BAND_TAP), acc[0])));
   }
 }
 
@@ -1049,9 +1059,10 @@ __device__ __forceinline__ void partial_task(const Job &J, float *part, int b0, 
                                              int a_begin, int AB, int nbands, const BandGeom &g,
                                              const AngleConst *ang, int *status, float *buf,
                                              AngleConst *sc, int *sai, int *spos, int *wsum,
-                                             long long *s0c, float *s0f,
-                                             const Job *JX = nullptr, float *partx = nullptr,
-                                             int bx = 0, const BandGeom *gx = nullptr) {
+                                             long long *s0c, float *s0f, const float *wlo,
+                                             const float *whi, const Job *JX = nullptr,
+                                             float *partx = nullptr, int bx = 0,
+                                             const BandGeom *gx = nullptr) {
   constexpr int PAD = kPartPad(SB);
   const int tid = threadIdx.x;
   const int na = min(AB, J.m - a_begin);
@@ -1099,9 +1110,9 @@ __device__ __forceinline__ void partial_task(const Job &J, float *part, int b0, 
         stage1<PAD>(JX->in, (size_t)bx * N * N, JX->in_bf16, N, mode, s0, nl, bufx, Px,
                     gx->fast != 0);
       // lines past the image (last band) read as zeros
-      for (int e = tid; e < (SB - nl) * P * NI; e += kThreads) buf[nl * P * NI + e] = 0.0f;
+      for (int e = tid; e < (SB - nl) * P * NI; e += kThreads) sts(buf + nl * P * NI + e, 0.0f);
       if (XTRA)
-        for (int e = tid; e < (SB - nl) * Px; e += kThreads) bufx[nl * Px + e] = 0.0f;
+        for (int e = tid; e < (SB - nl) * Px; e += kThreads) sts(bufx + nl * Px + e, 0.0f);
       __syncthreads();
     }
     for (int a = 0; a < na; ++a) {
@@ -1121,8 +1132,10 @@ __device__ __forceinline__ void partial_task(const Job &J, float *part, int b0, 
             bpadj_band<SB, NI>(sc[a], s0c[a], s0f[a], k, N, buf, P, acc);
         }
 #pragma unroll
-        for (int i = 0; i < NI; ++i) pa[i * plane + k] = acc[i];
-        if (XTRA) pax[k] = ax;
+        for (int i = 0; i < NI; ++i)
+          if (!SKEI_CHECK || ck_range(pa + i * plane + k, 4, wlo, whi, CK_BAND_SUMS))
+            pa[i * plane + k] = acc[i];
+        if (XTRA && (!SKEI_CHECK || ck_range(pax + k, 4, wlo, whi, CK_BAND_SUMS))) pax[k] = ax;
       }
     }
   }
@@ -1150,7 +1163,8 @@ __global__ void __launch_bounds__(kThreads, MINB) band_partial_kernel(const Part
       partial_task<OP, 4, SB, true>(args.jobs.j[1], args.part + args.off[1], 4 * z, blockIdx.x,
                                     blockIdx.y * args.AB, args.AB, args.nbands, args.g4,
                                     args.ang, args.status, reinterpret_cast<float *>(smem4), sc,
-                                    sai, spos, wsum, s0c, s0f, &J0, args.part + args.off[0], z,
+                                    sai, spos, wsum, s0c, s0f, args.part,
+                                    args.part + args.work_floats, &J0, args.part + args.off[0], z,
                                     &args.g1);
       return;
     }
@@ -1164,14 +1178,14 @@ __global__ void __launch_bounds__(kThreads, MINB) band_partial_kernel(const Part
   partial_task<OP, NI, SB>(J, args.part + args.off[jn], b0, blockIdx.x, blockIdx.y * args.AB,
                            args.AB, args.nbands, NI == 4 ? args.g4 : args.g1, args.ang,
                            args.status, reinterpret_cast<float *>(smem4), sc, sai, spos, wsum,
-                           s0c, s0f);
+                           s0c, s0f, args.part, args.part + args.work_floats);
 }
 
 // out[b][a][k] = epilogue(sum over bands, in order, of the band sums).
 template <int OP>
 __global__ void __launch_bounds__(256)
     band_reduce_kernel(const Jobs jobs, const AngleConst *ang, int n_angles, int nd, int nbands,
-                       const float *part, size_t off0, size_t off1) {
+                       const float *part, size_t off0, size_t off1, size_t work_floats) {
   pdl_enter();
   const int y = blockIdx.y;
   const int jn = (jobs.njobs > 1 && y >= jobs.j[0].nimg) ? 1 : 0;
@@ -1191,6 +1205,12 @@ __global__ void __launch_bounds__(256)
       for (int u = 0; u < 16; ++u) s += v[u];
     }
     for (; q < nbands; ++q) s += __ldg(pb + (size_t)q * n + e);
+    if (SKEI_CHECK) {
+      // the first and last band this output read, and the output
+      ck_range(pb + e, 4, part, part + work_floats, CK_BAND_SUMS);
+      ck_range(pb + (size_t)(nbands - 1) * n + e, 4, part, part + work_floats, CK_BAND_SUMS);
+      if (!ck((long long)b * n + e, (long long)J.nimg * n, CK_BAND_OUT)) continue;
+    }
     const int a = e / nd, k = e - a * nd;
     const int *idx = job_idx(J, b);
     int ai = idx ? idx[a] : a;
@@ -1320,7 +1340,7 @@ int launch_band_partial(skei_plan p, const Jobs &jobs, float *work, size_t work_
   const int nblk = (m_max + AB - 1) / AB;
   AB = (m_max + nblk - 1) / nblk;   // balanced blocks
   PartArgs a{jobs, p->d_ang, p->d_status, g1, g4, {gmj[0], gmj[1]}, AB, nbands, work,
-             {off[0], off[1]}, merge};
+             {off[0], off[1]}, merge, work_floats};
   const size_t smem4 = part_smem(g4) + (merge ? part_smem(g1) : 0);
   constexpr int sb4 = SKEI_PART_SBL4, sb1 = SKEI_PART_SBL1;
   if (n4 > 0 && one_wave) {
@@ -1347,18 +1367,21 @@ int launch_band_partial(skei_plan p, const Jobs &jobs, float *work, size_t work_
   }
   SKEI_TRY(check_launch("band partial sums launch"));
   if (fr)
-    return launch_band_sum_filter(p, OP, jobs, nbands, nbands, work, off[0], off[1], *fr, st);
+    return launch_band_sum_filter(p, OP, jobs, nbands, nbands, work, off[0], off[1], work_floats,
+                                  *fr, st);
   int nimg = 0;
   for (int q = 0; q < jobs.njobs; ++q) nimg += jobs.j[q].nimg;
   const int n_max = m_max * p->n_det;
   const int gx = std::max(1, std::min((n_max + 255) / 256, 4 * sm_count() / std::max(nimg, 1) + 1));
   launch_k(band_reduce_kernel<OP>, dim3(gx, nimg), dim3(256), 0, st, jobs,
            (const AngleConst *)p->d_ang, p->n_angles, p->n_det, nbands, (const float *)work,
-           off[0], off[1]);
+           off[0], off[1], work_floats);
   return check_launch("band sums reduction launch");
 }
 
 }  // namespace
+
+SKEI_CHECK_READER(check_read_band)
 
 int launch_band_jobs(skei_plan p, int op, const Jobs &jobs, cudaStream_t st) {
   if (op == OP_JOSEPH) return launch_band<OP_JOSEPH>(p, jobs, st);

@@ -128,6 +128,100 @@ inline void launch_k(void (*kern)(ExpTypes...), dim3 grid, dim3 block, size_t sm
   cudaLaunchKernelEx(&cfg, kern, std::forward<ActTypes>(args)...);
 }
 
+// ---------------------------------------------------- bounds-check build --
+// SKEI_CHECK = 1 (a separate build, libskei_check.so) range-checks the shared
+// and global indices of the operator kernels.  An index outside its buffer
+// (shared: outside the CTA's shared allocation; global: outside the
+// buffer's extent) sets the site's bit in its translation unit's check
+// word, and the access is skipped (a load reads 0).  No assert, no trap:
+// the kernel finishes and the host reads the bits (skei_check_status).
+// With SKEI_CHECK = 0 the checks compile to nothing.
+#ifndef SKEI_CHECK
+#define SKEI_CHECK 0
+#endif
+#if SKEI_CHECK
+static __device__ unsigned g_skei_check;   // one word per translation unit
+#endif
+// Bits: band kernels 0-7, tile kernels 8-15, filter and rotations 16-23.
+enum : unsigned {
+  CK_BAND_STAGE = 1u << 0, CK_BAND_TAP = 1u << 1, CK_BAND_SUMS = 1u << 2,
+  CK_BAND_OUT = 1u << 3,
+  CK_TILE_WIN = 1u << 8, CK_TILE_TAP = 1u << 9, CK_TILE_IN = 1u << 10, CK_TILE_OUT = 1u << 11,
+  CK_FILT_STAGE = 1u << 16, CK_FILT_TAP = 1u << 17, CK_FILT_SUMS = 1u << 18,
+  CK_FILT_OUT = 1u << 19,
+};
+// Whether index i lies in [0, n); records `bit` if not.
+__device__ __forceinline__ bool ck(long long i, long long n, unsigned bit) {
+#if SKEI_CHECK
+  if ((unsigned long long)i < (unsigned long long)n) return true;
+  atomicOr(&g_skei_check, bit);
+  return false;
+#else
+  (void)i; (void)n; (void)bit;
+  return true;
+#endif
+}
+// Whether the `bytes` at pointer p lie inside the CTA's dynamic shared
+// memory (where every checked shared buffer lives: all extern __shared__
+// arrays start at its base); records `bit` if not.
+extern __shared__ float4 skei_dyn_smem[];
+__device__ __forceinline__ bool ck_smem(const void *p, int bytes, unsigned bit) {
+#if SKEI_CHECK
+  unsigned dyn;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+  const unsigned base = (unsigned)__cvta_generic_to_shared(skei_dyn_smem);
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  if (__isShared(p) && a >= base && a + (unsigned)bytes <= base + dyn) return true;
+  atomicOr(&g_skei_check, bit);
+  return false;
+#else
+  (void)p; (void)bytes; (void)bit;
+  return true;
+#endif
+}
+// Whether [p, p + bytes) lies inside [lo, hi); records `bit` if not.
+__device__ __forceinline__ bool ck_range(const void *p, int bytes, const void *lo, const void *hi,
+                                         unsigned bit) {
+#if SKEI_CHECK
+  const char *c = static_cast<const char *>(p);
+  if (c >= static_cast<const char *>(lo) && c + bytes <= static_cast<const char *>(hi))
+    return true;
+  atomicOr(&g_skei_check, bit);
+  return false;
+#else
+  (void)p; (void)bytes; (void)lo; (void)hi; (void)bit;
+  return true;
+#endif
+}
+// Checked shared-memory loads (0 where out of range).
+template <typename V>
+__device__ __forceinline__ V lds_ck(const V *p, unsigned bit) {
+  if (SKEI_CHECK && !ck_smem(p, sizeof(V), bit)) return V{};
+  return *p;
+}
+// Host side: ORs this translation unit's check word into *bits (reset: then
+// clears it).  One per .cu file (SKEI_CHECK_READER).
+#if SKEI_CHECK
+#define SKEI_CHECK_READER(name)                                                         \
+  int name(unsigned *bits, int reset) {                                                 \
+    unsigned v = 0;                                                                     \
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_skei_check, sizeof v);                   \
+    if (e == cudaSuccess && reset) {                                                    \
+      const unsigned z = 0;                                                             \
+      e = cudaMemcpyToSymbol(g_skei_check, &z, sizeof z);                               \
+    }                                                                                   \
+    if (e != cudaSuccess) return cuda_error(e, "check word");                           \
+    *bits |= v;                                                                         \
+    return SKEI_OK;                                                                     \
+  }
+#else
+#define SKEI_CHECK_READER(name) \
+  int name(unsigned *bits, int) { (void)bits; return SKEI_OK; }
+#endif
+int check_read_band(unsigned *bits, int reset);
+int check_read_tile(unsigned *bits, int reset);
+int check_read_filter(unsigned *bits, int reset);
+
 // ---------------------------------------------------------------- errors --
 int set_error(int code, const char *fmt, ...);
 int cuda_error(cudaError_t e, const char *where);
@@ -389,8 +483,8 @@ int launch_band_partial_jobs(skei_plan p, int op, const Jobs &jobs, float *work,
 // The second pass of the band sums fused with the filter (in the filter's
 // translation unit, next to its taps).
 int launch_band_sum_filter(skei_plan p, int op, const Jobs &jobs, int nb0, int nb1,
-                           const float *part, size_t off0, size_t off1, const FilterReq &fr,
-                           cudaStream_t st);
+                           const float *part, size_t off0, size_t off1, size_t part_floats,
+                           const FilterReq &fr, cudaStream_t st);
 // Whether Joseph's band sums over these two jobs carry job 0's images in the
 // CTAs of job 1's groups of 4 (same angle lists, 4 images of job 1 per image
 // of job 0).

@@ -190,15 +190,15 @@ __device__ __forceinline__ void f_stage(F load, int nd, int len, float *pe, floa
   for (int e = threadIdx.x; e < len; e += blockDim.x) {
     const int k = e - lp;
     const float v = (k >= 0 && k < nd) ? load(k) : 0.0f;
-    pe[skewL(e)] = v;
+    if (!SKEI_CHECK || ck_smem(pe + skewL(e), 4, CK_FILT_STAGE)) pe[skewL(e)] = v;
     if (e > 0) {
-      pl[skewL(e - 1)] = v;
-      pr[skewR(e - 1)] = v;
+      if (!SKEI_CHECK || ck_smem(pl + skewL(e - 1), 4, CK_FILT_STAGE)) pl[skewL(e - 1)] = v;
+      if (!SKEI_CHECK || ck_smem(pr + skewR(e - 1), 4, CK_FILT_STAGE)) pr[skewR(e - 1)] = v;
     }
   }
   if (threadIdx.x == 0) {
-    pl[skewL(len - 1)] = 0.0f;
-    pr[skewR(len - 1)] = 0.0f;
+    if (!SKEI_CHECK || ck_smem(pl + skewL(len - 1), 4, CK_FILT_STAGE)) pl[skewL(len - 1)] = 0.0f;
+    if (!SKEI_CHECK || ck_smem(pr + skewR(len - 1), 4, CK_FILT_STAGE)) pr[skewR(len - 1)] = 0.0f;
   }
   __syncthreads();
 }
@@ -219,9 +219,15 @@ __device__ __forceinline__ void f_compute(int nd, float scale, float *red, const
   const f2x h0 = reinterpret_cast<const f2x *>(c_ramlak_pair0)[0];
   const f2x *hodd = reinterpret_cast<const f2x *>(c_ramlak_odd);
   // the pair (p[k], p[k+1]) for k + lp odd (shifted copies) and even (pe)
-  auto ldl = [&](int k) { return *reinterpret_cast<const f2x *>(pl + skewL(k + lp - 1)); };
-  auto ldr = [&](int k) { return *reinterpret_cast<const f2x *>(pr + skewR(k + lp - 1)); };
-  auto lde = [&](int k) { return *reinterpret_cast<const f2x *>(pe + skewL(k + lp)); };
+  auto ldl = [&](int k) {
+    return lds_ck(reinterpret_cast<const f2x *>(pl + skewL(k + lp - 1)), CK_FILT_TAP);
+  };
+  auto ldr = [&](int k) {
+    return lds_ck(reinterpret_cast<const f2x *>(pr + skewR(k + lp - 1)), CK_FILT_TAP);
+  };
+  auto lde = [&](int k) {
+    return lds_ck(reinterpret_cast<const f2x *>(pe + skewL(k + lp)), CK_FILT_TAP);
+  };
   for (int kb = pass0 * outs; kb < nd; kb += pstep * outs) {
     const int ko = 8 * (lane + 32 * gw);
     const int k0 = kb + ko;
@@ -246,13 +252,15 @@ __device__ __forceinline__ void f_compute(int nd, float scale, float *red, const
         const f2x hh = hg[t];
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[j] = f2_fma(hh, f2_add(L[j], R[j]), acc[j]);
-        L[3] = L[2]; L[2] = L[1]; L[1] = L[0]; L[0] = ql[-t];
-        R[0] = R[1]; R[1] = R[2]; R[2] = R[3]; R[3] = qr[t];
+        L[3] = L[2]; L[2] = L[1]; L[1] = L[0]; L[0] = lds_ck(ql - t, CK_FILT_TAP);
+        R[0] = R[1]; R[1] = R[2]; R[2] = R[3]; R[3] = lds_ck(qr + t, CK_FILT_TAP);
       }
     }
     __syncthreads();   // red of the previous pass is no longer read
 #pragma unroll
-    for (int j = 0; j < 4; ++j) *reinterpret_cast<f2x *>(red + seg * outs + ko + 2 * j) = acc[j];
+    for (int j = 0; j < 4; ++j)
+      if (!SKEI_CHECK || ck_smem(red + seg * outs + ko + 2 * j, 8, CK_FILT_STAGE))
+        *reinterpret_cast<f2x *>(red + seg * outs + ko + 2 * j) = acc[j];
     __syncthreads();
     for (int o = threadIdx.x; o < outs; o += blockDim.x) {
       const int k = kb + o;
@@ -332,8 +340,8 @@ __global__ void __launch_bounds__(kFilterThreads)
 template <int OP, int GW>
 __global__ void __launch_bounds__(32 * GW * kFSeg)
     band_sum_filter_kernel(const Jobs jobs, const AngleConst *ang, int n_angles, int nd, int nb0,
-                           int nb1, const float *part, size_t off0, size_t off1, int fjob,
-                           float fscale, float *fout) {
+                           int nb1, const float *part, size_t off0, size_t off1,
+                           size_t part_floats, int fjob, float fscale, float *fout) {
   pdl_enter();
   extern __shared__ float4 smem4[];
   constexpr int outs = f_outs(GW);
@@ -362,6 +370,11 @@ __global__ void __launch_bounds__(32 * GW * kFSeg)
       for (int u = 0; u < 32; ++u) s += v[u];
     }
     for (; q < nb; ++q) s += __ldg(pb + (size_t)q * n + k);
+    if (SKEI_CHECK) {
+      // the first and last band this value read
+      ck_range(pb + k, 4, part, part + part_floats, CK_FILT_SUMS);
+      ck_range(pb + (size_t)(nb - 1) * n + k, 4, part, part + part_floats, CK_FILT_SUMS);
+    }
     float v;
     if (dead) {
       v = 0.0f;
@@ -822,6 +835,8 @@ __global__ void __launch_bounds__(kAdjT *kAdjT)
 
 }  // namespace
 
+SKEI_CHECK_READER(check_read_filter)
+
 // Dynamic shared memory of a batched filter CTA for rows of nd bins.
 static size_t filter_smem(int nd) { return f_smem(nd, kFBatchGW); }
 
@@ -891,7 +906,8 @@ int launch_filter(skei_plan p, const Tin *in, int rows, float scale, Tout *out,
 
 template <int OP, int GW>
 int launch_band_sum_filter_gw(skei_plan p, const Jobs &jobs, int nb0, int nb1, const float *part,
-                              size_t off0, size_t off1, const FilterReq &fr, cudaStream_t st) {
+                              size_t off0, size_t off1, size_t part_floats, const FilterReq &fr,
+                              cudaStream_t st) {
   const int nd = p->n_det;
   const size_t smem = f_smem(nd, GW);
   auto kern = band_sum_filter_kernel<OP, GW>;
@@ -909,23 +925,33 @@ int launch_band_sum_filter_gw(skei_plan p, const Jobs &jobs, int nb0, int nb1, c
   for (int q = 0; q < jobs.njobs; ++q) rows += (long long)jobs.j[q].nimg * jobs.j[q].m;
   if (rows > 0x7fffffff) return set_error(SKEI_EINVAL, "band sums + filter: too many rows");
   launch_k(kern, dim3((unsigned)rows), dim3(32 * GW * kFSeg), smem, st, jobs,
-           (const AngleConst *)p->d_ang, p->n_angles, nd, nb0, nb1, part, off0, off1, fr.job,
-           fr.scale, fr.out);
+           (const AngleConst *)p->d_ang, p->n_angles, nd, nb0, nb1, part, off0, off1,
+           part_floats, fr.job, fr.scale, fr.out);
   return check_launch("band sums + filter launch");
 }
 
 int launch_band_sum_filter(skei_plan p, int op, const Jobs &jobs, int nb0, int nb1,
-                           const float *part, size_t off0, size_t off1, const FilterReq &fr,
-                           cudaStream_t st) {
+                           const float *part, size_t off0, size_t off1, size_t part_floats,
+                           const FilterReq &fr, cudaStream_t st) {
   const int gw = f_group_warps(p->n_det);
   if (op == OP_JOSEPH) {
-    if (gw == 1) return launch_band_sum_filter_gw<OP_JOSEPH, 1>(p, jobs, nb0, nb1, part, off0, off1, fr, st);
-    if (gw == 2) return launch_band_sum_filter_gw<OP_JOSEPH, 2>(p, jobs, nb0, nb1, part, off0, off1, fr, st);
-    return launch_band_sum_filter_gw<OP_JOSEPH, 3>(p, jobs, nb0, nb1, part, off0, off1, fr, st);
+    if (gw == 1)
+      return launch_band_sum_filter_gw<OP_JOSEPH, 1>(p, jobs, nb0, nb1, part, off0, off1,
+                                                      part_floats, fr, st);
+    if (gw == 2)
+      return launch_band_sum_filter_gw<OP_JOSEPH, 2>(p, jobs, nb0, nb1, part, off0, off1,
+                                                      part_floats, fr, st);
+    return launch_band_sum_filter_gw<OP_JOSEPH, 3>(p, jobs, nb0, nb1, part, off0, off1,
+                                                    part_floats, fr, st);
   }
-  if (gw == 1) return launch_band_sum_filter_gw<OP_BP_ADJ, 1>(p, jobs, nb0, nb1, part, off0, off1, fr, st);
-  if (gw == 2) return launch_band_sum_filter_gw<OP_BP_ADJ, 2>(p, jobs, nb0, nb1, part, off0, off1, fr, st);
-  return launch_band_sum_filter_gw<OP_BP_ADJ, 3>(p, jobs, nb0, nb1, part, off0, off1, fr, st);
+  if (gw == 1)
+    return launch_band_sum_filter_gw<OP_BP_ADJ, 1>(p, jobs, nb0, nb1, part, off0, off1,
+                                                    part_floats, fr, st);
+  if (gw == 2)
+    return launch_band_sum_filter_gw<OP_BP_ADJ, 2>(p, jobs, nb0, nb1, part, off0, off1,
+                                                    part_floats, fr, st);
+  return launch_band_sum_filter_gw<OP_BP_ADJ, 3>(p, jobs, nb0, nb1, part, off0, off1,
+                                                  part_floats, fr, st);
 }
 
 template <typename Tin, typename Tout>

@@ -150,6 +150,19 @@ extern "C" {
 
 int skei_version(void) { return 10000; }
 
+int skei_check_build(void) { return SKEI_CHECK; }
+
+int skei_check_status(unsigned *bits, int reset) {
+  if (!bits) return set_error(SKEI_EINVAL, "skei_check_status: bits is NULL");
+  *bits = 0;
+  if (!SKEI_CHECK) return SKEI_OK;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_error(e, "skei_check_status: synchronize");
+  SKEI_TRY(check_read_band(bits, reset));
+  SKEI_TRY(check_read_tile(bits, reset));
+  return check_read_filter(bits, reset);
+}
+
 const char *skei_last_error(void) { return g_last_error.c_str(); }
 
 int skei_plan_create(int N, int n_det, int n_angles, const double *angles_deg,

@@ -130,6 +130,20 @@ __device__ __forceinline__ void tile_window(const Job &J, int b0, int c0, int na
     const int k = sm.kw0[slot][a] + w;
     const bool ok = sm.sai[slot][a] >= 0 && k >= 0 && k < nd;
     const int kk = ok ? k : 0;
+    if (SKEI_CHECK) {
+      // every window slot this thread fills lies in shared memory, and every
+      // bin it reads in the job's input
+      bool in = ck_smem(win + e * NI, 4 * NI, CK_TILE_WIN) &&
+                (!XTRA || ck_smem(winx + e, 4, CK_TILE_WIN));
+      if (ok) {
+        in = in && ck((long long)((size_t)(b0 + NI - 1) * J.m + c0 + a) * nd + kk,
+                      (long long)J.nimg * J.m * nd, CK_TILE_IN);
+        if (XTRA)
+          in = in && ck((long long)((size_t)bx * JX->m + c0 + a) * nd + kk,
+                        (long long)JX->nimg * JX->m * nd, CK_TILE_IN);
+      }
+      if (!in) continue;
+    }
     if (async) {
       const float *src = static_cast<const float *>(J.in);
 #pragma unroll
@@ -234,16 +248,19 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
           const float w2 =
               fmaxf(fmaf(W, __int_as_float(0x40000000 - abs(D2 >> (kFxBits - 23))), -W), 0.0f);
           if (NI == 4) {
-            const float4 v1 = reinterpret_cast<const float4 *>(wa)[s1];
-            const float4 v2 = reinterpret_cast<const float4 *>(wa)[s2];
+            const float4 v1 = lds_ck(reinterpret_cast<const float4 *>(wa) + s1, CK_TILE_TAP);
+            const float4 v2 = lds_ck(reinterpret_cast<const float4 *>(wa) + s2, CK_TILE_TAP);
             acc[0][q] = fmaf(w1, v1.x, fmaf(w2, v2.x, acc[0][q]));
             acc[1][q] = fmaf(w1, v1.y, fmaf(w2, v2.y, acc[1][q]));
             acc[2][q] = fmaf(w1, v1.z, fmaf(w2, v2.z, acc[2][q]));
             acc[3][q] = fmaf(w1, v1.w, fmaf(w2, v2.w, acc[3][q]));
           } else {
-            acc[0][q] = fmaf(w1, wa[s1], fmaf(w2, wa[s2], acc[0][q]));
+            acc[0][q] = fmaf(w1, lds_ck(wa + s1, CK_TILE_TAP),
+                             fmaf(w2, lds_ck(wa + s2, CK_TILE_TAP), acc[0][q]));
           }
-          if (XTRA) accx[q] = fmaf(w1, wx[s1], fmaf(w2, wx[s2], accx[q]));
+          if (XTRA)
+            accx[q] = fmaf(w1, lds_ck(wx + s1, CK_TILE_TAP),
+                           fmaf(w2, lds_ck(wx + s2, CK_TILE_TAP), accx[q]));
           u += du;
         }
       } else {
@@ -257,16 +274,19 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
           const float w = frac23(t);
           const float g = 1.0f - w;
           if (NI == 4) {
-            const float4 v0 = reinterpret_cast<const float4 *>(wa)[k0];
-            const float4 v1 = reinterpret_cast<const float4 *>(wa)[k0 + 1];
+            const float4 v0 = lds_ck(reinterpret_cast<const float4 *>(wa) + k0, CK_TILE_TAP);
+            const float4 v1 = lds_ck(reinterpret_cast<const float4 *>(wa) + k0 + 1, CK_TILE_TAP);
             acc[0][q] = fmaf(w, v1.x, fmaf(g, v0.x, acc[0][q]));
             acc[1][q] = fmaf(w, v1.y, fmaf(g, v0.y, acc[1][q]));
             acc[2][q] = fmaf(w, v1.z, fmaf(g, v0.z, acc[2][q]));
             acc[3][q] = fmaf(w, v1.w, fmaf(g, v0.w, acc[3][q]));
           } else {
-            acc[0][q] = fmaf(w, wa[k0 + 1], fmaf(g, wa[k0], acc[0][q]));
+            acc[0][q] = fmaf(w, lds_ck(wa + k0 + 1, CK_TILE_TAP),
+                             fmaf(g, lds_ck(wa + k0, CK_TILE_TAP), acc[0][q]));
           }
-          if (XTRA) accx[q] = fmaf(w, wx[k0 + 1], fmaf(g, wx[k0], accx[q]));
+          if (XTRA)
+            accx[q] = fmaf(w, lds_ck(wx + k0 + 1, CK_TILE_TAP),
+                           fmaf(g, lds_ck(wx + k0, CK_TILE_TAP), accx[q]));
           t += tj;
         }
       }
@@ -306,6 +326,8 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
 #pragma unroll
     for (int q = 0; q < kPPT; ++q) {
       if (jb + 32 * q >= N) break;
+      if (SKEI_CHECK && !ck((long long)(o + 32 * q), (long long)J.nimg * N * N, CK_TILE_OUT))
+        continue;
       float v = J.alpha * acc[n][q];
       if (J.beta != 0.0f && J.aux) v = fmaf(J.beta, ld_any(J.aux, o + 32 * q, J.aux_bf16), v);
       st_any(J.out, o + 32 * q, v, J.out_bf16);
@@ -323,6 +345,8 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
 #pragma unroll
     for (int q = 0; q < kPPT; ++q) {
       if (jb + 32 * q >= N) break;
+      if (SKEI_CHECK && !ck((long long)(o + 32 * q), (long long)JX->nimg * N * N, CK_TILE_OUT))
+        continue;
       float v = JX->alpha * accx[q];
       if (JX->beta != 0.0f && JX->aux) v = fmaf(JX->beta, ld_any(JX->aux, o + 32 * q, JX->aux_bf16), v);
       st_any(JX->out, o + 32 * q, v, JX->out_bf16);
@@ -462,6 +486,8 @@ int launch_tile(skei_plan p, const Jobs &jobs, cudaStream_t st) {
 }
 
 }  // namespace
+
+SKEI_CHECK_READER(check_read_tile)
 
 int launch_tile_jobs(skei_plan p, int op, const Jobs &jobs, cudaStream_t st) {
   if (op == OP_JOSEPH_ADJ) return launch_tile<OP_JOSEPH_ADJ>(p, jobs, st);

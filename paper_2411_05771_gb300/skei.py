@@ -28,14 +28,17 @@ __all__ = [
     "bn_workspace_size", "bn_act_fwd", "bn_act_bwd",
     "mri_workspace_size", "mri_fwd", "mri_adj", "mri_dinv", "coil_mix",
     "Batch", "BatchItem", "PROJ_FWD", "PROJ_ADJ", "BACKPROJECT", "BACKPROJECT_ADJ", "FILTER",
-    "FBP", "measure_roofs", "ROOFS_WORK_BYTES", "ttt_residual_workspace_size",
+    "FBP", "measure_roofs", "ROOFS_WORK_BYTES", "ttt_residual_workspace_size", "check_build",
+    "check_status",
     "ttt_residual_step",
 ]
 
 F32, BF16 = 0, 1
 ROOFS_WORK_BYTES = 1 << 30
 
-library_path = _build.LIB
+# SKEI_LIBRARY selects another build of the same library (the bounds-check
+# build, libskei_check.so)
+library_path = os.environ.get("SKEI_LIBRARY") or _build.LIB
 if not os.path.exists(library_path):
     raise ImportError(
         f"libskei.so not found at {library_path}; build it with "
@@ -132,6 +135,8 @@ _SIGS = {
                          ctypes.POINTER(_i)], _i),
     "skei_batch_destroy": ([_BATCH], _i),
     "skei_measure_roofs": ([_vp, _sz, ctypes.POINTER(_Roofs), _vp], _i),
+    "skei_check_build": ([], _i),
+    "skei_check_status": ([ctypes.POINTER(ctypes.c_uint), _i], _i),
     "skei_ttt_residual_workspace_size": ([_PLAN, _i, _i, _i, _i, _i], _sz),
     "skei_ttt_residual_step": ([_PLAN, _i, _vp, _vp, _vp, _vp, _vp, _vp, _i, _vp, _i, _vp, _i,
                                 _vp, _i, _d, _d, _d, _d, _d, _d] + [_vp] * 11 + [_vp, _sz, _vp],
@@ -929,3 +934,16 @@ def measure_roofs(work=None) -> dict:
            "skei_measure_roofs")
     return {"fp32_flops": out.fp32_flops, "smem_bytes": out.smem_bytes,
             "l2_bytes": out.l2_bytes, "dram_read_bytes": out.dram_read_bytes, "sms": out.sms}
+
+
+def check_build() -> bool:
+    """Whether the loaded library is the bounds-check build."""
+    return bool(_lib.skei_check_build())
+
+
+def check_status(reset: bool = True) -> int:
+    """skei_check_status: the range-check bits seen since the last reset (0
+    in the normal build); synchronises the device."""
+    bits = ctypes.c_uint(0)
+    _check(_lib.skei_check_status(ctypes.byref(bits), int(reset)), "skei_check_status")
+    return bits.value

@@ -106,3 +106,12 @@ def test_batch_validation_needs_no_gpu(lib):
     assert lib.skei_batch_run(None, None) == EINVAL
     assert lib.skei_batch_tune(None, 3, None) == EINVAL
     assert lib.skei_batch_destroy(None) == 0
+
+
+def test_check_entry_points_of_the_normal_build(lib):
+    """The normal build is not the bounds-check build and reports no bits
+    (without touching a GPU)."""
+    assert lib.skei_check_build() == 0
+    bits = ctypes.c_uint(7)
+    assert lib.skei_check_status(ctypes.byref(bits), 1) == 0
+    assert bits.value == 0
