@@ -61,8 +61,9 @@ def parse():
                          "of the other workloads: single operators at 64^2 and 8 x 256^2, the "
                          "differentiated EI step at 8 x 4 x 256^2, the 16-instance batch")
     ap.add_argument("--profile", action="store_true",
-                    help="set up the sketched arm, run one warm and one more step, and exit "
-                         "(a short, untimed run for ncu: 2 launches of set-up, then 14 per step)")
+                    help="set up the sketched arm, run one warm and one more step, then each "
+                         "operator of the kernel breakdown once, and exit (a short, untimed run "
+                         "for ncu; it prints its launch counts)")
     return ap.parse_args()
 
 
@@ -362,14 +363,12 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_breakdown(S, arm, stream, reps=20):
-    """Device time of every operator of one step, each re-issued with the
-    step's own arguments through its public entry point (A and B^T in the
-    band-sums form: sums, then their reduction, two launches; the step
-    itself fuses that reduction with the filter, and the network and Adam
-    into the rotations and the back-projection): `reps` copies are captured
-    in a CUDA graph and the replay is timed with CUDA events on the
-    launching stream."""
+def breakdown_ops(S, arm):
+    """Every operator of one step as a call through its public entry point
+    with the step's own arguments (A and B^T in the band-sums form: sums,
+    then their reduction, two launches; the step itself fuses that
+    reduction with the filter, and the network and Adam into the rotations
+    and the back-projection), by the names the bench reports."""
     import torch
     p = arm.plan
     mc_idx = arm.idx if arm.wl.mc_sketched else None
@@ -411,6 +410,15 @@ def kernel_breakdown(S, arm, stream, reps=20):
                 S.Job(qbuf, gtot.reshape(BG, N, N), sk_idx, aux=gx2, beta=1.0)]),
         "rotate_adj": lambda: S.rotate_adj(gtot_t, arm.g, beta=1.0, out=arm.gx1),
     }
+    return ops
+
+
+def kernel_breakdown(S, arm, stream, reps=20):
+    """Device time of every operator of one step (`breakdown_ops`): `reps`
+    copies are captured in a CUDA graph and the replay is timed with CUDA
+    events on the launching stream."""
+    import torch
+    ops = breakdown_ops(S, arm)
     times = {}
     with torch.cuda.stream(stream):
         for name, fn in ops.items():
@@ -1026,10 +1034,16 @@ def main():
     plan = S.Plan(N_IMG, N_VIEWS, prob["angs"])
     if args.profile:
         arm = Arm(S, plan, prob, SKETCHED, args.dtype, dev)
+        ops = breakdown_ops(S, arm)
+        torch.cuda.synchronize()
         arm.step()
         arm.step()
         torch.cuda.synchronize()
-        print(json.dumps({"profile_run": "ok", "launches": 2 + 2 * arm.launches_per_step}))
+        for fn in ops.values():
+            fn()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_run": "ok", "launches_per_step": arm.launches_per_step,
+                          "breakdown": list(ops)}))
         return
     sk = Arm(S, plan, prob, SKETCHED, args.dtype, dev)
     pl = Arm(S, plan, prob, PLAIN, "f32", dev)

@@ -234,15 +234,19 @@ __device__ __forceinline__ void stage1(const void *x, size_t xo, int bf16, int N
 
 // The same for 4 images (element offset xo + i N^2), interleaved: position
 // p of line l holds the 4 images' values at buf[4 (l P + PAD + p) + i].
-// Needs nl <= 8 and an odd pitch P.
+// Needs an odd pitch P.
 //
 // FP32 fast path (N, s0, nl multiples of 4): every thread loads 4
 // consecutive values of each image with one 16-byte load, transposes the
 // 4 x 4 block in registers and stores 4 positions of 16 bytes; loads are
-// issued in batches of two blocks before the stores.  The thread mapping
+// issued in batches of kStageBatch blocks before the stores.  The thread mapping
 // keeps the stores of each quarter warp in distinct bank quads: rows (mode
 // 1): 8 lines x 4 position groups per warp; columns (mode 0): pairs of
 // 4-line groups x consecutive positions.
+#ifndef SKEI_STAGE_BATCH
+#define SKEI_STAGE_BATCH 4
+#endif
+constexpr int kStageBatch = SKEI_STAGE_BATCH;   // 4 x 4 blocks in flight per thread before their stores
 __device__ __forceinline__ void store_block(float4 *dst, int step, const float4 (&v)[4]) {
   sts(dst, make_float4(v[0].x, v[1].x, v[2].x, v[3].x));
   sts(dst + step, make_float4(v[0].y, v[1].y, v[2].y, v[3].y));
@@ -260,23 +264,22 @@ __device__ __forceinline__ void stage4(const void *x, size_t xo, int bf16, int N
   const float4 *x4 = reinterpret_cast<const float4 *>(static_cast<const float *>(x) + xo);
   const size_t plane4 = plane >> 2;
   if (fast && mode == 1) {
-    const int r = tid & 7, pg = tid >> 3;             // line, position group
+    const int pg = tid >> 3;                          // position group
     const int ngroups = N >> 2, step_g = kThreads >> 3;
-    if (r < nl) {
+    for (int r = tid & 7; r < nl; r += 8) {           // line
       const size_t row4 = ((size_t)(s0 + r) * N) >> 2;
       float4 *dst = b4 + r * P + PAD;
       int g = pg;
-      for (; g + step_g < ngroups; g += 2 * step_g) {
-        float4 va[4], vb[4];
+      for (; g + (kStageBatch - 1) * step_g < ngroups; g += kStageBatch * step_g) {
+        float4 v[kStageBatch][4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          va[i] = __ldg(x4 + i * plane4 + row4 + g);
-          vb[i] = __ldg(x4 + i * plane4 + row4 + g + step_g);
-        }
-        store_block(dst + 4 * g, 1, va);
-        store_block(dst + 4 * (g + step_g), 1, vb);
+        for (int u = 0; u < kStageBatch; ++u)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) v[u][i] = __ldg(x4 + i * plane4 + row4 + g + u * step_g);
+#pragma unroll
+        for (int u = 0; u < kStageBatch; ++u) store_block(dst + 4 * (g + u * step_g), 1, v[u]);
       }
-      if (g < ngroups) {
+      for (; g < ngroups; g += step_g) {
         float4 va[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) va[i] = __ldg(x4 + i * plane4 + row4 + g);
@@ -288,17 +291,17 @@ __device__ __forceinline__ void stage4(const void *x, size_t xo, int bf16, int N
     const int lg = tid % lgs, p0 = tid / lgs, step_p = kThreads / lgs;
     float4 *dst = b4 + (4 * lg) * P + PAD;
     int p = p0;
-    for (; p + step_p < N; p += 2 * step_p) {
-      float4 va[4], vb[4];
+    for (; p + (kStageBatch - 1) * step_p < N; p += kStageBatch * step_p) {
+      float4 v[kStageBatch][4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        va[i] = __ldg(x4 + i * plane4 + (((size_t)p * N + s0) >> 2) + lg);
-        vb[i] = __ldg(x4 + i * plane4 + (((size_t)(p + step_p) * N + s0) >> 2) + lg);
-      }
-      store_block(dst + p, P, va);
-      store_block(dst + p + step_p, P, vb);
+      for (int u = 0; u < kStageBatch; ++u)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          v[u][i] = __ldg(x4 + i * plane4 + (((size_t)(p + u * step_p) * N + s0) >> 2) + lg);
+#pragma unroll
+      for (int u = 0; u < kStageBatch; ++u) store_block(dst + p + u * step_p, P, v[u]);
     }
-    if (p < N) {
+    for (; p < N; p += step_p) {
       float4 va[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) va[i] = __ldg(x4 + i * plane4 + (((size_t)p * N + s0) >> 2) + lg);
@@ -317,8 +320,7 @@ __device__ __forceinline__ void stage4(const void *x, size_t xo, int bf16, int N
   } else {
     // 8 consecutive threads take the 8 lines of one position: with an odd
     // pitch their 16-byte stores fall in distinct bank quads
-    const int l = tid & 7;
-    if (l < nl) {
+    for (int l = tid & 7; l < nl; l += 8) {
       for (int p = tid >> 3; p < N; p += kThreads / 8) {
         const size_t src = xo + (size_t)p * N + s0 + l;
         sts(b4 + l * P + PAD + p,
@@ -332,6 +334,54 @@ __device__ __forceinline__ void stage4(const void *x, size_t xo, int bf16, int N
     const int r = e / npad, c = e - r * npad;
     sts(b4 + r * P + (c < PAD ? c : N + c), make_float4(0.0f, 0.0f, 0.0f, 0.0f));
   }
+}
+
+// A riding single image's band of 8 lines (FP32, N <= 512, s0 % 4 == 0)
+// in two halves, so that its loads fly while the group's band is staged:
+// ride_load issues the thread's (at most 4) 16-byte loads in stage1's
+// thread mapping, ride_store stores them and zeroes the padding; together
+// they write what stage1 writes.
+__device__ __forceinline__ bool ride_split(int bf16, int N, int s0, int nl, bool fast) {
+  return fast && !bf16 && N <= 512 && nl == 8 && kWarps == 8 && (s0 & 3) == 0;
+}
+__device__ __forceinline__ void ride_load(const void *x, size_t xo, int N, int mode, int s0,
+                                          float4 (&v)[4]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    v[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (mode == 1) {
+      const int c = 4 * lane + 128 * u;   // line s0 + warp, positions c .. c+3
+      if (c < N) v[u] = load4(x, xo + (size_t)(s0 + warp) * N + c, 0);
+    } else {
+      const int p = warp * 16 + (lane >> 1) + 128 * u;   // column p, lines s0 + 4 (lane & 1) ..
+      if (p < N) v[u] = load4(x, xo + (size_t)p * N + s0 + 4 * (lane & 1), 0);
+    }
+  }
+}
+template <int PAD>
+__device__ __forceinline__ void ride_store(int N, int mode, float *buf, int P,
+                                           const float4 (&v)[4]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    if (mode == 1) {
+      const int c = 4 * lane + 128 * u;
+      if (c < N) sts(reinterpret_cast<float4 *>(buf + warp * P + PAD + c), v[u]);
+    } else {
+      const int p = warp * 16 + (lane >> 1) + 128 * u;
+      if (p < N) {
+        float *dst = buf + (4 * (lane & 1)) * P + PAD + p;
+        sts(dst, v[u].x);
+        sts(dst + P, v[u].y);
+        sts(dst + 2 * P, v[u].z);
+        sts(dst + 3 * P, v[u].w);
+      }
+    }
+  }
+  const int npad = P - N;
+  for (int r = warp; r < 8; r += kWarps)
+    for (int c = lane; c < npad; c += 32) sts(buf + r * P + (c < PAD ? c : N + c), 0.0f);
 }
 
 // Line range [lo, hi) within [s0, s1) on which lam0 + L * lam1 lies in
@@ -859,6 +909,9 @@ int band_batch_clusters(size_t smem, int *clusters) {
 #ifndef SKEI_PART_CTAS
 #define SKEI_PART_CTAS 2      // CTAs per SM of the one wave the angle block aims at
 #endif
+#ifndef SKEI_PART_MINB4
+#define SKEI_PART_MINB4 2     // CTAs per SM the one-wave 4-image kernel's registers must allow
+#endif
 constexpr int kMaxABP = 32;      // angles per partial CTA
 
 // Staging geometry of one band of SB lines (0: the group size's default).
@@ -1104,9 +1157,13 @@ __device__ __forceinline__ void partial_task(const Job &J, float *part, int b0, 
     const int Px = XTRA ? (mode ? gx->Prow : gx->Pcol) : 0;
     if (any) {
       __syncthreads();  // the previous mode's band is no longer read
+      const bool split = XTRA && ride_split(JX->in_bf16, N, s0, nl, gx->fast != 0);
+      float4 rv[4];
+      if (split) ride_load(JX->in, (size_t)bx * N * N, N, mode, s0, rv);
       if (NI == 4) stage4<PAD>(J.in, xo, J.in_bf16, N, mode, s0, nl, buf, P);
       else stage1<PAD>(J.in, xo, J.in_bf16, N, mode, s0, nl, buf, P, g.fast != 0);
-      if (XTRA)
+      if (split) ride_store<PAD>(N, mode, bufx, Px, rv);
+      else if (XTRA)
         stage1<PAD>(JX->in, (size_t)bx * N * N, JX->in_bf16, N, mode, s0, nl, bufx, Px,
                     gx->fast != 0);
       // lines past the image (last band) read as zeros
@@ -1344,8 +1401,9 @@ int launch_band_partial(skei_plan p, const Jobs &jobs, float *work, size_t work_
   const size_t smem4 = part_smem(g4) + (merge ? part_smem(g1) : 0);
   constexpr int sb4 = SKEI_PART_SBL4, sb1 = SKEI_PART_SBL1;
   if (n4 > 0 && one_wave) {
-    SKEI_TRY((set_partial_smem<OP, 4, 2, sb4>(smem4)));
-    launch_k(band_partial_kernel<OP, 4, 2, sb4>, dim3(nbands, nblk, n4), dim3(kThreads), smem4,
+    constexpr int m4 = SKEI_PART_MINB4;
+    SKEI_TRY((set_partial_smem<OP, 4, m4, sb4>(smem4)));
+    launch_k(band_partial_kernel<OP, 4, m4, sb4>, dim3(nbands, nblk, n4), dim3(kThreads), smem4,
              st, a);
   } else if (n4 > 0) {
     SKEI_TRY((set_partial_smem<OP, 4, 3, sb4>(smem4)));

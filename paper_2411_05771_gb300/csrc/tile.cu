@@ -41,21 +41,30 @@ namespace {
 // picks between 4 and this to balance its CTAs over the SMs, the batch
 // kernel uses it as is); angle split (1 or 2): with 2 (measured faster for
 // B on GB300), two warps share each tile row, taking alternate angles of
-// every chunk, and their sums are added in a fixed order at the end.
+// every chunk, and their sums are added in a fixed order at the end;
+// pixels per thread (4: 8 measured slower at 96 registers, one CTA per SM);
+// angles per chunk (16: half the chunk barriers of 8, measured faster at
+// 512^2 with 30 angles; 4 slower).
 #ifndef SKEI_TILE_ROWS
 #define SKEI_TILE_ROWS 8
 #endif
 #ifndef SKEI_TILE_SPLIT
 #define SKEI_TILE_SPLIT 2
 #endif
+#ifndef SKEI_TILE_PPT
+#define SKEI_TILE_PPT 4
+#endif
+#ifndef SKEI_TILE_AC
+#define SKEI_TILE_AC 16
+#endif
 
-constexpr int kPPT = 4;                  // pixels per thread, 32 columns apart
+constexpr int kPPT = SKEI_TILE_PPT;      // pixels per thread, 32 columns apart
 constexpr int kTW = 32 * kPPT;           // tile width (columns)
 constexpr int kTH = SKEI_TILE_ROWS;      // tile height (rows)
 constexpr int kSplit = SKEI_TILE_SPLIT;  // warps per tile row
 constexpr int kThreads = 32 * kTH * kSplit;
-constexpr int kWin = 160;                // staged bins per angle (>= kTW + kTH + 6)
-constexpr int kAC = 8;                   // angles per chunk
+constexpr int kWin = kTW + 32;           // staged bins per angle (>= kTW + kTH + 6)
+constexpr int kAC = SKEI_TILE_AC;        // angles per chunk
 
 struct TileArgs {
   Jobs jobs;
