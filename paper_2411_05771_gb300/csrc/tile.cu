@@ -124,52 +124,53 @@ __device__ __forceinline__ void tile_setup(const Job &J, int b0, int c0, int nac
   sm.kw0[slot][tid] = (int)floorf(lo) - 3;
 }
 
-// Window of chunk c (constants in `slot`) into window buffer `wb`: one
-// (angle, bin) per thread, the group's images side by side; bins outside
-// the sinogram and dead angles read as 0.  FP32 inputs are copied by
-// cp.async (the caller waits); BF16 inputs are converted and stored.
+// Window of chunk c (constants in `slot`) into window buffer `wb`, the
+// group's images side by side; bins outside the sinogram and dead angles
+// read as 0.  A warp fills runs of 32 bins of one angle at a time, so that
+// the angle's row addresses are computed once per run.  FP32 inputs are
+// copied by cp.async (the caller waits); BF16 inputs are converted and
+// stored.
 template <int NI, bool XTRA>
 __device__ __forceinline__ void tile_window(const Job &J, int b0, int c0, int nac, int nd,
                                             TileSmem &sm, int slot, int wb, const Job *JX,
                                             int bx) {
+  constexpr int kRuns = (kWin + 31) / 32;   // runs of 32 bins per angle
   const bool async = !J.in_bf16 && (!XTRA || !JX->in_bf16);
   float *win = sm.win[wb], *winx = sm.winx[wb];
-  for (int e = threadIdx.x; e < nac * kWin; e += blockDim.x) {
-    const int a = e / kWin, w = e - a * kWin;
+  const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int u = threadIdx.x >> 5; u < nac * kRuns; u += nwarps) {
+    const int a = u / kRuns, w = (u - a * kRuns) * 32 + lane;   // a is warp-uniform
+    if (w >= kWin) continue;
     const int k = sm.kw0[slot][a] + w;
     const bool ok = sm.sai[slot][a] >= 0 && k >= 0 && k < nd;
     const int kk = ok ? k : 0;
+    const size_t row = ((size_t)b0 * J.m + c0 + a) * nd;     // image b0's row of angle a
+    const size_t img = (size_t)J.m * nd;                      // one image's rows
+    const size_t rowx = XTRA ? ((size_t)bx * JX->m + c0 + a) * nd : 0;
+    const int e = a * kWin + w;
     if (SKEI_CHECK) {
       // every window slot this thread fills lies in shared memory, and every
       // bin it reads in the job's input
       bool in = ck_smem(win + e * NI, 4 * NI, CK_TILE_WIN) &&
                 (!XTRA || ck_smem(winx + e, 4, CK_TILE_WIN));
       if (ok) {
-        in = in && ck((long long)((size_t)(b0 + NI - 1) * J.m + c0 + a) * nd + kk,
-                      (long long)J.nimg * J.m * nd, CK_TILE_IN);
+        in = in && ck((long long)(row + (NI - 1) * img + kk), (long long)J.nimg * img,
+                      CK_TILE_IN);
         if (XTRA)
-          in = in && ck((long long)((size_t)bx * JX->m + c0 + a) * nd + kk,
-                        (long long)JX->nimg * JX->m * nd, CK_TILE_IN);
+          in = in && ck((long long)(rowx + kk), (long long)JX->nimg * JX->m * nd, CK_TILE_IN);
       }
       if (!in) continue;
     }
     if (async) {
-      const float *src = static_cast<const float *>(J.in);
+      const float *src = static_cast<const float *>(J.in) + row + kk;
 #pragma unroll
-      for (int n = 0; n < NI; ++n)
-        cp_async4(win + e * NI + n, src + ((size_t)(b0 + n) * J.m + c0 + a) * nd + kk, ok);
-      if (XTRA)
-        cp_async4(winx + e,
-                  static_cast<const float *>(JX->in) + ((size_t)bx * JX->m + c0 + a) * nd + kk,
-                  ok);
+      for (int n = 0; n < NI; ++n) cp_async4(win + e * NI + n, src + n * img, ok);
+      if (XTRA) cp_async4(winx + e, static_cast<const float *>(JX->in) + rowx + kk, ok);
     } else {
 #pragma unroll
       for (int n = 0; n < NI; ++n)
-        win[e * NI + n] =
-            ok ? ld_any(J.in, ((size_t)(b0 + n) * J.m + c0 + a) * nd + k, J.in_bf16) : 0.0f;
-      if (XTRA)
-        winx[e] = ok ? ld_any(JX->in, ((size_t)bx * JX->m + c0 + a) * nd + k, JX->in_bf16)
-                     : 0.0f;
+        win[e * NI + n] = ok ? ld_any(J.in, row + n * img + k, J.in_bf16) : 0.0f;
+      if (XTRA) winx[e] = ok ? ld_any(JX->in, rowx + k, JX->in_bf16) : 0.0f;
     }
   }
   cp_async_commit();
@@ -364,7 +365,8 @@ __device__ __forceinline__ void tile_task(const Job &J, int b0, int i0, int j0, 
 }
 
 template <int OP>
-__global__ void __launch_bounds__(kThreads) tile_kernel(const TileArgs args) {
+// two CTAs per SM: at most 64 registers
+__global__ void __launch_bounds__(kThreads, 2) tile_kernel(const TileArgs args) {
   pdl_enter();
   extern __shared__ float4 tile_smem4[];
   TileSmem &sm = *reinterpret_cast<TileSmem *>(tile_smem4);
