@@ -236,8 +236,8 @@ __device__ __forceinline__ void stage1(const void *x, size_t xo, int bf16, int N
 // p of line l holds the 4 images' values at buf[4 (l P + PAD + p) + i].
 // Needs an odd pitch P.
 //
-// FP32 fast path (N, s0, nl multiples of 4): every thread loads 4
-// consecutive values of each image with one 16-byte load, transposes the
+// Fast path (N, s0, nl multiples of 4): every thread loads 4 consecutive
+// values of each image with one 16-byte load (8 bytes for BF16), transposes the
 // 4 x 4 block in registers and stores 4 positions of 16 bytes; loads are
 // issued in batches of kStageBatch blocks before the stores.  The thread mapping
 // keeps the stores of each quarter warp in distinct bank quads: rows (mode
@@ -254,15 +254,17 @@ __device__ __forceinline__ void store_block(float4 *dst, int step, const float4 
   sts(dst + 3 * step, make_float4(v[0].w, v[1].w, v[2].w, v[3].w));
 }
 
-template <int PAD = kPad>
-__device__ __forceinline__ void stage4(const void *x, size_t xo, int bf16, int N, int mode,
+template <int PAD = kPad, bool BF = false>
+__device__ __forceinline__ void stage4_t(const void *x, size_t xo, int N, int mode,
                                        int s0, int nl, float *buf, int P) {
   const size_t plane = (size_t)N * N;
   float4 *b4 = reinterpret_cast<float4 *>(buf);
   const int tid = threadIdx.x;
-  const bool fast = !bf16 && (N & 3) == 0 && (s0 & 3) == 0 && (nl & 3) == 0;
-  const float4 *x4 = reinterpret_cast<const float4 *>(static_cast<const float *>(x) + xo);
-  const size_t plane4 = plane >> 2;
+  const bool fast = (N & 3) == 0 && (s0 & 3) == 0 && (nl & 3) == 0;
+  // 4 consecutive values of image i at element offset 4 q of the job's
+  // group (16 bytes of FP32, 8 of BF16)
+  constexpr int bf16 = BF ? 1 : 0;
+  auto ld4 = [&](int i, size_t q4) { return load4(x, xo + i * plane + 4 * q4, bf16); };
   if (fast && mode == 1) {
     const int pg = tid >> 3;                          // position group
     const int ngroups = N >> 2, step_g = kThreads >> 3;
@@ -275,14 +277,14 @@ __device__ __forceinline__ void stage4(const void *x, size_t xo, int bf16, int N
 #pragma unroll
         for (int u = 0; u < kStageBatch; ++u)
 #pragma unroll
-          for (int i = 0; i < 4; ++i) v[u][i] = __ldg(x4 + i * plane4 + row4 + g + u * step_g);
+          for (int i = 0; i < 4; ++i) v[u][i] = ld4(i, row4 + g + u * step_g);
 #pragma unroll
         for (int u = 0; u < kStageBatch; ++u) store_block(dst + 4 * (g + u * step_g), 1, v[u]);
       }
       for (; g < ngroups; g += step_g) {
         float4 va[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) va[i] = __ldg(x4 + i * plane4 + row4 + g);
+        for (int i = 0; i < 4; ++i) va[i] = ld4(i, row4 + g);
         store_block(dst + 4 * g, 1, va);
       }
     }
@@ -297,14 +299,14 @@ __device__ __forceinline__ void stage4(const void *x, size_t xo, int bf16, int N
       for (int u = 0; u < kStageBatch; ++u)
 #pragma unroll
         for (int i = 0; i < 4; ++i)
-          v[u][i] = __ldg(x4 + i * plane4 + (((size_t)(p + u * step_p) * N + s0) >> 2) + lg);
+          v[u][i] = ld4(i, (((size_t)(p + u * step_p) * N + s0) >> 2) + lg);
 #pragma unroll
       for (int u = 0; u < kStageBatch; ++u) store_block(dst + p + u * step_p, P, v[u]);
     }
     for (; p < N; p += step_p) {
       float4 va[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) va[i] = __ldg(x4 + i * plane4 + (((size_t)p * N + s0) >> 2) + lg);
+      for (int i = 0; i < 4; ++i) va[i] = ld4(i, (((size_t)p * N + s0) >> 2) + lg);
       store_block(dst + p, P, va);
     }
   } else if (mode == 1) {
@@ -334,6 +336,14 @@ __device__ __forceinline__ void stage4(const void *x, size_t xo, int bf16, int N
     const int r = e / npad, c = e - r * npad;
     sts(b4 + r * P + (c < PAD ? c : N + c), make_float4(0.0f, 0.0f, 0.0f, 0.0f));
   }
+}
+
+// stage4 with the storage type a template argument (no per-load test).
+template <int PAD = kPad>
+__device__ __forceinline__ void stage4(const void *x, size_t xo, int bf16, int N, int mode,
+                                       int s0, int nl, float *buf, int P) {
+  if (bf16) stage4_t<PAD, true>(x, xo, N, mode, s0, nl, buf, P);
+  else stage4_t<PAD, false>(x, xo, N, mode, s0, nl, buf, P);
 }
 
 // A riding single image's band of 8 lines (FP32, N <= 512, s0 % 4 == 0)

@@ -128,14 +128,16 @@ __device__ __forceinline__ void tile_setup(const Job &J, int b0, int c0, int nac
 // group's images side by side; bins outside the sinogram and dead angles
 // read as 0.  A warp fills runs of 32 bins of one angle at a time, so that
 // the angle's row addresses are computed once per run.  FP32 inputs are
-// copied by cp.async (the caller waits); BF16 inputs are converted and
-// stored.
+// copied by cp.async (the caller waits, then synchronises the CTA); BF16
+// inputs are converted and stored.
 template <int NI, bool XTRA>
 __device__ __forceinline__ void tile_window(const Job &J, int b0, int c0, int nac, int nd,
                                             TileSmem &sm, int slot, int wb, const Job *JX,
                                             int bx) {
   constexpr int kRuns = (kWin + 31) / 32;   // runs of 32 bins per angle
-  const bool async = !J.in_bf16 && (!XTRA || !JX->in_bf16);
+  // FP32 inputs by cp.async, BF16 ones through registers (a riding BF16
+  // image does not hold back the group's copies)
+  const bool async = !J.in_bf16, asyncx = XTRA && !JX->in_bf16;
   float *win = sm.win[wb], *winx = sm.winx[wb];
   const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   for (int u = threadIdx.x >> 5; u < nac * kRuns; u += nwarps) {
@@ -165,13 +167,13 @@ __device__ __forceinline__ void tile_window(const Job &J, int b0, int c0, int na
       const float *src = static_cast<const float *>(J.in) + row + kk;
 #pragma unroll
       for (int n = 0; n < NI; ++n) cp_async4(win + e * NI + n, src + n * img, ok);
-      if (XTRA) cp_async4(winx + e, static_cast<const float *>(JX->in) + rowx + kk, ok);
     } else {
 #pragma unroll
       for (int n = 0; n < NI; ++n)
         win[e * NI + n] = ok ? ld_any(J.in, row + n * img + k, J.in_bf16) : 0.0f;
-      if (XTRA) winx[e] = ok ? ld_any(JX->in, rowx + k, JX->in_bf16) : 0.0f;
     }
+    if (asyncx) cp_async4(winx + e, static_cast<const float *>(JX->in) + rowx + kk, ok);
+    else if (XTRA) winx[e] = ok ? ld_any(JX->in, rowx + k, JX->in_bf16) : 0.0f;
   }
   cp_async_commit();
 }
