@@ -396,7 +396,8 @@ int ei_finish_impl(const T *x2, const T *x3, const T *r, int B, int G, int64_t n
            cpi, r_len, cpr, kappa, g_x2, g_x3, partial);
   if (int rc = check_launch("loss partial sums launch")) return rc;
   const size_t smem = sizeof(double) * (size_t)(B * G + B);
-  if (smem > 48 * 1024) return set_error(SKEI_EINVAL, "B*G + B = %d segments is too many", B * G + B);
+  // dynamic shared memory below 40 KB: with the kernel's static part, under the 48 KB default
+  if (smem > 40 * 1024) return set_error(SKEI_EINVAL, "B*G + B = %d segments is too many", B * G + B);
   launch_k(ei_final_kernel, dim3(1), dim3(kRedThreads), smem, st, (const double *)partial, B, G,
            cpi, cpr, lambda, mc_scale, mc_out, ei_out, loss_out);
   return check_launch("loss final reduction launch");

@@ -739,7 +739,7 @@ int set_band_smem(size_t smem) {
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
-  if (smem > 48 * 1024 && smem > configured[dev]) {
+  if (smem > configured[dev]) {
     cudaError_t e = cudaFuncSetAttribute(band_kernel<OP>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
@@ -1320,7 +1320,7 @@ int set_partial_smem(size_t smem) {
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
-  if (smem > 48 * 1024 && smem > configured[dev]) {
+  if (smem > configured[dev]) {
     cudaError_t e = cudaFuncSetAttribute(band_partial_kernel<OP, NI, MINB, SB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_error(e, "band partial kernel: shared memory attribute");

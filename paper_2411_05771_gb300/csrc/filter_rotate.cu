@@ -845,7 +845,7 @@ static int set_filter_batch_smem(size_t smem) {
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
-  if (smem > 48 * 1024 && smem > configured[dev]) {
+  if (smem > configured[dev]) {
     cudaError_t e = cudaFuncSetAttribute(ramlak_batch_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_error(e, "batched ramlak: shared memory attribute");
@@ -883,7 +883,7 @@ int launch_filter_gw(skei_plan p, const Tin *in, int rows, float scale, Tout *ou
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
-  if (smem > 48 * 1024 && smem > configured[dev]) {
+  if (smem > configured[dev]) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return cuda_error(e, "ramlak: shared memory attribute");
@@ -915,7 +915,7 @@ int launch_band_sum_filter_gw(skei_plan p, const Jobs &jobs, int nb0, int nb1, c
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
-  if (smem > 48 * 1024 && smem > configured[dev]) {
+  if (smem > configured[dev]) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return cuda_error(e, "band sums + filter: shared memory attribute");
@@ -972,7 +972,7 @@ int launch_filter_tc(skei_plan p, const Tin *in, int rows, float scale, Tout *ou
     if (e != cudaSuccess) return cuda_error(e, "ramlak taps: symbol address");
     taps[dev] = static_cast<const float *>(a);
   }
-  if (smem > 48 * 1024 && smem > configured[dev]) {
+  if (smem > configured[dev]) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return cuda_error(e, "ramlak tensor-core form: shared memory attribute");
@@ -1013,7 +1013,7 @@ int launch_filter_fft(skei_plan p, const Tin *in, int rows, float scale, Tout *o
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
-  if (smem > 48 * 1024 && smem > configured[dev]) {
+  if (smem > configured[dev]) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return cuda_error(e, "ramlak FFT: shared memory attribute");
@@ -1056,7 +1056,9 @@ int launch_rotate_adj_adam(const float *gout, int N, const double *g_deg, int G,
                            cudaStream_t st) {
   dim3 grid((N + kAdjT - 1) / kAdjT, (N + kAdjT * kAdjQ - 1) / (kAdjT * kAdjQ), 1);
   const size_t smem = sizeof(double) * (size_t)(lf.B * lf.G + lf.B);
-  if (smem > 48 * 1024) return set_error(SKEI_EINVAL, "B*G + B = %d segments is too many", lf.B * lf.G + lf.B);
+  // dynamic shared memory below 40 KB: with the kernel's static part, under the 48 KB default
+  if (smem > 40 * 1024)
+    return set_error(SKEI_EINVAL, "B*G + B = %d segments is too many", lf.B * lf.G + lf.B);
   launch_k(rotate_adj_adam_kernel<T>, grid, dim3(kAdjT, kAdjT), smem, st, gout, N, G, g_deg, gx,
            g_x3, adam, lf);
   return check_launch("rotation transpose + Adam launch");

@@ -228,7 +228,7 @@ int mri_set_smem(K kern, size_t smem, size_t *configured) {
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) dev = 0;
-  if (smem > 48 * 1024 && configured[dev] < smem) {
+  if (configured[dev] < smem) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return cuda_error(e, "MRI kernel: shared memory attribute");

@@ -37,6 +37,11 @@ def _separate(S, plan, x0, theta, m, v, step, y, g, mc_idx, sk_idx, lam, mc_scal
     (512, 60, 1, 4, 60, False, torch.float32),    # the plain arm: all angles
     (64, 60, 2, 4, 15, True, torch.float32),      # two measurements: Adam on its own
     (37, 24, 1, 3, 6, True, torch.float32),       # ragged, G = 3
+    # 8 measurements at 256^2 with the MC images riding in A's band sums:
+    # 46 KB of dynamic shared memory, under the 48 KB default on its own but
+    # not with the kernel's static part (the launch must opt in)
+    (256, 180, 8, 4, 45, True, torch.float32),
+    (256, 180, 8, 4, 180, False, torch.float32),  # the plain form: all angles, both terms
 ])
 def test_fused_step_is_bitwise_the_separate_calls(S, N, n_ang, B, G, m, sketch_mc, dtype):
     rng = np.random.default_rng(N + m)
