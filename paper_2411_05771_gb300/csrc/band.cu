@@ -234,19 +234,22 @@ __device__ __forceinline__ void stage1(const void *x, size_t xo, int bf16, int N
 
 // The same for 4 images (element offset xo + i N^2), interleaved: position
 // p of line l holds the 4 images' values at buf[4 (l P + PAD + p) + i].
-// Needs an odd pitch P.
+// Needs nl <= 8 and an odd pitch P.
 //
 // Fast path (N, s0, nl multiples of 4): every thread loads 4 consecutive
 // values of each image with one 16-byte load (8 bytes for BF16), transposes the
 // 4 x 4 block in registers and stores 4 positions of 16 bytes; loads are
-// issued in batches of kStageBatch blocks before the stores.  The thread mapping
+// issued in batches of NB blocks before the stores.  The thread mapping
 // keeps the stores of each quarter warp in distinct bank quads: rows (mode
 // 1): 8 lines x 4 position groups per warp; columns (mode 0): pairs of
 // 4-line groups x consecutive positions.
 #ifndef SKEI_STAGE_BATCH
 #define SKEI_STAGE_BATCH 4
 #endif
-constexpr int kStageBatch = SKEI_STAGE_BATCH;   // 4 x 4 blocks in flight per thread before their stores
+// 4 x 4 blocks in flight per thread before their stores: the band-sums form
+// (whose kernels hold 128 registers) takes kStageBatch, the cluster form 2
+// (more would raise its register count and spill)
+constexpr int kStageBatch = SKEI_STAGE_BATCH;
 __device__ __forceinline__ void store_block(float4 *dst, int step, const float4 (&v)[4]) {
   sts(dst, make_float4(v[0].x, v[1].x, v[2].x, v[3].x));
   sts(dst + step, make_float4(v[0].y, v[1].y, v[2].y, v[3].y));
@@ -254,7 +257,7 @@ __device__ __forceinline__ void store_block(float4 *dst, int step, const float4 
   sts(dst + 3 * step, make_float4(v[0].w, v[1].w, v[2].w, v[3].w));
 }
 
-template <int PAD = kPad, bool BF = false>
+template <int PAD = kPad, bool BF = false, int NB = 2>
 __device__ __forceinline__ void stage4_t(const void *x, size_t xo, int N, int mode,
                                        int s0, int nl, float *buf, int P) {
   const size_t plane = (size_t)N * N;
@@ -264,24 +267,36 @@ __device__ __forceinline__ void stage4_t(const void *x, size_t xo, int N, int mo
   // 4 consecutive values of image i at element offset 4 q of the job's
   // group (16 bytes of FP32, 8 of BF16)
   constexpr int bf16 = BF ? 1 : 0;
-  auto ld4 = [&](int i, size_t q4) { return load4(x, xo + i * plane + 4 * q4, bf16); };
+  const size_t plane4 = plane >> 2;
+  const float4 *x4 = reinterpret_cast<const float4 *>(static_cast<const float *>(x) + xo);
+  const uint2 *h4 = reinterpret_cast<const uint2 *>(static_cast<const __nv_bfloat16 *>(x) + xo);
+  auto ld4 = [&](int i, size_t q4) {
+    if constexpr (BF) {
+      const uint2 u = __ldg(h4 + i * plane4 + q4);
+      return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u),
+                         __uint_as_float(u.y << 16), __uint_as_float(u.y & 0xffff0000u));
+    } else {
+      return __ldg(x4 + i * plane4 + q4);
+    }
+  };
   if (fast && mode == 1) {
     const int pg = tid >> 3;                          // position group
     const int ngroups = N >> 2, step_g = kThreads >> 3;
-    for (int r = tid & 7; r < nl; r += 8) {           // line
+    const int r = tid & 7;                            // line
+    if (r < nl) {
       const size_t row4 = ((size_t)(s0 + r) * N) >> 2;
       float4 *dst = b4 + r * P + PAD;
       int g = pg;
-      for (; g + (kStageBatch - 1) * step_g < ngroups; g += kStageBatch * step_g) {
-        float4 v[kStageBatch][4];
+      for (; g + (NB - 1) * step_g < ngroups; g += NB * step_g) {
+        float4 v[NB][4];
 #pragma unroll
-        for (int u = 0; u < kStageBatch; ++u)
+        for (int u = 0; u < NB; ++u)
 #pragma unroll
           for (int i = 0; i < 4; ++i) v[u][i] = ld4(i, row4 + g + u * step_g);
 #pragma unroll
-        for (int u = 0; u < kStageBatch; ++u) store_block(dst + 4 * (g + u * step_g), 1, v[u]);
+        for (int u = 0; u < NB; ++u) store_block(dst + 4 * (g + u * step_g), 1, v[u]);
       }
-      for (; g < ngroups; g += step_g) {
+      for (; g < ngroups; g += (NB == 2 ? ngroups : step_g)) {   // NB - 1 blocks at most
         float4 va[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) va[i] = ld4(i, row4 + g);
@@ -293,17 +308,17 @@ __device__ __forceinline__ void stage4_t(const void *x, size_t xo, int N, int mo
     const int lg = tid % lgs, p0 = tid / lgs, step_p = kThreads / lgs;
     float4 *dst = b4 + (4 * lg) * P + PAD;
     int p = p0;
-    for (; p + (kStageBatch - 1) * step_p < N; p += kStageBatch * step_p) {
-      float4 v[kStageBatch][4];
+    for (; p + (NB - 1) * step_p < N; p += NB * step_p) {
+      float4 v[NB][4];
 #pragma unroll
-      for (int u = 0; u < kStageBatch; ++u)
+      for (int u = 0; u < NB; ++u)
 #pragma unroll
         for (int i = 0; i < 4; ++i)
           v[u][i] = ld4(i, (((size_t)(p + u * step_p) * N + s0) >> 2) + lg);
 #pragma unroll
-      for (int u = 0; u < kStageBatch; ++u) store_block(dst + p + u * step_p, P, v[u]);
+      for (int u = 0; u < NB; ++u) store_block(dst + p + u * step_p, P, v[u]);
     }
-    for (; p < N; p += step_p) {
+    for (; p < N; p += (NB == 2 ? N : step_p)) {   // NB - 1 blocks at most
       float4 va[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) va[i] = ld4(i, (((size_t)p * N + s0) >> 2) + lg);
@@ -322,7 +337,8 @@ __device__ __forceinline__ void stage4_t(const void *x, size_t xo, int N, int mo
   } else {
     // 8 consecutive threads take the 8 lines of one position: with an odd
     // pitch their 16-byte stores fall in distinct bank quads
-    for (int l = tid & 7; l < nl; l += 8) {
+    const int l = tid & 7;
+    if (l < nl) {
       for (int p = tid >> 3; p < N; p += kThreads / 8) {
         const size_t src = xo + (size_t)p * N + s0 + l;
         sts(b4 + l * P + PAD + p,
@@ -338,12 +354,13 @@ __device__ __forceinline__ void stage4_t(const void *x, size_t xo, int N, int mo
   }
 }
 
-// stage4 with the storage type a template argument (no per-load test).
-template <int PAD = kPad>
+// stage4 with the storage type a template argument (no per-load test) and
+// NB blocks in flight per thread.
+template <int PAD = kPad, int NB = 2>
 __device__ __forceinline__ void stage4(const void *x, size_t xo, int bf16, int N, int mode,
                                        int s0, int nl, float *buf, int P) {
-  if (bf16) stage4_t<PAD, true>(x, xo, N, mode, s0, nl, buf, P);
-  else stage4_t<PAD, false>(x, xo, N, mode, s0, nl, buf, P);
+  if (bf16) stage4_t<PAD, true, NB>(x, xo, N, mode, s0, nl, buf, P);
+  else stage4_t<PAD, false, NB>(x, xo, N, mode, s0, nl, buf, P);
 }
 
 // A riding single image's band of 8 lines (FP32, N <= 512, s0 % 4 == 0)
@@ -735,19 +752,10 @@ __global__ void __cluster_dims__(kBands, 1, 1) __launch_bounds__(kThreads)
 
 template <int OP>
 int set_band_smem(size_t smem) {
-  static size_t configured[64] = {0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) dev = 0;
-  if (smem > configured[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(band_kernel<OP>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(band_batch_kernel<OP>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_error(e, "band kernel: shared memory attribute");
-    configured[dev] = smem;
-  }
+  static size_t configured[64] = {0}, configured_batch[64] = {0};
+  SKEI_TRY(opt_in_smem(band_kernel<OP>, smem, configured, "band kernel: shared memory attribute"));
+  SKEI_TRY(opt_in_smem(band_batch_kernel<OP>, smem, configured_batch,
+                       "band kernel: shared memory attribute"));
   return SKEI_OK;
 }
 
@@ -913,6 +921,7 @@ int band_batch_clusters(size_t smem, int *clusters) {
 #ifndef SKEI_PART_SBL4
 #define SKEI_PART_SBL4 8
 #endif
+static_assert(SKEI_PART_SBL4 == 8, "4-image bands are staged 8 lines at a time");
 #ifndef SKEI_PART_GROUP
 #define SKEI_PART_GROUP 4
 #endif
@@ -1117,7 +1126,7 @@ __device__ __forceinline__ void bpadj_band(const AngleConst &C, long long T0, fl
 // shares every crossing's position and weights and costs only its taps;
 // its sums go to partx.  Bands are SB lines; a band past the last image
 // line stages zero lines.
-template <int OP, int NI, int SB, bool XTRA = false>
+template <int OP, int NI, int SB, bool XTRA = false, int NB = kStageBatch>
 __device__ __forceinline__ void partial_task(const Job &J, float *part, int b0, int band,
                                              int a_begin, int AB, int nbands, const BandGeom &g,
                                              const AngleConst *ang, int *status, float *buf,
@@ -1167,10 +1176,11 @@ __device__ __forceinline__ void partial_task(const Job &J, float *part, int b0, 
     const int Px = XTRA ? (mode ? gx->Prow : gx->Pcol) : 0;
     if (any) {
       __syncthreads();  // the previous mode's band is no longer read
-      const bool split = XTRA && ride_split(JX->in_bf16, N, s0, nl, gx->fast != 0);
+      // (the 80-register kernels have no registers to hold the prefetch)
+      const bool split = XTRA && NB > 2 && ride_split(JX->in_bf16, N, s0, nl, gx->fast != 0);
       float4 rv[4];
       if (split) ride_load(JX->in, (size_t)bx * N * N, N, mode, s0, rv);
-      if (NI == 4) stage4<PAD>(J.in, xo, J.in_bf16, N, mode, s0, nl, buf, P);
+      if (NI == 4) stage4<PAD, NB>(J.in, xo, J.in_bf16, N, mode, s0, nl, buf, P);
       else stage1<PAD>(J.in, xo, J.in_bf16, N, mode, s0, nl, buf, P, g.fast != 0);
       if (split) ride_store<PAD>(N, mode, bufx, Px, rv);
       else if (XTRA)
@@ -1216,6 +1226,8 @@ __device__ __forceinline__ int quads(int nimg, int gmax) { return gmax == 4 ? ni
 // blockIdx.z among the launch's groups of NI images (job 0's, then job 1's).
 template <int OP, int NI, int MINB, int SB>
 __global__ void __launch_bounds__(kThreads, MINB) band_partial_kernel(const PartArgs args) {
+  // staging batch: the 80-register kernels keep two blocks in flight
+  constexpr int kNB = MINB >= 3 ? 2 : kStageBatch;
   pdl_enter();
   extern __shared__ float4 smem4[];
   __shared__ AngleConst sc[kMaxABP];
@@ -1227,7 +1239,7 @@ __global__ void __launch_bounds__(kThreads, MINB) band_partial_kernel(const Part
   if constexpr (OP == OP_JOSEPH && NI == 4) {
     if (args.merge) {
       // group z of job 1 (images 4z .. 4z+3) with image z of job 0
-      partial_task<OP, 4, SB, true>(args.jobs.j[1], args.part + args.off[1], 4 * z, blockIdx.x,
+      partial_task<OP, 4, SB, true, kNB>(args.jobs.j[1], args.part + args.off[1], 4 * z, blockIdx.x,
                                     blockIdx.y * args.AB, args.AB, args.nbands, args.g4,
                                     args.ang, args.status, reinterpret_cast<float *>(smem4), sc,
                                     sai, spos, wsum, s0c, s0f, args.part,
@@ -1242,7 +1254,7 @@ __global__ void __launch_bounds__(kThreads, MINB) band_partial_kernel(const Part
   const Job &J = args.jobs.j[jn];
   const int zz = z - (jn ? c0 : 0);
   const int b0 = NI == 4 ? 4 * zz : 4 * quads(J.nimg, args.gmax[jn]) + zz;
-  partial_task<OP, NI, SB>(J, args.part + args.off[jn], b0, blockIdx.x, blockIdx.y * args.AB,
+  partial_task<OP, NI, SB, false, kNB>(J, args.part + args.off[jn], b0, blockIdx.x, blockIdx.y * args.AB,
                            args.AB, args.nbands, NI == 4 ? args.g4 : args.g1, args.ang,
                            args.status, reinterpret_cast<float *>(smem4), sc, sai, spos, wsum,
                            s0c, s0f, args.part, args.part + args.work_floats);
@@ -1317,16 +1329,8 @@ int set_partial_smem(size_t smem) {
   if (smem > 227 * 1024)
     return set_error(SKEI_EINVAL, "band of %zu bytes needs too much shared memory", smem);
   static size_t configured[64] = {0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) dev = 0;
-  if (smem > configured[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(band_partial_kernel<OP, NI, MINB, SB>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_error(e, "band partial kernel: shared memory attribute");
-    configured[dev] = smem;
-  }
-  return SKEI_OK;
+  return opt_in_smem(band_partial_kernel<OP, NI, MINB, SB>, smem, configured,
+                     "band partial kernel: shared memory attribute");
 }
 
 }  // namespace

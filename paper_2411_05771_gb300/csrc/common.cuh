@@ -237,6 +237,24 @@ inline int check_launch(const char *where) {
 int check_plan(skei_plan p);
 int check_dtype(int dtype);
 int sm_count();   // SMs of the current device
+
+// Opts kernel `kern` in to `smem` bytes of dynamic shared memory where they
+// and its static shared memory together pass the 48 KB default; once per
+// device and size increase (`configured`: the caller's record, 64 devices).
+template <typename K>
+int opt_in_smem(K kern, size_t smem, size_t *configured, const char *what) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (smem <= configured[dev]) return SKEI_OK;
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+  if (e == cudaSuccess && smem + fa.sharedSizeBytes > 48 * 1024)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_error(e, what);
+  configured[dev] = smem;
+  return SKEI_OK;
+}
 int check_dev_ptr(const void *p, const char *name);
 int check_idx(skei_plan p, const int *idx, int m);
 int check_batch(int B);

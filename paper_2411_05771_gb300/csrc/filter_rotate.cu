@@ -842,16 +842,8 @@ static size_t filter_smem(int nd) { return f_smem(nd, kFBatchGW); }
 
 static int set_filter_batch_smem(size_t smem) {
   static size_t configured[64] = {0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) dev = 0;
-  if (smem > configured[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(ramlak_batch_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_error(e, "batched ramlak: shared memory attribute");
-    configured[dev] = smem;
-  }
-  return SKEI_OK;
+  return opt_in_smem(ramlak_batch_kernel, smem, configured,
+                     "batched ramlak: shared memory attribute");
 }
 
 size_t filter_batch_smem(int n_det_max) { return filter_smem(n_det_max); }
@@ -880,15 +872,7 @@ int launch_filter_gw(skei_plan p, const Tin *in, int rows, float scale, Tout *ou
   const size_t smem = f_smem(nd, GW);
   auto kern = ramlak_kernel<GW, Tin, Tout>;
   static size_t configured[64] = {0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) dev = 0;
-  if (smem > configured[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return cuda_error(e, "ramlak: shared memory attribute");
-    configured[dev] = smem;
-  }
+  SKEI_TRY(opt_in_smem(kern, smem, configured, "ramlak: shared memory attribute"));
   const int passes = (nd + f_outs(GW) - 1) / f_outs(GW);
   launch_k(kern, dim3(rows, passes), dim3(32 * GW * kFSeg), smem, st, in, out, nd, scale);
   return check_launch("ramlak filter launch");
@@ -912,15 +896,7 @@ int launch_band_sum_filter_gw(skei_plan p, const Jobs &jobs, int nb0, int nb1, c
   const size_t smem = f_smem(nd, GW);
   auto kern = band_sum_filter_kernel<OP, GW>;
   static size_t configured[64] = {0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) dev = 0;
-  if (smem > configured[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return cuda_error(e, "band sums + filter: shared memory attribute");
-    configured[dev] = smem;
-  }
+  SKEI_TRY(opt_in_smem(kern, smem, configured, "band sums + filter: shared memory attribute"));
   long long rows = 0;
   for (int q = 0; q < jobs.njobs; ++q) rows += (long long)jobs.j[q].nimg * jobs.j[q].m;
   if (rows > 0x7fffffff) return set_error(SKEI_EINVAL, "band sums + filter: too many rows");
@@ -972,12 +948,7 @@ int launch_filter_tc(skei_plan p, const Tin *in, int rows, float scale, Tout *ou
     if (e != cudaSuccess) return cuda_error(e, "ramlak taps: symbol address");
     taps[dev] = static_cast<const float *>(a);
   }
-  if (smem > configured[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return cuda_error(e, "ramlak tensor-core form: shared memory attribute");
-    configured[dev] = smem;
-  }
+  SKEI_TRY(opt_in_smem(kern, smem, configured, "ramlak tensor-core form: shared memory attribute"));
   launch_k(kern, dim3((nd + kTcOuts - 1) / kTcOuts, (rows + kTcRows - 1) / kTcRows),
            dim3(kTcThreads), smem, st, in, out, rows, nd, scale, taps[dev]);
   return check_launch("ramlak tensor-core launch");
@@ -1010,15 +981,7 @@ int launch_filter_fft(skei_plan p, const Tin *in, int rows, float scale, Tout *o
   const size_t smem = (size_t)(L / 2 + 2 * L) * sizeof(float2);
   auto kern = ramlak_fft_kernel<Tin, Tout>;
   static size_t configured[64] = {0};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) dev = 0;
-  if (smem > configured[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return cuda_error(e, "ramlak FFT: shared memory attribute");
-    configured[dev] = smem;
-  }
+  SKEI_TRY(opt_in_smem(kern, smem, configured, "ramlak FFT: shared memory attribute"));
   launch_k(kern, dim3((rows + 1) / 2), dim3(kFftThreads), smem, st, in, out, rows, p->n_det, L,
            (const float *)p->d_hspec, scale);
   return check_launch("ramlak FFT filter launch");

@@ -225,16 +225,7 @@ size_t cols_smem(int N, int cpc) { return (size_t)(N / 2 + 2 * N * cpc) * sizeof
 
 template <typename K>
 int mri_set_smem(K kern, size_t smem, size_t *configured) {
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64) dev = 0;
-  if (configured[dev] < smem) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return cuda_error(e, "MRI kernel: shared memory attribute");
-    configured[dev] = smem;
-  }
-  return SKEI_OK;
+  return opt_in_smem(kern, smem, configured, "MRI kernel: shared memory attribute");
 }
 
 int mri_launch_pair(bool fwd, MriArgs &a, int B, cudaStream_t st) {
