@@ -1176,8 +1176,7 @@ __device__ __forceinline__ void partial_task(const Job &J, float *part, int b0, 
     const int Px = XTRA ? (mode ? gx->Prow : gx->Pcol) : 0;
     if (any) {
       __syncthreads();  // the previous mode's band is no longer read
-      // (the 80-register kernels have no registers to hold the prefetch)
-      const bool split = XTRA && NB > 2 && ride_split(JX->in_bf16, N, s0, nl, gx->fast != 0);
+      const bool split = XTRA && ride_split(JX->in_bf16, N, s0, nl, gx->fast != 0);
       float4 rv[4];
       if (split) ride_load(JX->in, (size_t)bx * N * N, N, mode, s0, rv);
       if (NI == 4) stage4<PAD, NB>(J.in, xo, J.in_bf16, N, mode, s0, nl, buf, P);
@@ -1226,8 +1225,7 @@ __device__ __forceinline__ int quads(int nimg, int gmax) { return gmax == 4 ? ni
 // blockIdx.z among the launch's groups of NI images (job 0's, then job 1's).
 template <int OP, int NI, int MINB, int SB>
 __global__ void __launch_bounds__(kThreads, MINB) band_partial_kernel(const PartArgs args) {
-  // staging batch: the 80-register kernels keep two blocks in flight
-  constexpr int kNB = MINB >= 3 ? 2 : kStageBatch;
+  constexpr int kNB = kStageBatch;   // staging blocks in flight per thread
   pdl_enter();
   extern __shared__ float4 smem4[];
   __shared__ AngleConst sc[kMaxABP];
