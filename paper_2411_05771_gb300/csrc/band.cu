@@ -1011,6 +1011,12 @@ __device__ __forceinline__ void joseph_band(const AngleConst &C, long long G0, i
   const long long lo = p0 < pl ? p0 : pl, hi = p0 < pl ? pl : p0;
   if (hi <= -kFxOne || lo >= ((long long)N << kFxBits)) return;
   const int T32 = (int)T;
+  // the 4 images' sums as two FP32 pairs (f32x2 FMAs)
+  f2x a01 = 0ull, a23 = 0ull;
+  if constexpr (NI == 4) {
+    a01 = f2_pack(acc[0], acc[1]);
+    a23 = f2_pack(acc[2], acc[3]);
+  }
 #pragma unroll
   for (int h = 0; h < SB; h += 8) {
     const long long ph = p0 + (long long)h * T;
@@ -1026,12 +1032,11 @@ __device__ __forceinline__ void joseph_band(const AngleConst &C, long long G0, i
       const float g = 1.0f - f;
       const float *q = row + (l * P + j) * NI;
       if (NI == 4) {
-        const float4 v0 = lds_ck(reinterpret_cast<const float4 *>(q), CK_BAND_TAP);
-        const float4 v1 = lds_ck(reinterpret_cast<const float4 *>(q + 4), CK_BAND_TAP);
-        acc[0] = fmaf(g, v0.x, fmaf(f, v1.x, acc[0]));
-        acc[1] = fmaf(g, v0.y, fmaf(f, v1.y, acc[1]));
-        acc[2] = fmaf(g, v0.z, fmaf(f, v1.z, acc[2]));
-        acc[3] = fmaf(g, v0.w, fmaf(f, v1.w, acc[3]));
+        const ulonglong2 v0 = lds_ck(reinterpret_cast<const ulonglong2 *>(q), CK_BAND_TAP);
+        const ulonglong2 v1 = lds_ck(reinterpret_cast<const ulonglong2 *>(q + 4), CK_BAND_TAP);
+        const f2x ff = f2_pack(f, f), gg = f2_pack(g, g);
+        a01 = f2_fma(gg, v0.x, f2_fma(ff, v1.x, a01));
+        a23 = f2_fma(gg, v0.y, f2_fma(ff, v1.y, a23));
       } else {
         acc[0] = fmaf(g, lds_ck(q, CK_BAND_TAP), fmaf(f, lds_ck(q + 1, CK_BAND_TAP), acc[0]));
       }
@@ -1041,6 +1046,12 @@ __device__ __forceinline__ void joseph_band(const AngleConst &C, long long G0, i
       }
       r += T32;
     }
+  }
+  if constexpr (NI == 4) {
+    acc[0] = f2_lo(a01);
+    acc[1] = f2_hi(a01);
+    acc[2] = f2_lo(a23);
+    acc[3] = f2_hi(a23);
   }
 }
 
@@ -1061,7 +1072,8 @@ __device__ __forceinline__ float side_weight_sat(int E) {
 // from an FP32 estimate).
 template <int NI, bool FIRST, bool UP>
 __device__ __forceinline__ void bpadj_line(int &r, int &D, int half, int abs_bs, int sgn,
-                                           const float *row, float (&acc)[NI]) {
+                                           const float *row, float (&acc)[NI], f2x &a01,
+                                           f2x &a23) {
   if (FIRST ? D > half : (UP && D > half)) { r -= sgn; D -= abs_bs; }
   else if (FIRST ? D < -half : (!UP && D < -half)) { r += sgn; D += abs_bs; }
   const float w_m = side_weight_sat<true>(D - abs_bs);     // pixel r - sgn
@@ -1070,13 +1082,13 @@ __device__ __forceinline__ void bpadj_line(int &r, int &D, int half, int abs_bs,
   const float wl = sgn > 0 ? w_m : w_p, wr = sgn > 0 ? w_p : w_m;
   const float *q = row + r * NI;
   if (NI == 4) {
-    const float4 a = lds_ck(reinterpret_cast<const float4 *>(q - 4), CK_BAND_TAP);
-    const float4 b = lds_ck(reinterpret_cast<const float4 *>(q), CK_BAND_TAP);
-    const float4 c = lds_ck(reinterpret_cast<const float4 *>(q + 4), CK_BAND_TAP);
-    acc[0] = fmaf(wr, c.x, fmaf(w_mid, b.x, fmaf(wl, a.x, acc[0])));
-    acc[1] = fmaf(wr, c.y, fmaf(w_mid, b.y, fmaf(wl, a.y, acc[1])));
-    acc[2] = fmaf(wr, c.z, fmaf(w_mid, b.z, fmaf(wl, a.z, acc[2])));
-    acc[3] = fmaf(wr, c.w, fmaf(w_mid, b.w, fmaf(wl, a.w, acc[3])));
+    // the 4 images' sums as two FP32 pairs (f32x2 FMAs)
+    const ulonglong2 a = lds_ck(reinterpret_cast<const ulonglong2 *>(q - 4), CK_BAND_TAP);
+    const ulonglong2 b = lds_ck(reinterpret_cast<const ulonglong2 *>(q), CK_BAND_TAP);
+    const ulonglong2 c = lds_ck(reinterpret_cast<const ulonglong2 *>(q + 4), CK_BAND_TAP);
+    const f2x wl2 = f2_pack(wl, wl), wm2 = f2_pack(w_mid, w_mid), wr2 = f2_pack(wr, wr);
+    a01 = f2_fma(wr2, c.x, f2_fma(wm2, b.x, f2_fma(wl2, a.x, a01)));
+    a23 = f2_fma(wr2, c.y, f2_fma(wm2, b.y, f2_fma(wl2, a.y, a23)));
   } else {
     acc[0] = fmaf(wr, lds_ck(q + 1, CK_BAND_TAP),
                   fmaf(w_mid, lds_ck(q, CK_BAND_TAP), fmaf(wl, lds_ck(q - 1, CK_BAND_TAP), acc[0])));
@@ -1105,19 +1117,30 @@ __device__ __forceinline__ void bpadj_band(const AngleConst &C, long long T0, fl
   // D = t(s0, r) - k on the low words (exact: |D| < 2^31)
   int D = (int)((unsigned)T0 + (unsigned)r * (unsigned)bs - ((unsigned)k << kFxBits));
   const float *row = buf + PAD * NI;
-  bpadj_line<NI, true, true>(r, D, half, abs_bs, sgn, row, acc);
+  f2x a01 = 0ull, a23 = 0ull;
+  if constexpr (NI == 4) {
+    a01 = f2_pack(acc[0], acc[1]);
+    a23 = f2_pack(acc[2], acc[3]);
+  }
+  bpadj_line<NI, true, true>(r, D, half, abs_bs, sgn, row, acc, a01, a23);
   if (bl >= 0) {
 #pragma unroll
     for (int l = 1; l < SB; ++l) {
       D += bl;
-      bpadj_line<NI, false, true>(r, D, half, abs_bs, sgn, row + l * P * NI, acc);
+      bpadj_line<NI, false, true>(r, D, half, abs_bs, sgn, row + l * P * NI, acc, a01, a23);
     }
   } else {
 #pragma unroll
     for (int l = 1; l < SB; ++l) {
       D += bl;
-      bpadj_line<NI, false, false>(r, D, half, abs_bs, sgn, row + l * P * NI, acc);
+      bpadj_line<NI, false, false>(r, D, half, abs_bs, sgn, row + l * P * NI, acc, a01, a23);
     }
+  }
+  if constexpr (NI == 4) {
+    acc[0] = f2_lo(a01);
+    acc[1] = f2_hi(a01);
+    acc[2] = f2_lo(a23);
+    acc[3] = f2_hi(a23);
   }
 }
 

@@ -236,6 +236,34 @@ inline int check_launch(const char *where) {
 
 int check_plan(skei_plan p);
 int check_dtype(int dtype);
+// A pair of FP32 values held in one 64-bit register pair (low word first),
+// the operand of the packed instructions (add.rn.f32x2, mul.rn.f32x2,
+// fma.rn.f32x2: two IEEE operations each, the same results as two scalar
+// ones); loads, stores and arithmetic move it whole.
+typedef unsigned long long f2x;
+__device__ __forceinline__ f2x f2_add(f2x a, f2x b) {
+  f2x d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x f2_mul(f2x a, f2x b) {
+  f2x d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2x f2_fma(f2x a, f2x b, f2x c) {
+  f2x d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2x f2_pack(float lo, float hi) {
+  f2x d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+__device__ __forceinline__ float f2_lo(f2x a) { return __uint_as_float((unsigned)a); }
+__device__ __forceinline__ float f2_hi(f2x a) { return __uint_as_float((unsigned)(a >> 32)); }
+
 int sm_count();   // SMs of the current device
 
 // Opts kernel `kern` in to `smem` bytes of dynamic shared memory where they

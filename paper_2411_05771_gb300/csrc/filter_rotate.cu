@@ -161,26 +161,6 @@ inline size_t f_smem(int nd, int GW) {
   return sizeof(float) * ((size_t)kFSeg * outs + 3 * (size_t)f_words(f_len(nd, outs)));
 }
 
-// A pair of FP32 values held in one 64-bit register pair (low word first),
-// the operand of the packed instructions: loads, stores and arithmetic move
-// it whole, so no packing or unpacking moves are needed.
-typedef unsigned long long f2x;
-__device__ __forceinline__ f2x f2_add(f2x a, f2x b) {
-  f2x d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2x f2_mul(f2x a, f2x b) {
-  f2x d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2x f2_fma(f2x a, f2x b, f2x c) {
-  f2x d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-
 // Stages one row, p[k] = load(k) for k < nd, into pe (pe[e] = p[e - lp],
 // skewL) and the shifted copies pl, pr (p[e + 1 - lp], skewL and skewR),
 // zero outside the row; all threads, then a barrier.
