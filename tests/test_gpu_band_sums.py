@@ -77,7 +77,11 @@ def test_forward_with_band_sums(S, N, n_ang, j0, j1):
 
 
 @pytest.mark.parametrize("N,n_ang,B,m", [(37, 24, 1, 8), (64, 60, 3, 15), (256, 180, 2, 45),
-                                         (512, 60, 1, 60)])
+                                         (512, 60, 1, 60),
+                                         # N % 8 = 4: the riding image's general staging
+                                         (100, 36, 2, 12),
+                                         # N > 512: staged after the group, not prefetched
+                                         (520, 36, 1, 12)])
 def test_forward_band_sums_single_image_rides_with_its_group(S, N, n_ang, B, m):
     """Two jobs on one angle list with 4 images of job 1 per image of job 0
     (the MC and EI terms of a step with G = 4): image b of job 0 is summed in

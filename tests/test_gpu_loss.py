@@ -56,6 +56,7 @@ def _setup(N, n_ang, B, G, m, sketch_mc, seed=0):
     (37, 24, 3, 2, 6, True),       # ragged sizes
     (64, 60, 2, 4, 15, True),      # G = 4, shared sketch: MC images ride with EI groups
     (100, 30, 1, 4, 10, True),     # the same, one ragged image
+    (256, 180, 8, 4, 45, True),    # riding MC images at 256^2 (the shared-memory opt-in)
 ])
 def test_ei_step_matches_oracle(S, N, n_ang, B, G, m, sketch_mc):
     P = _setup(N, n_ang, B, G, m, sketch_mc)

@@ -42,6 +42,7 @@ def _separate(S, plan, x0, theta, m, v, step, y, g, mc_idx, sk_idx, lam, mc_scal
     # not with the kernel's static part (the launch must opt in)
     (256, 180, 8, 4, 45, True, torch.float32),
     (256, 180, 8, 4, 180, False, torch.float32),  # the plain form: all angles, both terms
+    (100, 36, 2, 4, 12, True, torch.bfloat16),    # N % 8 = 4, BF16 storage, riding MC images
 ])
 def test_fused_step_is_bitwise_the_separate_calls(S, N, n_ang, B, G, m, sketch_mc, dtype):
     rng = np.random.default_rng(N + m)
