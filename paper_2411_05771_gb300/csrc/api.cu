@@ -544,6 +544,7 @@ extern "C" {
 
 int skei_proj_fwd(skei_plan plan, int dtype, const void *x, int B, const int *idx, int m,
                   const void *y, void *out, void *stream) {
+  SKEI_RANGE("skei_proj_fwd");
   SKEI_TRY(check_common(plan, dtype, B));
   SKEI_TRY(check_dev_ptr(x, "x"));
   SKEI_TRY(check_dev_ptr(out, "out"));
@@ -557,6 +558,7 @@ int skei_proj_fwd(skei_plan plan, int dtype, const void *x, int B, const int *id
 }
 
 int skei_proj_fwd_multi(skei_plan plan, const skei_job *jobs, int njobs, void *stream) {
+  SKEI_RANGE("skei_proj_fwd_multi");
   SKEI_TRY(check_plan(plan));
   Jobs J{};
   SKEI_TRY(to_jobs(plan, jobs, njobs, true, &J));
@@ -577,6 +579,7 @@ size_t skei_band_sums_workspace_size(skei_plan plan, const skei_job *jobs, int n
 
 int skei_proj_fwd_multi_ws(skei_plan plan, const skei_job *jobs, int njobs, void *work,
                            size_t work_bytes, void *stream) {
+  SKEI_RANGE("skei_proj_fwd_multi_ws");
   SKEI_TRY(check_plan(plan));
   Jobs J{};
   SKEI_TRY(to_jobs(plan, jobs, njobs, true, &J));
@@ -588,6 +591,7 @@ int skei_proj_fwd_multi_ws(skei_plan plan, const skei_job *jobs, int njobs, void
 
 int skei_backproject_adj_multi_ws(skei_plan plan, const skei_job *jobs, int njobs, void *work,
                                   size_t work_bytes, void *stream) {
+  SKEI_RANGE("skei_backproject_adj_multi_ws");
   SKEI_TRY(check_plan(plan));
   Jobs J{};
   SKEI_TRY(to_jobs(plan, jobs, njobs, false, &J));
@@ -602,6 +606,7 @@ int skei_backproject_adj_multi_ws(skei_plan plan, const skei_job *jobs, int njob
 }
 
 int skei_proj_adj_multi(skei_plan plan, const skei_job *jobs, int njobs, void *stream) {
+  SKEI_RANGE("skei_proj_adj_multi");
   SKEI_TRY(check_plan(plan));
   Jobs J{};
   SKEI_TRY(to_jobs(plan, jobs, njobs, false, &J));
@@ -610,6 +615,7 @@ int skei_proj_adj_multi(skei_plan plan, const skei_job *jobs, int njobs, void *s
 
 int skei_proj_adj(skei_plan plan, int dtype, const void *sino, int B, const int *idx, int m,
                   float alpha, float beta, void *x, void *stream) {
+  SKEI_RANGE("skei_proj_adj");
   SKEI_TRY(check_common(plan, dtype, B));
   SKEI_TRY(check_dev_ptr(sino, "sino"));
   SKEI_TRY(check_dev_ptr(x, "x"));
@@ -623,6 +629,7 @@ int skei_proj_adj(skei_plan plan, int dtype, const void *sino, int B, const int 
 
 int skei_filter(skei_plan plan, int dtype, const void *p, int rows, float scale, void *q,
                 void *stream) {
+  SKEI_RANGE("skei_filter");
   SKEI_TRY(check_plan(plan));
   SKEI_TRY(check_dtype(dtype));
   if (rows < 1) return set_error(SKEI_EINVAL, "rows=%d must be >= 1", rows);
@@ -637,6 +644,7 @@ int skei_filter(skei_plan plan, int dtype, const void *p, int rows, float scale,
 
 int skei_filter_fft(skei_plan plan, int dtype, const void *p, int rows, float scale, void *q,
                     void *stream) {
+  SKEI_RANGE("skei_filter_fft");
   SKEI_TRY(check_plan(plan));
   SKEI_TRY(check_dtype(dtype));
   if (rows < 1) return set_error(SKEI_EINVAL, "rows=%d must be >= 1", rows);
@@ -652,6 +660,7 @@ int skei_filter_fft(skei_plan plan, int dtype, const void *p, int rows, float sc
 
 int skei_filter_tc(skei_plan plan, int dtype, const void *p, int rows, float scale, void *q,
                    void *stream) {
+  SKEI_RANGE("skei_filter_tc");
   SKEI_TRY(check_plan(plan));
   SKEI_TRY(check_dtype(dtype));
   if (rows < 1) return set_error(SKEI_EINVAL, "rows=%d must be >= 1", rows);
@@ -667,6 +676,7 @@ int skei_filter_tc(skei_plan plan, int dtype, const void *p, int rows, float sca
 
 int skei_backproject(skei_plan plan, int dtype, const void *q, int B, const int *idx, int m,
                      float alpha, float beta, void *x, void *stream) {
+  SKEI_RANGE("skei_backproject");
   SKEI_TRY(check_common(plan, dtype, B));
   SKEI_TRY(check_dev_ptr(q, "q"));
   SKEI_TRY(check_dev_ptr(x, "x"));
@@ -681,6 +691,7 @@ int skei_backproject(skei_plan plan, int dtype, const void *q, int B, const int 
 
 int skei_backproject_adj(skei_plan plan, int dtype, const void *x, int B, const int *idx, int m,
                          float alpha, void *q, void *stream) {
+  SKEI_RANGE("skei_backproject_adj");
   SKEI_TRY(check_common(plan, dtype, B));
   SKEI_TRY(check_dev_ptr(x, "x"));
   SKEI_TRY(check_dev_ptr(q, "q"));
@@ -699,6 +710,7 @@ size_t skei_fbp_workspace_size(skei_plan plan, int dtype, int B, int m) {
 
 int skei_fbp(skei_plan plan, int dtype, const void *sino, int B, const int *idx, int m, void *x,
              void *work, size_t work_bytes, void *stream) {
+  SKEI_RANGE("skei_fbp");
   SKEI_TRY(check_common(plan, dtype, B));
   SKEI_TRY(check_dev_ptr(sino, "sino"));
   SKEI_TRY(check_dev_ptr(x, "x"));
@@ -713,6 +725,7 @@ int skei_fbp(skei_plan plan, int dtype, const void *sino, int B, const int *idx,
 
 int skei_fbp_adj(skei_plan plan, int dtype, const void *x, int B, const int *idx, int m,
                  void *sino, void *work, size_t work_bytes, void *stream) {
+  SKEI_RANGE("skei_fbp_adj");
   SKEI_TRY(check_common(plan, dtype, B));
   SKEI_TRY(check_dev_ptr(x, "x"));
   SKEI_TRY(check_dev_ptr(sino, "sino"));
@@ -727,6 +740,7 @@ int skei_fbp_adj(skei_plan plan, int dtype, const void *x, int B, const int *idx
 
 int skei_rotate_channels(int dtype, const void *x, int B, int Ch, int N, const double *g_deg,
                          int G, void *out, void *stream) {
+  SKEI_RANGE("skei_rotate_channels");
   SKEI_TRY(check_rot(dtype, B, N, g_deg, G));
   if (Ch < 1 || (int64_t)B * G * Ch > 65535)
     return set_error(SKEI_EINVAL, "rotation: Ch=%d outside [1, 65535 / (B G)]", Ch);
@@ -741,12 +755,14 @@ int skei_rotate_channels(int dtype, const void *x, int B, int Ch, int N, const d
 
 int skei_rotate(int dtype, const void *x, int B, int N, const double *g_deg, int G, void *out,
                 void *stream) {
+  SKEI_RANGE("skei_rotate");
   return skei_rotate_channels(dtype, x, B, 1, N, g_deg, G, out, stream);
 }
 
 int skei_rotate_adj_channels(int dtype, const void *gout, int B, int Ch, int N,
                              const double *g_deg, int G, float alpha, float beta, void *gx,
                              void *stream) {
+  SKEI_RANGE("skei_rotate_adj_channels");
   SKEI_TRY(check_rot(dtype, B, N, g_deg, G));
   if (Ch < 1 || (int64_t)B * Ch > 65535)
     return set_error(SKEI_EINVAL, "rotation transpose: Ch=%d outside [1, 65535 / B]", Ch);
@@ -761,6 +777,7 @@ int skei_rotate_adj_channels(int dtype, const void *gout, int B, int Ch, int N,
 
 int skei_rotate_adj(int dtype, const void *gout, int B, int N, const double *g_deg, int G,
                     float alpha, float beta, void *gx, void *stream) {
+  SKEI_RANGE("skei_rotate_adj");
   return skei_rotate_adj_channels(dtype, gout, B, 1, N, g_deg, G, alpha, beta, gx, stream);
 }
 
@@ -806,6 +823,7 @@ int skei_ei_loss_fwd(skei_plan plan, int dtype, const void *x1, const void *y, i
                      const int *mc_idx, int mc_m, const int *sk_idx, int sk_m,
                      const double *g_deg, int G, void *r, void *x2, void *z, void *work,
                      size_t work_bytes, void *stream) {
+  SKEI_RANGE("skei_ei_loss_fwd");
   return ei_fwd_entry(plan, dtype, x1, y, B, mc_idx, mc_m, sk_idx, sk_m, g_deg, G, r, x2, z,
                       work, work_bytes, stream, false);
 }
@@ -814,6 +832,7 @@ int skei_ei_loss_fwd_per_sample(skei_plan plan, int dtype, const void *x1, const
                                 const int *mc_idx, int mc_m, const int *sk_idx, int sk_m,
                                 const double *g_deg, int G, void *r, void *x2, void *z,
                                 void *work, size_t work_bytes, void *stream) {
+  SKEI_RANGE("skei_ei_loss_fwd_per_sample");
   return ei_fwd_entry(plan, dtype, x1, y, B, mc_idx, mc_m, sk_idx, sk_m, g_deg, G, r, x2, z,
                       work, work_bytes, stream, true);
 }
@@ -833,6 +852,7 @@ int skei_ei_loss_finish_len(int dtype, const void *x2, const void *x3, const voi
                             int G, int64_t img_len, int r_len, double lambda, double mc_scale,
                             double *mc_out, double *ei_out, double *loss_out, void *g_x2,
                             void *g_x3, void *work, size_t work_bytes, void *stream) {
+  SKEI_RANGE("skei_ei_loss_finish_len");
   SKEI_TRY(check_dtype(dtype));
   SKEI_TRY(check_batch(B));
   if (G < 1 || (int64_t)B * G > 65535) return set_error(SKEI_EINVAL, "bad G=%d", G);
@@ -862,6 +882,7 @@ int skei_ei_loss_finish(int dtype, const void *x2, const void *x3, const void *r
                         int N, int r_len, double lambda, double mc_scale, double *mc_out,
                         double *ei_out, double *loss_out, void *g_x2, void *g_x3, void *work,
                         size_t work_bytes, void *stream) {
+  SKEI_RANGE("skei_ei_loss_finish");
   if (N < 1 || N > SKEI_MAX_N) return set_error(SKEI_EINVAL, "N=%d outside [1, %d]", N, SKEI_MAX_N);
   return skei_ei_loss_finish_len(dtype, x2, x3, r, B, G, (int64_t)N * N, r_len, lambda, mc_scale,
                                  mc_out, ei_out, loss_out, g_x2, g_x3, work, work_bytes, stream);
@@ -893,6 +914,7 @@ int skei_ei_loss_bwd(skei_plan plan, int dtype, const void *r, const void *g_x2,
                      int B, const int *mc_idx, int mc_m, const int *sk_idx, int sk_m,
                      const double *g_deg, int G, double mc_coef, void *g_x1, void *work,
                      size_t work_bytes, void *stream) {
+  SKEI_RANGE("skei_ei_loss_bwd");
   return ei_bwd_entry(plan, dtype, r, g_x2, g_z, B, mc_idx, mc_m, sk_idx, sk_m, g_deg, G,
                       mc_coef, g_x1, work, work_bytes, stream, false);
 }
@@ -902,6 +924,7 @@ int skei_ei_loss_bwd_per_sample(skei_plan plan, int dtype, const void *r, const 
                                 const int *sk_idx, int sk_m, const double *g_deg, int G,
                                 double mc_coef, void *g_x1, void *work, size_t work_bytes,
                                 void *stream) {
+  SKEI_RANGE("skei_ei_loss_bwd_per_sample");
   return ei_bwd_entry(plan, dtype, r, g_x2, g_z, B, mc_idx, mc_m, sk_idx, sk_m, g_deg, G,
                       mc_coef, g_x1, work, work_bytes, stream, true);
 }
@@ -920,6 +943,7 @@ int skei_ttt_residual_step(skei_plan plan, int dtype, const void *x0, float *the
                            double eps, void *x1, void *r, void *x2, void *z, void *x3, void *g_x2,
                            void *g_x3, void *g_x1, double *mc_out, double *ei_out,
                            double *loss_out, void *work, size_t work_bytes, void *stream) {
+  SKEI_RANGE("skei_ttt_residual_step");
   SKEI_TRY(check_common(plan, dtype, B));
   SKEI_TRY(check_rot(dtype, B, plan->N, g_deg, G));
   const void *ptrs[] = {x0, theta, m, v, y, x1, r, x2, z, x3, g_x2, g_x3, g_x1};
@@ -956,6 +980,7 @@ int skei_ttt_residual_step(skei_plan plan, int dtype, const void *x0, float *the
 
 int skei_residual_add(int dtype, const void *u, const float *theta, int count, int64_t n,
                       void *out, void *stream) {
+  SKEI_RANGE("skei_residual_add");
   SKEI_TRY(check_dtype(dtype));
   if (count < 1 || n < 1) return set_error(SKEI_EINVAL, "count=%d, n=%lld must be >= 1", count, (long long)n);
   SKEI_TRY(check_dev_ptr(u, "u"));
@@ -979,6 +1004,7 @@ int skei_residual_add(int dtype, const void *u, const float *theta, int count, i
 
 int skei_step_draws(const void *table, int n_rows, int64_t row_bytes, int *counter, void *dst,
                     void *stream) {
+  SKEI_RANGE("skei_step_draws");
   if (n_rows < 1 || row_bytes < 1)
     return set_error(SKEI_EINVAL, "step draws: n_rows=%d, row_bytes=%lld must be >= 1", n_rows,
                      (long long)row_bytes);
@@ -1000,6 +1026,7 @@ int skei_step_draws(const void *table, int n_rows, int64_t row_bytes, int *count
 int skei_adam_step(float *theta, int64_t n, int dtype, const void *g1, int c1, const void *g2,
                    int c2, float *m, float *v, const int *step, double lr, double beta1,
                    double beta2, double eps, void *stream) {
+  SKEI_RANGE("skei_adam_step");
   SKEI_TRY(check_dtype(dtype));
   if (n < 1 || c1 < 1 || c2 < 0) return set_error(SKEI_EINVAL, "bad sizes n=%lld c1=%d c2=%d", (long long)n, c1, c2);
   SKEI_TRY(check_dev_ptr(theta, "theta"));

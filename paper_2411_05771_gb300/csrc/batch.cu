@@ -253,6 +253,7 @@ int make_phase(skei_batch b, int kernel, std::vector<BatchItem> items) {
 extern "C" {
 
 int skei_batch_create(int op, const skei_batch_item *items, int n_items, skei_batch *out) {
+  SKEI_RANGE("skei_batch_create");
   if (!out) return set_error(SKEI_EINVAL, "out is NULL");
   *out = nullptr;
   if (op < SKEI_BATCH_PROJ_FWD || op > SKEI_BATCH_FBP)
@@ -319,6 +320,7 @@ int skei_batch_create(int op, const skei_batch_item *items, int n_items, skei_ba
 }
 
 int skei_batch_run(skei_batch b, void *stream) {
+  SKEI_RANGE("skei_batch_run");
   if (!b) return set_error(SKEI_EINVAL, "batch is NULL");
   int dev = -1;
   cudaGetDevice(&dev);
@@ -329,6 +331,7 @@ int skei_batch_run(skei_batch b, void *stream) {
 }
 
 int skei_batch_tune(skei_batch b, int reps, void *stream) {
+  SKEI_RANGE("skei_batch_tune");
   if (!b) return set_error(SKEI_EINVAL, "batch is NULL");
   if (reps < 1 || reps > 1000) return set_error(SKEI_EINVAL, "reps=%d outside [1, 1000]", reps);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -397,6 +400,7 @@ int skei_batch_info(skei_batch b, int phase, int *n_phases, int *n_tasks, int *w
 }
 
 int skei_batch_destroy(skei_batch b) {
+  SKEI_RANGE("skei_batch_destroy");
   if (!b) return SKEI_OK;
   free_batch(b);
   return SKEI_OK;

@@ -298,6 +298,7 @@ size_t skei_bn_workspace_size(int B, int C, int64_t HW) {
 int skei_bn_act_fwd(int dtype, const void *v, int B, int C, int64_t HW, const float *scale,
                     const float *shift, int relu, double eps, void *out, float *mean,
                     float *rstd, void *work, size_t work_bytes, void *stream) {
+  SKEI_RANGE("skei_bn_act_fwd");
   SKEI_TRY(check_dtype(dtype));
   BnGrid g;
   SKEI_TRY(bn_grid(B, C, HW, &g));
@@ -340,6 +341,7 @@ int skei_bn_act_bwd(int dtype, const void *v, const void *g_out, int B, int C, i
                     const float *scale, const float *shift, const float *mean,
                     const float *rstd, int relu, void *g_v, float *g_scale, float *g_shift,
                     void *work, size_t work_bytes, void *stream) {
+  SKEI_RANGE("skei_bn_act_bwd");
   SKEI_TRY(check_dtype(dtype));
   BnGrid g;
   SKEI_TRY(bn_grid(B, C, HW, &g));

@@ -1,6 +1,7 @@
 // Internal definitions shared by the kernels of libskei (sm_103a).
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -263,6 +264,17 @@ __device__ __forceinline__ f2x f2_pack(float lo, float hi) {
 }
 __device__ __forceinline__ float f2_lo(f2x a) { return __uint_as_float((unsigned)a); }
 __device__ __forceinline__ float f2_hi(f2x a) { return __uint_as_float((unsigned)(a >> 32)); }
+
+// An NVTX range over one C-ABI call, named after it (the calls show up on
+// Nsight timelines and can be selected with ncu --nvtx); a few nanoseconds
+// when no tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define SKEI_RANGE(name) ::skei::NvtxRange skei_nvtx_range_(name)
 
 int sm_count();   // SMs of the current device
 

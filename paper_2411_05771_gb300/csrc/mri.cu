@@ -266,6 +266,7 @@ size_t skei_mri_workspace_size(int N, int Nc, int B) {
 int skei_mri_fwd(int N, int Nc, int B, const float *x, const float *maps, const float *mask,
                  const float *xw, const float *aux, float alpha, float *k, void *work,
                  size_t work_bytes, void *stream) {
+  SKEI_RANGE("skei_mri_fwd");
   SKEI_TRY(mri_check(N, Nc, B));
   SKEI_TRY(check_dev_ptr(x, "x"));
   SKEI_TRY(check_dev_ptr(maps, "maps"));
@@ -287,6 +288,7 @@ int skei_mri_fwd(int N, int Nc, int B, const float *x, const float *maps, const 
 int skei_mri_adj(int N, int Nc, int B, const float *k, const float *maps, const float *mask,
                  const float *dinv, float alpha, float beta, float *x, void *work,
                  size_t work_bytes, void *stream) {
+  SKEI_RANGE("skei_mri_adj");
   SKEI_TRY(mri_check(N, Nc, B));
   SKEI_TRY(check_dev_ptr(k, "k"));
   SKEI_TRY(check_dev_ptr(maps, "maps"));
@@ -313,6 +315,7 @@ int skei_mri_adj(int N, int Nc, int B, const float *k, const float *maps, const 
 }
 
 int skei_mri_dinv(int N, int Nc, const float *maps, float *dinv, void *stream) {
+  SKEI_RANGE("skei_mri_dinv");
   SKEI_TRY(mri_check(N, Nc, 1));
   SKEI_TRY(check_dev_ptr(maps, "maps"));
   SKEI_TRY(check_dev_ptr(dinv, "dinv"));
@@ -324,6 +327,7 @@ int skei_mri_dinv(int N, int Nc, const float *maps, float *dinv, void *stream) {
 
 int skei_coil_mix(int plane, int B, int n_in, int n_out, const float *Wm, const float *in,
                   float *out, void *stream) {
+  SKEI_RANGE("skei_coil_mix");
   if (plane < 1 || B < 1 || B > 65535 || n_in < 1 || n_out < 1 || n_in > 64 || n_out > 64)
     return set_error(SKEI_EINVAL, "coil mix: bad sizes plane=%d B=%d n_in=%d n_out=%d", plane,
                      B, n_in, n_out);

@@ -167,6 +167,7 @@ const char *skei_last_error(void) { return g_last_error.c_str(); }
 
 int skei_plan_create(int N, int n_det, int n_angles, const double *angles_deg,
                      skei_plan *out) {
+  SKEI_RANGE("skei_plan_create");
   if (!out) return set_error(SKEI_EINVAL, "out is NULL");
   *out = nullptr;
   if (N < 1 || N > SKEI_MAX_N) return set_error(SKEI_EINVAL, "N=%d outside [1, %d]", N, SKEI_MAX_N);
@@ -221,6 +222,7 @@ int skei_plan_create(int N, int n_det, int n_angles, const double *angles_deg,
 }
 
 int skei_plan_destroy(skei_plan p) {
+  SKEI_RANGE("skei_plan_destroy");
   if (!p) return SKEI_OK;
   cudaFree(p->d_ang);
   cudaFree(p->d_status);

@@ -112,6 +112,7 @@ int time_ms(cudaStream_t st, F launch, float *ms) {
 using namespace skei;
 
 extern "C" int skei_measure_roofs(void *work, size_t work_bytes, skei_roofs *out, void *stream) {
+  SKEI_RANGE("skei_measure_roofs");
   if (!out) return set_error(SKEI_EINVAL, "skei_measure_roofs: out is NULL");
   SKEI_TRY(check_dev_ptr(work, "work"));
   if (work_bytes < SKEI_ROOFS_WORK_BYTES)

@@ -115,3 +115,31 @@ def test_check_entry_points_of_the_normal_build(lib):
     bits = ctypes.c_uint(7)
     assert lib.skei_check_status(ctypes.byref(bits), 1) == 0
     assert bits.value == 0
+
+
+def test_every_call_is_an_nvtx_range(tmp_path):
+    """Each C-ABI call opens and closes an NVTX range named after it (seen
+    through a test injection library; calls rejected before any GPU work
+    still do)."""
+    import shutil
+    import subprocess
+    import sys
+    from paper_2411_05771_gb300 import build
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    probe = tmp_path / "libnvtx_probe.so"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(build.nvcc()))), "include")
+    subprocess.run([gcc, "-shared", "-fPIC", "-O1", "-I", inc,
+                    os.path.join(ROOT, "tests", "nvtx_probe.c"), "-o", str(probe)], check=True)
+    log = tmp_path / "nvtx.log"
+    code = (
+        "import ctypes, sys\n"
+        f"lib = ctypes.CDLL({build.build()!r})\n"
+        "assert lib.skei_proj_fwd(None, 0, None, 1, None, 0, None, None, None) == -1\n"
+        "assert lib.skei_rotate(0, None, 1, 0, None, 1, None, None) == -1\n")
+    env = dict(os.environ, NVTX_INJECTION64_PATH=str(probe), SKEI_TEST_NVTX_LOG=str(log))
+    subprocess.run([sys.executable, "-c", code], check=True, env=env)
+    lines = log.read_text().split("\n")
+    assert "push skei_proj_fwd" in lines and "push skei_rotate" in lines
+    assert lines.count("pop") == sum(1 for x in lines if x.startswith("push "))
