@@ -569,7 +569,12 @@ int skei_coil_mix(int plane, int B, int n_in, int n_out, const float *W, const f
  * task 1..8 for A and B^T; 1..max resident CTAs per SM for the others)
  * reps + 1 times on the items' own buffers (overwriting the outputs), times
  * them with events on `stream`, and keeps the fastest.  It synchronises and
- * returns SKEI_EINVAL inside a stream capture.
+ * returns SKEI_EINVAL inside a stream capture.  With the environment variable
+ * SKEI_AUTOTUNE_CACHE naming a file, a launch phase whose signature (device
+ * name and SM count, phase kernel, every item's N, n_det, n_angles, m, B and
+ * storage types) the file records takes the recorded shape without timing,
+ * and newly tuned phases are appended to it (text, one line per phase; a
+ * file that cannot be read or written is skipped).
  * skei_batch_info(b, phase, ...) reports launch `phase` (0, or 1 for the
  * back-projection of SKEI_BATCH_FBP): the number of launches, tasks, workers
  * (CTAs, or 8-CTA clusters for A and B^T) and the block (angles per task for

@@ -18,6 +18,10 @@
 // skei_batch_tune times the candidate task shapes (angles per band task) and
 // worker counts on the caller's stream and keeps the fastest.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -330,6 +334,63 @@ int skei_batch_run(skei_batch b, void *stream) {
   return SKEI_OK;
 }
 
+namespace {
+
+// On-disk tuning cache (file named by SKEI_AUTOTUNE_CACHE): one line per tuned
+// phase, "<signature>\t<block>", the signature naming the device, the phase's
+// kernel and every item's shape and storage types.  A phase whose signature
+// is in the file takes the recorded block without timing; newly tuned phases
+// are appended (one short write each).
+std::string phase_signature(const Phase &ph) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop{};
+  cudaGetDeviceProperties(&prop, dev);
+  std::string sig = std::string(prop.name) + "/sm" + std::to_string(prop.multiProcessorCount) +
+                    "/k" + std::to_string(ph.kernel) + ":";
+  for (const BatchItem &it : ph.items) {
+    char buf[96];
+    std::snprintf(buf, sizeof buf, "%dx%dx%dx%dx%d%s%s,", it.N, it.n_det, it.n_angles, it.m,
+                  it.B, it.in_bf16 ? "h" : "f", it.out_bf16 ? "h" : "f");
+    sig += buf;
+  }
+  for (char &c : sig)
+    if (c == '\t' || c == '\n') c = ' ';
+  return sig;
+}
+
+// The block recorded for `sig` in the cache file (the last matching line),
+// or 0.
+int cache_lookup(const char *path, const std::string &sig) {
+  FILE *f = std::fopen(path, "r");
+  if (!f) return 0;
+  int found = 0;
+  std::string line;
+  int ch;
+  while (true) {
+    line.clear();
+    while ((ch = std::fgetc(f)) != EOF && ch != '\n') line.push_back((char)ch);
+    const size_t tab = line.rfind('\t');
+    if (tab != std::string::npos && line.compare(0, tab, sig) == 0 && tab == sig.size()) {
+      const int v = std::atoi(line.c_str() + tab + 1);
+      if (v > 0) found = v;
+    }
+    if (ch == EOF) break;
+  }
+  std::fclose(f);
+  return found;
+}
+
+void cache_store(const char *path, const std::string &sig, int block) {
+  FILE *f = std::fopen(path, "a");
+  if (!f) return;   // a cache that cannot be written only costs the next tuning
+  const std::string line = sig + "\t" + std::to_string(block) + "\n";
+  std::fwrite(line.data(), 1, line.size(), f);
+  std::fclose(f);
+}
+
+}  // namespace
+
 int skei_batch_tune(skei_batch b, int reps, void *stream) {
   SKEI_RANGE("skei_batch_tune");
   if (!b) return set_error(SKEI_EINVAL, "batch is NULL");
@@ -348,7 +409,15 @@ int skei_batch_tune(skei_batch b, int reps, void *stream) {
     return set_error(SKEI_ECUDA, "tune: event");
   }
   int rc = SKEI_OK;
+  const char *cache = std::getenv("SKEI_AUTOTUNE_CACHE");
+  if (cache && !*cache) cache = nullptr;
   for (Phase &ph : b->phases) {
+    std::string sig;
+    if (cache) {
+      sig = phase_signature(ph);
+      const int cached = cache_lookup(cache, sig);
+      if (cached > 0 && configure(ph, cached) == SKEI_OK) continue;
+    }
     std::vector<int> cands;
     if (is_band(ph.kernel)) {
       int m_max = 1;
@@ -379,6 +448,7 @@ int skei_batch_tune(skei_batch b, int reps, void *stream) {
     }
     if (rc) break;
     if ((rc = configure(ph, best))) break;
+    if (cache) cache_store(cache, sig, best);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -188,6 +188,38 @@ def test_batch_fbp_tune_keeps_results(S):
         assert torch.equal(it["out"], _single(S, S.FBP, it))
 
 
+def test_batch_tune_cache_on_disk(S, tmp_path, monkeypatch):
+    """SKEI_AUTOTUNE_CACHE: a tuned batch records its phases' shapes; a new
+    batch of the same items takes them from the file without timing (shown
+    by a recorded shape the timing would not pick), and keeps its results."""
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("SKEI_AUTOTUNE_CACHE", str(path))
+    items = _items(S, S.FBP, MIXED, seed=4)
+    mk = lambda: S.Batch(S.FBP, [S.BatchItem(it["plan"], it["inp"], it["out"], it["idx"])  # noqa: E731
+                                 for it in items])
+    first = mk()
+    first.tune(reps=1)
+    lines = path.read_text().splitlines()
+    assert len(lines) == 2                      # the filter and the back-projection phases
+    assert all("\t" in ln and ln.split("\t")[1].isdigit() for ln in lines)
+    # overwrite the recorded shapes with 1 (a valid candidate of every phase)
+    path.write_text("".join(ln.rsplit("\t", 1)[0] + "\t1\n" for ln in lines))
+    second = mk()
+    second.tune(reps=1)
+    assert [second.info(q)["block"] for q in range(2)] == [1, 1]
+    assert path.read_text().count("\n") == 2   # nothing timed, nothing appended
+    second.run()
+    torch.cuda.synchronize()
+    for it in items:
+        assert torch.equal(it["out"], _single(S, S.FBP, it))
+    # another item set is not in the file: timed and appended
+    other = _items(S, S.FBP, MIXED[:3], seed=5)
+    third = S.Batch(S.FBP, [S.BatchItem(it["plan"], it["inp"], it["out"], it["idx"])
+                            for it in other])
+    third.tune(reps=1)
+    assert path.read_text().count("\n") == 4
+
+
 def test_batch_rejects_bad_items(S):
     p = S.Plan(32, 12)
     x = torch.zeros(1, 32, 32, device="cuda")
