@@ -112,5 +112,5 @@ class ResidualTTT:
         """A run with the given problem and configuration (as passed to the
         constructor) resumed from the checkpoint at `path`."""
         run = cls(plan, x0, y, **config)
-        run.load_state_dict(torch.load(path, weights_only=False))
+        run.load_state_dict(torch.load(path, weights_only=True))   # tensors and plain values only
         return run
