@@ -84,18 +84,20 @@ class ResidualTTT:
         return self.x0.float() + self.theta
 
     # ---------------------------------------------- checkpoint / resume --
+    def _config(self) -> dict:
+        return {"B": self.B, "N": self.N, "G": self.G, "m": self.m,
+                "mc_sketched": self.mc_sketched, "lam": self.lam, "lr": self.lr,
+                "n_angles": self.plan.n_angles, "n_det": self.plan.n_det}
+
     def state_dict(self) -> dict:
         return {"format": _FORMAT, "t": self.t, "theta": self.theta.detach().cpu(),
                 "m": self.m1.detach().cpu(), "v": self.v1.detach().cpu(),
-                "rng": self.rng.bit_generator.state,
-                "config": {"B": self.B, "N": self.N, "G": self.G, "m": self.m,
-                           "mc_sketched": self.mc_sketched, "lam": self.lam, "lr": self.lr,
-                           "n_angles": self.plan.n_angles, "n_det": self.plan.n_det}}
+                "rng": self.rng.bit_generator.state, "config": self._config()}
 
     def load_state_dict(self, sd: dict) -> None:
         if sd.get("format") != _FORMAT:
             raise ValueError("not a residual-TTT checkpoint")
-        mine = self.state_dict()["config"]
+        mine = self._config()
         if sd["config"] != mine:
             raise ValueError(f"checkpoint of another run: {sd['config']} vs {mine}")
         self.theta.copy_(sd["theta"])
