@@ -311,9 +311,17 @@ int ei_fwd_impl(skei_plan p, const T *x1, const T *y, int B, const int *mc_idx, 
   // one launch: r = S_mc y - A_mc x1 (MC term) and p = A_S x2 (EI term)
   const Jobs J = ei_fwd_jobs(x1, y, r, B, mc_idx, mc_m, x2, pbuf, sk_idx, sk_m, G, tb, per_sample);
   const int sk_per = per_sample && sk_idx ? G : 0;
+  // q passes from the filter to B interleaved by groups of 4 images (one
+  // 16-byte copy per bin of a group in B's windows) where all groups are 4
+  Job jq{};
+  jq.idx = sk_idx;
+  jq.idx_per = sk_per;
+  const int il4 = (BG % 4 == 0 && job_groupable(jq)) ? 1 : 0;
+  bool q_il4 = false;
   if (ei_fwd_sums(p, w, J)) {
     // band sums; their reduction also filters the EI rows: q = (pi/m) H A_S x2
-    const FilterReq fr{1, (float)(kPi / sk_m), qbuf};
+    const FilterReq fr{1, (float)(kPi / sk_m), qbuf, il4};
+    q_il4 = il4 != 0;
     if ((rc = launch_band_partial_jobs(p, OP_JOSEPH, J,
                                       reinterpret_cast<float *>(work + w.band_off),
                                       w.band_floats, st, &fr)))
@@ -327,6 +335,7 @@ int ei_fwd_impl(skei_plan p, const T *x1, const T *y, int B, const int *mc_idx, 
   Jobs Jz{};
   Jz.njobs = 1;
   Jz.j[0] = Job{qbuf, nullptr, z, sk_idx, sk_m, BG, 1.0f, 0.0f, 0, tb, tb, sk_per};
+  Jz.j[0].in_il4 = q_il4 ? 1 : 0;
   if (res.x3) {
     Jz.j[0].out2 = res.x3;
     Jz.j[0].add2 = res.theta;
@@ -359,7 +368,9 @@ int ei_bwd_impl(skei_plan p, const T *r, const T *g_x2, const T *g_z, int B, con
     Jb.njobs = 1;
     Jb.j[0] = Job{g_z, nullptr, ubuf, sk_idx, sk_m, BG, 1.0f, 0.0f, tb, 0, 0, sk_per};
     // band sums of B_S^T g_z; their reduction also filters: v = (pi/m) H B_S^T g_z
-    const FilterReq fr{0, (float)(kPi / sk_m), vbuf};
+    // (interleaved by groups of 4 images for A^T's windows where all groups are 4)
+    const int il4 = (BG % 4 == 0 && job_groupable(Jb.j[0])) ? 1 : 0;
+    const FilterReq fr{0, (float)(kPi / sk_m), vbuf, il4};
     if ((rc = launch_band_partial_jobs(p, OP_BP_ADJ, Jb,
                                       reinterpret_cast<float *>(work + w.band_off),
                                       w.band_floats, st, &fr)))
@@ -370,6 +381,7 @@ int ei_bwd_impl(skei_plan p, const T *r, const T *g_x2, const T *g_z, int B, con
     J.njobs = 2;
     J.j[0] = Job{r, nullptr, g_x1, mc_idx, mc_m, B, amc, 0.0f, tb, tb, tb, mc_per};
     J.j[1] = Job{vbuf, g_x2, gtot, sk_idx, sk_m, BG, 1.0f, g_x2 ? 1.0f : 0.0f, 0, tb, 0, sk_per};
+    J.j[1].in_il4 = il4;
     if ((rc = launch_tile_jobs(p, OP_JOSEPH_ADJ, J, st))) return rc;
     if (!last_rotation) return SKEI_OK;
     return launch_rotate_adj<float, T>(gtot, B, p->N, g_deg, G, 1.0f, 1.0f, g_x1, st);

@@ -87,6 +87,13 @@ __device__ __forceinline__ void cp_async4(void *smem, const void *gmem, bool ok)
                "r"(ok ? 4 : 0)
                : "memory");
 }
+// 16 bytes, zero-filled when !ok (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool ok) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem),
+               "r"(ok ? 16 : 0)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 }
@@ -478,6 +485,11 @@ struct Job {
   void *out2 = nullptr;
   const float *add2 = nullptr;
   int out2_bf16 = 0;
+  // tile operators only: the FP32 input holds the images interleaved by
+  // groups of 4, value (b, row, k) at ((b / 4 * m + row) n_det + k) 4 + b % 4,
+  // so a group's 4 bins are one 16-byte load (written so by the fused band
+  // sums + filter of the SkEI step)
+  int in_il4 = 0;
 };
 constexpr int kMaxJobs = 2;
 struct Jobs {
@@ -533,7 +545,8 @@ size_t band_partial_floats(skei_plan p, const Jobs &jobs);
 struct FilterReq {
   int job;        // 0 or 1
   float scale;
-  float *out;     // [rows of the job][n_det]
+  float *out;     // [rows of the job][n_det], or interleaved by 4 images (il4)
+  int il4 = 0;    // out in the layout of Job::in_il4
 };
 int launch_band_partial_jobs(skei_plan p, int op, const Jobs &jobs, float *work,
                              size_t work_floats, cudaStream_t st,

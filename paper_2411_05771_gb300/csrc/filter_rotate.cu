@@ -188,7 +188,7 @@ __device__ __forceinline__ void f_stage(F load, int nd, int len, float *pe, floa
 template <int GW, typename Tout>
 __device__ __forceinline__ void f_compute(int nd, float scale, float *red, const float *pe,
                                           const float *pl, const float *pr, Tout *out, int pass0,
-                                          int pstep) {
+                                          int pstep, int ostride = 1) {
   constexpr int outs = f_outs(GW);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int gw = warp % GW, seg = warp / GW;
@@ -248,7 +248,7 @@ __device__ __forceinline__ void f_compute(int nd, float scale, float *red, const
       float v = red[o];
 #pragma unroll
       for (int sg = 1; sg < kFSeg; ++sg) v += red[sg * outs + o];
-      st_f(out + k, scale * v);
+      st_f(out + (size_t)k * ostride, scale * v);
     }
   }
 }
@@ -321,7 +321,8 @@ template <int OP, int GW>
 __global__ void __launch_bounds__(32 * GW * kFSeg)
     band_sum_filter_kernel(const Jobs jobs, const AngleConst *ang, int n_angles, int nd, int nb0,
                            int nb1, const float *part, size_t off0, size_t off1,
-                           size_t part_floats, int fjob, float fscale, float *fout) {
+                           size_t part_floats, int fjob, float fscale, float *fout,
+                           int fil4) {
   pdl_enter();
   extern __shared__ float4 smem4[];
   constexpr int outs = f_outs(GW);
@@ -376,7 +377,11 @@ __global__ void __launch_bounds__(32 * GW * kFSeg)
   float *red = reinterpret_cast<float *>(smem4), *pe = red + kFSeg * outs, *pl = pe + words,
         *prr = pl + words;
   f_stage(value, nd, len, pe, pl, prr);
-  f_compute<GW>(nd, fscale, red, pe, pl, prr, fout + (size_t)r * nd, 0, 1);
+  if (fil4)   // interleaved by groups of 4 images (Job::in_il4)
+    f_compute<GW>(nd, fscale, red, pe, pl, prr,
+                  fout + ((size_t)(b >> 2) * J.m + a) * nd * 4 + (b & 3), 0, 1, 4);
+  else
+    f_compute<GW>(nd, fscale, red, pe, pl, prr, fout + (size_t)r * nd, 0, 1);
 }
 
 // ----------------------------------------- Ram-Lak, tensor-core form --
@@ -882,7 +887,7 @@ int launch_band_sum_filter_gw(skei_plan p, const Jobs &jobs, int nb0, int nb1, c
   if (rows > 0x7fffffff) return set_error(SKEI_EINVAL, "band sums + filter: too many rows");
   launch_k(kern, dim3((unsigned)rows), dim3(32 * GW * kFSeg), smem, st, jobs,
            (const AngleConst *)p->d_ang, p->n_angles, nd, nb0, nb1, part, off0, off1,
-           part_floats, fr.job, fr.scale, fr.out);
+           part_floats, fr.job, fr.scale, fr.out, fr.il4);
   return check_launch("band sums + filter launch");
 }
 

@@ -148,6 +148,10 @@ __device__ __forceinline__ void tile_window(const Job &J, int b0, int c0, int na
     const int kk = ok ? k : 0;
     const size_t row = ((size_t)b0 * J.m + c0 + a) * nd;     // image b0's row of angle a
     const size_t img = (size_t)J.m * nd;                      // one image's rows
+    // interleaved input: the group's 4 values of bin k at il(k)
+    auto il = [&](int k) {
+      return ((((size_t)(b0 >> 2) * J.m + c0 + a) * nd + k) << 2) + (b0 & 3);
+    };
     const size_t rowx = XTRA ? ((size_t)bx * JX->m + c0 + a) * nd : 0;
     const int e = a * kWin + w;
     if (SKEI_CHECK) {
@@ -156,14 +160,19 @@ __device__ __forceinline__ void tile_window(const Job &J, int b0, int c0, int na
       bool in = ck_smem(win + e * NI, 4 * NI, CK_TILE_WIN) &&
                 (!XTRA || ck_smem(winx + e, 4, CK_TILE_WIN));
       if (ok) {
-        in = in && ck((long long)(row + (NI - 1) * img + kk), (long long)J.nimg * img,
-                      CK_TILE_IN);
+        in = in && ck(J.in_il4 ? (long long)(il(kk) + NI - 1)
+                               : (long long)(row + (NI - 1) * img + kk),
+                      (long long)J.nimg * img, CK_TILE_IN);
         if (XTRA)
           in = in && ck((long long)(rowx + kk), (long long)JX->nimg * JX->m * nd, CK_TILE_IN);
       }
       if (!in) continue;
     }
-    if (async) {
+    if (async && J.in_il4) {
+      const float *src = static_cast<const float *>(J.in) + il(kk);
+      if (NI == 4) cp_async16(win + e * 4, src, ok);
+      else cp_async4(win + e * NI, src, ok);
+    } else if (async) {
       const float *src = static_cast<const float *>(J.in) + row + kk;
 #pragma unroll
       for (int n = 0; n < NI; ++n) cp_async4(win + e * NI + n, src + n * img, ok);
