@@ -64,7 +64,9 @@ extern "C" {
 
 #define SKEI_OK        0
 #define SKEI_EINVAL   (-1)  /* bad shape, pointer, alignment, dtype or size   */
-#define SKEI_ENOMEM   (-2)  /* plan allocation failed                          */
+#define SKEI_ENOMEM   (-2)  /* a device allocation failed (plans, batches);    */
+                            /* SKEI_FAULT_ALLOC=n refuses the n-th one of the */
+                            /* process, for tests of the failure paths        */
 #define SKEI_ECUDA    (-3)  /* a CUDA runtime call or kernel launch failed     */
 
 #define SKEI_F32  0

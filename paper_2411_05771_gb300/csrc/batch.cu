@@ -156,7 +156,7 @@ int configure(Phase &ph, int block) {
     if (ph.d_tasks) cudaFree(ph.d_tasks);
     ph.d_tasks = nullptr;
     ph.cap_tasks = 0;
-    cudaError_t e = cudaMalloc(&ph.d_tasks, tasks.size() * sizeof(int4));
+    cudaError_t e = dev_malloc(reinterpret_cast<void **>(&ph.d_tasks), tasks.size() * sizeof(int4));
     if (e != cudaSuccess) return set_error(SKEI_ENOMEM, "batch: task list of %zu tasks", tasks.size());
     ph.cap_tasks = (int)tasks.size();
   }
@@ -240,12 +240,12 @@ int make_phase(skei_batch b, int kernel, std::vector<BatchItem> items) {
   ph.items = std::move(items);
   b->phases.push_back(ph);
   Phase &p = b->phases.back();
-  cudaError_t e = cudaMalloc(&p.d_items, p.items.size() * sizeof(BatchItem));
+  cudaError_t e = dev_malloc(reinterpret_cast<void **>(&p.d_items), p.items.size() * sizeof(BatchItem));
   if (e != cudaSuccess) return set_error(SKEI_ENOMEM, "batch: item table");
   e = cudaMemcpy(p.d_items, p.items.data(), p.items.size() * sizeof(BatchItem),
                  cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_error(e, "batch: item upload");
-  e = cudaMalloc(&p.d_queue, 2 * sizeof(int));
+  e = dev_malloc(reinterpret_cast<void **>(&p.d_queue), 2 * sizeof(int));
   if (e != cudaSuccess) return set_error(SKEI_ENOMEM, "batch: work queue");
   e = cudaMemset(p.d_queue, 0, 2 * sizeof(int));
   if (e != cudaSuccess) return cuda_error(e, "batch: work queue reset");
@@ -286,7 +286,8 @@ int skei_batch_create(int op, const skei_batch_item *items, int n_items, skei_ba
   b->op = op;
   b->device = dev;
   if (op == SKEI_BATCH_FBP) {
-    cudaError_t e = cudaMalloc(&b->d_work, std::max<size_t>(work_floats, 4) * sizeof(float));
+    cudaError_t e = dev_malloc(reinterpret_cast<void **>(&b->d_work),
+                               std::max<size_t>(work_floats, 4) * sizeof(float));
     if (e != cudaSuccess) {
       free_batch(b);
       return set_error(SKEI_ENOMEM, "batch: FBP workspace of %zu floats", work_floats);

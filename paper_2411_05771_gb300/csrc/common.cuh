@@ -283,6 +283,12 @@ struct NvtxRange {
 };
 #define SKEI_RANGE(name) ::skei::NvtxRange skei_nvtx_range_(name)
 
+// Device allocations of the library go through dev_malloc, which fails
+// the n-th of them in the process (cudaErrorMemoryAllocation, nothing
+// allocated) when the environment variable SKEI_FAULT_ALLOC is n >= 1: a
+// host-side fault injection for the failure paths' tests.
+cudaError_t dev_malloc(void **ptr, size_t bytes);
+
 int sm_count();   // SMs of the current device
 
 // Opts kernel `kern` in to `smem` bytes of dynamic shared memory where they

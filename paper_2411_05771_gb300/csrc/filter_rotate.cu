@@ -63,7 +63,7 @@ int make_filter_spectrum(skei_plan p) {
            std::cos(2.0 * M_PI * (double)(((long long)f * n) % L) / (double)L);
     H[f] = (float)s;
   }
-  cudaError_t e = cudaMalloc(&p->d_hspec, sizeof(float) * L);
+  cudaError_t e = dev_malloc(reinterpret_cast<void **>(&p->d_hspec), sizeof(float) * L);
   if (e == cudaSuccess)
     e = cudaMemcpy(p->d_hspec, H.data(), sizeof(float) * L, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {

@@ -1,4 +1,6 @@
 // Plans, status codes and argument validation of libskei.
+#include <atomic>
+#include <cstdlib>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -9,6 +11,19 @@
 #include "common.cuh"
 
 namespace skei {
+
+cudaError_t dev_malloc(void **ptr, size_t bytes) {
+  static std::atomic<long long> count{0};
+  static const long long fail_at = [] {
+    const char *v = std::getenv("SKEI_FAULT_ALLOC");
+    return v ? std::atoll(v) : 0LL;
+  }();
+  if (fail_at > 0 && ++count == fail_at) {
+    *ptr = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(ptr, bytes);
+}
 
 static thread_local std::string g_last_error;
 
@@ -200,8 +215,10 @@ int skei_plan_create(int N, int n_det, int n_angles, const double *angles_deg,
   cudaError_t e = cudaSuccess;
   if (rc != SKEI_OK) {
     // message already set
-  } else if ((e = cudaMalloc(&p->d_ang, sizeof(AngleConst) * n_angles)) != cudaSuccess ||
-      (e = cudaMalloc(&p->d_status, sizeof(int))) != cudaSuccess) {
+  } else if ((e = dev_malloc(reinterpret_cast<void **>(&p->d_ang),
+                             sizeof(AngleConst) * n_angles)) != cudaSuccess ||
+             (e = dev_malloc(reinterpret_cast<void **>(&p->d_status), sizeof(int))) !=
+                 cudaSuccess) {
     rc = e == cudaErrorMemoryAllocation ? set_error(SKEI_ENOMEM, "plan device allocation failed")
                                         : cuda_error(e, "skei_plan_create: cudaMalloc");
   } else if ((e = cudaMemcpy(p->d_ang, host.data(), sizeof(AngleConst) * n_angles,
