@@ -51,6 +51,11 @@
  *     *_workspace_size queries.
  *   - results do not depend on the stream or on the launch order of
  *     independent calls; calls that write the same buffer concurrently race.
+ *   - each call that does work opens an NVTX range named after it (visible
+ *     to Nsight tools; a few nanoseconds when none is attached), except the
+ *     allocation-free skei_fbp_noalloc.
+ *   - environment: SKEI_AUTOTUNE_CACHE (skei_batch_tune's on-disk cache),
+ *     SKEI_FAULT_ALLOC (tests: refuse the n-th device allocation).
  */
 #ifndef SKEI_H
 #define SKEI_H
